@@ -1,0 +1,560 @@
+/*
+ * srfmg_oracle.c -- plain, serial, FP64 CPU oracle for the one-pass FMG-FAS
+ * solve with segmental refinement (SR) of
+ *   M. F. Adams, "A low memory, highly concurrent multigrid algorithm".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, obviously correct restatement
+ * of the method that the CUDA path is checked against.  Only the tests, the
+ * package smoke check and the benchmark's CPU-baseline leg may load it.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Problem (Sec. 4): -u'' = f on (0,1), u(0) = u(1) = 0, cell-centred second
+ * order finite volumes.  Level l has n = 2^l cells of width h = 1/n, centres
+ * x_i = (i + 1/2) h; the Dirichlet wall is an odd ghost cell (u_{-1} = -u_0,
+ * u_n = -u_{n-1}), which is where the diagonal 3/h^2 of the first and last
+ * rows of the appendix operator comes from.
+ *
+ * Arithmetic: IEEE double, built with -ffp-contract=off.  The operator is
+ * applied in flux form, (L u)_i = (F_{i-1/2} - F_{i+1/2}) / h^2 with
+ * F_{i+1/2} = u_{i+1} - u_i; the difference of two nearby doubles is exact,
+ * so residuals carry no O(eps |u| / h^2) rounding noise.
+ *
+ * The routines follow the paper's algorithms in its order:
+ *   Fig. 1 (FAS V-cycle), Fig. 2 (FMG), Eq. 6 (correction update), Eq. 7
+ *   (full update), Eqs. 4-5 (tau correction), Fig. 3 (FMG-FAS-SR), Fig. 4
+ *   (Kaczmarz compatible relaxation) and the operators of Sec. 4.
+ * Points where the paper is silent carry a "Reading:" note.
+ *
+ * Vectors are passed as (array, offset) pairs: a[i - off] holds cell i.  The
+ * stored levels use offset 0; a segment's patch buffer uses the index of its
+ * first cell.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXLEV 31
+
+/* Parameters of one solve.  Level tables are indexed by level l. */
+typedef struct {
+    int32_t M;              /* finest level, N = 2^M cells */
+    int32_t M0;             /* coarsest level (exact solve), >= 2 */
+    int32_t nRS;            /* number of SR levels: {M-nRS+1 .. M} */
+    int32_t nu1, nu2;       /* V(nu1, nu2) */
+    int32_t smoother;       /* 0: lexicographic Gauss-Seidel, direction reversed
+                                  after every sweep (appendix; default);
+                               1: red-black Gauss-Seidel, even cells first */
+    int32_t tau_src;        /* 0: tau from the assembled level, as the appendix
+                                  program computes it (default);
+                               1: tau from each segment's own extended patch,
+                                  the literal reading of Fig. 3 line 4 */
+    int32_t seg_w[OR_MAXLEV + 1]; /* per level: segment interior width, 0 = whole level */
+    int32_t seg_b[OR_MAXLEV + 1]; /* per level: buffer cells on each side */
+} or_params;
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2 };
+
+static double cell(const double *a, int off, int i) { return a[i - off]; }
+
+/* ------------------------------------------------------------------ */
+/* Operators of Sec. 4 (one level of n cells, h = 1/n)                 */
+/* ------------------------------------------------------------------ */
+
+/* F_{i-1/2}; at the left wall F_{-1/2} = u_0 - (-u_0). */
+static double flux_left(const double *u, int off, int i) {
+    return i == 0 ? 2.0 * cell(u, off, 0) : cell(u, off, i) - cell(u, off, i - 1);
+}
+/* F_{i+1/2}; at the right wall F_{n-1/2} = (-u_{n-1}) - u_{n-1}. */
+static double flux_right(const double *u, int off, int i, int n) {
+    return i == n - 1 ? -2.0 * cell(u, off, n - 1) : cell(u, off, i + 1) - cell(u, off, i);
+}
+/* (L u)_i = (F_{i-1/2} - F_{i+1/2}) / h^2, with 1/h^2 = n^2 exactly. */
+static double Lu_at(const double *u, int off, int i, int n) {
+    double inv_h2 = (double)n * (double)n;
+    return (flux_left(u, off, i) - flux_right(u, off, i, n)) * inv_h2;
+}
+/* Diagonal of L: 2/h^2 inside, 3/h^2 in the two wall cells. */
+static double Ldiag_at(int i, int n) {
+    double inv_h2 = (double)n * (double)n;
+    return (i == 0 || i == n - 1) ? 3.0 * inv_h2 : 2.0 * inv_h2;
+}
+
+/* Restriction (Sec. 4, first order): mean of the two children of coarse J. */
+static double restrict_at(const double *uf, int off, int J) {
+    return (cell(uf, off, 2 * J) + cell(uf, off, 2 * J + 1)) * 0.5;
+}
+
+/* Coarse value with the odd reflection at the walls (both prolongations). */
+static double coarse_ghost(const double *uc, int j, int nc) {
+    if (j < 0) return -uc[-j - 1];
+    if (j >= nc) return -uc[2 * nc - 1 - j];
+    return uc[j];
+}
+
+/* Second order prolongation P (Sec. 4): a child takes 3/4 of its parent and
+ * 1/4 of the parent's neighbour on its side; odd reflection at a wall. */
+static double prolong_lin_at(const double *uc, int i, int nc) {
+    int J = i >> 1;
+    int nb = (i & 1) ? J + 1 : J - 1;
+    return (3.0 * uc[J] + coarse_ghost(uc, nb, nc)) * 0.25;
+}
+
+/* Fourth order FMG interpolation Pi (Sec. 4): cubic Lagrange interpolation
+ * at the child centre (1/4 of a coarse cell left or right of its parent)
+ * through the four nearest coarse centres: weights (-5, 35, 105, -7)/128 for
+ * the left child and the mirror for the right child.  The appendix's special
+ * rows at the walls are this formula with odd ghosts. */
+static double prolong_fmg_at(const double *uc, int i, int nc) {
+    int J = i >> 1;
+    double s;
+    if ((i & 1) == 0)
+        s = -5.0 * coarse_ghost(uc, J - 2, nc) + 35.0 * coarse_ghost(uc, J - 1, nc)
+            + 105.0 * uc[J] - 7.0 * coarse_ghost(uc, J + 1, nc);
+    else
+        s = -7.0 * coarse_ghost(uc, J - 1, nc) + 105.0 * uc[J]
+            + 35.0 * coarse_ghost(uc, J + 1, nc) - 5.0 * coarse_ghost(uc, J + 2, nc);
+    return s / 128.0;
+}
+
+/* Exact solve of L u = rhs on one level (the coarsest-grid solve of Figs. 1-2):
+ * L is tridiagonal and diagonally dominant, so the Thomas algorithm. */
+static int thomas(int n, const double *rhs, double *u) {
+    if (n < 1) return OR_EINVAL;
+    double *cp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *dp = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!cp || !dp) { free(cp); free(dp); return OR_ENOMEM; }
+    double off = -((double)n * (double)n);
+    for (int i = 0; i < n; i++) {
+        double lower = i > 0 ? off : 0.0;
+        double upper = i < n - 1 ? off : 0.0;
+        double denom = Ldiag_at(i, n) - (i > 0 ? lower * cp[i - 1] : 0.0);
+        cp[i] = upper / denom;
+        dp[i] = (rhs[i] - (i > 0 ? lower * dp[i - 1] : 0.0)) / denom;
+    }
+    u[n - 1] = dp[n - 1];
+    for (int i = n - 2; i >= 0; i--) u[i] = dp[i] - cp[i] * u[i + 1];
+    free(cp); free(dp);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The smoother S of Sec. 3 and Fig. 4 on one extended patch           */
+/* ------------------------------------------------------------------ */
+
+/* One Gauss-Seidel update (omega = 1): u_i += (f_i - (L u)_i) / L_ii. */
+static void gs_update(double *v, int voff, const double *rhs, int roff, int i, int n) {
+    v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - Lu_at(v, voff, i, n)) / Ldiag_at(i, n);
+}
+
+/* Kaczmarz pass of Fig. 4 over every coarse cell J whose children both lie in
+ * [e0, e1): r = uH_J - (R v)_J, t = r / (R R^T)_JJ = r / (1/2), and
+ * v += R(J,:)^T t, i.e. each child gets t/2.  The pairs are disjoint, so the
+ * order of J does not matter.  Reading: e0 is even (segments and buffers have
+ * even widths), so the pairs are the true sibling pairs. */
+static void kaczmarz_pass(double *v, int voff, const double *uH, int e0, int e1) {
+    for (int i = e0; i + 1 < e1; i += 2) {
+        int J = i >> 1;
+        double r = uH[J] - restrict_at(v, voff, J);
+        double t = r / 0.5;
+        v[i - voff] = cell(v, voff, i) + 0.5 * t;
+        v[i + 1 - voff] = cell(v, voff, i + 1) + 0.5 * t;
+    }
+}
+
+/* nsweeps iterations of S on the cells [e0, e1); v also holds the frozen cells
+ * just outside [e0, e1) (read, never written).  With uH != NULL every
+ * iteration starts with the Kaczmarz pass (compatible relaxation, Fig. 4,
+ * whose order "Kaczmarz, then the standard smoother" the appendix keeps).
+ * Then one Gauss-Seidel sweep:
+ *   smoother 0: lexicographic, ascending first and reversed after every
+ *     sweep of the call (the appendix's "symmetrize");
+ *   smoother 1: every even cell of [e0,e1), then every odd cell (red-black;
+ *     colour = global cell index mod 2).  Kept as an option: with V(1,1) on
+ *     this discretization its V-cycle factor grows with the depth and one FMG
+ *     cycle misses discretization accuracy. */
+static void patch_sweeps(int smoother, double *v, int voff, const double *rhs, int roff,
+                         int n, int e0, int e1, int nsweeps, const double *uH) {
+    int ascending = 1;
+    for (int k = 0; k < nsweeps; k++) {
+        if (uH) kaczmarz_pass(v, voff, uH, e0, e1);
+        if (smoother == 1) {
+            for (int colour = 0; colour < 2; colour++)
+                for (int i = e0; i < e1; i++)
+                    if ((i & 1) == colour) gs_update(v, voff, rhs, roff, i, n);
+        } else {
+            if (ascending) for (int i = e0; i < e1; i++) gs_update(v, voff, rhs, roff, i, n);
+            else           for (int i = e1 - 1; i >= e0; i--) gs_update(v, voff, rhs, roff, i, n);
+            ascending = !ascending;
+        }
+    }
+}
+
+/* Extended patch of the segment with interior [s, s+w) on a level of n cells:
+ * E = [s - b, s + w + b) clipped to the domain (Sec. 3, buffer cells), and
+ * the cells [lo, hi) the patch reads: E plus one frozen cell on each side
+ * that lies inside the domain. */
+static void extended_patch(int s, int w, int b, int n, int *e0, int *e1, int *lo, int *hi) {
+    *e0 = s - b < 0 ? 0 : s - b;
+    *e1 = s + w + b > n ? n : s + w + b;
+    *lo = *e0 > 0 ? *e0 - 1 : 0;
+    *hi = *e1 < n ? *e1 + 1 : n;
+}
+
+/* ------------------------------------------------------------------ */
+/* tau-corrected coarse right-hand side (Eqs. 4-5, Fig. 3 lines 3-5)   */
+/* ------------------------------------------------------------------ */
+
+/* rhs_c(J) = (R rhs_f)_J + (L_c R ubar)_J - (R L_f ubar)_J, evaluated left to
+ * right as in the appendix's down leg.  The restricted solution R ubar plays
+ * the role of Ihat ubar in Eq. 5 (Ihat = I here).  Reads fine cells 2J-2 ..
+ * 2J+3 of ubar (fewer at a wall) and 2J, 2J+1 of rhs_f. */
+static double tau_rhs_at(const double *ubar, int uoff, const double *rhs_f, int roff,
+                         int J, int nf) {
+    int nc = nf / 2;
+    double Rrhs = (cell(rhs_f, roff, 2 * J) + cell(rhs_f, roff, 2 * J + 1)) * 0.5;
+    double inv_H2 = (double)nc * (double)nc;
+    double uJ = restrict_at(ubar, uoff, J);
+    double Gl = J == 0 ? 2.0 * uJ : uJ - restrict_at(ubar, uoff, J - 1);
+    double Gr = J == nc - 1 ? -2.0 * uJ : restrict_at(ubar, uoff, J + 1) - uJ;
+    double Lc = (Gl - Gr) * inv_H2;
+    double RLf = (Lu_at(ubar, uoff, 2 * J, nf) + Lu_at(ubar, uoff, 2 * J + 1, nf)) * 0.5;
+    return (Rrhs + Lc) - RLf;
+}
+
+/* ------------------------------------------------------------------ */
+/* Every level stored ("horizontal" processing, Sec. 4)                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const or_params *p;
+    double *u[OR_MAXLEV + 1];
+    double *rhs[OR_MAXLEV + 1];
+    double *tmp;      /* scratch, 2^M doubles */
+    double *tmp2;     /* scratch, 2^M doubles */
+    double *patch;    /* one extended patch incl. frozen cells */
+} or_state;
+
+static int is_sr_level(const or_params *p, int l) { return l > p->M - p->nRS; }
+static int segmented(const or_params *p, int l) {
+    return p->seg_w[l] != 0 && p->seg_w[l] < (1 << l);
+}
+
+/* S applied to a whole level (Sec. 3): a level that is not segmented is one
+ * patch; otherwise each segment's extended patch is smoothed from a copy of
+ * the input and only its interior is kept, i.e. the patch solves are
+ * assembled additively (block Jacobi), independent of processing order. */
+static void smooth_level(or_state *st, int l, const double *u_in, double *u_out,
+                         int nsweeps, const double *uH) {
+    const or_params *p = st->p;
+    int n = 1 << l;
+    if (!segmented(p, l)) {
+        if (u_out != u_in) memcpy(u_out, u_in, sizeof(double) * (size_t)n);
+        patch_sweeps(p->smoother, u_out, 0, st->rhs[l], 0, n, 0, n, nsweeps, uH);
+        return;
+    }
+    int w = p->seg_w[l];
+    for (int s = 0; s < n; s += w) {
+        int e0, e1, lo, hi;
+        extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
+        memcpy(st->patch, u_in + lo, sizeof(double) * (size_t)(hi - lo));
+        patch_sweeps(p->smoother, st->patch, lo, st->rhs[l], 0, n, e0, e1, nsweeps, uH);
+        memcpy(u_out + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
+    }
+}
+
+/* Pre-smoothing of level l and the transfer to level l-1 (Fig. 3 lines 2-5,
+ * appendix down leg): u_l <- S(u_l); u_{l-1} <- R u_l;
+ * rhs_{l-1} <- R rhs_l + L_{l-1} R u_l - R L_l u_l.
+ * Reading (tau_src = 0, default): both come from the assembled level, as in
+ * the appendix program, which the paper states has the same semantics as
+ * Fig. 3.  With tau_src = 1 each segment forms them on its interior coarse
+ * cells from its own smoothed extended patch ubar (Fig. 3 line 4 read
+ * literally); tau at a segment edge then reads buffer cells that differ from
+ * the assembled values the restricted solution comes from. */
+static void presmooth_and_restrict(or_state *st, int l) {
+    const or_params *p = st->p;
+    int n = 1 << l, nc = n / 2;
+    double *ul = st->u[l], *uc = st->u[l - 1], *rc = st->rhs[l - 1], *rf = st->rhs[l];
+    if (!segmented(p, l) || p->tau_src == 0) {
+        smooth_level(st, l, ul, st->tmp, p->nu1, NULL);
+        memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
+        for (int J = 0; J < nc; J++) uc[J] = restrict_at(ul, 0, J);
+        for (int J = 0; J < nc; J++) rc[J] = tau_rhs_at(ul, 0, rf, 0, J, n);
+        return;
+    }
+    int w = p->seg_w[l];
+    for (int s = 0; s < n; s += w) {
+        int e0, e1, lo, hi;
+        extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
+        memcpy(st->patch, ul + lo, sizeof(double) * (size_t)(hi - lo));
+        patch_sweeps(p->smoother, st->patch, lo, rf, 0, n, e0, e1, p->nu1, NULL);
+        memcpy(st->tmp + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
+        for (int J = s / 2; J < (s + w) / 2; J++) {
+            uc[J] = restrict_at(st->patch, lo, J);
+            rc[J] = tau_rhs_at(st->patch, lo, rf, 0, J, n);
+        }
+    }
+    memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
+}
+
+/* Post-smoothing leg update of level l from the corrected level l-1
+ * (Fig. 3 post-smoothing leg, appendix up leg):
+ *   SR level:  u_l <- Pi u_{l-1} (Eq. 7, full update), then S with the
+ *              Kaczmarz compatible relaxation against u_{l-1} (Fig. 4);
+ *   otherwise: u_l <- u_l + P (u_{l-1} - R u_l) (Eq. 6), then S. */
+static void postsmooth_update(or_state *st, int l) {
+    const or_params *p = st->p;
+    int n = 1 << l, nc = n / 2;
+    double *ul = st->u[l], *uc = st->u[l - 1], *t = st->tmp;
+    if (is_sr_level(p, l)) {
+        for (int i = 0; i < n; i++) t[i] = prolong_fmg_at(uc, i, nc);
+        smooth_level(st, l, t, ul, p->nu2, uc);
+    } else {
+        double *corr = st->tmp2;
+        for (int J = 0; J < nc; J++) corr[J] = uc[J] - restrict_at(ul, 0, J);
+        for (int i = 0; i < n; i++) t[i] = ul[i] + prolong_lin_at(corr, i, nc);
+        smooth_level(st, l, t, ul, p->nu2, NULL);
+    }
+}
+
+/* One FAS V-cycle (Fig. 1) with finest level `top`; u[top], rhs[top] set.
+ * Each level is smoothed and transferred down, the coarsest level M0 is
+ * solved exactly, and each level is corrected and smoothed on the way up. */
+static int vcycle(or_state *st, int top) {
+    const or_params *p = st->p;
+    for (int l = top; l > p->M0; l--) presmooth_and_restrict(st, l);
+    int rc = thomas(1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    if (rc) return rc;
+    for (int l = p->M0 + 1; l <= top; l++) postsmooth_update(st, l);
+    return OR_OK;
+}
+
+static void free_state(or_state *st) {
+    for (int l = 0; l <= OR_MAXLEV; l++) { free(st->u[l]); free(st->rhs[l]); }
+    free(st->tmp); free(st->tmp2); free(st->patch);
+}
+
+static int check_params(const or_params *p) {
+    if (p->M0 < 2 || p->M < p->M0 || p->M > 28) return OR_EINVAL;
+    if (p->nRS < 0 || p->nRS > p->M - p->M0) return OR_EINVAL;
+    if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16) return OR_EINVAL;
+    if (p->smoother < 0 || p->smoother > 1 || p->tau_src < 0 || p->tau_src > 1) return OR_EINVAL;
+    for (int l = p->M0 + 1; l <= p->M; l++) {
+        int w = p->seg_w[l], b = p->seg_b[l], n = 1 << l;
+        if (w == 0) continue;
+        if (w < 2 || (w & (w - 1)) || w > n) return OR_EINVAL;
+        if (w < n && (b < 2 || (b & 1) || b > (1 << 20))) return OR_EINVAL;
+    }
+    return OR_OK;
+}
+
+static int max_patch(const or_params *p) {
+    int m = 4;
+    for (int l = p->M0 + 1; l <= p->M; l++)
+        if (p->seg_w[l] && p->seg_w[l] + 2 * p->seg_b[l] + 2 > m) m = p->seg_w[l] + 2 * p->seg_b[l] + 2;
+    return m;
+}
+
+static int alloc_state(or_state *st, const or_params *p) {
+    memset(st, 0, sizeof(*st));
+    st->p = p;
+    for (int l = p->M0; l <= p->M; l++) {
+        st->u[l] = (double *)calloc((size_t)1 << l, sizeof(double));
+        st->rhs[l] = (double *)calloc((size_t)1 << l, sizeof(double));
+        if (!st->u[l] || !st->rhs[l]) { free_state(st); return OR_ENOMEM; }
+    }
+    st->tmp = (double *)calloc((size_t)1 << p->M, sizeof(double));
+    st->tmp2 = (double *)calloc((size_t)1 << p->M, sizeof(double));
+    st->patch = (double *)calloc((size_t)max_patch(p), sizeof(double));
+    if (!st->tmp || !st->tmp2 || !st->patch) { free_state(st); return OR_ENOMEM; }
+    return OR_OK;
+}
+
+/* Right-hand sides on every level (appendix operator set-up): rhs_M = f and
+ * each coarser level is the restriction of the next finer one. */
+static void rhs_hierarchy(or_state *st, int top, const double *f_top) {
+    const or_params *p = st->p;
+    memcpy(st->rhs[top], f_top, sizeof(double) * ((size_t)1 << top));
+    for (int l = top; l > p->M0; l--)
+        for (int J = 0; J < (1 << (l - 1)); J++) st->rhs[l - 1][J] = restrict_at(st->rhs[l], 0, J);
+}
+
+/* FMG (Fig. 2) up to level `top`: exact solve on M0, then for each finer level
+ * the FMG interpolation Pi followed by one V-cycle. */
+static int fmg_up_to(or_state *st, int top) {
+    const or_params *p = st->p;
+    int rc = thomas(1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    for (int k = p->M0; k < top && !rc; k++) {
+        int nc = 1 << k;
+        for (int i = 0; i < 2 * nc; i++) st->u[k + 1][i] = prolong_fmg_at(st->u[k], i, nc);
+        rc = vcycle(st, k + 1);
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exported entry points                                               */
+/* ------------------------------------------------------------------ */
+
+int or_apply_L(int n, const double *u, double *out) {
+    for (int i = 0; i < n; i++) out[i] = Lu_at(u, 0, i, n);
+    return OR_OK;
+}
+int or_restrict(int nc, const double *uf, double *uc) {
+    for (int J = 0; J < nc; J++) uc[J] = restrict_at(uf, 0, J);
+    return OR_OK;
+}
+int or_prolong_lin(int nc, const double *uc, double *uf) {
+    for (int i = 0; i < 2 * nc; i++) uf[i] = prolong_lin_at(uc, i, nc);
+    return OR_OK;
+}
+int or_prolong_fmg(int nc, const double *uc, double *uf) {
+    if (nc < 2) return OR_EINVAL;
+    for (int i = 0; i < 2 * nc; i++) uf[i] = prolong_fmg_at(uc, i, nc);
+    return OR_OK;
+}
+int or_thomas(int n, const double *rhs, double *u) { return thomas(n, rhs, u); }
+
+/* tau-corrected coarse rhs from an assembled fine vector, every coarse cell. */
+int or_tau_rhs(int nf, const double *ubar, const double *rhs_f, double *rhs_c) {
+    for (int J = 0; J < nf / 2; J++) rhs_c[J] = tau_rhs_at(ubar, 0, rhs_f, 0, J, nf);
+    return OR_OK;
+}
+
+/* One application of the level smoother S (segmentation from p->seg_w[l]). */
+int or_smooth(const or_params *p, int l, const double *u_in, const double *rhs,
+              int nsweeps, const double *uH, double *u_out) {
+    if (check_params(p) || l < 1 || l > OR_MAXLEV) return OR_EINVAL;
+    or_state st;
+    memset(&st, 0, sizeof(st));
+    st.p = p;
+    st.rhs[l] = (double *)rhs;
+    st.patch = (double *)calloc((size_t)max_patch(p), sizeof(double));
+    if (!st.patch) return OR_ENOMEM;
+    smooth_level(&st, l, u_in, u_out, nsweeps, uH);
+    free(st.patch);
+    return OR_OK;
+}
+
+/* Kaczmarz pass (Fig. 4) over [e0, e1) of a level vector, against uH. */
+int or_kaczmarz(double *v, const double *uH, int e0, int e1) {
+    kaczmarz_pass(v, 0, uH, e0, e1);
+    return OR_OK;
+}
+
+/* One FMG-FAS(-SR) solve, every level stored ("horizontal"): Fig. 2 with the
+ * V-cycle of Fig. 1 and the SR changes of Fig. 3 on the SR levels. */
+int or_fmg_h(const or_params *p, const double *f, double *u_out) {
+    if (check_params(p)) return OR_EINVAL;
+    or_state st;
+    int rc = alloc_state(&st, p);
+    if (rc) return rc;
+    rhs_hierarchy(&st, p->M, f);
+    rc = fmg_up_to(&st, p->M);
+    if (!rc) memcpy(u_out, st.u[p->M], sizeof(double) * ((size_t)1 << p->M));
+    free_state(&st);
+    return rc;
+}
+
+/* `ncycles` FAS V-cycles (Fig. 1) on level M from the iterate u_inout, every
+ * level stored; the coarse right-hand sides are rebuilt by each down leg. */
+int or_vcycles_h(const or_params *p, const double *f, double *u_inout, int ncycles) {
+    if (check_params(p)) return OR_EINVAL;
+    or_state st;
+    int rc = alloc_state(&st, p);
+    if (rc) return rc;
+    rhs_hierarchy(&st, p->M, f);
+    memcpy(st.u[p->M], u_inout, sizeof(double) * ((size_t)1 << p->M));
+    for (int c = 0; c < ncycles && !rc; c++) rc = vcycle(&st, p->M);
+    if (!rc) memcpy(u_inout, st.u[p->M], sizeof(double) * ((size_t)1 << p->M));
+    free_state(&st);
+    return rc;
+}
+
+/* The same solve as or_fmg_h, run serially with segmental refinement: the
+ * finest level M is never stored.  The FMG steps up to level M-1 run on stored
+ * levels.  In the last step each segment of level M is interpolated from level
+ * M-1 (Fig. 3 line 1) and smoothed (line 2); its interior is appended to a
+ * short window of assembled fine values, from which the restricted solution
+ * and the tau-corrected right-hand side of every coarse cell are formed as
+ * soon as the six fine cells they read are assembled (lines 3-5), and the
+ * window is then trimmed.  After the coarse part of the V-cycle the segment is
+ * regenerated from the corrected level M-1 (Eq. 7), smoothed with compatible
+ * relaxation and only its interior is emitted (Fig. 3 post-smoothing leg).
+ * Memory for level M: one extended patch and a window of at most w + 8 cells.
+ * Requires level M to be an SR level, segmented, with tau from the assembled
+ * level (tau_src = 0). */
+int or_fmg_v(const or_params *p, const double *f, double *u_out) {
+    if (check_params(p)) return OR_EINVAL;
+    int M = p->M, n = 1 << M, nc = n / 2;
+    if (p->nRS < 1 || !segmented(p, M) || p->tau_src != 0 || M - 1 < p->M0) return OR_EINVAL;
+    int w = p->seg_w[M], b = p->seg_b[M];
+    or_params pc = *p;            /* the stored part: levels M0 .. M-1 */
+    pc.M = M - 1;
+    pc.nRS = p->nRS - 1;
+    or_state st;
+    int rc = alloc_state(&st, &pc);
+    if (rc) return rc;
+    int cap = w + 2 * b + 2, wcap = 2 * w + 16;
+    double *patch = (double *)malloc(sizeof(double) * (size_t)cap);
+    double *frhs = (double *)malloc(sizeof(double) * (size_t)cap);
+    double *win = (double *)malloc(sizeof(double) * (size_t)wcap);
+    double *uc_new = (double *)malloc(sizeof(double) * (size_t)nc);
+    if (!patch || !frhs || !win || !uc_new) { rc = OR_ENOMEM; goto done; }
+
+    /* right-hand sides of levels M-1 .. M0 (restriction of f), FMG to M-1 */
+    for (int J = 0; J < nc; J++) uc_new[J] = restrict_at(f, 0, J);
+    rhs_hierarchy(&st, M - 1, uc_new);
+    rc = fmg_up_to(&st, M - 1);
+    if (rc) goto done;
+
+    /* last step, level M, segment by segment: lines 1-5 of Fig. 3 */
+    {
+        int win_lo = 0, win_hi = 0;   /* win[i - win_lo] holds assembled cell i */
+        int Jnext = 0;                /* next coarse cell whose rhs is pending */
+        for (int s = 0; s < n; s += w) {
+            int e0, e1, lo, hi;
+            extended_patch(s, w, b, n, &e0, &e1, &lo, &hi);
+            for (int i = lo; i < hi; i++) {
+                patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
+                frhs[i - lo] = f[i];
+            }
+            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL);
+            memcpy(win + (win_hi - win_lo), patch + (s - lo), sizeof(double) * (size_t)w);
+            win_hi += w;
+            /* coarse cells whose fine stencil 2J-2 .. 2J+3 is now assembled */
+            while (Jnext < nc && (2 * Jnext + 3 < win_hi || win_hi == n)) {
+                uc_new[Jnext] = restrict_at(win, win_lo, Jnext);
+                st.rhs[M - 1][Jnext] = tau_rhs_at(win, win_lo, f, 0, Jnext, n);
+                Jnext++;
+            }
+            /* keep only the cells a pending coarse cell can still read */
+            int keep_from = 2 * Jnext - 2 < win_lo ? win_lo : 2 * Jnext - 2;
+            memmove(win, win + (keep_from - win_lo), sizeof(double) * (size_t)(win_hi - keep_from));
+            win_lo = keep_from;
+        }
+    }
+    memcpy(st.u[M - 1], uc_new, sizeof(double) * (size_t)nc);
+
+    /* coarse part of the last V-cycle on the stored levels M-1 .. M0 */
+    rc = vcycle(&st, M - 1);
+    if (rc) goto done;
+
+    /* post-smoothing leg of level M, segment by segment: full update from the
+     * corrected level M-1, compatible relaxation, interior emitted */
+    for (int s = 0; s < n; s += w) {
+        int e0, e1, lo, hi;
+        extended_patch(s, w, b, n, &e0, &e1, &lo, &hi);
+        for (int i = lo; i < hi; i++) {
+            patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
+            frhs[i - lo] = f[i];
+        }
+        patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, st.u[M - 1]);
+        memcpy(u_out + s, patch + (s - lo), sizeof(double) * (size_t)w);
+    }
+done:
+    free(patch); free(frhs); free(win); free(uc_new);
+    free_state(&st);
+    return rc;
+}

@@ -1,0 +1,72 @@
+"""Seeded synthetic inputs for the 1D model problem (Sec. 4).
+
+This module holds no arithmetic of the multigrid method: it only draws the
+manufactured solution's coefficients and samples the right-hand side and the
+exact solution at cell centres.  Both the CUDA path's tests and benchmark and
+the CPU oracle's tests take their inputs from here.
+
+Problem: -u'' = f on (0, 1), u(0) = u(1) = 0, N = 2^M cells, centres
+x_i = (i + 1/2)/N.
+
+* ``sine_series``: u = sum_{k=1..K} c_k sin(k pi x) with c_k ~ N(0,1)/k^2
+  from ``numpy.random.default_rng(seed)``, so f = sum c_k (k pi)^2 sin(k pi x).
+* ``paper_series``: the appendix program's problem, f = sum over odd j below
+  N/16 of sin(j pi x)/j, u = sum sin(j pi x)/(j (j pi)^2).
+"""
+import numpy as np
+
+
+def centres(M):
+    n = 1 << M
+    return (np.arange(n, dtype=np.float64) + 0.5) / n
+
+
+def sine_coefficients(nmodes, seed):
+    """c_k = z_k / k^2 with z ~ N(0, 1) drawn from default_rng(seed), k = 1..nmodes."""
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal(nmodes)
+    k = np.arange(1, nmodes + 1, dtype=np.float64)
+    return z / k**2
+
+
+def sine_series(M, nmodes, seed, scale=1.0):
+    """(f, u_exact, c) sampled at the 2^M cell centres."""
+    x = centres(M)
+    c = scale * sine_coefficients(nmodes, seed)
+    f = np.zeros_like(x)
+    u = np.zeros_like(x)
+    for k in range(1, nmodes + 1):
+        s = np.sin(k * np.pi * x)
+        f += c[k - 1] * (k * np.pi) ** 2 * s
+        u += c[k - 1] * s
+    return f, u, c
+
+
+def paper_series(M):
+    """(f, u_exact): odd modes j < N/16 with f-amplitude 1/j (appendix program)."""
+    n = 1 << M
+    x = centres(M)
+    f = np.zeros_like(x)
+    u = np.zeros_like(x)
+    for j in range(1, max(n // 16, 2), 2):
+        s = np.sin(j * np.pi * x)
+        f += s / j
+        u += s / j / (j * np.pi) ** 2
+    return f, u
+
+
+def discrete_solution(M, c):
+    """Exact solution of the discrete system for a sine-series right-hand side.
+
+    The sampled sines are eigenvectors of the cell-centred operator with the
+    odd-ghost wall (eigenvalue 4 n^2 sin^2(k pi / (2n))), so the discrete
+    solution is the same series with each coefficient scaled by
+    (k pi)^2 / lambda_k.  Used by the tests as a closed form.
+    """
+    n = 1 << M
+    x = centres(M)
+    u = np.zeros_like(x)
+    for k in range(1, len(c) + 1):
+        lam = 4.0 * n * n * np.sin(k * np.pi / (2 * n)) ** 2
+        u += c[k - 1] * (k * np.pi) ** 2 / lam * np.sin(k * np.pi * x)
+    return u

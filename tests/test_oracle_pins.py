@@ -1,0 +1,426 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU needed).
+
+Each test checks an oracle routine against something the paper or the
+mathematics fixes: values printed in the paper's appendix, closed forms
+(eigenvectors of the operator, polynomial reproduction, the eigen-expansion of
+the discrete solution), invariants stated in the text (the tau fixed point of
+Sec. 2.3, the compatible-relaxation constraint of Eq. 8), brute force with
+independently built dense matrices on tiny grids, and the paper's convergence
+claims (one FMG cycle reaches discretization accuracy; Sec. 4 studies).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1207_6720_gb300 import workloads as wl
+from conftest import read_golden
+
+GOLD = read_golden("operators_appendix.txt")
+
+
+def matrix_of(fn, n_in):
+    """Dense matrix of a linear routine, column j = fn(e_j)."""
+    return np.array([fn(e) for e in np.eye(n_in)]).T
+
+
+def centres(n):
+    return (np.arange(n) + 0.5) / n
+
+
+def L_printed(n):
+    """The operator as printed: tridiag(-1, 2, -1) with 3 in the two wall rows, times n^2."""
+    s_w, wall = GOLD["L_wall_row"]
+    s_i, inner = GOLD["L_interior_row"]
+    A = np.zeros((n, n))
+    for i in range(1, n - 1):
+        A[i, i - 1:i + 2] = inner
+    A[0, :2] = wall
+    A[n - 1, n - 2:] = wall[::-1]
+    return A * n * n / s_w
+
+
+# ---------------------------------------------------------------------------
+# Operators against the printed stencils and closed forms (Sec. 4, appendix)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 8, 32])
+def test_operator_matches_printed_matrix(n):
+    A = matrix_of(oracle.apply_L, n)
+    assert np.array_equal(A, L_printed(n))
+
+
+@pytest.mark.parametrize("n", [8, 64, 1024])
+def test_operator_sine_eigenvectors(n):
+    # sin(k pi x_i) at cell centres vanishes on the odd ghost reflection, so it
+    # is an exact eigenvector with eigenvalue 4 n^2 sin^2(k pi / (2n)).
+    i = np.arange(n)
+    for k in [1, 2, 7, n // 2, n - 1, n]:
+        # argument reduced exactly in integers: k pi (i + 1/2)/n = pi m / (2n)
+        m = (k * (2 * i + 1)) % (4 * n)
+        v = np.sin(np.pi * m / (2 * n))
+        lam = 4.0 * n * n * np.sin(k * np.pi / (2 * n)) ** 2
+        Lv = oracle.apply_L(v)
+        # the sampled sine carries rounding of ~eps, which L amplifies by up to 4 n^2
+        tol = 64 * np.finfo(float).eps * 4.0 * n * n * np.max(np.abs(v))
+        assert np.max(np.abs(Lv - lam * v)) <= tol
+
+
+@pytest.mark.parametrize("nc", [4, 16])
+def test_restriction_printed_and_sine_relation(nc):
+    s, row = GOLD["restrict_row"]
+    R = matrix_of(oracle.restrict, 2 * nc)
+    want = np.zeros((nc, 2 * nc))
+    for J in range(nc):
+        want[J, 2 * J:2 * J + 2] = np.array(row) / s
+    assert np.array_equal(R, want)
+    assert np.array_equal(R @ R.T, 0.5 * np.eye(nc))          # R R^T = I/2 (Fig. 4's P)
+    xf, xc = centres(2 * nc), centres(nc)
+    for k in [1, 3, nc]:
+        got = oracle.restrict(np.sin(k * np.pi * xf))
+        want_k = np.cos(k * np.pi / (4 * nc)) * np.sin(k * np.pi * xc)
+        assert np.max(np.abs(got - want_k)) < 1e-14
+
+
+@pytest.mark.parametrize("nc", [4, 8, 32])
+def test_linear_prolongation_printed_columns(nc):
+    P = matrix_of(oracle.prolong_lin, nc)
+    s, col = GOLD["prolong_lin_interior_column"]
+    for J in range(1, nc - 1):
+        assert np.array_equal(P[2 * J - 1:2 * J + 3, J] * s, col)
+        assert np.count_nonzero(P[:, J]) == 4
+    s, wall = GOLD["prolong_lin_wall_column"]
+    assert np.array_equal(P[0:3, 0] * s, wall)
+    assert np.array_equal(P[-3:, nc - 1][::-1] * s, wall)
+
+
+def test_linear_prolongation_reproduces_linear_functions():
+    nc = 16
+    xc, xf = centres(nc), centres(2 * nc)
+    up = oracle.prolong_lin(0.3 + 2.0 * xc)
+    assert np.max(np.abs(up[1:-1] - (0.3 + 2.0 * xf[1:-1]))) < 1e-14
+    up = oracle.prolong_lin(xc)                 # odd about the left wall
+    assert abs(up[0] - xf[0]) < 1e-15
+    up = oracle.prolong_lin(xc - 1.0)           # odd about the right wall
+    assert abs(up[-1] - (xf[-1] - 1.0)) < 1e-15
+
+
+@pytest.mark.parametrize("nc", [4, 8, 32])
+def test_fmg_interpolation_printed_rows(nc):
+    Pi = matrix_of(oracle.prolong_fmg, nc) * 128.0
+    _, left = GOLD["fmg_left_child"]
+    _, right = GOLD["fmg_right_child"]
+    for J in range(2, nc - 2):
+        assert np.array_equal(Pi[2 * J, J - 2:J + 2], left)
+        assert np.array_equal(Pi[2 * J + 1, J - 1:J + 3], right)
+        assert np.count_nonzero(Pi[2 * J]) == 4
+    for r in range(4):
+        _, row = GOLD["fmg_wall_row%d" % r]
+        assert np.array_equal(Pi[r, :4], row)
+        assert np.array_equal(Pi[2 * nc - 1 - r, nc - 4:][::-1], row)   # mirror at the right wall
+
+
+def test_fmg_interpolation_is_fourth_order():
+    nc = 32
+    xc, xf = centres(nc), centres(2 * nc)
+    p = lambda x: 0.7 - 1.3 * x + 2.1 * x ** 2 - 0.9 * x ** 3
+    up = oracle.prolong_fmg(p(xc))
+    inner = slice(4, 2 * nc - 4)
+    assert np.max(np.abs(up[inner] - p(xf)[inner])) < 1e-14
+    for q in (lambda x: x, lambda x: x ** 3 - 0.5 * x):          # odd about x = 0
+        assert np.max(np.abs(oracle.prolong_fmg(q(xc))[:4] - q(xf)[:4])) < 1e-14
+    for q in (lambda x: x - 1, lambda x: (x - 1) ** 3 + 2 * (x - 1)):   # odd about x = 1
+        assert np.max(np.abs(oracle.prolong_fmg(q(xc))[-4:] - q(xf)[-4:])) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Coarsest-grid solve, discrete solution, tau correction, Kaczmarz
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 8, 64])
+def test_thomas_against_dense_solve(n):
+    rhs = np.random.default_rng(n).standard_normal(n)
+    want = np.linalg.solve(L_printed(n), rhs)
+    assert np.max(np.abs(oracle.thomas(rhs) - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("M", [6, 10])
+def test_thomas_against_eigen_expansion(M):
+    f, _, c = wl.sine_series(M, 8, seed=3)
+    us = wl.discrete_solution(M, c)
+    assert np.max(np.abs(oracle.thomas(f) - us)) <= 1e-12 * np.max(np.abs(us))
+
+
+@pytest.mark.parametrize("M", [5, 9])
+def test_tau_rhs_against_dense_matrices(M):
+    n = 1 << M
+    rng = np.random.default_rng(M)
+    u, f = rng.standard_normal(n), rng.standard_normal(n)
+    R = np.zeros((n // 2, n))
+    for J in range(n // 2):
+        R[J, 2 * J:2 * J + 2] = 0.5
+    want = R @ f + L_printed(n // 2) @ (R @ u) - R @ (L_printed(n) @ u)   # Eqs. 4-5
+    got = oracle.tau_rhs(u, f)
+    assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(L_printed(n) @ u))
+
+
+@pytest.mark.parametrize("M", [6, 11])
+def test_tau_fixed_point(M):
+    # Sec. 2.3: with the fine discrete solution, the tau-corrected coarse
+    # equation is solved exactly by the restricted fine solution.
+    f, _, c = wl.sine_series(M, 8, seed=5)
+    us = wl.discrete_solution(M, c)
+    rhs_c = oracle.tau_rhs(us, f)
+    uc = oracle.thomas(rhs_c)
+    assert np.max(np.abs(uc - oracle.restrict(us))) <= 1e-11 * np.max(np.abs(us))
+
+
+def test_kaczmarz_enforces_coarse_constraint():
+    # Eq. 8: after one pass over all pairs, R u_h equals u_H (to rounding);
+    # cells outside [e0, e1) are untouched.
+    rng = np.random.default_rng(7)
+    v, uH = rng.standard_normal(64), rng.standard_normal(32)
+    out = oracle.kaczmarz(v, uH, 0, 64)
+    assert np.max(np.abs(oracle.restrict(out) - uH)) < 1e-15
+    part = oracle.kaczmarz(v, uH, 8, 24)
+    assert np.array_equal(part[:8], v[:8]) and np.array_equal(part[24:], v[24:])
+    assert np.max(np.abs(oracle.restrict(part)[4:12] - uH[4:12])) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# The smoother S (Sec. 3, Fig. 4, appendix): brute force with matrix splittings
+# ---------------------------------------------------------------------------
+
+def lex_sweeps_dense(A, u, f, lo, hi, nsweeps):
+    """Lexicographic GS on rows [lo, hi) written as a triangular splitting solve,
+    cells outside [lo, hi) frozen; ascending, then reversed each sweep."""
+    u = u.copy()
+    idx = np.arange(lo, hi)
+    out = np.setdiff1d(np.arange(len(u)), idx)
+    B = A[np.ix_(idx, idx)]
+    for k in range(nsweeps):
+        b = f[idx] - A[np.ix_(idx, out)] @ u[out]
+        if k % 2 == 0:
+            lower, upper = np.tril(B), np.triu(B, 1)
+        else:
+            lower, upper = np.triu(B), np.tril(B, -1)
+        u[idx] = np.linalg.solve(lower, b - upper @ u[idx])
+    return u
+
+
+@pytest.mark.parametrize("nsweeps", [1, 2, 3])
+def test_global_lexicographic_sweep_matches_splitting(nsweeps):
+    M = 6
+    n = 1 << M
+    rng = np.random.default_rng(11)
+    u, f = rng.standard_normal(n), rng.standard_normal(n) * n * n
+    got = oracle.smooth(oracle.Params(M, nRS=0), M, u, f, nsweeps)
+    want = lex_sweeps_dense(L_printed(n), u, f, 0, n, nsweeps)
+    assert np.max(np.abs(got - want)) < 1e-11
+
+
+@pytest.mark.parametrize("w,b", [(4, 2), (8, 4), (2, 4)])
+def test_segmented_smoother_is_additive_block_jacobi(w, b):
+    # Sec. 3: each extended patch is solved from the same input and only its
+    # interior is kept.
+    M = 5
+    n = 1 << M
+    rng = np.random.default_rng(w * 10 + b)
+    u, f = rng.standard_normal(n), rng.standard_normal(n) * n * n
+    p = oracle.Params(M, nRS=0, seg={M: (w, b)})
+    got = oracle.smooth(p, M, u, f, 2)
+    want = np.empty(n)
+    for s in range(0, n, w):
+        lo, hi = max(0, s - b), min(n, s + w + b)
+        want[s:s + w] = lex_sweeps_dense(L_printed(n), u, f, lo, hi, 2)[s:s + w]
+    assert np.max(np.abs(got - want)) < 1e-11
+
+
+def test_compatible_relaxation_patch_matches_brute_force():
+    # Fig. 4 on each extended patch: Kaczmarz over the patch's pairs, then GS.
+    M, w, b = 5, 8, 4
+    n = 1 << M
+    rng = np.random.default_rng(3)
+    u, f, uH = rng.standard_normal(n), rng.standard_normal(n) * n * n, rng.standard_normal(n // 2)
+    p = oracle.Params(M, nRS=1, seg={M: (w, b)})
+    got = oracle.smooth(p, M, u, f, 1, uH)
+    A = L_printed(n)
+    want = np.empty(n)
+    for s in range(0, n, w):
+        lo, hi = max(0, s - b), min(n, s + w + b)
+        v = u.copy()
+        for i in range(lo, hi, 2):
+            r = uH[i // 2] - 0.5 * (v[i] + v[i + 1])
+            v[i] += r
+            v[i + 1] += r
+        want[s:s + w] = lex_sweeps_dense(A, v, f, lo, hi, 1)[s:s + w]
+    assert np.max(np.abs(got - want)) < 1e-11
+
+
+@pytest.mark.parametrize("smoother", ["lex", "rb"])
+def test_discrete_solution_is_a_fixed_point(smoother):
+    M = 8
+    f, _, c = wl.sine_series(M, 8, seed=2)
+    us = wl.discrete_solution(M, c)
+    for seg in ({}, {M: (16, 4)}):
+        p = oracle.Params(M, nRS=0, smoother=smoother, seg=seg)
+        out = oracle.smooth(p, M, us, f, 2)
+        assert np.max(np.abs(out - us)) <= 1e-13 * np.max(np.abs(us))
+        out = oracle.smooth(p, M, us, f, 2, uH=oracle.restrict(us))
+        assert np.max(np.abs(out - us)) <= 1e-13 * np.max(np.abs(us))
+
+
+# ---------------------------------------------------------------------------
+# Cycles (Figs. 1-3) and the paper's accuracy claims
+# ---------------------------------------------------------------------------
+
+def test_vcycles_converge_to_discrete_solution():
+    M = 10
+    f, _, c = wl.sine_series(M, 8, seed=4)
+    us = wl.discrete_solution(M, c)
+    u = np.zeros(1 << M)
+    errs = []
+    for _ in range(12):
+        u = oracle.vcycles_h(oracle.Params(M, nRS=0), f, u, 1)
+        errs.append(np.max(np.abs(u - us)))
+    assert errs[-1] <= 1e-12 * np.max(np.abs(us))
+    factor = (errs[8] / errs[2]) ** (1 / 6)
+    assert factor < 0.2
+
+
+def test_vcycle_spectral_radius_bounded_with_depth():
+    for M in (4, 6):
+        n = 1 << M
+        V = matrix_of(lambda e: oracle.vcycles_h(oracle.Params(M, nRS=0), np.zeros(n), e, 1), n)
+        assert np.max(np.abs(np.linalg.eigvals(V))) < 0.15
+
+
+@pytest.mark.parametrize("nRS,W,b", [(0, 0, 0), (1, 256, 8), (1, 64, 4), (2, 256, 8)])
+def test_one_fmg_cycle_reaches_discretization_accuracy(nRS, W, b):
+    # Sec. 2.2 / Sec. 4: one F-cycle reduces the error to the order of the
+    # truncation error; second-order convergence (error ratio ~4 per halving h).
+    errs = []
+    for M in (10, 12, 14):
+        f, ue, c = wl.sine_series(M, 16, seed=1)
+        us = wl.discrete_solution(M, c)
+        p = oracle.Params(M, nRS=0) if nRS == 0 else oracle.sr_params(M, W, b, nRS=nRS)
+        u = oracle.fmg_h(p, f)
+        disc = np.linalg.norm(us - ue) / np.sqrt(len(f))       # RMS over the cells
+        err = np.linalg.norm(u - ue) / np.sqrt(len(f))
+        assert err <= 1.5 * disc
+        errs.append(err)
+    for a, b2 in zip(errs, errs[1:]):
+        assert 3.5 * 3.5 < a / b2 < 4.5 * 4.5         # two halvings of h per step
+
+
+@pytest.mark.parametrize("params", [
+    lambda M: oracle.sr_params(M, 64, 8, nRS=1),
+    lambda M: oracle.sr_params(M, 16, 4, nRS=2),
+    lambda M: oracle.sr_params(M, 32, 2, nRS=3, nu1=2, nu2=1),
+    lambda M: oracle.paper_params(M, 1, 2, 1),
+    lambda M: oracle.paper_params(M, 3, 1, 2),
+])
+def test_serial_sr_never_storing_finest_level_equals_stored_solve(params):
+    # Sec. 4: the horizontal processing has the same semantics as the
+    # segment-by-segment algorithm of Fig. 3.
+    for M in (8, 11):
+        f, _, _ = wl.sine_series(M, 8, seed=9)
+        p = params(M)
+        assert np.array_equal(oracle.fmg_h(p, f), oracle.fmg_v(p, f))
+
+
+def _paper_errors(halo_type, ns, nRS, Ms):
+    out = []
+    for M in Ms:
+        f, ue = wl.paper_series(M)
+        u = oracle.fmg_h(oracle.paper_params(M, nRS, halo_type, ns), f)
+        out.append(np.linalg.norm(ue - u) / np.linalg.norm(ue))
+    return np.array(out)
+
+
+def test_paper_study_second_order_everywhere():
+    # Sec. 4: all configurations converge at second order.
+    Ms = [9, 10, 11, 12]
+    for halo_type in (1, 2, 3):
+        for ns in (1, 2):
+            for nRS in range(4):
+                e = _paper_errors(halo_type, ns, nRS, Ms)
+                ratios = e[:-1] / e[1:]
+                assert np.all((ratios > 3.0) & (ratios < 5.5)), (halo_type, ns, nRS, ratios)
+
+
+def test_paper_study_two_halo_three_sr_levels_v11_loses_accuracy():
+    # Fig. 5 discussion: with two halo cells, accuracy is lost to some extent
+    # with three SR levels and V(1,1); the other two-halo curves stay at FMG
+    # accuracy.
+    Ms = [12]
+    base = _paper_errors(1, 1, 0, Ms)[0]
+    worst = _paper_errors(1, 1, 3, Ms)[0]
+    assert worst > 1.5 * base
+    for ns, nRS in [(1, 1), (1, 2), (2, 1), (2, 2), (2, 3)]:
+        other = _paper_errors(1, ns, nRS, Ms)[0]
+        assert other < 1.25 * _paper_errors(1, ns, 0, Ms)[0]
+        assert other < worst
+
+
+def test_paper_study_four_halo_good_in_all_configurations():
+    # Fig. 6 discussion: with four halo cells the accuracy is very good in all
+    # solver configurations.
+    Ms = [10, 12]
+    for ns in (1, 2):
+        base = _paper_errors(2, ns, 0, Ms)
+        for nRS in (1, 2, 3):
+            assert np.all(_paper_errors(2, ns, nRS, Ms) <= 1.1 * base)
+
+
+def test_paper_study_global_smoother_cleaner():
+    # Fig. 7 discussion: the global point-wise GS smoother gives "cleaner"
+    # convergence than the block-Jacobi smoothers: its error ratios per halving
+    # of h stay closer to 4.
+    Ms = list(range(6, 13))
+    spread = {}
+    for halo_type in (1, 2, 3):
+        devs = []
+        for ns in (1, 2):
+            for nRS in range(4):
+                e = _paper_errors(halo_type, ns, nRS, Ms)
+                devs.append(np.max(np.abs(np.log(e[:-1] / e[1:]) - np.log(4.0))))
+        spread[halo_type] = max(devs)
+    assert spread[3] < spread[1] and spread[3] < spread[2]
+
+
+# ---------------------------------------------------------------------------
+# Readings where the paper is silent (recorded so that a change is noticed)
+# ---------------------------------------------------------------------------
+
+def test_reading_red_black_v11_misses_discretization_accuracy():
+    # Red-black ordering with V(1,1) has a V-cycle factor that grows with the
+    # depth here, so one FMG cycle drifts away from discretization accuracy;
+    # this is why the paper's lexicographic smoother is the default.
+    ratios = []
+    for M in (10, 14):
+        f, ue, c = wl.sine_series(M, 8, seed=0)
+        us = wl.discrete_solution(M, c)
+        u = oracle.fmg_h(oracle.Params(M, nRS=0, smoother="rb"), f)
+        ratios.append(np.linalg.norm(u - ue) / np.linalg.norm(us - ue))
+    assert ratios[0] > 3 and ratios[1] > 3 * ratios[0]
+    # red-black with V(2,2) does reach it
+    f, ue, c = wl.sine_series(14, 8, seed=0)
+    us = wl.discrete_solution(14, c)
+    u = oracle.fmg_h(oracle.Params(14, nRS=0, smoother="rb", nu1=2, nu2=2), f)
+    assert np.linalg.norm(u - ue) <= 1.5 * np.linalg.norm(us - ue)
+
+
+@pytest.mark.slow
+def test_reading_segment_local_tau_seam_error():
+    # tau taken from a segment's own buffer cells (Fig. 3 line 4 read
+    # literally) is inconsistent with the restricted solution at segment
+    # edges; at large N the rounding-level mismatch, amplified by 1/h^2,
+    # dominates.  tau from the assembled level matches the stored solve.
+    M = 21
+    f, _, c = wl.sine_series(M, 32, seed=1)
+    us = wl.discrete_solution(M, c)
+    stored = np.max(np.abs(oracle.fmg_h(oracle.Params(M, nRS=0), f) - us))
+    asm = np.max(np.abs(oracle.fmg_h(oracle.sr_params(M, 4096, 4, tau_src="assembled"), f) - us))
+    loc = np.max(np.abs(oracle.fmg_h(oracle.sr_params(M, 4096, 4, tau_src="segment"), f) - us))
+    assert asm < 1.5 * stored
+    assert loc > 10 * asm
