@@ -1,0 +1,135 @@
+/*
+ * srfmg.h -- C ABI of the GB300 (sm_103a) one-pass FMG-FAS solver with
+ * segmental refinement (SR), after M. F. Adams, "A low memory, highly
+ * concurrent multigrid algorithm".
+ *
+ * Problem (Sec. 4 of the paper): -u'' = f on (0,1) with u(0) = u(1) = 0,
+ * discretised by cell-centred second order finite volumes on N = 2^M cells
+ * (centres x_i = (i + 1/2)/N; the Dirichlet wall is an odd ghost cell).
+ *
+ * Method: one FMG cycle (Fig. 2) of FAS V(nu1, nu2)-cycles (Fig. 1) with the
+ * tau correction of Eqs. 4-5; the finest n_sr_levels levels are SR levels
+ * (Fig. 3): they are split into segments of segment_width cells with
+ * buffer_width buffer cells per side, smoothed additively (block Jacobi), and
+ * in the post-smoothing leg they are rebuilt from the coarse grid by the full
+ * update of Eq. 7 and smoothed with the Kaczmarz compatible relaxation of
+ * Fig. 4.  The finest level is never stored: it lives in on-chip memory only.
+ * The smoother is the paper's lexicographic Gauss-Seidel (omega = 1, the
+ * sweep direction reversed after every sweep within one smoothing call); tau
+ * at segment edges is formed from the assembled level, as in the paper's
+ * appendix program.  With n_sr_levels = 0 the same entry points run plain
+ * FMG-FAS with every level stored.
+ *
+ * Conventions for every entry point:
+ *   - No C++ types or exceptions cross this boundary.
+ *   - Arguments are checked on the host before anything is enqueued; a bad
+ *     argument returns SRFMG_EINVAL (or SRFMG_EUNSUPPORTED for a valid but
+ *     not implemented option) and enqueues nothing.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  srfmg_solve is asynchronous on it.
+ *   - The caller owns f and u; the handle owns its device workspace (the
+ *     stored coarse levels, the seam buffer, the coarsest-grid inverse and
+ *     the captured CUDA graphs).
+ *   - A handle may be used from one host thread at a time.
+ *   - There is no CPU fallback: without a usable CUDA device srfmg_create
+ *     returns SRFMG_ECUDA.
+ */
+#ifndef SRFMG_H
+#define SRFMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct srfmg_plan *srfmg_handle;
+
+typedef enum {
+    SRFMG_OK = 0,
+    SRFMG_EINVAL = 1,          /* invalid argument; nothing was enqueued */
+    SRFMG_ENOMEM = 2,          /* device workspace allocation failed */
+    SRFMG_ECUDA = 3,           /* a CUDA call failed; see srfmg_last_error */
+    SRFMG_ETIMEOUT = 4,        /* a bounded device wait expired */
+    SRFMG_ENONFINITE = 5,      /* non-finite value detected */
+    SRFMG_EUNSUPPORTED = 6     /* valid option that this build does not implement */
+} srfmg_status;
+
+typedef enum { SRFMG_OP_LAPLACE = 0 } srfmg_op;          /* -u'' = f */
+typedef enum { SRFMG_FP64 = 0, SRFMG_MIXED = 1 } srfmg_precision;
+typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
+
+/* Solve parameters (the paper's problem statement and cycle type). */
+typedef struct {
+    int32_t op;                /* srfmg_op */
+    int32_t precision;         /* srfmg_precision */
+    int32_t log2_n;            /* M: N = 2^M fine cells, M0 < M <= 28 */
+    int32_t log2_n_coarsest;   /* M0: coarsest level, solved exactly; 2 <= M0 <= 6 (default 2) */
+    int32_t n_sr_levels;       /* number of SR levels: 0 (plain stored FMG-FAS) or 1 */
+    int32_t segment_width;     /* W: finest-level cells per segment; power of two, 16 <= W <= 4096, W <= N */
+    int32_t buffer_width;      /* b: buffer cells per segment side; even, 2 <= b <= 64, b <= W */
+    int32_t nu1, nu2;          /* V(nu1, nu2): 1 <= nu1, nu2 <= 4 */
+    int32_t smoother;          /* srfmg_smoother */
+    int32_t reserved[6];       /* must be zero */
+} srfmg_params;
+
+/* Information about a created plan. */
+typedef struct {
+    int64_t workspace_bytes;   /* device memory owned by the handle */
+    int32_t kernels_per_solve; /* kernel launches enqueued by one srfmg_solve */
+    int32_t coarse_tail_level; /* finest level handled by the one-block coarse tail */
+    int32_t n_segments;        /* segments on the finest level (0 without SR) */
+    int32_t reserved[7];
+} srfmg_info;
+
+/* Fill *p with the defaults for N = 2^log2_n: M0 = 2, one SR level,
+ * W = min(4096, N/4) (at least 16), b = 8, V(1,1), FP64, lexicographic GS.
+ * Returns SRFMG_EINVAL if p is NULL. */
+srfmg_status srfmg_default_params(int32_t log2_n, srfmg_params *p);
+
+/* Create a plan on CUDA device `device`: validates *p (Sec. 3/4 parameter
+ * meanings above), allocates the device workspace and records the level
+ * schedule (the FMG loop of Fig. 2 with the SR steps of Fig. 3).
+ * On success *out is a new handle; on failure *out is NULL. */
+srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
+
+/* One FMG-FAS(-SR) solve (Figs. 2-4).
+ * f: device pointer, N doubles, the right-hand side at the cell centres.
+ * u: device pointer, N doubles, receives the solution at the cell centres.
+ * f and u must not overlap and must stay valid until the stream reaches the
+ * end of the solve.  Enqueued asynchronously on `stream`; the launch sequence
+ * is captured into a CUDA graph the first time a (f, u, stream) triple is seen
+ * and replayed afterwards.  Errors: SRFMG_EINVAL for NULL or misaligned
+ * (not 16-byte aligned) pointers, SRFMG_ECUDA if a launch fails. */
+srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream);
+
+/* The same solve from and to HOST memory: copies f (N doubles) to a device
+ * staging buffer owned by the handle, solves, copies the solution back into u
+ * (N doubles) and synchronises `stream` before returning.  Pinned host
+ * buffers give the fastest copies; pageable ones work.  f and u may alias. */
+srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream);
+
+/* Gradient of a loss through the solve.  Reserved: returns SRFMG_EUNSUPPORTED
+ * in this build (nothing is enqueued). */
+srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream);
+
+/* Plan information (workspace size, launches per solve, ...). */
+srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info);
+
+/* Release the device workspace and graphs.  Synchronises the device first.
+ * Accepts NULL (returns SRFMG_OK). */
+srfmg_status srfmg_destroy(srfmg_handle h);
+
+/* Message describing the last error on h (or the last creation error when h
+ * is NULL).  Never NULL; owned by the library; valid until the next call on
+ * the same handle. */
+const char *srfmg_last_error(srfmg_handle h);
+
+/* Library version string, e.g. "srfmg 0.1 sm_103a". */
+const char *srfmg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRFMG_H */

@@ -1,0 +1,565 @@
+// srfmg.cu -- host side of the FMG-FAS-SR solver: parameter checks, device
+// workspace, the level schedule of one FMG cycle (Fig. 2 with the SR steps of
+// Fig. 3), CUDA-graph capture and replay, and the C ABI declared in srfmg.h.
+#include "srfmg.h"
+#include "srfmg_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace srfmg;
+
+namespace {
+
+constexpr int kMaxTailLevel = 12;      // levels <= 12 fit one block's shared memory in FP64
+constexpr int kTailThreads = 1024;
+constexpr int kRhsThreads = 256;
+constexpr int kRhsDepth = 12;          // levels reduced per rhs-hierarchy launch
+constexpr int kTileMax = 2048;
+
+thread_local std::string g_create_error = "no error";
+
+enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST };
+
+// Pointers that are only known at solve time are patched through these tags.
+enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };
+
+struct Op {
+    OpKind kind;
+    dim3 grid, block;
+    size_t smem;
+    RhsArgs rhs;
+    LevelArgs lev;
+    SegArgs seg;
+    TailArgs tail;
+    int nseg;
+    // tags for pointer fields patched per solve
+    PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
+};
+
+}  // namespace
+
+struct srfmg_plan {
+    srfmg_params p;
+    int device;
+    int M, M0, Mc, nRS, W, b;
+    size_t n;
+    std::vector<void *> allocs;
+    double *ulev[32][2] = {};
+    double *glev[32] = {};
+    double *seam = nullptr;
+    double *Ainv = nullptr;
+    double *f_stage = nullptr, *u_stage = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<Op> ops;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double *g_f = nullptr;
+    double *g_u = nullptr;
+    bool use_graph = true;
+    std::string err = "no error";
+};
+
+namespace {
+
+srfmg_status fail(srfmg_plan *h, srfmg_status st, const std::string &msg) {
+    if (h) h->err = msg; else g_create_error = msg;
+    return st;
+}
+
+srfmg_status cuda_fail(srfmg_plan *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, SRFMG_ECUDA, m);
+}
+
+bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
+
+std::string check_params(const srfmg_params *p) {
+    if (!p) return "params is NULL";
+    for (int i = 0; i < 6; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    if (p->op != SRFMG_OP_LAPLACE) return "op must be SRFMG_OP_LAPLACE";
+    if (p->precision != SRFMG_FP64 && p->precision != SRFMG_MIXED) return "unknown precision";
+    if (p->smoother != SRFMG_SMOOTH_LEX) return "smoother must be SRFMG_SMOOTH_LEX";
+    if (p->log2_n_coarsest < 2 || p->log2_n_coarsest > 6) return "log2_n_coarsest must be in [2, 6]";
+    if (p->log2_n <= p->log2_n_coarsest || p->log2_n > 28) return "log2_n must be in (log2_n_coarsest, 28]";
+    if (p->n_sr_levels < 0 || p->n_sr_levels > 1) return "n_sr_levels must be 0 or 1";
+    if (p->nu1 < 1 || p->nu1 > 4 || p->nu2 < 1 || p->nu2 > 4) return "nu1 and nu2 must be in [1, 4]";
+    if (p->n_sr_levels == 1) {
+        long long N = 1LL << p->log2_n;
+        if (!pow2(p->segment_width) || p->segment_width < 16 || p->segment_width > 4096 ||
+            p->segment_width > N)
+            return "segment_width must be a power of two in [16, min(4096, N)]";
+        if (p->buffer_width < 2 || p->buffer_width > 64 || (p->buffer_width & 1) ||
+            p->buffer_width > p->segment_width)
+            return "buffer_width must be even, in [2, 64] and <= segment_width";
+    }
+    return "";
+}
+
+// Inverse of the scaled coarsest operator h^2 L (tridiag(-1,2,-1), 3 in the
+// wall rows) by Gauss-Jordan elimination in long double.
+std::vector<double> coarsest_inverse(int n) {
+    std::vector<long double> A(n * 2 * n, 0.0L);
+    auto at = [&](int i, int j) -> long double & { return A[i * 2 * n + j]; };
+    for (int i = 0; i < n; ++i) {
+        at(i, i) = (i == 0 || i == n - 1) ? 3.0L : 2.0L;
+        if (i > 0) at(i, i - 1) = -1.0L;
+        if (i < n - 1) at(i, i + 1) = -1.0L;
+        at(i, n + i) = 1.0L;
+    }
+    for (int c = 0; c < n; ++c) {
+        long double piv = at(c, c);
+        for (int j = 0; j < 2 * n; ++j) at(c, j) /= piv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            long double f = at(r, c);
+            if (f == 0.0L) continue;
+            for (int j = 0; j < 2 * n; ++j) at(r, j) -= f * at(c, j);
+        }
+    }
+    std::vector<double> inv(n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[i * n + j] = (double)at(i, n + j);
+    return inv;
+}
+
+// Shared-memory layout of a block that sweeps up to `cells` cells: three
+// level buffers, the coarse cells it reads, two per-chunk carry arrays; one
+// thread per chunk (rounded up to whole warps).
+size_t sweep_layout(int cells, int *maxlen, int *maxc, int *maxch, int *threads) {
+    *maxlen = cells + 2;
+    *maxc = cells / 2 + 8;
+    *maxch = (cells + kChunk - 1) / kChunk + 2;
+    *threads = ((*maxch + 31) / 32) * 32;
+    return (size_t)3 * *maxlen + *maxc + 2 * *maxch;
+}
+
+size_t tail_smem_doubles(int M0, int Mc) {
+    size_t tot = (1u << (Mc + 1)) - (1u << M0);
+    return 2 * tot + (1u << Mc) + 8 + 2 * kTailThreads;
+}
+
+srfmg_status alloc_dev(srfmg_plan *h, double **out, size_t count) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SRFMG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(ptr);
+    h->ws_bytes += count * sizeof(double);
+    *out = (double *)ptr;
+    return SRFMG_OK;
+}
+
+Op make_op(OpKind k) {
+    Op o;
+    std::memset(&o, 0, sizeof(o));
+    o.kind = k;
+    return o;
+}
+
+// Level pass of a stored level (global smoothing), tile decomposition.
+Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double *uc_src,
+            double *u_out, double *uc_out, double *gc_out) {
+    Op o = make_op(kind);
+    const int n = 1 << l;
+    const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
+    const int T = n < kTileMax ? n : kTileMax;
+    // halo: each sweep's values become tile-independent (J+2)*kChunk cells
+    // after its range start, and the tau stencil reaches 2 cells past the tile
+    const int H = 4 + 100 * nu;
+    o.lev.l = l;
+    o.lev.n = n;
+    o.lev.tile = T;
+    o.lev.halo = H;
+    o.lev.nu = nu;
+    o.lev.u_src = u_src;
+    o.lev.uc_src = uc_src;
+    o.lev.u_out = u_out;
+    o.lev.uc_out = uc_out;
+    o.lev.gc_out = gc_out;
+    if (l == h->M) {               // finest level without SR: rhs from f
+        o.lev.g = nullptr;
+        o.lev_g = TAG_F;
+        o.lev.g_exp = -2 * l;
+    } else {
+        o.lev.g = h->glev[l];
+        o.lev.g_exp = 0;
+    }
+    int threads;
+    o.grid = dim3(n / T);
+    o.smem = sweep_layout(T + 2 * H, &o.lev.maxlen, &o.lev.maxc, &o.lev.maxch, &threads) * sizeof(double);
+    o.block = dim3(threads);
+    return o;
+}
+
+Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, double *gc_out) {
+    Op o = make_op(kind);
+    o.seg.M = h->M;
+    o.seg.n = 1 << h->M;
+    o.seg.W = h->W;
+    o.seg.b = h->b;
+    o.seg.nu = (kind == OP_SR_POST) ? h->p.nu2 : h->p.nu1;
+    o.seg.uc_src = uc_src;
+    o.seg.uc_out = uc_out;
+    o.seg.gc_out = gc_out;
+    o.seg.seam = h->seam;
+    o.seg_f = TAG_F;
+    if (kind == OP_SR_POST) o.seg_u = TAG_U;
+    o.nseg = (int)(h->n / h->W);
+    if (kind == OP_SEAM) {
+        o.grid = dim3((o.nseg + 127) / 128);
+        o.block = dim3(128);
+        o.smem = 0;
+    } else {
+        int threads;
+        o.grid = dim3(o.nseg);
+        o.smem = sweep_layout(h->W + 2 * h->b, &o.seg.maxlen, &o.seg.maxc, &o.seg.maxch, &threads) *
+                 sizeof(double);
+        o.block = dim3(threads);
+    }
+    return o;
+}
+
+Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int g_exp,
+           double *u_out, bool g_from_f, bool out_is_u) {
+    Op o = make_op(OP_TAIL);
+    o.tail.M0 = h->M0;
+    o.tail.Mc = h->Mc;
+    o.tail.nu1 = h->p.nu1;
+    o.tail.nu2 = h->p.nu2;
+    o.tail.mode = mode;
+    o.tail.u_in = u_in;
+    o.tail.g_in = g_in;
+    o.tail.g_exp = g_exp;
+    o.tail.u_out = u_out;
+    o.tail.Ainv = h->Ainv;
+    if (g_from_f) o.tail_g = TAG_F;
+    if (out_is_u) o.tail_out = TAG_U;
+    o.grid = dim3(1);
+    o.block = dim3(kTailThreads);
+    o.smem = tail_smem_doubles(h->M0, h->Mc) * sizeof(double);
+    return o;
+}
+
+// The level schedule of one FMG cycle.  cur[l] tracks which of the two
+// buffers of level l holds its current iterate.
+void build_schedule(srfmg_plan *h) {
+    const int M = h->M, Mc = h->Mc;
+    int cur[32] = {0};
+    auto U = [&](int l) { return h->ulev[l][cur[l]]; };
+    auto Unext = [&](int l) { return h->ulev[l][cur[l] ^ 1]; };
+
+    // K1: rhs hierarchy g_{M-1} .. g_Mc from f
+    if (Mc < M) {
+        int lin = M;
+        while (lin > Mc) {
+            int depth = lin - Mc < kRhsDepth ? lin - Mc : kRhsDepth;
+            Op o = make_op(OP_RHS);
+            o.rhs.lin = lin;
+            o.rhs.lstop = lin - depth;
+            o.rhs.depth = depth;
+            if (lin == M) { o.rhs_in = TAG_F; o.rhs.in_exp = -2 * M; }
+            else { o.rhs.in = h->glev[lin]; o.rhs.in_exp = 0; }
+            for (int l = lin - depth; l < lin; ++l) o.rhs.out[l] = h->glev[l];
+            o.grid = dim3((unsigned)((1ULL << lin) >> depth));
+            o.block = dim3(kRhsThreads);
+            o.smem = (size_t)(1 << depth) * 3 / 2 * sizeof(double);
+            h->ops.push_back(o);
+            lin -= depth;
+        }
+    }
+    // FMG up to level Mc in the tail block
+    if (Mc == M) {
+        h->ops.push_back(tail_op(h, 0, nullptr, nullptr, -2 * M, nullptr, true, true));
+        return;
+    }
+    h->ops.push_back(tail_op(h, 0, nullptr, h->glev[Mc], 0, Unext(Mc), false, false));
+    cur[Mc] ^= 1;
+
+    // one V-cycle below a level that was just restricted to Mc
+    auto vcycle_below = [&](int top_stored) {
+        for (int l = top_stored; l > Mc; --l) {
+            h->ops.push_back(level_op(h, OP_DOWN, l, U(l), nullptr, Unext(l), Unext(l - 1), h->glev[l - 1]));
+            cur[l] ^= 1;
+            cur[l - 1] ^= 1;
+        }
+        h->ops.push_back(tail_op(h, 1, U(Mc), h->glev[Mc], 0, Unext(Mc), false, false));
+        cur[Mc] ^= 1;
+        for (int l = Mc + 1; l <= top_stored; ++l) {
+            h->ops.push_back(level_op(h, OP_UP, l, U(l), U(l - 1), Unext(l), nullptr, nullptr));
+            cur[l] ^= 1;
+        }
+    };
+
+    const int last_stored = (h->nRS == 1) ? M - 1 : M;
+    // FMG steps whose top level is a stored level below the finest
+    for (int k = Mc; k < M - 1; ++k) {
+        int top = k + 1;
+        h->ops.push_back(level_op(h, OP_DOWN_PI, top, U(k), nullptr, Unext(top), Unext(k), h->glev[k]));
+        cur[top] ^= 1;
+        cur[k] ^= 1;
+        vcycle_below(k);
+        h->ops.push_back(level_op(h, OP_UP, top, U(top), U(k), Unext(top), nullptr, nullptr));
+        cur[top] ^= 1;
+    }
+    // last step: top level M
+    if (h->nRS == 1) {
+        h->ops.push_back(seg_op(h, OP_SR_PRE, U(M - 1), Unext(M - 1), h->glev[M - 1]));
+        cur[M - 1] ^= 1;
+        h->ops.push_back(seg_op(h, OP_SEAM, nullptr, U(M - 1), h->glev[M - 1]));
+        vcycle_below(M - 1);
+        h->ops.push_back(seg_op(h, OP_SR_POST, U(M - 1), nullptr, nullptr));
+    } else {
+        // level M stored in ulev[M][0]; the up pass writes the user's u
+        h->ops.push_back(level_op(h, OP_DOWN_PI, M, U(M - 1), nullptr, h->ulev[M][0], Unext(M - 1),
+                                  h->glev[M - 1]));
+        cur[M - 1] ^= 1;
+        vcycle_below(M - 1);
+        Op o = level_op(h, OP_UP, M, h->ulev[M][0], U(M - 1), nullptr, nullptr, nullptr);
+        o.lev_out = TAG_U;
+        h->ops.push_back(o);
+    }
+    (void)last_stored;
+}
+
+cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s) {
+    Op o = o0;
+    if (o.rhs_in == TAG_F) o.rhs.in = f;
+    if (o.lev_g == TAG_F) o.lev.g = f;
+    if (o.lev_out == TAG_U) o.lev.u_out = u;
+    if (o.tail_g == TAG_F) o.tail.g_in = f;
+    if (o.tail_out == TAG_U) o.tail.u_out = u;
+    if (o.seg_f == TAG_F) o.seg.f = f;
+    if (o.seg_u == TAG_U) o.seg.u_out = u;
+    switch (o.kind) {
+    case OP_RHS: rhs_hierarchy_kernel<<<o.grid, o.block, o.smem, s>>>(o.rhs); break;
+    case OP_TAIL: tail_kernel<<<o.grid, o.block, o.smem, s>>>(o.tail); break;
+    case OP_DOWN_PI: level_down_kernel<true><<<o.grid, o.block, o.smem, s>>>(o.lev); break;
+    case OP_DOWN: level_down_kernel<false><<<o.grid, o.block, o.smem, s>>>(o.lev); break;
+    case OP_UP: level_up_kernel<<<o.grid, o.block, o.smem, s>>>(o.lev); break;
+    case OP_SR_PRE: sr_pre_kernel<<<o.grid, o.block, o.smem, s>>>(o.seg); break;
+    case OP_SEAM: seam_tau_kernel<<<o.grid, o.block, 0, s>>>(o.seg, o.nseg); break;
+    case OP_SR_POST: sr_post_kernel<<<o.grid, o.block, o.smem, s>>>(o.seg); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_all(srfmg_plan *h, const double *f, double *u, cudaStream_t s) {
+    for (const Op &o : h->ops) {
+        cudaError_t e = launch(o, f, u, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Every kernel may use up to the device's opt-in shared-memory limit; the
+// attribute is per function and shared by all plans, so it is set to the
+// maximum rather than to one plan's need.
+srfmg_status set_smem_limits(srfmg_plan *h) {
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceGetAttribute");
+    size_t need = 0;
+    for (const Op &o : h->ops) need = std::max(need, o.smem);
+    if (need > (size_t)optin) return fail(h, SRFMG_EUNSUPPORTED, "shared memory need exceeds the device limit");
+    const void *fns[] = {(const void *)level_down_kernel<true>, (const void *)level_down_kernel<false>,
+                         (const void *)level_up_kernel, (const void *)sr_pre_kernel,
+                         (const void *)sr_post_kernel, (const void *)tail_kernel,
+                         (const void *)rhs_hierarchy_kernel};
+    for (const void *fn : fns) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+    }
+    return SRFMG_OK;
+}
+
+void release(srfmg_plan *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (void *ptr : h->allocs) cudaFree(ptr);
+    h->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+srfmg_status srfmg_default_params(int32_t log2_n, srfmg_params *p) {
+    if (!p) return fail(nullptr, SRFMG_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->op = SRFMG_OP_LAPLACE;
+    p->precision = SRFMG_FP64;
+    p->log2_n = log2_n;
+    p->log2_n_coarsest = 2;
+    p->n_sr_levels = 1;
+    long long N = (log2_n >= 0 && log2_n < 62) ? (1LL << log2_n) : 0;
+    long long W = N / 4 < 4096 ? N / 4 : 4096;
+    p->segment_width = (int32_t)(W < 16 ? 16 : W);
+    p->buffer_width = 8;
+    p->nu1 = 1;
+    p->nu2 = 1;
+    p->smoother = SRFMG_SMOOTH_LEX;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) {
+    if (!out) return fail(nullptr, SRFMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string msg = check_params(p);
+    if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
+    if (p->precision == SRFMG_MIXED) return fail(nullptr, SRFMG_EUNSUPPORTED, "mixed precision is not built yet");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, SRFMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= ndev) return fail(nullptr, SRFMG_EINVAL, "device index out of range");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, SRFMG_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+
+    srfmg_plan *h = new srfmg_plan();
+    h->p = *p;
+    h->device = device;
+    h->M = p->log2_n;
+    h->M0 = p->log2_n_coarsest;
+    h->nRS = p->n_sr_levels;
+    h->W = p->segment_width;
+    h->b = p->buffer_width;
+    h->n = (size_t)1 << h->M;
+    int top_stored = h->M - h->nRS;
+    h->Mc = top_stored < kMaxTailLevel ? top_stored : kMaxTailLevel;
+    if (h->Mc < h->M0) h->Mc = h->M0;
+    const char *env = std::getenv("SRFMG_NO_GRAPH");
+    h->use_graph = !(env && env[0] == '1');
+
+    srfmg_status st = SRFMG_OK;
+    for (int l = h->Mc; l <= h->M && st == SRFMG_OK; ++l) {
+        if (l == h->M) {
+            if (h->nRS == 0 && h->Mc < h->M) st = alloc_dev(h, &h->ulev[l][0], (size_t)1 << l);
+            break;
+        }
+        st = alloc_dev(h, &h->ulev[l][0], (size_t)1 << l);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->ulev[l][1], (size_t)1 << l);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], (size_t)1 << l);
+    }
+    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, (h->n / h->W) * 6);
+    const int n0 = 1 << h->M0;
+    if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
+    if (st == SRFMG_OK) {
+        std::vector<double> inv = coarsest_inverse(n0);
+        e = cudaMemcpy(h->Ainv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemcpy(coarsest inverse)");
+    }
+    if (st == SRFMG_OK) {
+        build_schedule(h);
+        st = set_smem_limits(h);
+    }
+    if (st == SRFMG_OK) {
+        e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamCreate");
+    }
+    if (st != SRFMG_OK) {
+        g_create_error = h->err;
+        release(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be device pointers");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned");
+    if ((const double *)u < f + h->n && f < (const double *)u + h->n) return fail(h, SRFMG_EINVAL, "f and u overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!h->use_graph) {
+        e = enqueue_all(h, f, u, s);
+        return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "kernel launch");
+    }
+    if (!h->gexec || h->g_f != f || h->g_u != u) {
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+        cudaError_t le = enqueue_all(h, f, u, h->cap_stream);
+        e = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, le, "kernel launch during capture"); }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+        h->g_f = f;
+        h->g_u = u;
+    }
+    e = cudaGraphLaunch(h->gexec, s);
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "cudaGraphLaunch");
+}
+
+srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be host pointers");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!h->f_stage) {
+        srfmg_status st = alloc_dev(h, &h->f_stage, h->n);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->u_stage, h->n);
+        if (st != SRFMG_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(h->f_stage, f, h->n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(f)");
+    srfmg_status st = srfmg_solve(h, h->f_stage, h->u_stage, stream);
+    if (st != SRFMG_OK) return st;
+    e = cudaMemcpyAsync(u, h->u_stage, h->n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(u)");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream) {
+    (void)dL_du; (void)dL_df; (void)stream;
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    return fail(h, SRFMG_EUNSUPPORTED, "the adjoint solve is not built yet");
+}
+
+srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {
+    if (!h || !info) return fail(h, SRFMG_EINVAL, "handle or info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->workspace_bytes = (int64_t)h->ws_bytes;
+    info->kernels_per_solve = (int32_t)h->ops.size();
+    info->coarse_tail_level = h->Mc;
+    info->n_segments = h->nRS ? (int32_t)(h->n / h->W) : 0;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_destroy(srfmg_handle h) {
+    if (!h) return SRFMG_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    release(h);
+    delete h;
+    return SRFMG_OK;
+}
+
+const char *srfmg_last_error(srfmg_handle h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+const char *srfmg_version(void) { return "srfmg 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,629 @@
+// srfmg_kernels.cuh -- sm_103a kernels of the FMG-FAS-SR solve (FP64 path).
+//
+// Notation: level l has n = 2^l cells; the solution u is stored unscaled, the
+// right-hand side is stored scaled, g_l = h_l^2 rhs_l (h_l = 2^-l), so that
+// the operator reads (h^2 L u)_i = F_{i-1/2} - F_{i+1/2} with the fluxes
+// F_{i+1/2} = u_{i+1} - u_i and the odd ghost at the walls (F_{-1/2} = 2u_0,
+// F_{n-1/2} = -2u_{n-1}), Sec. 4.  Scaling by powers of two is exact, so the
+// scaled hierarchy is bit-identical to the unscaled one.
+//
+// FP64 runs at about 1/70 of the FP32 rate on this part, so every exact
+// power-of-two scaling is done on the exponent bits with integer operations
+// (scale2) instead of an FP64 multiply.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace srfmg {
+
+// Terms of the Gauss-Seidel recurrence weighted below 2^-kTrunc are dropped;
+// 2^-72 is far below the FP64 rounding of any value the recurrence produces.
+constexpr int kTrunc = 72;
+
+// Chunk length of the tiled and segment sweeps (one chunk per thread).
+constexpr int kChunk = 16;
+
+// Exact 2^k as a double, -1022 <= k <= 1023.
+__device__ __forceinline__ double exp2i(int k) {
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+// x * 2^k by an exponent add (zero stays zero).  Valid for normal x whose
+// result stays normal; the solver's values are many orders of magnitude away
+// from the subnormal and overflow ranges.
+__device__ __forceinline__ double scale2(double x, int k) {
+    long long b = __double_as_longlong(x);
+    long long inc = (b & 0x7ff0000000000000LL) ? ((long long)k << 52) : 0LL;
+    return __longlong_as_double(b + inc);
+}
+
+// Coarse value with the odd reflection at the walls (u_{-1-j} = -u_j and
+// u_{n+j} = -u_{n-1-j}); src[j - base] holds coarse cell j.
+__device__ __forceinline__ double coarse_reflect(const double *src, int base, int j, int nc) {
+    if (j < 0) return -src[-j - 1 - base];
+    if (j >= nc) return -src[2 * nc - 1 - j - base];
+    return src[j - base];
+}
+
+// Fourth order FMG interpolation Pi (Sec. 4): the left child of J takes
+// (-5, 35, 105, -7)/128 of coarse cells J-2..J+1, the right child the mirror.
+// Written as u_J plus a combination of the coarse fluxes G_{j+1/2} = u_{j+1}-u_j
+// (exact differences of nearby values), so the interpolated value carries a
+// single rounding:  left  = u_J + (5G_{J-3/2} - 30G_{J-1/2} - 7G_{J+1/2})/128,
+//                   right = u_J + (7G_{J-1/2} + 30G_{J+1/2} - 5G_{J+3/2})/128.
+// c[j - cbase] must hold coarse cells J-2..J+2 (ghosts already reflected).
+__device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) {
+    int J = i >> 1;
+    const double *p = c + (J - cbase);
+    double s;
+    if ((i & 1) == 0) {
+        double gm3 = p[-1] - p[-2], gm1 = p[0] - p[-1], gp1 = p[1] - p[0];
+        s = fma(5.0, gm3, fma(-30.0, gm1, -7.0 * gp1));
+    } else {
+        double gm1 = p[0] - p[-1], gp1 = p[1] - p[0], gp3 = p[2] - p[1];
+        s = fma(7.0, gm1, fma(30.0, gp1, -5.0 * gp3));
+    }
+    return p[0] + scale2(s, -7);
+}
+
+// ---------------------------------------------------------------------------
+// Lexicographic Gauss-Seidel sweep (omega = 1) over the cells [lo, hi) of a
+// level of n cells held in shared memory (uo[i - base]: values before the
+// sweep, including the neighbours lo-1 and hi; un[i - base]: values after;
+// g[i - base]: scaled right-hand side).
+//
+// Residual form.  With r_i = g_i - (F_{i-1/2} - F_{i+1/2}) the residual of the
+// old values (flux form, odd ghost at the walls), the sweep adds
+//   delta_i = (r_i + delta_{i-1}) / 2        (ascending; mirror descending)
+// with delta = r/3 at the first wall cell and (r + delta_prev)/3 at the last
+// wall cell (wall diagonal 3), and u_new = u_old + delta: one rounding per
+// cell.  The correction entering the range (delta at lo-1) is zero: exact for
+// a frozen patch neighbour, an approximation in a tile halo that is wider than
+// the recurrence's memory.
+//
+// delta is a first-order linear recurrence with multiplier 1/2.  Cells are
+// grouped in chunks of C consecutive cells aligned to the level (in sweep
+// order), one chunk per thread: each chunk runs the recurrence from a zero
+// carry, the carry into a chunk is then
+//   KS = false: the fixed sum  sum_{j<=J} 2^(-jC) X_{c-1-j}  of the chunk-end
+//               values of the J+1 preceding chunks, J+1 = ceil(kTrunc / C);
+//   KS = true:  a Kogge-Stone scan over all chunks of the range;
+// and every cell adds 2^-(d+1) times its chunk's carry (d: position in the
+// chunk).  Terms weighted below 2^-kTrunc are dropped, so the result is the
+// sequential sweep up to rounding.  With the fixed sum and level-aligned
+// chunks, a cell's value depends only on the data of the (J+2)C cells before
+// it, so two tiles that both hold a cell more than (J+2)C cells from their
+// range start compute bitwise the same value: tiles agree exactly with their
+// neighbours' halos, which keeps the tau correction consistent with the
+// restricted solution at tile edges.
+//
+// All threads of the block must call it.  X and Y hold one double per chunk
+// (KS = false: at least the number of chunks; KS = true: blockDim.x).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double flux_lo(const double *u, int base, int i) {   // F_{i-1/2}
+    return (i == 0) ? scale2(u[0 - base], 1) : u[i - base] - u[i - 1 - base];
+}
+__device__ __forceinline__ double flux_hi(const double *u, int base, int i, int n) {   // F_{i+1/2}
+    return (i == n - 1) ? -scale2(u[i - base], 1) : u[i + 1 - base] - u[i - base];
+}
+
+template <bool KS>
+__device__ void lex_sweep(const double *__restrict__ uo, double *__restrict__ un,
+                          const double *__restrict__ g, int base, int lo, int hi, int n,
+                          bool asc, int C, double *X, double *Y) {
+    const int t = threadIdx.x, T = blockDim.x;
+    // sweep coordinate q: q = i ascending, q = n-1-i descending
+    const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const int start_wall = asc ? 0 : n - 1, end_wall = asc ? n - 1 : 0;
+
+    // phase 1: residuals and the zero-carry chain of every chunk
+    for (int ch = t; ch < nch; ch += T) {
+        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
+        double p = 0.0;
+        for (int q = q0; q < q1; ++q) {
+            const int i = asc ? q : n - 1 - q;
+            double r = g[i - base] - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+            double a = (i == start_wall || i == end_wall) ? r * (1.0 / 3.0) : scale2(r, -1);
+            p = (q == q0 || i == start_wall) ? a : fma(0.5, p, a);
+            un[i - base] = p;
+        }
+        X[ch] = p;
+    }
+    __syncthreads();
+
+    // phase 2: carry into each chunk
+    const int J = (kTrunc + C - 1) / C - 1;
+    double *src = X;
+    if (KS) {
+        double *dst = Y;
+        double y = (t < nch) ? X[t] : 0.0;
+        for (int d = 1; d * C < kTrunc && d < nch; d <<= 1) {
+            double prev = (t >= d && t < nch) ? src[t - d] : 0.0;
+            y = fma(exp2i(-C * d), prev, y);
+            if (t < nch) dst[t] = y;
+            __syncthreads();
+            double *tmp = src; src = dst; dst = tmp;
+        }
+    }
+    // phase 3: fix-up and update
+    for (int ch = t; ch < nch; ch += T) {
+        double cin = 0.0;
+        if (KS) {
+            cin = (ch > 0) ? src[ch - 1] : 0.0;
+        } else {
+            for (int j = J; j >= 0; --j) {
+                double x = (ch - 1 - j >= 0) ? X[ch - 1 - j] : 0.0;
+                cin = fma(exp2i(-C), cin, x);
+            }
+        }
+        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
+        for (int q = q0; q < q1; ++q) {
+            const int i = asc ? q : n - 1 - q;
+            double d = un[i - base];
+            if (q - q0 + 1 < kTrunc) d = fma(exp2i(-(q - q0 + 1)), cin, d);
+            un[i - base] = uo[i - base] + d;
+        }
+    }
+    __syncthreads();
+    const bool has_end = asc ? (hi == n) : (lo == 0);
+    if (has_end && t == 0) {
+        const int i = end_wall, ip = asc ? i - 1 : i + 1;
+        double r = g[i - base] - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+        double dprev = un[ip - base] - uo[ip - base];
+        un[i - base] = uo[i - base] + (r + dprev) * (1.0 / 3.0);
+    }
+    __syncthreads();
+}
+
+// Scaled tau-corrected coarse right-hand side at coarse cell J (Eqs. 4-5,
+// Fig. 3 lines 3-5): g_{l-1,J} = 2(g_{2J} + g_{2J+1}) + (G_{J-1/2} - G_{J+1/2})
+// - 2(F_{2J-1/2} - F_{2J+3/2}), where G are fluxes of uhat = R u on the coarse
+// level and F fluxes of u; the value is h_{l-1}^2 times R rhs + L_{l-1} R u -
+// R L_l u.  um1..up2 are u at fine cells 2J-2 .. 2J+3 (unused at a wall).
+__device__ __forceinline__ double tau_rhs(double g0, double g1, double um2, double um1,
+                                          double u0, double u1, double u2, double u3,
+                                          int J, int nc) {
+    double hJ = scale2(u0 + u1, -1);
+    double Gl = (J == 0) ? scale2(hJ, 1) : hJ - scale2(um2 + um1, -1);
+    double Gr = (J == nc - 1) ? -scale2(hJ, 1) : scale2(u2 + u3, -1) - hJ;
+    double Fl = (J == 0) ? scale2(u0, 1) : u0 - um1;
+    double Fr = (J == nc - 1) ? -scale2(u1, 1) : u2 - u1;
+    double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+    return scale2(g0 + g1, 1) + tau;
+}
+
+// ---------------------------------------------------------------------------
+// K1: right-hand side hierarchy (appendix operator set-up): g on levels
+// lin-1 .. lstop from level lin, g_{l-1,J} = 2 (g_{l,2J} + g_{l,2J+1}).
+// Level lin is read from `in` scaled by 2^in_exp (f with in_exp = -2M).
+// Each block reduces 2^depth consecutive cells of level lin in shared memory.
+// ---------------------------------------------------------------------------
+struct RhsArgs {
+    const double *in;
+    int in_exp;
+    int lin, lstop, depth;
+    double *out[32];           // out[l] for the written levels
+};
+
+__global__ void rhs_hierarchy_kernel(RhsArgs a) {
+    extern __shared__ double sm[];
+    const int chunk = 1 << a.depth;
+    double *cur = sm, *nxt = sm + chunk;
+    const long long base = (long long)blockIdx.x * chunk;
+    for (int i = threadIdx.x; i < chunk; i += blockDim.x)
+        cur[i] = scale2(a.in[base + i], a.in_exp);
+    __syncthreads();
+    int len = chunk;
+    for (int l = a.lin; l > a.lstop && len > 1; --l) {
+        const int half = len >> 1;
+        double *dst = a.out[l - 1] + (base >> (a.lin - l + 1));
+        for (int J = threadIdx.x; J < half; J += blockDim.x) {
+            double x = scale2(cur[2 * J] + cur[2 * J + 1], 1);
+            nxt[J] = x;
+            dst[J] = x;
+        }
+        __syncthreads();
+        double *tmp = cur; cur = nxt; nxt = tmp;
+        len = half;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stored-level passes (global lexicographic smoothing).  A block owns the
+// tile [s, s+T) of level l and loads it with a halo of H cells per side; the
+// halo is wider than the Gauss-Seidel carry horizon, so the tile's values are
+// those of the sequential sweep over the whole level (Sec. 4: "subdomain
+// solver applied to the entire grid").
+// ---------------------------------------------------------------------------
+struct LevelArgs {
+    int l, n, tile, halo, nu;
+    int maxlen, maxc, maxch;   // shared-memory layout sizes (doubles)
+    const double *u_src;       // level l iterate, or level l-1 for the FMG interpolation
+    const double *g;           // g_l, or f when g_exp != 0 (scaled by 2^g_exp on load)
+    int g_exp;
+    const double *uc_src;      // up pass: corrected level l-1
+    double *u_out;             // level l after the pass (tile)
+    double *uc_out;            // down pass: restricted solution on level l-1
+    double *gc_out;            // down pass: tau-corrected g_{l-1}
+};
+
+// Shared-memory layout of one stored-level block.
+struct LevelSmem {
+    double *uo, *un, *g, *c, *X, *Y;
+    int L0, L1, C0, C1;       // fine range [L0,L1), coarse range [C0,C1)
+};
+
+__device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H, int n, int maxlen, int maxc,
+                                                int maxch) {
+    LevelSmem m;
+    m.L0 = max(0, s - H);
+    m.L1 = min(n, s + T + H);
+    m.C0 = (m.L0 >> 1) - 2;
+    m.C1 = ((m.L1 - 1) >> 1) + 3;
+    m.uo = sm;
+    m.un = m.uo + maxlen;
+    m.g = m.un + maxlen;
+    m.c = m.g + maxlen;
+    m.X = m.c + maxc;
+    m.Y = m.X + maxch;
+    return m;
+}
+
+// Smoothing of a loaded range by nu sweeps, ascending first and reversed
+// after every sweep (appendix "symmetrize").  The swept range shrinks by one
+// cell per sweep on each side that is not a wall, so that every sweep reads
+// neighbours the previous one wrote.  Returns the array holding the result.
+__device__ double *smooth_range(LevelSmem &m, int n, int nu) {
+    int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
+    int hi = (m.L1 == n) ? n : m.L1 - 1;
+    double *a = m.uo, *b = m.un;
+    for (int k = 0; k < nu; ++k) {
+        lex_sweep<false>(a, b, m.g, m.L0, lo, hi, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        // cells of [L0, L1) outside the swept range keep their old values
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            if (i < lo || i >= hi) b[i - m.L0] = a[i - m.L0];
+        __syncthreads();
+        double *tmp = a; a = b; b = tmp;
+        if (lo > 0) ++lo;
+        if (hi < n) --hi;
+    }
+    return a;
+}
+
+template <bool FROM_PI>
+__global__ void level_down_kernel(LevelArgs a) {
+    extern __shared__ double sm[];
+    const int s = blockIdx.x * a.tile;
+    const int n = a.n, nc = n >> 1;
+    LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+        m.g[i - m.L0] = a.g_exp ? scale2(a.g[i], a.g_exp) : a.g[i];
+    if (FROM_PI) {
+        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
+            m.c[j - m.C0] = coarse_reflect(a.u_src, 0, j, nc);
+        __syncthreads();
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
+    } else {
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.uo[i - m.L0] = a.u_src[i];
+    }
+    __syncthreads();
+    const double *u = smooth_range(m, n, a.nu);
+    // restriction of the solution and tau-corrected coarse rhs of the tile
+    for (int J = (s >> 1) + threadIdx.x; J < ((s + a.tile) >> 1); J += blockDim.x) {
+        int i0 = 2 * J - m.L0;
+        double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
+        double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
+        a.uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
+        a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+    }
+    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
+}
+
+// Up pass (Eq. 6): u_l += P (u_{l-1} - R u_l), then nu sweeps.
+__global__ void level_up_kernel(LevelArgs a) {
+    extern __shared__ double sm[];
+    const int s = blockIdx.x * a.tile;
+    const int n = a.n, nc = n >> 1;
+    LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
+        m.g[i - m.L0] = a.g_exp ? scale2(a.g[i], a.g_exp) : a.g[i];
+        m.uo[i - m.L0] = a.u_src[i];
+    }
+    // coarse correction c_J = u_{l-1,J} - (R u_l)_J with odd reflection
+    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) {
+        double v = 0.0;
+        if (j >= -1 && j <= nc) {
+            int jj = (j < 0) ? 0 : ((j >= nc) ? nc - 1 : j);
+            double cj = a.uc_src[jj] - scale2(a.u_src[2 * jj] + a.u_src[2 * jj + 1], -1);
+            v = (j == jj) ? cj : -cj;
+        }
+        m.c[j - m.C0] = v;
+    }
+    __syncthreads();
+    // second order prolongation: child = 3/4 parent + 1/4 neighbour on its side
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
+        int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+        double corr = scale2(fma(3.0, m.c[J - m.C0], m.c[nb - m.C0]), -2);
+        m.uo[i - m.L0] += corr;
+    }
+    __syncthreads();
+    const double *u = smooth_range(m, n, a.nu);
+    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
+}
+
+// ---------------------------------------------------------------------------
+// SR level (Fig. 3): one block per segment [s, s+W) with extended patch
+// E = [s-b, s+W+b) clipped to the domain and one frozen cell on each side.
+// The fine level exists only in shared memory.
+// ---------------------------------------------------------------------------
+struct SegArgs {
+    int M, n, W, b, nu;
+    int maxlen, maxc, maxch;   // shared-memory layout sizes (doubles)
+    const double *f;           // right-hand side, unscaled
+    const double *uc_src;      // level M-1
+    double *uc_out;            // pre-leg: restricted solution on level M-1
+    double *gc_out;            // pre-leg: tau-corrected g_{M-1}
+    double *seam;              // pre-leg: 6 fine values per segment
+    double *u_out;             // post-leg: the solution
+};
+
+struct SegSmem {
+    double *uo, *un, *g, *c, *X, *Y;
+    int e0, e1, lo, hi, C0, C1;
+};
+
+__device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s) {
+    SegSmem m;
+    m.e0 = max(0, s - a.b);
+    m.e1 = min(a.n, s + a.W + a.b);
+    m.lo = (m.e0 > 0) ? m.e0 - 1 : 0;
+    m.hi = (m.e1 < a.n) ? m.e1 + 1 : a.n;
+    m.C0 = (m.lo >> 1) - 2;
+    m.C1 = ((m.hi - 1) >> 1) + 3;
+    m.uo = sm;
+    m.un = m.uo + a.maxlen;
+    m.g = m.un + a.maxlen;
+    m.c = m.g + a.maxlen;
+    m.X = m.c + a.maxc;
+    m.Y = m.X + a.maxch;
+    return m;
+}
+
+// Load Pi u_{M-1} on [lo, hi) into both sweep buffers (the frozen cells must
+// be present in both) and the scaled rhs.
+__device__ void seg_load(SegSmem &m, const SegArgs &a) {
+    const int nc = a.n >> 1;
+    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
+        m.c[j - m.C0] = coarse_reflect(a.uc_src, 0, j, nc);
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
+        m.g[i - m.lo] = scale2(a.f[i], -2 * a.M);
+    __syncthreads();
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
+        double v = fmg_interp(m.c, m.C0, i);
+        m.uo[i - m.lo] = v;
+        m.un[i - m.lo] = v;
+    }
+    __syncthreads();
+}
+
+// K5: pre-smoothing leg of the SR level (Fig. 3 lines 1-5): Pi, nu1 sweeps on
+// the extended patch, restricted solution on the segment's coarse cells, tau
+// rhs on the coarse cells whose stencil lies in the segment, seam values for
+// the two edge cells (formed from the assembled level by seam_tau_kernel).
+__global__ void sr_pre_kernel(SegArgs a) {
+    extern __shared__ double sm[];
+    const int s = blockIdx.x * a.W;
+    const int n = a.n, nc = n >> 1;
+    SegSmem m = seg_smem(sm, a, s);
+    seg_load(m, a);
+    double *p = m.uo, *q = m.un;
+    for (int k = 0; k < a.nu; ++k) {
+        lex_sweep<false>(p, q, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        double *tmp = p; p = q; q = tmp;
+    }
+    const double *u = p;
+    const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
+        int i0 = 2 * J - m.lo;
+        a.uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
+        bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
+        if (!edge) {
+            double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
+            double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
+            a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        }
+    }
+    if (threadIdx.x < 6) {
+        int k = threadIdx.x;
+        int i = (k < 3) ? s + k : s + a.W - 6 + k;
+        a.seam[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
+    }
+}
+
+// tau rhs of the two coarse cells at each interior segment boundary, from the
+// assembled fine values (seams) and the restricted solution (appendix down
+// leg).  Thread k handles the boundary s = (k+1) W.
+__global__ void seam_tau_kernel(SegArgs a, int nseg) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nseg - 1) return;
+    const int s = (k + 1) * a.W;
+    const double *L = a.seam + (size_t)k * 6, *R = a.seam + (size_t)(k + 1) * 6;
+    // fine cells s-3 .. s+2 of the assembled level
+    double f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
+    const int J = (s >> 1) - 1;         // last coarse cell of the left segment
+    // coarse fluxes G from the restricted solution, fine fluxes F from the seams
+    const double hm1 = a.uc_out[J - 1], h0 = a.uc_out[J], h1 = a.uc_out[J + 1], h2 = a.uc_out[J + 2];
+    {
+        double Gl = h0 - hm1, Gr = h1 - h0;
+        double Fl = f2 - f3, Fr = p0 - f1;
+        double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+        a.gc_out[J] = scale2(a.f[2 * J] + a.f[2 * J + 1], 1 - 2 * a.M) + tau;
+    }
+    {
+        int J2 = J + 1;
+        double Gl = h1 - h0, Gr = h2 - h1;
+        double Fl = p0 - f1, Fr = p2 - p1;
+        double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+        a.gc_out[J2] = scale2(a.f[2 * J2] + a.f[2 * J2 + 1], 1 - 2 * a.M) + tau;
+    }
+}
+
+// K6: post-smoothing leg of the SR level (Fig. 3, Eq. 7, Fig. 4): full update
+// Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
+// Gauss-Seidel sweep), and the segment interior is written out.
+__global__ void sr_post_kernel(SegArgs a) {
+    extern __shared__ double sm[];
+    const int s = blockIdx.x * a.W;
+    const int n = a.n;
+    SegSmem m = seg_smem(sm, a, s);
+    seg_load(m, a);
+    double *p = m.uo, *q = m.un;
+    for (int k = 0; k < a.nu; ++k) {
+        // Kaczmarz (Fig. 4): r = u^H_J - (R u)_J added to both children
+        for (int J = (m.e0 >> 1) + threadIdx.x; J < (m.e1 >> 1); J += blockDim.x) {
+            int i0 = 2 * J - m.lo;
+            double r = m.c[J - m.C0] - scale2(p[i0] + p[i0 + 1], -1);
+            p[i0] += r;
+            p[i0 + 1] += r;
+        }
+        __syncthreads();
+        lex_sweep<false>(p, q, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        double *tmp = p; p = q; q = tmp;
+    }
+    for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) a.u_out[i] = p[i - m.lo];
+}
+
+// ---------------------------------------------------------------------------
+// Coarse tail: levels M0..Mc in the shared memory of one block.  Level l
+// occupies [2^l - 2^M0, 2^(l+1) - 2^M0) of the u and g arrays.
+// mode 0: FMG (Fig. 2) from scratch up to level Mc from g_Mc;
+// mode 1: one V-cycle (Fig. 1) on levels Mc..M0 from u_Mc, g_Mc.
+// ---------------------------------------------------------------------------
+struct TailArgs {
+    int M0, Mc, nu1, nu2, mode;
+    const double *u_in;        // mode 1: level Mc iterate
+    const double *g_in;        // level Mc rhs, scaled by 2^g_exp on load
+    int g_exp;
+    double *u_out;             // level Mc result
+    const double *Ainv;        // inverse of the scaled coarsest operator, row-major
+};
+
+struct TailSmem {
+    double *u, *g, *S, *X, *Y;
+    int M0;
+    __device__ int off(int l) const { return (1 << l) - (1 << M0); }
+};
+
+__device__ void tail_smooth(TailSmem &m, int l, int nu) {
+    const int n = 1 << l;
+    double *u = m.u + m.off(l), *g = m.g + m.off(l);
+    for (int k = 0; k < nu; ++k) {
+        lex_sweep<true>(u, m.S, g, 0, 0, n, n, (k & 1) == 0, (n + (int)blockDim.x - 1) / (int)blockDim.x,
+                        m.X, m.Y);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = m.S[i];
+        __syncthreads();
+    }
+}
+
+// smooth level l, then restriction and tau rhs into level l-1
+__device__ void tail_down(TailSmem &m, int l, int nu) {
+    tail_smooth(m, l, nu);
+    const int nc = 1 << (l - 1);
+    const double *u = m.u + m.off(l), *g = m.g + m.off(l);
+    double *uc = m.u + m.off(l - 1), *gc = m.g + m.off(l - 1);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x) {
+        int i0 = 2 * J;
+        double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
+        double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
+        uc[J] = scale2(u[i0] + u[i0 + 1], -1);
+        gc[J] = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+    }
+    __syncthreads();
+}
+
+__device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
+    const int n0 = 1 << m.M0;
+    double *u = m.u + m.off(m.M0);
+    const double *g = m.g + m.off(m.M0);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < n0; ++j) s = fma(Ainv[i * n0 + j], g[j], s);
+        m.S[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) u[i] = m.S[i];
+    __syncthreads();
+}
+
+// u_l += P (u_{l-1} - R u_l), then smoothing
+__device__ void tail_up(TailSmem &m, int l, int nu) {
+    const int n = 1 << l, nc = n >> 1;
+    double *u = m.u + m.off(l);
+    const double *uc = m.u + m.off(l - 1);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x)
+        m.S[J] = uc[J] - scale2(u[2 * J] + u[2 * J + 1], -1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+        double cn = (nb < 0) ? -m.S[0] : ((nb >= nc) ? -m.S[nc - 1] : m.S[nb]);
+        u[i] += scale2(fma(3.0, m.S[J], cn), -2);
+    }
+    __syncthreads();
+    tail_smooth(m, l, nu);
+}
+
+__device__ void tail_interp(TailSmem &m, int l) {
+    const int n = 1 << l, nc = n >> 1;
+    const double *uc = m.u + m.off(l - 1);
+    double *u = m.u + m.off(l);
+    // stage the coarse level with two reflected ghosts per side
+    for (int j = (int)threadIdx.x - 2; j < nc + 2; j += (int)blockDim.x)
+        if (j >= -2) m.S[j + 2] = coarse_reflect(uc, 0, j, nc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = fmg_interp(m.S, -2, i);
+    __syncthreads();
+}
+
+__global__ void tail_kernel(TailArgs a) {
+    extern __shared__ double sm[];
+    TailSmem m;
+    m.M0 = a.M0;
+    const int tot = (1 << (a.Mc + 1)) - (1 << a.M0);
+    m.u = sm;
+    m.g = m.u + tot;
+    m.S = m.g + tot;
+    m.X = m.S + (1 << a.Mc) + 8;
+    m.Y = m.X + blockDim.x;
+    const int nMc = 1 << a.Mc;
+    for (int i = threadIdx.x; i < nMc; i += blockDim.x) {
+        m.g[m.off(a.Mc) + i] = a.g_exp ? scale2(a.g_in[i], a.g_exp) : a.g_in[i];
+        if (a.mode == 1) m.u[m.off(a.Mc) + i] = a.u_in[i];
+    }
+    __syncthreads();
+    if (a.mode == 0) {
+        for (int l = a.Mc; l > a.M0; --l) {
+            const double *g = m.g + m.off(l);
+            double *gc = m.g + m.off(l - 1);
+            for (int J = threadIdx.x; J < (1 << (l - 1)); J += blockDim.x)
+                gc[J] = scale2(g[2 * J] + g[2 * J + 1], 1);
+            __syncthreads();
+        }
+        tail_coarsest(m, a.Ainv);
+        for (int k = a.M0; k < a.Mc; ++k) {
+            tail_interp(m, k + 1);
+            for (int l = k + 1; l > a.M0; --l) tail_down(m, l, a.nu1);
+            tail_coarsest(m, a.Ainv);
+            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up(m, l, a.nu2);
+        }
+    } else {
+        for (int l = a.Mc; l > a.M0; --l) tail_down(m, l, a.nu1);
+        tail_coarsest(m, a.Ainv);
+        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up(m, l, a.nu2);
+    }
+    for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out[i] = m.u[m.off(a.Mc) + i];
+}
+
+}  // namespace srfmg

@@ -1,0 +1,161 @@
+"""Python binding of the C ABI in include/srfmg.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA kernels of libsrfmg.so; PyTorch is
+used only to hold device memory and to supply the current CUDA stream.  There
+is no CPU fallback: if the library is missing or no GPU is visible the calls
+raise.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_ECUDA",
+                4: "SRFMG_ETIMEOUT", 5: "SRFMG_ENONFINITE", 6: "SRFMG_EUNSUPPORTED"}
+FP64, MIXED = 0, 1
+
+EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
+           "srfmg_adjoint", "srfmg_query", "srfmg_destroy", "srfmg_last_error", "srfmg_version")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int32) for name in (
+        "op", "precision", "log2_n", "log2_n_coarsest", "n_sr_levels", "segment_width",
+        "buffer_width", "nu1", "nu2", "smoother")] + [("reserved", ctypes.c_int32 * 6)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_int64), ("kernels_per_solve", ctypes.c_int32),
+                ("coarse_tail_level", ctypes.c_int32), ("n_segments", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class SrfmgError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libsrfmg.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA extension not built: {path} is missing")
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    H = ctypes.c_void_p
+    lib.srfmg_default_params.argtypes = [ctypes.c_int32, ctypes.POINTER(Params)]
+    lib.srfmg_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(H)]
+    lib.srfmg_solve.argtypes = [H, vp, vp, vp]
+    lib.srfmg_solve_host.argtypes = [H, dp, dp, vp]
+    lib.srfmg_adjoint.argtypes = [H, vp, vp, vp]
+    lib.srfmg_query.argtypes = [H, ctypes.POINTER(Info)]
+    lib.srfmg_destroy.argtypes = [H]
+    lib.srfmg_last_error.argtypes = [H]
+    lib.srfmg_last_error.restype = ctypes.c_char_p
+    lib.srfmg_version.argtypes = []
+    lib.srfmg_version.restype = ctypes.c_char_p
+    for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
+                 "srfmg_adjoint", "srfmg_query", "srfmg_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def default_params(log2_n, **overrides):
+    p = Params()
+    st = load().srfmg_default_params(log2_n, ctypes.byref(p))
+    if st != OK:
+        raise SrfmgError(st, "default_params")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, int(v))
+    return p
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Solver:
+    """One plan: ``Solver(log2_n, segment_width=..., buffer_width=..., ...)``.
+
+    ``solve(f)`` takes a CUDA float64 tensor of 2^log2_n right-hand-side values
+    at the cell centres and returns the solution tensor (same device).
+    """
+
+    def __init__(self, log2_n, device=0, params=None, **overrides):
+        self.lib = load()
+        self.params = params if params is not None else default_params(log2_n, **overrides)
+        self.n = 1 << self.params.log2_n
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.srfmg_create(ctypes.byref(self.params), device, ctypes.byref(h))
+        if st != OK:
+            raise SrfmgError(st, self.lib.srfmg_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            raise SrfmgError(st, f"{what}: {self.lib.srfmg_last_error(self.h).decode()}")
+
+    def info(self):
+        inf = Info()
+        self._check(self.lib.srfmg_query(self.h, ctypes.byref(inf)), "query")
+        return inf
+
+    def solve(self, f, u=None, stream=None):
+        import torch
+        if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.numel() == self.n):
+            raise ValueError("f must be a contiguous CUDA float64 tensor of 2^log2_n values")
+        if u is None:
+            u = torch.empty_like(f)
+        self._check(self.lib.srfmg_solve(self.h, ctypes.c_void_p(f.data_ptr()),
+                                          ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)),
+                    "solve")
+        return u
+
+    def solve_host(self, f, u=None, stream=None):
+        """Solve from and to host numpy arrays (copies inside; synchronises)."""
+        import numpy as np
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.size != self.n:
+            raise ValueError("f must hold 2^log2_n values")
+        if u is None:
+            u = np.empty_like(f)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.srfmg_solve_host(self.h, f.ctypes.data_as(dp), u.ctypes.data_as(dp),
+                                               _stream_ptr(stream)), "solve_host")
+        return u
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.srfmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version():
+    return load().srfmg_version().decode()

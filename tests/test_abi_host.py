@@ -1,0 +1,85 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+function include/srfmg.h declares, and rejects bad arguments on the host
+before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1207_6720_gb300 import srfmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "srfmg.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:srfmg_status|const char \*)\s*(srfmg_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("srfmg_create", "srfmg_solve", "srfmg_adjoint", "srfmg_destroy"):
+        assert want in names
+    assert set(names) == set(srfmg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = srfmg.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert srfmg.version().startswith("srfmg")
+
+
+def test_default_params():
+    p = srfmg.default_params(24)
+    assert (p.log2_n, p.log2_n_coarsest, p.n_sr_levels) == (24, 2, 1)
+    assert (p.segment_width, p.buffer_width, p.nu1, p.nu2) == (4096, 8, 1, 1)
+    assert srfmg.default_params(10).segment_width == 256
+    assert srfmg.load().srfmg_default_params(10, None) == srfmg.EINVAL
+
+
+@pytest.mark.parametrize("field,value", [
+    ("log2_n", 2), ("log2_n", 29), ("log2_n_coarsest", 1), ("log2_n_coarsest", 7),
+    ("n_sr_levels", 2), ("n_sr_levels", -1), ("segment_width", 24), ("segment_width", 8),
+    ("segment_width", 8192), ("buffer_width", 3), ("buffer_width", 0), ("buffer_width", 66),
+    ("nu1", 0), ("nu2", 5), ("op", 1), ("smoother", 1), ("precision", 7),
+])
+def test_create_rejects_bad_params_before_cuda(field, value):
+    lib = srfmg.load()
+    p = srfmg.default_params(12)
+    setattr(p, field, value)
+    h = ctypes.c_void_p(1)
+    st = lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h))
+    assert st == srfmg.EINVAL
+    assert h.value is None
+    assert lib.srfmg_last_error(None)
+
+
+def test_create_rejects_reserved_and_null():
+    lib = srfmg.load()
+    p = srfmg.default_params(12)
+    p.reserved[0] = 1
+    h = ctypes.c_void_p()
+    assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL
+    assert lib.srfmg_create(None, 0, ctypes.byref(h)) == srfmg.EINVAL
+    p = srfmg.default_params(12)
+    assert lib.srfmg_create(ctypes.byref(p), 0, None) == srfmg.EINVAL
+
+
+def test_null_handle_calls():
+    lib = srfmg.load()
+    assert lib.srfmg_solve(None, None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_solve_host(None, None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_adjoint(None, None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_query(None, None) == srfmg.EINVAL
+    assert lib.srfmg_destroy(None) == srfmg.OK
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    with pytest.raises(srfmg.SrfmgError) as ei:
+        srfmg.Solver(12)
+    assert ei.value.status == srfmg.ECUDA
