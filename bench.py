@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark: fine-grid unknowns/s of one FMG-FAS-SR solve on GB300.
+
+Workload (default): -u'' = f on (0,1), u(0) = u(1) = 0, N = 2^24 cells,
+4096 SR segments of 4096 cells with 8 buffer cells, one FMG cycle of
+V(1,1) FAS cycles, lexicographic Gauss-Seidel, FP64; f from the exact
+solution u = sum_{k=1..32} c_k sin(k pi x), c_k ~ N(0,1)/k^2 (seed 1).
+
+One step = one srfmg_solve (the whole hot path: rhs hierarchy, FMG steps,
+fused SR pre- and post-leg).  Inputs are resident in HBM; the timed region is
+bracketed by a barrier and a device synchronisation and timed with CUDA events
+on the launching stream; f, u and the workspace (about 640 MiB) exceed the
+129 MB L2, so no flush is needed between steps.  The JSON line also carries:
+e2e (srfmg_solve_host from pinned host buffers, copies inside the timed
+region), the plain FP64 stored-grid FMG-FAS on the same GPU, the roofline of
+the dominant kernel, the oracle on the host cores, clocks sampled during the
+timed region, and the accuracy of the result against the exact solution.
+
+--impl reference times the CPU oracle (the method's plain serial C
+restatement) on the host cores, one bounded sample of the workload per step.
+
+Multi-GPU: the solve does not shard across GPUs here; with --gpus N every rank
+solves its own copy (replicas, weak scaling) and the value is the sum over
+ranks with the time taken as the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine-grid unknowns/s per FMG-FAS-SR solve at discretization accuracy vs plain FP64"
+UNIT = "unknowns/s"
+NOMINAL_FP64_TFLOPS = 1.26        # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic FP64 flops per cell of each launch kind (residual-form method
+# arithmetic, sequential sweep; exact power-of-two scalings not counted) and
+# algorithmic DRAM bytes per cell of the level the launch sweeps.
+FLOPS_PER_CELL = {"sr_post": 13.5, "sr_pre": 15.5, "level_down_fmg": 15.5,
+                  "level_down": 9.0, "level_up": 9.0}
+BYTES_PER_CELL = {"sr_post": 20.0, "sr_pre": 20.0, "level_down_fmg": 20.0,
+                  "level_down": 24.0, "level_up": 28.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["srfmg", "reference"], default="srfmg")
+    ap.add_argument("--log2n", type=int, default=24)
+    ap.add_argument("--segment-width", type=int, default=4096)
+    ap.add_argument("--buffer-width", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
+                         "the minimal run used for ncu captures")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {
+        "workload": f"1D -u''=f, N=2^{a.log2n}, FMG-FAS V(1,1) lexicographic GS, 1 SR level of "
+                    f"{(1 << a.log2n) // a.segment_width} segments x {a.segment_width} cells, "
+                    f"buffer {a.buffer_width}, FP64",
+        "N": 1 << a.log2n, "segment_width": a.segment_width, "buffer_width": a.buffer_width,
+        "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2, "modes": 32, "seed": 1,
+        "l2": "inputs larger than L2 (f and u 128 MiB each plus the stored coarse levels)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, want_gpus, use_cuda):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if use_cuda else "gloo"
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64,
+                         device="cuda" if self.pg.get_backend() == "nccl" else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="srfmg_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_1207_6720_gb300/csrc/srfmg_kernels.cuh", "paper_1207_6720_gb300/csrc/srfmg.cu"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_kind):
+    """DRAM bytes per launch of `kernel_kind` from the committed ncu summary,
+    or None if there is none or the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_kind}_ncu.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not (m_src and m_b) or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(f, M, W, b, u_exact):
+    """The CPU oracle (serial C, FP64) on the full workload, repeated for
+    about 10 s; also returns the oracle's error against the exact solution."""
+    import oracle
+    p = oracle.sr_params(M, W, b, nRS=1)
+    t0 = time.perf_counter()
+    ref = oracle.fmg_v(p, f)
+    reps, elapsed = 1, time.perf_counter() - t0
+    while elapsed < 10.0 and reps < 20:
+        oracle.fmg_v(p, f)
+        reps += 1
+        elapsed = time.perf_counter() - t0
+    value = reps * (1 << M) / elapsed
+    return ref, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": f"{reps} serial solves of the full N=2^{M} workload "
+                           f"(C oracle, serial SR with the finest level never stored)"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(a):
+    dist = Dist(a.gpus, use_cuda=False)
+    if dist.rank != 0:
+        dist.close()
+        return
+    import oracle
+    from paper_1207_6720_gb300 import workloads
+    Ms = min(a.log2n, 20)            # bounded sample per step: one solve at N = 2^20
+    Ws = min(a.segment_width, (1 << Ms) // 4)
+    f, _, _ = workloads.sine_series(Ms, 32, seed=1)
+    p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
+    for _ in range(a.warmup):
+        oracle.fmg_v(p, f)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.fmg_v(p, f)
+    dt = time.perf_counter() - t0
+    value = a.steps * (1 << Ms) / dt
+    sample = f"one serial oracle solve of the same workload family at N=2^{Ms} per step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    dist.close()
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def time_solves(solver, fd, ud, steps, warmup, dist, stream):
+    import torch
+    for _ in range(warmup):
+        solver.solve(fd, ud, stream=stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        solver.solve(fd, ud, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    dist.barrier()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_gpu(a):
+    import torch
+    from paper_1207_6720_gb300 import srfmg, workloads
+
+    dist = Dist(a.gpus, use_cuda=True)
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    M, W, b = a.log2n, a.segment_width, a.buffer_width
+    N = 1 << M
+    f, u_exact, _ = workloads.sine_series(M, 32, seed=1)
+    fd = torch.from_numpy(f).to(dev)
+    ud = torch.empty_like(fd)
+
+    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b)
+    info = solver.info()
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ms = time_solves(solver, fd, ud, a.steps, a.warmup, dist, stream)
+    clocks = sampler.stop()
+    ms = dist.max(ms)
+    value = dist.world * N / (ms * 1e-3)
+    u = ud.cpu().numpy()
+    if a.only_solve:
+        if dist.rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
+                              "steps": a.steps, "warmup": a.warmup, "config": workload_config(a),
+                              "gpu_launches": info.kernels_per_solve * a.steps}), flush=True)
+        solver.close()
+        dist.close()
+        return
+
+    # plain FP64 stored-grid FMG-FAS (every level stored, no SR) on the same GPU
+    plain = srfmg.Solver(M, device=dev, n_sr_levels=0)
+    ms_plain = dist.max(time_solves(plain, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
+    u_plain = ud.cpu().numpy()
+    plain_info = plain.info()
+    plain.close()
+
+    # end to end through the public API from pinned host buffers
+    fh = torch.from_numpy(f).pin_memory()
+    uh = torch.empty(N, dtype=torch.float64).pin_memory()
+    fh_np, uh_np = fh.numpy(), uh.numpy()
+    for _ in range(2):
+        solver.solve_host(fh_np, uh_np, stream=stream)
+    dist.barrier()
+    e2e_steps = max(5, a.steps // 10)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.solve_host(fh_np, uh_np, stream=stream)
+    dt_e2e = dist.max((time.perf_counter() - t0) / e2e_steps)
+    e2e = {"value": dist.world * N / dt_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(uh_np.nbytes)}
+
+    # per-launch durations (CUDA events around every kernel on this stream)
+    prof = solver.profile(fd, torch.empty_like(fd), nsolves=5, stream=stream)
+    torch.cuda.synchronize()
+    top_name, top_ms = max(prof, key=lambda x: x[1])
+    kind, lvl = top_name.split(" L")
+    cells = 1 << int(lvl)
+    peaks = measured_peaks()
+    flops = FLOPS_PER_CELL.get(kind, 0.0) * cells
+    achieved_tf = flops / (top_ms * 1e-3) / 1e12
+    bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * cells
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = recorded_traffic(kind)
+    by_kind = {}
+    for name, t in prof:
+        k = name.split(" L")[0]
+        by_kind[k] = by_kind.get(k, 0.0) + t
+    tot = sum(by_kind.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+        "e2e": e2e,
+        "gpu_launches": info.kernels_per_solve * a.steps,
+        "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                       "kernels_per_solve": plain_info.kernels_per_solve,
+                       "speedup_sr_over_plain": ms_plain / ms},
+        "roofline": {"bound": "alu", "kernel": top_name, "achieved": achieved_tf,
+                     "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / NOMINAL_FP64_TFLOPS,
+                     "peak_source": "nominal FP64 from unit counts and max clock (no FP64 figure in "
+                                    "MEASURED_PEAKS.json)",
+                     "traffic": traffic,
+                     "hbm_view": {"achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak,
+                                  "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+                     "launch_ms": top_ms},
+        "kernel_share": {k: round(v / tot, 4) for k, v in sorted(by_kind.items(), key=lambda x: -x[1])},
+        "clocks": clocks,
+    }
+    err_gpu = float(np.max(np.abs(u - u_exact)))
+    acc = {"err_max_vs_exact": err_gpu,
+           "rel_err_max_vs_exact": err_gpu / float(np.max(np.abs(u_exact))),
+           "plain_fp64_err_max_vs_exact": float(np.max(np.abs(u_plain - u_exact)))}
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline:
+        ref, cpu = cpu_baseline(f, M, W, b, u_exact)
+        err_ref = float(np.max(np.abs(ref - u_exact)))
+        acc.update({"oracle_err_max_vs_exact": err_ref,
+                    "rel_maxnorm_vs_oracle": float(np.max(np.abs(u - ref)) / np.max(np.abs(ref))),
+                    "at_discretization_accuracy": bool(err_gpu <= 1.5 * err_ref)})
+        line["cpu_baseline"] = cpu
+    line["accuracy"] = acc
+    solver.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

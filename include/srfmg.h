@@ -116,6 +116,18 @@ srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, v
 /* Plan information (workspace size, launches per solve, ...). */
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info);
 
+/* Per-kernel timing: runs `nsolves` solves with individual launches (no
+ * graph) and a CUDA event pair around every kernel on `stream`, synchronises,
+ * and writes the average duration in milliseconds of each launch of one solve
+ * to ms_per_launch[0 .. kernels_per_solve-1] (kernels_per_solve from
+ * srfmg_query; `capacity` is the array length).  f and u as in srfmg_solve. */
+srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *stream,
+                           int32_t nsolves, float *ms_per_launch, int32_t capacity);
+
+/* Name of launch i of one solve, e.g. "sr_post L24" or "level_down L23";
+ * NULL if i is out of range. */
+const char *srfmg_launch_name(srfmg_handle h, int32_t i);
+
 /* Release the device workspace and graphs.  Synchronises the device first.
  * Accepts NULL (returns SRFMG_OK). */
 srfmg_status srfmg_destroy(srfmg_handle h);

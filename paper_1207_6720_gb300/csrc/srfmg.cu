@@ -33,6 +33,7 @@ enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };
 
 struct Op {
     OpKind kind;
+    int level;
     dim3 grid, block;
     size_t smem;
     RhsArgs rhs;
@@ -59,6 +60,7 @@ struct srfmg_plan {
     double *f_stage = nullptr, *u_stage = nullptr;
     size_t ws_bytes = 0;
     std::vector<Op> ops;
+    std::vector<std::string> names;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const double *g_f = nullptr;
@@ -170,6 +172,7 @@ Op make_op(OpKind k) {
 Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double *uc_src,
             double *u_out, double *uc_out, double *gc_out) {
     Op o = make_op(kind);
+    o.level = l;
     const int n = 1 << l;
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
     const int T = n < kTileMax ? n : kTileMax;
@@ -203,6 +206,7 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
 
 Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, double *gc_out) {
     Op o = make_op(kind);
+    o.level = h->M;
     o.seg.M = h->M;
     o.seg.n = 1 << h->M;
     o.seg.W = h->W;
@@ -232,6 +236,7 @@ Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, doub
 Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int g_exp,
            double *u_out, bool g_from_f, bool out_is_u) {
     Op o = make_op(OP_TAIL);
+    o.level = h->Mc;
     o.tail.M0 = h->M0;
     o.tail.Mc = h->Mc;
     o.tail.nu1 = h->p.nu1;
@@ -264,6 +269,7 @@ void build_schedule(srfmg_plan *h) {
         while (lin > Mc) {
             int depth = lin - Mc < kRhsDepth ? lin - Mc : kRhsDepth;
             Op o = make_op(OP_RHS);
+            o.level = lin;
             o.rhs.lin = lin;
             o.rhs.lstop = lin - depth;
             o.rhs.depth = depth;
@@ -351,6 +357,20 @@ cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s) {
     case OP_SR_POST: sr_post_kernel<<<o.grid, o.block, o.smem, s>>>(o.seg); break;
     }
     return cudaGetLastError();
+}
+
+const char *kind_name(OpKind k) {
+    switch (k) {
+    case OP_RHS: return "rhs_hierarchy";
+    case OP_TAIL: return "coarse_tail";
+    case OP_DOWN_PI: return "level_down_fmg";
+    case OP_DOWN: return "level_down";
+    case OP_UP: return "level_up";
+    case OP_SR_PRE: return "sr_pre";
+    case OP_SEAM: return "seam_tau";
+    case OP_SR_POST: return "sr_post";
+    }
+    return "?";
 }
 
 cudaError_t enqueue_all(srfmg_plan *h, const double *f, double *u, cudaStream_t s) {
@@ -462,6 +482,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     }
     if (st == SRFMG_OK) {
         build_schedule(h);
+        for (const Op &o : h->ops)
+            h->names.push_back(std::string(kind_name(o.kind)) + " L" + std::to_string(o.level));
         st = set_smem_limits(h);
     }
     if (st == SRFMG_OK) {
@@ -545,6 +567,47 @@ srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {
     info->coarse_tail_level = h->Mc;
     info->n_segments = h->nRS ? (int32_t)(h->n / h->W) : 0;
     return SRFMG_OK;
+}
+
+srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *stream,
+                           int32_t nsolves, float *ms_per_launch, int32_t capacity) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    const int nops = (int)h->ops.size();
+    if (!f || !u || !ms_per_launch || capacity < nops || nsolves < 1)
+        return fail(h, SRFMG_EINVAL, "bad arguments to srfmg_profile");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<cudaEvent_t> ev((size_t)nops * nsolves * 2, nullptr);
+    for (auto &x : ev) {
+        e = cudaEventCreate(&x);
+        if (e != cudaSuccess) break;
+    }
+    for (int k = 0; k < nsolves && e == cudaSuccess; ++k)
+        for (int i = 0; i < nops && e == cudaSuccess; ++i) {
+            size_t idx = ((size_t)k * nops + i) * 2;
+            e = cudaEventRecord(ev[idx], s);
+            if (e == cudaSuccess) e = launch(h->ops[i], f, u, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[idx + 1], s);
+        }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int i = 0; i < nops && e == cudaSuccess; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < nsolves; ++k) {
+            size_t idx = ((size_t)k * nops + i) * 2;
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[idx], ev[idx + 1]);
+            acc += ms;
+        }
+        ms_per_launch[i] = (float)(acc / nsolves);
+    }
+    for (auto &x : ev) if (x) cudaEventDestroy(x);
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "srfmg_profile");
+}
+
+const char *srfmg_launch_name(srfmg_handle h, int32_t i) {
+    if (!h || i < 0 || i >= (int32_t)h->names.size()) return nullptr;
+    return h->names[i].c_str();
 }
 
 srfmg_status srfmg_destroy(srfmg_handle h) {

@@ -16,7 +16,8 @@ STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_E
 FP64, MIXED = 0, 1
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
-           "srfmg_adjoint", "srfmg_query", "srfmg_destroy", "srfmg_last_error", "srfmg_version")
+           "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
+           "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
 class Params(ctypes.Structure):
@@ -66,10 +67,14 @@ def load(build_if_missing=True):
     lib.srfmg_destroy.argtypes = [H]
     lib.srfmg_last_error.argtypes = [H]
     lib.srfmg_last_error.restype = ctypes.c_char_p
+    lib.srfmg_profile.argtypes = [H, vp, vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                  ctypes.c_int32]
+    lib.srfmg_launch_name.argtypes = [H, ctypes.c_int32]
+    lib.srfmg_launch_name.restype = ctypes.c_char_p
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
-                 "srfmg_adjoint", "srfmg_query", "srfmg_destroy"):
+                 "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -144,6 +149,18 @@ class Solver:
         self._check(self.lib.srfmg_solve_host(self.h, f.ctypes.data_as(dp), u.ctypes.data_as(dp),
                                                _stream_ptr(stream)), "solve_host")
         return u
+
+    def profile(self, f, u=None, nsolves=3, stream=None):
+        """Per-launch average durations (ms) of one solve: list of (name, ms)."""
+        import torch
+        if u is None:
+            u = torch.empty_like(f)
+        nops = self.info().kernels_per_solve
+        buf = (ctypes.c_float * nops)()
+        self._check(self.lib.srfmg_profile(self.h, ctypes.c_void_p(f.data_ptr()),
+                                            ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream),
+                                            nsolves, buf, nops), "profile")
+        return [(self.lib.srfmg_launch_name(self.h, i).decode(), float(buf[i])) for i in range(nops)]
 
     def close(self):
         if getattr(self, "h", None):
