@@ -8,12 +8,12 @@
  * (centres x_i = (i + 1/2)/N; the Dirichlet wall is an odd ghost cell).
  *
  * Method: one FMG cycle (Fig. 2) of FAS V(nu1, nu2)-cycles (Fig. 1) with the
- * tau correction of Eqs. 4-5; the finest n_sr_levels levels are SR levels
+ * tau correction of Eqs. 6-7; the finest n_sr_levels levels are SR levels
  * (Fig. 3): they are split into segments of segment_width cells with
  * buffer_width buffer cells per side, smoothed additively (block Jacobi), and
  * in the post-smoothing leg they are rebuilt from the coarse grid by the full
- * update of Eq. 7 and smoothed with the Kaczmarz compatible relaxation of
- * Fig. 4.  The finest level is never stored: it lives in on-chip memory only.
+ * update of Eq. 5 and smoothed with the Kaczmarz compatible relaxation of
+ * Fig. 5.  The finest level is never stored: it lives in on-chip memory only.
  * The smoother is the paper's lexicographic Gauss-Seidel (omega = 1, the
  * sweep direction reversed after every sweep within one smoothing call); tau
  * at segment edges is formed from the assembled level, as in the paper's

@@ -20,8 +20,8 @@
  * so residuals carry no O(eps |u| / h^2) rounding noise.
  *
  * The routines follow the paper's algorithms in its order:
- *   Fig. 1 (FAS V-cycle), Fig. 2 (FMG), Eq. 6 (correction update), Eq. 7
- *   (full update), Eqs. 4-5 (tau correction), Fig. 3 (FMG-FAS-SR), Fig. 4
+ *   Fig. 1 (FAS V-cycle), Fig. 2 (FMG), Eq. 4 (correction update), Eq. 5
+ *   (full update), Eqs. 6-7 (tau correction), Fig. 3 (FMG-FAS-SR), Fig. 5
  *   (Kaczmarz compatible relaxation) and the operators of Sec. 4.
  * Points where the paper is silent carry a "Reading:" note.
  *
@@ -139,7 +139,7 @@ static int thomas(int n, const double *rhs, double *u) {
 }
 
 /* ------------------------------------------------------------------ */
-/* The smoother S of Sec. 3 and Fig. 4 on one extended patch           */
+/* The smoother S of Sec. 3 and Fig. 5 on one extended patch           */
 /* ------------------------------------------------------------------ */
 
 /* One Gauss-Seidel update (omega = 1): u_i += (f_i - (L u)_i) / L_ii. */
@@ -147,7 +147,7 @@ static void gs_update(double *v, int voff, const double *rhs, int roff, int i, i
     v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - Lu_at(v, voff, i, n)) / Ldiag_at(i, n);
 }
 
-/* Kaczmarz pass of Fig. 4 over every coarse cell J whose children both lie in
+/* Kaczmarz pass of Fig. 5 over every coarse cell J whose children both lie in
  * [e0, e1): r = uH_J - (R v)_J, t = r / (R R^T)_JJ = r / (1/2), and
  * v += R(J,:)^T t, i.e. each child gets t/2.  The pairs are disjoint, so the
  * order of J does not matter.  Reading: e0 is even (segments and buffers have
@@ -164,7 +164,7 @@ static void kaczmarz_pass(double *v, int voff, const double *uH, int e0, int e1)
 
 /* nsweeps iterations of S on the cells [e0, e1); v also holds the frozen cells
  * just outside [e0, e1) (read, never written).  With uH != NULL every
- * iteration starts with the Kaczmarz pass (compatible relaxation, Fig. 4,
+ * iteration starts with the Kaczmarz pass (compatible relaxation, Fig. 5,
  * whose order "Kaczmarz, then the standard smoother" the appendix keeps).
  * Then one Gauss-Seidel sweep:
  *   smoother 0: lexicographic, ascending first and reversed after every
@@ -202,12 +202,12 @@ static void extended_patch(int s, int w, int b, int n, int *e0, int *e1, int *lo
 }
 
 /* ------------------------------------------------------------------ */
-/* tau-corrected coarse right-hand side (Eqs. 4-5, Fig. 3 lines 3-5)   */
+/* tau-corrected coarse right-hand side (Eqs. 6-7, Fig. 3 lines 3-5)   */
 /* ------------------------------------------------------------------ */
 
 /* rhs_c(J) = (R rhs_f)_J + (L_c R ubar)_J - (R L_f ubar)_J, evaluated left to
  * right as in the appendix's down leg.  The restricted solution R ubar plays
- * the role of Ihat ubar in Eq. 5 (Ihat = I here).  Reads fine cells 2J-2 ..
+ * the role of Ihat ubar in Eq. 7 (Ihat = I here).  Reads fine cells 2J-2 ..
  * 2J+3 of ubar (fewer at a wall) and 2J, 2J+1 of rhs_f. */
 static double tau_rhs_at(const double *ubar, int uoff, const double *rhs_f, int roff,
                          int J, int nf) {
@@ -300,9 +300,9 @@ static void presmooth_and_restrict(or_state *st, int l) {
 
 /* Post-smoothing leg update of level l from the corrected level l-1
  * (Fig. 3 post-smoothing leg, appendix up leg):
- *   SR level:  u_l <- Pi u_{l-1} (Eq. 7, full update), then S with the
- *              Kaczmarz compatible relaxation against u_{l-1} (Fig. 4);
- *   otherwise: u_l <- u_l + P (u_{l-1} - R u_l) (Eq. 6), then S. */
+ *   SR level:  u_l <- Pi u_{l-1} (Eq. 5, full update), then S with the
+ *              Kaczmarz compatible relaxation against u_{l-1} (Fig. 5);
+ *   otherwise: u_l <- u_l + P (u_{l-1} - R u_l) (Eq. 4), then S. */
 static void postsmooth_update(or_state *st, int l) {
     const or_params *p = st->p;
     int n = 1 << l, nc = n / 2;
@@ -437,7 +437,7 @@ int or_smooth(const or_params *p, int l, const double *u_in, const double *rhs,
     return OR_OK;
 }
 
-/* Kaczmarz pass (Fig. 4) over [e0, e1) of a level vector, against uH. */
+/* Kaczmarz pass (Fig. 5) over [e0, e1) of a level vector, against uH. */
 int or_kaczmarz(double *v, const double *uH, int e0, int e1) {
     kaczmarz_pass(v, 0, uH, e0, e1);
     return OR_OK;
@@ -480,7 +480,7 @@ int or_vcycles_h(const or_params *p, const double *f, double *u_inout, int ncycl
  * and the tau-corrected right-hand side of every coarse cell are formed as
  * soon as the six fine cells they read are assembled (lines 3-5), and the
  * window is then trimmed.  After the coarse part of the V-cycle the segment is
- * regenerated from the corrected level M-1 (Eq. 7), smoothed with compatible
+ * regenerated from the corrected level M-1 (Eq. 5), smoothed with compatible
  * relaxation and only its interior is emitted (Fig. 3 post-smoothing leg).
  * Memory for level M: one extended patch and a window of at most w + 8 cells.
  * Requires level M to be an SR level, segmented, with tau from the assembled

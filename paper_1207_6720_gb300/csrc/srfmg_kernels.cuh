@@ -176,7 +176,7 @@ __device__ void lex_sweep(const double *__restrict__ uo, double *__restrict__ un
     __syncthreads();
 }
 
-// Scaled tau-corrected coarse right-hand side at coarse cell J (Eqs. 4-5,
+// Scaled tau-corrected coarse right-hand side at coarse cell J (Eqs. 6-7,
 // Fig. 3 lines 3-5): g_{l-1,J} = 2(g_{2J} + g_{2J+1}) + (G_{J-1/2} - G_{J+1/2})
 // - 2(F_{2J-1/2} - F_{2J+3/2}), where G are fluxes of uhat = R u on the coarse
 // level and F fluxes of u; the value is h_{l-1}^2 times R rhs + L_{l-1} R u -
@@ -322,7 +322,7 @@ __global__ void level_down_kernel(LevelArgs a) {
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
 }
 
-// Up pass (Eq. 6): u_l += P (u_{l-1} - R u_l), then nu sweeps.
+// Up pass (Eq. 4): u_l += P (u_{l-1} - R u_l), then nu sweeps.
 __global__ void level_up_kernel(LevelArgs a) {
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
@@ -471,7 +471,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     }
 }
 
-// K6: post-smoothing leg of the SR level (Fig. 3, Eq. 7, Fig. 4): full update
+// K6: post-smoothing leg of the SR level (Fig. 3, Eq. 5, Fig. 5): full update
 // Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
 // Gauss-Seidel sweep), and the segment interior is written out.
 __global__ void sr_post_kernel(SegArgs a) {
@@ -482,7 +482,7 @@ __global__ void sr_post_kernel(SegArgs a) {
     seg_load(m, a);
     double *p = m.uo, *q = m.un;
     for (int k = 0; k < a.nu; ++k) {
-        // Kaczmarz (Fig. 4): r = u^H_J - (R u)_J added to both children
+        // Kaczmarz (Fig. 5): r = u^H_J - (R u)_J added to both children
         for (int J = (m.e0 >> 1) + threadIdx.x; J < (m.e1 >> 1); J += blockDim.x) {
             int i0 = 2 * J - m.lo;
             double r = m.c[J - m.C0] - scale2(p[i0] + p[i0 + 1], -1);

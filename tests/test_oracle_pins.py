@@ -73,7 +73,7 @@ def test_restriction_printed_and_sine_relation(nc):
     for J in range(nc):
         want[J, 2 * J:2 * J + 2] = np.array(row) / s
     assert np.array_equal(R, want)
-    assert np.array_equal(R @ R.T, 0.5 * np.eye(nc))          # R R^T = I/2 (Fig. 4's P)
+    assert np.array_equal(R @ R.T, 0.5 * np.eye(nc))          # R R^T = I/2 (Fig. 5's P)
     xf, xc = centres(2 * nc), centres(nc)
     for k in [1, 3, nc]:
         got = oracle.restrict(np.sin(k * np.pi * xf))
@@ -158,14 +158,14 @@ def test_tau_rhs_against_dense_matrices(M):
     R = np.zeros((n // 2, n))
     for J in range(n // 2):
         R[J, 2 * J:2 * J + 2] = 0.5
-    want = R @ f + L_printed(n // 2) @ (R @ u) - R @ (L_printed(n) @ u)   # Eqs. 4-5
+    want = R @ f + L_printed(n // 2) @ (R @ u) - R @ (L_printed(n) @ u)   # Eqs. 6-7
     got = oracle.tau_rhs(u, f)
     assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(L_printed(n) @ u))
 
 
 @pytest.mark.parametrize("M", [6, 11])
 def test_tau_fixed_point(M):
-    # Sec. 2.3: with the fine discrete solution, the tau-corrected coarse
+    # Sec. 2.4: with the fine discrete solution, the tau-corrected coarse
     # equation is solved exactly by the restricted fine solution.
     f, _, c = wl.sine_series(M, 8, seed=5)
     us = wl.discrete_solution(M, c)
@@ -187,7 +187,7 @@ def test_kaczmarz_enforces_coarse_constraint():
 
 
 # ---------------------------------------------------------------------------
-# The smoother S (Sec. 3, Fig. 4, appendix): brute force with matrix splittings
+# The smoother S (Sec. 3, Fig. 5, appendix): brute force with matrix splittings
 # ---------------------------------------------------------------------------
 
 def lex_sweeps_dense(A, u, f, lo, hi, nsweeps):
@@ -236,7 +236,7 @@ def test_segmented_smoother_is_additive_block_jacobi(w, b):
 
 
 def test_compatible_relaxation_patch_matches_brute_force():
-    # Fig. 4 on each extended patch: Kaczmarz over the patch's pairs, then GS.
+    # Fig. 5 on each extended patch: Kaczmarz over the patch's pairs, then GS.
     M, w, b = 5, 8, 4
     n = 1 << M
     rng = np.random.default_rng(3)
@@ -296,7 +296,7 @@ def test_vcycle_spectral_radius_bounded_with_depth():
 
 @pytest.mark.parametrize("nRS,W,b", [(0, 0, 0), (1, 256, 8), (1, 64, 4), (2, 256, 8)])
 def test_one_fmg_cycle_reaches_discretization_accuracy(nRS, W, b):
-    # Sec. 2.2 / Sec. 4: one F-cycle reduces the error to the order of the
+    # Sec. 2.3 / Sec. 4: one F-cycle reduces the error to the order of the
     # truncation error; second-order convergence (error ratio ~4 per halving h).
     errs = []
     for M in (10, 12, 14):
@@ -349,7 +349,7 @@ def test_paper_study_second_order_everywhere():
 
 
 def test_paper_study_two_halo_three_sr_levels_v11_loses_accuracy():
-    # Fig. 5 discussion: with two halo cells, accuracy is lost to some extent
+    # Fig. 6 discussion: with two halo cells, accuracy is lost to some extent
     # with three SR levels and V(1,1); the other two-halo curves stay at FMG
     # accuracy.
     Ms = [12]
@@ -363,7 +363,7 @@ def test_paper_study_two_halo_three_sr_levels_v11_loses_accuracy():
 
 
 def test_paper_study_four_halo_good_in_all_configurations():
-    # Fig. 6 discussion: with four halo cells the accuracy is very good in all
+    # Fig. 7 discussion: with four halo cells the accuracy is very good in all
     # solver configurations.
     Ms = [10, 12]
     for ns in (1, 2):
@@ -373,7 +373,7 @@ def test_paper_study_four_halo_good_in_all_configurations():
 
 
 def test_paper_study_global_smoother_cleaner():
-    # Fig. 7 discussion: the global point-wise GS smoother gives "cleaner"
+    # Fig. 8 discussion: the global point-wise GS smoother gives "cleaner"
     # convergence than the block-Jacobi smoothers: its error ratios per halving
     # of h stay closer to 4.
     Ms = list(range(6, 13))
