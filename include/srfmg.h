@@ -128,6 +128,35 @@ srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *str
  * NULL if i is out of range. */
 const char *srfmg_launch_name(srfmg_handle h, int32_t i);
 
+/* Allocation-free small solve (the paper has no counterpart; this entry point
+ * exists for callers that cannot call cudaMalloc: code that runs while a CUDA
+ * stream capture is open in global mode, code whose device memory is owned by
+ * a caching allocator or a fixed pool, and loops that must not allocate after
+ * start-up).  It runs plain FMG-FAS (every level stored, no SR level: Fig. 2
+ * with the V-cycle of Fig. 1) for N = 2^log2_n <= SRFMG_NOALLOC_MAX_N cells in
+ * one thread block, exactly as srfmg_solve does for such sizes with
+ * n_sr_levels = 0, and allocates nothing: its one piece of scratch memory,
+ * the inverse of the coarsest-level operator, lives in a static device array
+ * of SRFMG_NOALLOC_MAX_COARSE^2 doubles (32 KiB) that every GPU which loads
+ * the library holds until the process exits.
+ *   log2_n: 2 <= log2_n_coarsest < log2_n <= 12; log2_n_coarsest <= 6;
+ *   nu1, nu2 in [1, 4]; f, u: device pointers, N doubles each, 16-byte
+ *   aligned, not overlapping; stream as in srfmg_solve.
+ * Sizes beyond these limits return SRFMG_EINVAL and enqueue nothing; errors
+ * are reported by the status code only (srfmg_last_error is not updated).
+ * The first call on a device (with that device current) does a synchronous
+ * set-up: it looks up the static array's device address, raises the kernel's
+ * shared-memory limit and uploads the inverse for log2_n_coarsest; a later
+ * call with a different log2_n_coarsest uploads again.  Make the first call,
+ * and any call that changes log2_n_coarsest, before any stream capture.  All
+ * calls share the array and it keeps the last upload: calls with different
+ * log2_n_coarsest that overlap on the GPU race.  Nothing in it has to start
+ * at zero. */
+#define SRFMG_NOALLOC_MAX_N 4096
+#define SRFMG_NOALLOC_MAX_COARSE 64
+srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n_coarsest, int32_t nu1,
+                                       int32_t nu2, const double *f, double *u, void *stream);
+
 /* Release the device workspace and graphs.  Synchronises the device first.
  * Accepts NULL (returns SRFMG_OK). */
 srfmg_status srfmg_destroy(srfmg_handle h);

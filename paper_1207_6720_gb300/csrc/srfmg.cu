@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -626,3 +627,117 @@ const char *srfmg_last_error(srfmg_handle h) {
 const char *srfmg_version(void) { return "srfmg 0.1 sm_103a"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free small solve.  The same one-block FMG kernel that
+// srfmg_solve launches for N <= 2^12 without SR, with its coarsest-level
+// inverse table in this static device array instead of plan memory from
+// cudaMalloc.  In host code s_noalloc_ainv is only a host-side stand-in for
+// the symbol: the device address comes from cudaGetSymbolAddress, once per
+// device, with that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double s_noalloc_ainv[SRFMG_NOALLOC_MAX_COARSE * SRFMG_NOALLOC_MAX_COARSE];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+
+struct NoallocDevice {
+    bool ready;        // symbol address looked up and smem limit raised
+    double *ainv;      // device address of s_noalloc_ainv on this device
+    int m0;            // log2_n_coarsest whose inverse the array holds (0: none)
+};
+
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+std::mutex g_noalloc_mutex;
+// host work arrays for the Gauss-Jordan inverse (static: no heap use)
+long double g_noalloc_gj[SRFMG_NOALLOC_MAX_COARSE][2 * SRFMG_NOALLOC_MAX_COARSE];
+double g_noalloc_inv[SRFMG_NOALLOC_MAX_COARSE * SRFMG_NOALLOC_MAX_COARSE];
+
+// Same inverse as coarsest_inverse(), in static storage.
+void noalloc_inverse(int n) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j) g_noalloc_gj[i][j] = 0.0L;
+    for (int i = 0; i < n; ++i) {
+        g_noalloc_gj[i][i] = (i == 0 || i == n - 1) ? 3.0L : 2.0L;
+        if (i > 0) g_noalloc_gj[i][i - 1] = -1.0L;
+        if (i < n - 1) g_noalloc_gj[i][i + 1] = -1.0L;
+        g_noalloc_gj[i][n + i] = 1.0L;
+    }
+    for (int c = 0; c < n; ++c) {
+        long double piv = g_noalloc_gj[c][c];
+        for (int j = 0; j < 2 * n; ++j) g_noalloc_gj[c][j] /= piv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            long double fct = g_noalloc_gj[r][c];
+            if (fct == 0.0L) continue;
+            for (int j = 0; j < 2 * n; ++j) g_noalloc_gj[r][j] -= fct * g_noalloc_gj[c][j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) g_noalloc_inv[i * n + j] = (double)g_noalloc_gj[i][n + j];
+}
+
+}  // namespace
+
+extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n_coarsest, int32_t nu1,
+                                                  int32_t nu2, const double *f, double *u, void *stream) {
+    if (log2_n_coarsest < 2 || log2_n_coarsest > 6 || log2_n <= log2_n_coarsest || log2_n > 12)
+        return SRFMG_EINVAL;
+    if (nu1 < 1 || nu1 > 4 || nu2 < 1 || nu2 > 4) return SRFMG_EINVAL;
+    const size_t n = (size_t)1 << log2_n;
+    if (!f || !u || ((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return SRFMG_EINVAL;
+    if ((const double *)u < f + n && f < (const double *)u + n) return SRFMG_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SRFMG_ECUDA; }
+    if (dev < 0 || dev >= kNoallocMaxDevices) return SRFMG_EUNSUPPORTED;
+
+    double *ainv = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoallocDevice &d = g_noalloc_dev[dev];
+        if (!d.ready) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, s_noalloc_ainv) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return SRFMG_ECUDA;
+            }
+            int optin = 0;
+            if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+                cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                return SRFMG_ECUDA;
+            }
+            d.ainv = (double *)ptr;
+            d.m0 = 0;
+            d.ready = true;
+        }
+        if (d.m0 != log2_n_coarsest) {
+            const int n0 = 1 << log2_n_coarsest;
+            noalloc_inverse(n0);
+            if (cudaMemcpy(d.ainv, g_noalloc_inv, sizeof(double) * n0 * n0, cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                d.m0 = 0;
+                return SRFMG_ECUDA;
+            }
+            d.m0 = log2_n_coarsest;
+        }
+        ainv = d.ainv;
+    }
+    TailArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.M0 = log2_n_coarsest;
+    a.Mc = log2_n;
+    a.nu1 = nu1;
+    a.nu2 = nu2;
+    a.mode = 0;
+    a.g_in = f;
+    a.g_exp = -2 * log2_n;
+    a.u_out = u;
+    a.Ainv = ainv;
+    const size_t smem = tail_smem_doubles(log2_n_coarsest, log2_n) * sizeof(double);
+    tail_kernel<<<1, kTailThreads, smem, (cudaStream_t)stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? SRFMG_OK : SRFMG_ECUDA;
+}

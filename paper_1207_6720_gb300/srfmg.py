@@ -17,7 +17,7 @@ FP64, MIXED = 0, 1
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
-           "srfmg_destroy", "srfmg_last_error", "srfmg_version")
+           "srfmg_solve_small_noalloc", "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
 class Params(ctypes.Structure):
@@ -71,6 +71,9 @@ def load(build_if_missing=True):
                                   ctypes.c_int32]
     lib.srfmg_launch_name.argtypes = [H, ctypes.c_int32]
     lib.srfmg_launch_name.restype = ctypes.c_char_p
+    lib.srfmg_solve_small_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, vp, vp, vp]
+    lib.srfmg_solve_small_noalloc.restype = ctypes.c_int
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
@@ -172,6 +175,27 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None):
+    """Plain FMG-FAS for N <= 4096 through srfmg_solve_small_noalloc, which
+    allocates no device memory (for callers that cannot call cudaMalloc: open
+    stream captures, pool-owned device memory, allocation-free loops).  f: CUDA
+    float64 tensor of 2^k values; returns u.  The first call on a device does a
+    synchronous set-up and should come before any stream capture."""
+    import torch
+    n = f.numel()
+    log2_n = n.bit_length() - 1
+    if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and n == 1 << log2_n):
+        raise ValueError("f must be a contiguous CUDA float64 tensor of 2^k values")
+    if u is None:
+        u = torch.empty_like(f)
+    st = load().srfmg_solve_small_noalloc(log2_n, log2_n_coarsest, nu1, nu2,
+                                           ctypes.c_void_p(f.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream))
+    if st != OK:
+        raise SrfmgError(st, "srfmg_solve_small_noalloc (status code only)")
+    return u
 
 
 def version():

@@ -76,6 +76,15 @@ def test_null_handle_calls():
     assert lib.srfmg_destroy(None) == srfmg.OK
 
 
+def test_noalloc_entry_checks_arguments_on_the_host():
+    lib = srfmg.load()
+    buf = (ctypes.c_double * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    for args in [(13, 2, 1, 1), (12, 1, 1, 1), (12, 7, 1, 1), (4, 4, 1, 1), (10, 2, 0, 1), (10, 2, 1, 5)]:
+        assert lib.srfmg_solve_small_noalloc(*args, p, p, None) == srfmg.EINVAL
+    assert lib.srfmg_solve_small_noalloc(10, 2, 1, 1, None, None, None) == srfmg.EINVAL
+
+
 def test_no_cpu_fallback_without_gpu():
     import torch
     if torch.cuda.is_available():
