@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--segment-width", type=int, default=4096)
     ap.add_argument("--buffer-width", type=int, default=8)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="mixed: 64-bit fixed point for solution/residual/tau, FP64 coarse solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
@@ -69,10 +71,13 @@ def parse_args():
 
 
 def workload_config(a):
+    prec = ("64-bit fixed point (solution, residual, tau, interpolation) + FP64 coarsest solve"
+            if getattr(a, "precision", "fp64") == "mixed" else "FP64")
     return {
         "workload": f"1D -u''=f, N=2^{a.log2n}, FMG-FAS V(1,1) lexicographic GS, 1 SR level of "
                     f"{(1 << a.log2n) // a.segment_width} segments x {a.segment_width} cells, "
-                    f"buffer {a.buffer_width}, FP64",
+                    f"buffer {a.buffer_width}, {prec}",
+        "precision": getattr(a, "precision", "fp64"),
         "N": 1 << a.log2n, "segment_width": a.segment_width, "buffer_width": a.buffer_width,
         "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2, "modes": 32, "seed": 1,
         "l2": "inputs larger than L2 (f and u 128 MiB each plus the stored coarse levels)",
@@ -175,10 +180,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_kind):
+def recorded_traffic(kernel_kind, precision):
     """DRAM bytes per launch of `kernel_kind` from the committed ncu summary,
     or None if there is none or the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_kind}_ncu.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel_kind}_{precision}_ncu.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -285,7 +290,8 @@ def run_gpu(a):
     fd = torch.from_numpy(f).to(dev)
     ud = torch.empty_like(fd)
 
-    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b)
+    prec = srfmg.MIXED if a.precision == "mixed" else srfmg.FP64
+    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, precision=prec)
     info = solver.info()
 
     sampler = ClockSampler(dev)
@@ -310,6 +316,15 @@ def run_gpu(a):
     u_plain = ud.cpu().numpy()
     plain_info = plain.info()
     plain.close()
+    # the same SR solve in FP64 arithmetic (when the headline is the fixed-point one)
+    sr64 = None
+    if prec != srfmg.FP64:
+        s64 = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, precision=srfmg.FP64)
+        ms64 = dist.max(time_solves(s64, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
+        u64 = ud.cpu().numpy()
+        s64.close()
+        sr64 = {"value": dist.world * N / (ms64 * 1e-3), "ms_per_step": ms64,
+                "err_max_vs_exact": float(np.max(np.abs(u64 - u_exact)))}
 
     # end to end through the public API from pinned host buffers
     fh = torch.from_numpy(f).pin_memory()
@@ -331,16 +346,17 @@ def run_gpu(a):
     torch.cuda.synchronize()
     top_name, top_ms = max(prof, key=lambda x: x[1])
     kind, lvl = top_name.split(" L")
+    kind = kind.replace("fx.", "")
     cells = 1 << int(lvl)
     peaks = measured_peaks()
     flops = FLOPS_PER_CELL.get(kind, 0.0) * cells
     achieved_tf = flops / (top_ms * 1e-3) / 1e12
     bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * cells
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = recorded_traffic(kind)
+    traffic = recorded_traffic(kind, a.precision)
     by_kind = {}
     for name, t in prof:
-        k = name.split(" L")[0]
+        k = name.split(" L")[0].replace("fx.", "")
         by_kind[k] = by_kind.get(k, 0.0) + t
     tot = sum(by_kind.values())
 
@@ -348,12 +364,14 @@ def run_gpu(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+        "dtype": "int64" if prec != srfmg.FP64 else "f64", "data": "synthetic",
+        "config": workload_config(a),
         "e2e": e2e,
         "gpu_launches": info.kernels_per_solve * a.steps,
         "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                        "kernels_per_solve": plain_info.kernels_per_solve,
-                       "speedup_sr_over_plain": ms_plain / ms},
+                       "speedup_over_plain": ms_plain / ms},
+        "sr_fp64": sr64,
         "roofline": {"bound": "alu", "kernel": top_name, "achieved": achieved_tf,
                      "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tf / NOMINAL_FP64_TFLOPS,

@@ -3,6 +3,7 @@
 // Fig. 3), CUDA-graph capture and replay, and the C ABI declared in srfmg.h.
 #include "srfmg.h"
 #include "srfmg_kernels.cuh"
+#include "srfmg_fixed.cuh"
 
 #include <cuda_runtime.h>
 
@@ -27,7 +28,7 @@ constexpr int kTileMax = 2048;
 
 thread_local std::string g_create_error = "no error";
 
-enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST };
+enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST, OP_SCALE };
 
 // Pointers that are only known at solve time are patched through these tags.
 enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };
@@ -44,6 +45,13 @@ struct Op {
     int nseg;
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
+    // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
+    bool fixed;
+    fx::RhsArgs frhs;
+    fx::LevelArgs flev;
+    fx::SegArgs fseg;
+    fx::TailArgs ftail;
+    fx::Scale *scale;
 };
 
 }  // namespace
@@ -58,6 +66,8 @@ struct srfmg_plan {
     double *glev[32] = {};
     double *seam = nullptr;
     double *Ainv = nullptr;
+    fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
+    bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
     size_t ws_bytes = 0;
     std::vector<Op> ops;
@@ -178,8 +188,10 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
     const int T = n < kTileMax ? n : kTileMax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
-    // after its range start, and the tau stencil reaches 2 cells past the tile
-    const int H = 4 + 100 * nu;
+    // after its range start (at most 6 * 17 = 102 cells, J+1 = ceil(72/17)),
+    // every sweep shrinks its range by one cell, and the tau stencil reaches
+    // 2 cells past the tile
+    const int H = 112 * nu;
     o.lev.l = l;
     o.lev.n = n;
     o.lev.tile = T;
@@ -256,9 +268,59 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
     return o;
 }
 
+// Fixed-point form of an op (same schedule, same buffers: a level array holds
+// doubles or 64-bit integers of the same size).
+void to_fixed(srfmg_plan *h, Op &o) {
+    o.fixed = true;
+    o.scale = h->scale;
+    typedef fx::i64 i64;
+    switch (o.kind) {
+    case OP_RHS:
+        o.frhs.sc = h->scale;
+        o.frhs.from_f = (o.rhs_in == TAG_F);
+        o.frhs.in = (const i64 *)o.rhs.in;
+        o.frhs.lin = o.rhs.lin;
+        o.frhs.lstop = o.rhs.lstop;
+        o.frhs.depth = o.rhs.depth;
+        for (int l = 0; l < 32; ++l) o.frhs.out[l] = (i64 *)o.rhs.out[l];
+        break;
+    case OP_DOWN_PI: case OP_DOWN: case OP_UP:
+        o.flev.l = o.lev.l; o.flev.n = o.lev.n; o.flev.tile = o.lev.tile; o.flev.halo = o.lev.halo;
+        o.flev.nu = o.lev.nu; o.flev.maxlen = o.lev.maxlen; o.flev.maxc = o.lev.maxc; o.flev.maxch = o.lev.maxch;
+        o.flev.sc = h->scale;
+        o.flev.u_src = (const i64 *)o.lev.u_src;
+        o.flev.g = (o.lev_g == TAG_F) ? nullptr : (const i64 *)o.lev.g;
+        o.flev.uc_src = (const i64 *)o.lev.uc_src;
+        o.flev.u_out = (i64 *)o.lev.u_out;
+        o.flev.uc_out = (i64 *)o.lev.uc_out;
+        o.flev.gc_out = (i64 *)o.lev.gc_out;
+        break;
+    case OP_SR_PRE: case OP_SEAM: case OP_SR_POST:
+        o.fseg.M = o.seg.M; o.fseg.n = o.seg.n; o.fseg.W = o.seg.W; o.fseg.b = o.seg.b; o.fseg.nu = o.seg.nu;
+        o.fseg.maxlen = o.seg.maxlen; o.fseg.maxc = o.seg.maxc; o.fseg.maxch = o.seg.maxch;
+        o.fseg.sc = h->scale;
+        o.fseg.uc_src = (const i64 *)o.seg.uc_src;
+        o.fseg.uc_out = (i64 *)o.seg.uc_out;
+        o.fseg.gc_out = (i64 *)o.seg.gc_out;
+        o.fseg.seam = (i64 *)o.seg.seam;
+        break;
+    case OP_TAIL:
+        o.ftail.M0 = o.tail.M0; o.ftail.Mc = o.tail.Mc; o.ftail.nu1 = o.tail.nu1; o.ftail.nu2 = o.tail.nu2;
+        o.ftail.mode = o.tail.mode;
+        o.ftail.sc = h->scale;
+        o.ftail.u_in = (const i64 *)o.tail.u_in;
+        o.ftail.g_in = (o.tail_g == TAG_F) ? nullptr : (const i64 *)o.tail.g_in;
+        o.ftail.u_out = (i64 *)o.tail.u_out;
+        o.ftail.Ainv = o.tail.Ainv;
+        break;
+    case OP_SCALE:
+        break;
+    }
+}
+
 // The level schedule of one FMG cycle.  cur[l] tracks which of the two
 // buffers of level l holds its current iterate.
-void build_schedule(srfmg_plan *h) {
+void build_schedule_ops(srfmg_plan *h) {
     const int M = h->M, Mc = h->Mc;
     int cur[32] = {0};
     auto U = [&](int l) { return h->ulev[l][cur[l]]; };
@@ -338,7 +400,48 @@ void build_schedule(srfmg_plan *h) {
     (void)last_stored;
 }
 
+void build_schedule(srfmg_plan *h) {
+    build_schedule_ops(h);
+    if (!h->fixed) return;
+    for (Op &o : h->ops) to_fixed(h, o);
+    Op sc = make_op(OP_SCALE);
+    sc.fixed = true;
+    sc.scale = h->scale;
+    sc.level = h->M;
+    sc.grid = dim3(608);
+    sc.block = dim3(256);
+    h->ops.insert(h->ops.begin(), sc);
+}
+
+cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t s) {
+    Op o = o0;
+    if (o.rhs_in == TAG_F) o.frhs.f = f;
+    if (o.lev_g == TAG_F) o.flev.f = f;
+    if (o.lev_out == TAG_U) { o.flev.u_out_f64 = u; o.flev.u_out = nullptr; }
+    if (o.tail_g == TAG_F) o.ftail.f = f;
+    if (o.tail_out == TAG_U) { o.ftail.u_out_f64 = u; o.ftail.u_out = nullptr; }
+    if (o.seg_f == TAG_F) o.fseg.f = f;
+    if (o.seg_u == TAG_U) o.fseg.u_out = u;
+    switch (o.kind) {
+    case OP_SCALE:
+        fx::scale_reset_kernel<<<1, 32, 0, s>>>(o.scale);
+        fx::scale_max_kernel<<<o.grid, o.block, 0, s>>>(f, (long long)o.level < 63 ? (1LL << o.level) : 0, o.scale);
+        fx::scale_finish_kernel<<<1, 32, 0, s>>>(o.scale);
+        break;
+    case OP_RHS: fx::rhs_hierarchy_kernel<<<o.grid, o.block, o.smem, s>>>(o.frhs); break;
+    case OP_TAIL: fx::tail_kernel<<<o.grid, o.block, o.smem, s>>>(o.ftail); break;
+    case OP_DOWN_PI: fx::level_down_kernel<true><<<o.grid, o.block, o.smem, s>>>(o.flev); break;
+    case OP_DOWN: fx::level_down_kernel<false><<<o.grid, o.block, o.smem, s>>>(o.flev); break;
+    case OP_UP: fx::level_up_kernel<<<o.grid, o.block, o.smem, s>>>(o.flev); break;
+    case OP_SR_PRE: fx::sr_pre_kernel<<<o.grid, o.block, o.smem, s>>>(o.fseg); break;
+    case OP_SEAM: fx::seam_tau_kernel<<<o.grid, o.block, 0, s>>>(o.fseg, o.nseg); break;
+    case OP_SR_POST: fx::sr_post_kernel<<<o.grid, o.block, o.smem, s>>>(o.fseg); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s) {
+    if (o0.fixed) return launch_fixed(o0, f, u, s);
     Op o = o0;
     if (o.rhs_in == TAG_F) o.rhs.in = f;
     if (o.lev_g == TAG_F) o.lev.g = f;
@@ -370,6 +473,7 @@ const char *kind_name(OpKind k) {
     case OP_SR_PRE: return "sr_pre";
     case OP_SEAM: return "seam_tau";
     case OP_SR_POST: return "sr_post";
+    case OP_SCALE: return "fixed_scale";
     }
     return "?";
 }
@@ -395,7 +499,11 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
     const void *fns[] = {(const void *)level_down_kernel<true>, (const void *)level_down_kernel<false>,
                          (const void *)level_up_kernel, (const void *)sr_pre_kernel,
                          (const void *)sr_post_kernel, (const void *)tail_kernel,
-                         (const void *)rhs_hierarchy_kernel};
+                         (const void *)rhs_hierarchy_kernel,
+                         (const void *)fx::level_down_kernel<true>, (const void *)fx::level_down_kernel<false>,
+                         (const void *)fx::level_up_kernel, (const void *)fx::sr_pre_kernel,
+                         (const void *)fx::sr_post_kernel, (const void *)fx::tail_kernel,
+                         (const void *)fx::rhs_hierarchy_kernel};
     for (const void *fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
@@ -437,7 +545,6 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     *out = nullptr;
     std::string msg = check_params(p);
     if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
-    if (p->precision == SRFMG_MIXED) return fail(nullptr, SRFMG_EUNSUPPORTED, "mixed precision is not built yet");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -460,6 +567,7 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     int top_stored = h->M - h->nRS;
     h->Mc = top_stored < kMaxTailLevel ? top_stored : kMaxTailLevel;
     if (h->Mc < h->M0) h->Mc = h->M0;
+    h->fixed = (p->precision == SRFMG_MIXED);
     const char *env = std::getenv("SRFMG_NO_GRAPH");
     h->use_graph = !(env && env[0] == '1');
 
@@ -474,6 +582,11 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], (size_t)1 << l);
     }
     if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, (h->n / h->W) * 6);
+    if (st == SRFMG_OK && h->fixed) {
+        double *sc = nullptr;
+        st = alloc_dev(h, &sc, 2);
+        h->scale = (fx::Scale *)sc;
+    }
     const int n0 = 1 << h->M0;
     if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
     if (st == SRFMG_OK) {
@@ -484,7 +597,7 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     if (st == SRFMG_OK) {
         build_schedule(h);
         for (const Op &o : h->ops)
-            h->names.push_back(std::string(kind_name(o.kind)) + " L" + std::to_string(o.level));
+            h->names.push_back(std::string(o.fixed ? "fx." : "") + kind_name(o.kind) + " L" + std::to_string(o.level));
         st = set_smem_limits(h);
     }
     if (st == SRFMG_OK) {

@@ -1,0 +1,642 @@
+// srfmg_fixed.cuh -- sm_103a kernels of the FMG-FAS-SR solve in 64-bit fixed
+// point (the SRFMG_MIXED precision).
+//
+// GB300 executes FP64 at about 1/70 of its FP32 rate, while 64-bit integer
+// adds run about 30 times faster than FP64 adds and 64-bit shifts and small
+// multiplies about 10 times faster (measured).  Here the quantities whose
+// accuracy the method depends on -- the solution, the residual, the tau
+// correction and the FMG interpolation -- are 64-bit fixed-point integers:
+//   u  = U * 2^-S                 on every level,
+//   g_l = G * 2^-(Sg0 + 2l)       (scaled right-hand side h_l^2 rhs_l),
+// with S = 62 - E and Sg0 = 60 - E, where 2^E bounds max|f| (computed on the
+// device before the solve).  |u| <= max|f|/8 keeps |U| below 2^59 with eight
+// times headroom, and |G| below 2^60; relative to the largest value every
+// quantity carries at least 59 bits (FP64: 53).  Sums and differences are
+// exact; the tau correction (differences of differences of u) is exact; the
+// only roundings are the explicit halvings of the smoother, the restriction,
+// the prolongations and the FMG interpolation (half a unit each, far below the
+// FP64 rounding of the same quantities).  Corrections stay integers too:
+// converting between integers and floating point costs as much as an FP64
+// operation on this part.  The coarsest-level direct solve stays in FP64.
+// f (input) and u (output) are FP64; they are converted with integer bit
+// operations.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace srfmg {
+namespace fx {
+
+typedef long long i64;
+typedef unsigned long long u64;
+
+// Fixed-point scales of one solve, written on the device by scale_kernel.
+struct Scale {
+    int S;       // u = U 2^-S
+    int Sg0;     // g_l = G 2^-(Sg0 + 2l)
+    int E;       // max|f| < 2^E
+    int pad;
+};
+
+// x / 2^k rounded half up, 0 < k < 63.
+__device__ __forceinline__ i64 shr_round(i64 x, int k) { return (x + (1LL << (k - 1))) >> k; }
+
+// round(x 2^k) for a double x with |x 2^k| < 2^62 (subnormals read as 0).
+__device__ __forceinline__ i64 f64_to_fixed(double x, int k) {
+    u64 b = (u64)__double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;
+    i64 m = (i64)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));   // |x| = m 2^(e-1075)
+    int sh = e - 1075 + k;
+    i64 v;
+    if (sh >= 0) v = m << sh;
+    else if (sh > -63) v = (m + (1LL << (-sh - 1))) >> (-sh);
+    else v = 0;
+    return (b >> 63) ? -v : v;
+}
+
+// U 2^-S as the nearest double (ties to even).
+__device__ __forceinline__ double fixed_to_f64(i64 U, int S) {
+    if (U == 0) return 0.0;
+    u64 sign = (U < 0) ? (1ULL << 63) : 0ULL;
+    u64 m = (U < 0) ? (u64)(-U) : (u64)U;
+    int p = 63 - __clzll((long long)m);          // position of the leading bit
+    u64 mant;
+    if (p > 52) {
+        int sh = p - 52;
+        u64 q = m >> sh, rem = m & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;
+        if (q >> 53) { q >>= 1; ++p; }
+        mant = q;
+    } else {
+        mant = m << (52 - p);
+    }
+    u64 expo = (u64)(p - S + 1023);
+    return __longlong_as_double((long long)(sign | (expo << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+}
+
+// Fourth order FMG interpolation Pi (Sec. 4) in fixed point: 128 Pi is the
+// integer combination (-5, 35, 105, -7) (or its mirror), formed in 128 bits
+// and rounded to the nearest unit.  c[j - cbase] holds coarse cells J-2..J+2.
+__device__ __forceinline__ i64 fmg_interp(const i64 *c, int cbase, int i) {
+    int J = i >> 1;
+    const i64 *p = c + (J - cbase);
+    __int128 s;
+    if ((i & 1) == 0)
+        s = (__int128)p[-2] * -5 + (__int128)p[-1] * 35 + (__int128)p[0] * 105 + (__int128)p[1] * -7;
+    else
+        s = (__int128)p[-1] * -7 + (__int128)p[0] * 105 + (__int128)p[1] * 35 + (__int128)p[2] * -5;
+    return (i64)((s + 64) >> 7);
+}
+
+// Fluxes F_{i-1/2}, F_{i+1/2} with the odd ghost at the walls.
+__device__ __forceinline__ i64 flux_lo(const i64 *u, int base, int i) {
+    return (i == 0) ? 2 * u[0 - base] : u[i - base] - u[i - 1 - base];
+}
+__device__ __forceinline__ i64 flux_hi(const i64 *u, int base, int i, int n) {
+    return (i == n - 1) ? -2 * u[i - base] : u[i + 1 - base] - u[i - base];
+}
+
+// Lexicographic Gauss-Seidel sweep, fixed point (same structure as the FP64
+// lex_sweep; see srfmg_kernels.cuh): residual r_i = gs_i - (F_{i-1/2} -
+// F_{i+1/2}) with the right-hand side shifted into solution units
+// (gs = G >> gsh), correction recurrence delta_i = (r_i + delta_{i-1}) / 2
+// (wall cells / 3), update U += delta.  Chunks of C cells, carries by a fixed
+// sum over the chunks that reach 64 cells back (KS = false) or a Kogge-Stone
+// scan (KS = true); a shift by 64 or more leaves nothing of a 63-bit value, so
+// dropping those terms changes nothing.
+template <bool KS>
+__device__ void lex_sweep(const i64 *__restrict__ uo, i64 *__restrict__ un, const i64 *__restrict__ g,
+                          int gsh, int base, int lo, int hi, int n, bool asc, int C, i64 *X, i64 *Y) {
+    const int t = threadIdx.x, T = blockDim.x;
+    const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const int start_wall = asc ? 0 : n - 1, end_wall = asc ? n - 1 : 0;
+
+    for (int ch = t; ch < nch; ch += T) {
+        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
+        i64 p = 0;
+        for (int q = q0; q < q1; ++q) {
+            const int i = asc ? q : n - 1 - q;
+            i64 r = shr_round(g[i - base], gsh) - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+            if (i == start_wall) p = r / 3;
+            else if (i == end_wall) p = 0;           // recomputed below
+            else p = (q == q0) ? ((r + 1) >> 1) : ((r + p + 1) >> 1);
+            un[i - base] = p;
+        }
+        X[ch] = p;
+    }
+    __syncthreads();
+    const int J = (64 + C - 1) / C - 1;
+    i64 *src = X;
+    if (KS) {
+        i64 *dst = Y;
+        i64 y = (t < nch) ? X[t] : 0;
+        for (int d = 1; d * C < 64 && d < nch; d <<= 1) {
+            i64 prev = (t >= d && t < nch) ? (src[t - d] >> (C * d)) : 0;
+            y += prev;
+            if (t < nch) dst[t] = y;
+            __syncthreads();
+            i64 *tmp = src; src = dst; dst = tmp;
+        }
+    }
+    for (int ch = t; ch < nch; ch += T) {
+        i64 cin = 0;
+        if (KS) {
+            cin = (ch > 0) ? src[ch - 1] : 0;
+        } else {
+            for (int j = J; j >= 0; --j) {
+                i64 x = (ch - 1 - j >= 0) ? X[ch - 1 - j] : 0;
+                cin = (C < 64 ? (cin >> C) : 0) + x;
+            }
+        }
+        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
+        for (int q = q0; q < q1; ++q) {
+            const int i = asc ? q : n - 1 - q;
+            const int d = q - q0 + 1;
+            i64 dl = un[i - base];
+            if (d < 63) dl += cin >> d;
+            un[i - base] = uo[i - base] + dl;
+        }
+    }
+    __syncthreads();
+    const bool has_end = asc ? (hi == n) : (lo == 0);
+    if (has_end && t == 0) {
+        const int i = end_wall, ip = asc ? i - 1 : i + 1;
+        i64 r = shr_round(g[i - base], gsh) - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+        i64 dprev = un[ip - base] - uo[ip - base];
+        un[i - base] = uo[i - base] + (r + dprev) / 3;
+    }
+    __syncthreads();
+}
+
+// tau-corrected coarse right-hand side (Eqs. 6-7), exact: the tau term is a
+// combination of differences of u in solution units, moved into the coarse
+// right-hand side's units by a left shift of tsh = 2l - 4 bits; the
+// restricted right-hand side is the mean of the two children in the coarse
+// units (one rounding).  um2..u3: U at fine cells 2J-2 .. 2J+3.  tau is
+// moved by a multiplication with 2^tsh (a shift that is defined for negatives).
+__device__ __forceinline__ i64 tau_rhs(i64 g0, i64 g1, i64 um2, i64 um1, i64 u0, i64 u1, i64 u2, i64 u3,
+                                       int J, int nc, int tsh) {
+    i64 hJ = (u0 + u1) >> 1;
+    i64 Gl = (J == 0) ? 2 * hJ : hJ - ((um2 + um1) >> 1);
+    i64 Gr = (J == nc - 1) ? -2 * hJ : ((u2 + u3) >> 1) - hJ;
+    i64 Fl = (J == 0) ? 2 * u0 : u0 - um1;
+    i64 Fr = (J == nc - 1) ? -2 * u1 : u2 - u1;
+    i64 tau = (Gl - Gr) - 2 * (Fl - Fr);
+    return ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+}
+
+// --------------------------------------------------------------------------
+// Scale: E with max|f| < 2^E from the largest exponent field of f.
+// --------------------------------------------------------------------------
+__global__ void scale_reset_kernel(Scale *sc) {
+    if (threadIdx.x == 0) { sc->E = -2000; sc->S = 0; sc->Sg0 = 0; }
+}
+
+__global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
+    int emax = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int e = (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff);
+        emax = max(emax, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&sc->E, emax - 1022);
+}
+
+__global__ void scale_finish_kernel(Scale *sc) {
+    if (threadIdx.x == 0) {
+        int E = sc->E;
+        E = E < -100 ? -100 : (E > 900 ? 900 : E);
+        sc->E = E;
+        sc->S = 62 - E;
+        sc->Sg0 = 60 - E;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Right-hand side hierarchy: G on levels lin-1 .. lstop; level lin is f
+// (converted) when from_f, else the fixed-point array `in`.
+// --------------------------------------------------------------------------
+struct RhsArgs {
+    const double *f;
+    const i64 *in;
+    const Scale *sc;
+    int from_f, lin, lstop, depth;
+    i64 *out[32];
+};
+
+__global__ void rhs_hierarchy_kernel(RhsArgs a) {
+    extern __shared__ i64 smi[];
+    const int chunk = 1 << a.depth;
+    i64 *cur = smi, *nxt = smi + chunk;
+    const long long base = (long long)blockIdx.x * chunk;
+    const int k = a.sc->Sg0;              // f 2^-2M 2^(Sg0+2M) = f 2^Sg0
+    for (int i = threadIdx.x; i < chunk; i += blockDim.x)
+        cur[i] = a.from_f ? f64_to_fixed(a.f[base + i], k) : a.in[base + i];
+    __syncthreads();
+    int len = chunk;
+    for (int l = a.lin; l > a.lstop && len > 1; --l) {
+        const int half = len >> 1;
+        i64 *dst = a.out[l - 1] + (base >> (a.lin - l + 1));
+        for (int J = threadIdx.x; J < half; J += blockDim.x) {
+            i64 x = (cur[2 * J] + cur[2 * J + 1] + 1) >> 1;
+            nxt[J] = x;
+            dst[J] = x;
+        }
+        __syncthreads();
+        i64 *tmp = cur; cur = nxt; nxt = tmp;
+        len = half;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Stored-level passes (tile + halo, global lexicographic smoothing).
+// --------------------------------------------------------------------------
+struct LevelArgs {
+    int l, n, tile, halo, nu;
+    int maxlen, maxc, maxch;
+    const Scale *sc;
+    const i64 *u_src;          // level l iterate, or level l-1 for the FMG interpolation
+    const i64 *g;              // G_l; NULL on the finest level (read f instead)
+    const double *f;
+    const i64 *uc_src;         // up pass: corrected level l-1
+    i64 *u_out;                // level l after the pass (tile), when u_out_f64 is NULL
+    double *u_out_f64;         // finest level without SR: the FP64 solution
+    i64 *uc_out, *gc_out;      // down pass: restricted solution and tau rhs on level l-1
+};
+
+struct LevelSmem {
+    i64 *uo, *un, *g, *c, *X, *Y;
+    int L0, L1, C0, C1;
+};
+
+__device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs &a) {
+    LevelSmem m;
+    m.L0 = max(0, s - a.halo);
+    m.L1 = min(a.n, s + a.tile + a.halo);
+    m.C0 = (m.L0 >> 1) - 2;
+    m.C1 = ((m.L1 - 1) >> 1) + 3;
+    m.uo = sm;
+    m.un = m.uo + a.maxlen;
+    m.g = m.un + a.maxlen;
+    m.c = m.g + a.maxlen;
+    m.X = m.c + a.maxc;
+    m.Y = m.X + a.maxch;
+    return m;
+}
+
+__device__ void load_g(LevelSmem &m, const LevelArgs &a) {
+    const int k = a.sc->Sg0;
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+        m.g[i - m.L0] = a.g ? a.g[i] : f64_to_fixed(a.f[i], k);
+}
+
+__device__ i64 *smooth_range(LevelSmem &m, int n, int nu, int gsh) {
+    int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
+    int hi = (m.L1 == n) ? n : m.L1 - 1;
+    i64 *a = m.uo, *b = m.un;
+    for (int k = 0; k < nu; ++k) {
+        lex_sweep<false>(a, b, m.g, gsh, m.L0, lo, hi, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            if (i < lo || i >= hi) b[i - m.L0] = a[i - m.L0];
+        __syncthreads();
+        i64 *tmp = a; a = b; b = tmp;
+        if (lo > 0) ++lo;
+        if (hi < n) --hi;
+    }
+    return a;
+}
+
+__device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
+    if (j < 0) return -src[-j - 1];
+    if (j >= nc) return -src[2 * nc - 1 - j];
+    return src[j];
+}
+
+template <bool FROM_PI>
+__global__ void level_down_kernel(LevelArgs a) {
+    extern __shared__ i64 smi[];
+    const int s = blockIdx.x * a.tile;
+    const int n = a.n, nc = n >> 1;
+    LevelSmem m = level_smem(smi, s, a);
+    load_g(m, a);
+    if (FROM_PI) {
+        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
+            m.c[j - m.C0] = coarse_reflect(a.u_src, j, nc);
+        __syncthreads();
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
+    } else {
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.uo[i - m.L0] = a.u_src[i];
+    }
+    __syncthreads();
+    const i64 *u = smooth_range(m, n, a.nu, 2 * a.l - 2);
+    const int tsh = 2 * a.l - 4;
+    for (int J = (s >> 1) + (int)threadIdx.x; J < ((s + a.tile) >> 1); J += (int)blockDim.x) {
+        int i0 = 2 * J - m.L0;
+        i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
+        i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
+        a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
+        a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+    }
+    for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) a.u_out[i] = u[i - m.L0];
+}
+
+// Up pass (Eq. 4): U_l += P (U_{l-1} - R U_l) (rounded to units), then nu sweeps.
+__global__ void level_up_kernel(LevelArgs a) {
+    extern __shared__ i64 smi[];
+    const int s = blockIdx.x * a.tile;
+    const int n = a.n, nc = n >> 1;
+    LevelSmem m = level_smem(smi, s, a);
+    load_g(m, a);
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) m.uo[i - m.L0] = a.u_src[i];
+    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) {
+        i64 v = 0;
+        if (j >= -1 && j <= nc) {
+            int jj = (j < 0) ? 0 : ((j >= nc) ? nc - 1 : j);
+            i64 cj = a.uc_src[jj] - ((a.u_src[2 * jj] + a.u_src[2 * jj + 1]) >> 1);
+            v = (j == jj) ? cj : -cj;
+        }
+        m.c[j - m.C0] = v;
+    }
+    __syncthreads();
+    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
+        int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+        m.uo[i - m.L0] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
+    }
+    __syncthreads();
+    const i64 *u = smooth_range(m, n, a.nu, 2 * a.l - 2);
+    if (a.u_out_f64) {
+        const int S = a.sc->S;
+        for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x)
+            a.u_out_f64[i] = fixed_to_f64(u[i - m.L0], S);
+    } else {
+        for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) a.u_out[i] = u[i - m.L0];
+    }
+}
+
+// --------------------------------------------------------------------------
+// SR level (Fig. 3): one block per segment.
+// --------------------------------------------------------------------------
+struct SegArgs {
+    int M, n, W, b, nu;
+    int maxlen, maxc, maxch;
+    const Scale *sc;
+    const double *f;
+    const i64 *uc_src;
+    i64 *uc_out, *gc_out, *seam;
+    double *u_out;
+};
+
+struct SegSmem {
+    i64 *uo, *un, *g, *c, *X, *Y;
+    int e0, e1, lo, hi, C0, C1;
+};
+
+__device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
+    SegSmem m;
+    m.e0 = max(0, s - a.b);
+    m.e1 = min(a.n, s + a.W + a.b);
+    m.lo = (m.e0 > 0) ? m.e0 - 1 : 0;
+    m.hi = (m.e1 < a.n) ? m.e1 + 1 : a.n;
+    m.C0 = (m.lo >> 1) - 2;
+    m.C1 = ((m.hi - 1) >> 1) + 3;
+    m.uo = sm;
+    m.un = m.uo + a.maxlen;
+    m.g = m.un + a.maxlen;
+    m.c = m.g + a.maxlen;
+    m.X = m.c + a.maxc;
+    m.Y = m.X + a.maxch;
+    return m;
+}
+
+__device__ void seg_load(SegSmem &m, const SegArgs &a) {
+    const int nc = a.n >> 1, k = a.sc->Sg0;
+    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
+        m.c[j - m.C0] = coarse_reflect(a.uc_src, j, nc);
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
+        m.g[i - m.lo] = f64_to_fixed(a.f[i], k);
+    __syncthreads();
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
+        i64 v = fmg_interp(m.c, m.C0, i);
+        m.uo[i - m.lo] = v;
+        m.un[i - m.lo] = v;
+    }
+    __syncthreads();
+}
+
+__global__ void sr_pre_kernel(SegArgs a) {
+    extern __shared__ i64 smi[];
+    const int s = blockIdx.x * a.W;
+    const int n = a.n, nc = n >> 1;
+    SegSmem m = seg_smem(smi, a, s);
+    seg_load(m, a);
+    const int gsh = 2 * a.M - 2, tsh = 2 * a.M - 4;
+    i64 *p = m.uo, *q = m.un;
+    for (int k = 0; k < a.nu; ++k) {
+        lex_sweep<false>(p, q, m.g, gsh, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        i64 *tmp = p; p = q; q = tmp;
+    }
+    const i64 *u = p;
+    const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) {
+        int i0 = 2 * J - m.lo;
+        a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
+        bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
+        if (!edge) {
+            i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
+            i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
+            a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+        }
+    }
+    if (threadIdx.x < 6) {
+        int k = threadIdx.x;
+        int i = (k < 3) ? s + k : s + a.W - 6 + k;
+        a.seam[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
+    }
+}
+
+// tau rhs at the two coarse cells of each interior segment boundary from the
+// assembled fine values (seams) and the restricted solution.
+__global__ void seam_tau_kernel(SegArgs a, int nseg) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nseg - 1) return;
+    const int s = (k + 1) * a.W;
+    const int kg = a.sc->Sg0, tsh = 2 * a.M - 4;
+    const i64 *L = a.seam + (size_t)k * 6, *R = a.seam + (size_t)(k + 1) * 6;
+    const i64 f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
+    const int J = (s >> 1) - 1;
+    const i64 hm1 = a.uc_out[J - 1], h0 = a.uc_out[J], h1 = a.uc_out[J + 1], h2 = a.uc_out[J + 2];
+    {
+        i64 tau = ((h0 - hm1) - (h1 - h0)) - 2 * ((f2 - f3) - (p0 - f1));
+        i64 g0 = f64_to_fixed(a.f[2 * J], kg), g1 = f64_to_fixed(a.f[2 * J + 1], kg);
+        a.gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+    }
+    {
+        const int J2 = J + 1;
+        i64 tau = ((h1 - h0) - (h2 - h1)) - 2 * ((p0 - f1) - (p2 - p1));
+        i64 g0 = f64_to_fixed(a.f[2 * J2], kg), g1 = f64_to_fixed(a.f[2 * J2 + 1], kg);
+        a.gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+    }
+}
+
+__global__ void sr_post_kernel(SegArgs a) {
+    extern __shared__ i64 smi[];
+    const int s = blockIdx.x * a.W;
+    const int n = a.n;
+    SegSmem m = seg_smem(smi, a, s);
+    seg_load(m, a);
+    const int gsh = 2 * a.M - 2;
+    i64 *p = m.uo, *q = m.un;
+    for (int k = 0; k < a.nu; ++k) {
+        for (int J = (m.e0 >> 1) + (int)threadIdx.x; J < (m.e1 >> 1); J += (int)blockDim.x) {
+            int i0 = 2 * J - m.lo;
+            i64 r = m.c[J - m.C0] - ((p[i0] + p[i0 + 1]) >> 1);
+            p[i0] += r;
+            p[i0 + 1] += r;
+        }
+        __syncthreads();
+        lex_sweep<false>(p, q, m.g, gsh, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
+        i64 *tmp = p; p = q; q = tmp;
+    }
+    const int S = a.sc->S;
+    for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
+        a.u_out[i] = fixed_to_f64(p[i - m.lo], S);
+}
+
+// --------------------------------------------------------------------------
+// Coarse tail (one block, levels M0..Mc in shared memory); the coarsest
+// level is solved in FP64 with the dense inverse.
+// --------------------------------------------------------------------------
+struct TailArgs {
+    int M0, Mc, nu1, nu2, mode;
+    const Scale *sc;
+    const i64 *u_in;
+    const i64 *g_in;           // G_Mc, or NULL to read f
+    const double *f;
+    i64 *u_out;
+    double *u_out_f64;         // whole problem in the tail: the FP64 solution
+    const double *Ainv;
+};
+
+struct TailSmem {
+    i64 *u, *g, *S, *X, *Y;
+    int M0;
+    __device__ int off(int l) const { return (1 << l) - (1 << M0); }
+};
+
+__device__ void tail_smooth(TailSmem &m, int l, int nu) {
+    const int n = 1 << l;
+    i64 *u = m.u + m.off(l), *g = m.g + m.off(l);
+    for (int k = 0; k < nu; ++k) {
+        lex_sweep<true>(u, m.S, g, 2 * l - 2, 0, 0, n, n, (k & 1) == 0,
+                        ((n + (int)blockDim.x - 1) / (int)blockDim.x) | 1, m.X, m.Y);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = m.S[i];
+        __syncthreads();
+    }
+}
+
+__device__ void tail_down(TailSmem &m, int l, int nu) {
+    tail_smooth(m, l, nu);
+    const int nc = 1 << (l - 1);
+    const i64 *u = m.u + m.off(l), *g = m.g + m.off(l);
+    i64 *uc = m.u + m.off(l - 1), *gc = m.g + m.off(l - 1);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x) {
+        int i0 = 2 * J;
+        i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
+        i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
+        uc[J] = (u[i0] + u[i0 + 1]) >> 1;
+        gc[J] = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4);
+    }
+    __syncthreads();
+}
+
+// U_M0 = A^{-1} g in FP64: value u = A^{-1} (G 2^-(Sg0+2 M0)) times 2^S.
+__device__ void tail_coarsest(TailSmem &m, const double *Ainv, const Scale *sc) {
+    const int n0 = 1 << m.M0;
+    i64 *u = m.u + m.off(m.M0);
+    const i64 *g = m.g + m.off(m.M0);
+    const int gexp = sc->Sg0 + 2 * m.M0, S = sc->S;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < n0; ++j) s = fma(Ainv[i * n0 + j], fixed_to_f64(g[j], gexp), s);
+        m.S[i] = f64_to_fixed(s, S);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) u[i] = m.S[i];
+    __syncthreads();
+}
+
+__device__ void tail_up(TailSmem &m, int l, int nu) {
+    const int n = 1 << l, nc = n >> 1;
+    i64 *u = m.u + m.off(l);
+    const i64 *uc = m.u + m.off(l - 1);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x) m.S[J] = uc[J] - ((u[2 * J] + u[2 * J + 1]) >> 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+        i64 cn = (nb < 0) ? -m.S[0] : ((nb >= nc) ? -m.S[nc - 1] : m.S[nb]);
+        u[i] += (3 * m.S[J] + cn + 2) >> 2;
+    }
+    __syncthreads();
+    tail_smooth(m, l, nu);
+}
+
+__device__ void tail_interp(TailSmem &m, int l) {
+    const int n = 1 << l, nc = n >> 1;
+    const i64 *uc = m.u + m.off(l - 1);
+    i64 *u = m.u + m.off(l);
+    for (int j = (int)threadIdx.x - 2; j < nc + 2; j += (int)blockDim.x)
+        if (j >= -2) m.S[j + 2] = coarse_reflect(uc, j, nc);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = fmg_interp(m.S, -2, i);
+    __syncthreads();
+}
+
+__global__ void tail_kernel(TailArgs a) {
+    extern __shared__ i64 smi[];
+    TailSmem m;
+    m.M0 = a.M0;
+    const int tot = (1 << (a.Mc + 1)) - (1 << a.M0);
+    m.u = smi;
+    m.g = m.u + tot;
+    m.S = m.g + tot;
+    m.X = m.S + (1 << a.Mc) + 8;
+    m.Y = m.X + blockDim.x;
+    const int nMc = 1 << a.Mc, kg = a.sc->Sg0;
+    for (int i = threadIdx.x; i < nMc; i += blockDim.x) {
+        m.g[m.off(a.Mc) + i] = a.g_in ? a.g_in[i] : f64_to_fixed(a.f[i], kg);
+        if (a.mode == 1) m.u[m.off(a.Mc) + i] = a.u_in[i];
+    }
+    __syncthreads();
+    if (a.mode == 0) {
+        for (int l = a.Mc; l > a.M0; --l) {
+            const i64 *g = m.g + m.off(l);
+            i64 *gc = m.g + m.off(l - 1);
+            for (int J = threadIdx.x; J < (1 << (l - 1)); J += blockDim.x) gc[J] = (g[2 * J] + g[2 * J + 1] + 1) >> 1;
+            __syncthreads();
+        }
+        tail_coarsest(m, a.Ainv, a.sc);
+        for (int k = a.M0; k < a.Mc; ++k) {
+            tail_interp(m, k + 1);
+            for (int l = k + 1; l > a.M0; --l) tail_down(m, l, a.nu1);
+            tail_coarsest(m, a.Ainv, a.sc);
+            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up(m, l, a.nu2);
+        }
+    } else {
+        for (int l = a.Mc; l > a.M0; --l) tail_down(m, l, a.nu1);
+        tail_coarsest(m, a.Ainv, a.sc);
+        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up(m, l, a.nu2);
+    }
+    if (a.u_out_f64) {
+        const int S = a.sc->S;
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out_f64[i] = fixed_to_f64(m.u[m.off(a.Mc) + i], S);
+    } else {
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out[i] = m.u[m.off(a.Mc) + i];
+    }
+}
+
+}  // namespace fx
+}  // namespace srfmg

@@ -20,8 +20,10 @@ namespace srfmg {
 // 2^-72 is far below the FP64 rounding of any value the recurrence produces.
 constexpr int kTrunc = 72;
 
-// Chunk length of the tiled and segment sweeps (one chunk per thread).
-constexpr int kChunk = 16;
+// Chunk length of the tiled and segment sweeps (one chunk per thread).  Odd,
+// so that the threads of a warp, each walking its own chunk, touch distinct
+// shared-memory banks (an even stride of 8-byte words serialises the warp).
+constexpr int kChunk = 17;
 
 // Exact 2^k as a double, -1022 <= k <= 1023.
 __device__ __forceinline__ double exp2i(int k) {
@@ -521,7 +523,7 @@ __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
     for (int k = 0; k < nu; ++k) {
-        lex_sweep<true>(u, m.S, g, 0, 0, n, n, (k & 1) == 0, (n + (int)blockDim.x - 1) / (int)blockDim.x,
+        lex_sweep<true>(u, m.S, g, 0, 0, n, n, (k & 1) == 0, ((n + (int)blockDim.x - 1) / (int)blockDim.x) | 1,
                         m.X, m.Y);
         for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = m.S[i];
         __syncthreads();

@@ -51,10 +51,14 @@ CASES = [
 ]
 
 
+PRECISIONS = [0, 1]       # SRFMG_FP64, SRFMG_MIXED (64-bit fixed point)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("M,nRS,W,b,nu1,nu2,M0", CASES)
-def test_fp64_parity_small(M, nRS, W, b, nu1, nu2, M0):
+def test_parity_small(M, nRS, W, b, nu1, nu2, M0, precision):
     f, _, _ = workloads.sine_series(M, 8 if M <= 10 else 32, seed=M)
-    kw = dict(n_sr_levels=nRS, nu1=nu1, nu2=nu2, log2_n_coarsest=M0)
+    kw = dict(n_sr_levels=nRS, nu1=nu1, nu2=nu2, log2_n_coarsest=M0, precision=precision)
     if nRS:
         kw.update(segment_width=W, buffer_width=b)
     u = gpu_solve(M, f, **kw)
@@ -62,12 +66,19 @@ def test_fp64_parity_small(M, nRS, W, b, nu1, nu2, M0):
     assert rel_maxnorm(u, ref) <= TOL
 
 
-def test_fp64_parity_full_size():
+@pytest.fixture(scope="module")
+def full_size_case():
     # the N = 2^24 workload: 4096 segments of 4096 cells, 8 buffer cells, V(1,1)
     M, W, b = 24, 4096, 8
     f, ue, c = workloads.sine_series(M, 32, seed=1)
-    u = gpu_solve(M, f, segment_width=W, buffer_width=b)
     ref = oracle.fmg_v(oracle.sr_params(M, W, b, nRS=1), f)
+    return M, W, b, f, ue, ref
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_parity_full_size(full_size_case, precision):
+    M, W, b, f, ue, ref = full_size_case
+    u = gpu_solve(M, f, segment_width=W, buffer_width=b, precision=precision)
     assert rel_maxnorm(u, ref) <= TOL
     # discretization accuracy of the GPU result: error vs exact within 1.5x the oracle's
     err_gpu = np.linalg.norm(u - ue)
