@@ -174,7 +174,8 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1207_6720_gb300/csrc/srfmg_kernels.cuh", "paper_1207_6720_gb300/csrc/srfmg.cu"):
+    for rel in ("paper_1207_6720_gb300/csrc/srfmg_kernels.cuh", "paper_1207_6720_gb300/csrc/srfmg_fixed.cuh",
+                "paper_1207_6720_gb300/csrc/srfmg.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

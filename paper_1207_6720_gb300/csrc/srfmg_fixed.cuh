@@ -115,10 +115,14 @@ __device__ void lex_sweep(const i64 *__restrict__ uo, i64 *__restrict__ un, cons
 
     for (int ch = t; ch < nch; ch += T) {
         const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        i64 p = 0;
+        i64 p = 0, ffar = 0;
         for (int q = q0; q < q1; ++q) {
             const int i = asc ? q : n - 1 - q;
-            i64 r = shr_round(g[i - base], gsh) - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+            // the face shared with the previous cell in sweep order is computed once
+            const i64 fnear = (q == q0) ? (asc ? flux_lo(uo, base, i) : flux_hi(uo, base, i, n)) : ffar;
+            ffar = asc ? flux_hi(uo, base, i, n) : flux_lo(uo, base, i);
+            const i64 d = asc ? (fnear - ffar) : (ffar - fnear);
+            i64 r = shr_round(g[i - base], gsh) - d;
             if (i == start_wall) p = r / 3;
             else if (i == end_wall) p = 0;           // recomputed below
             else p = (q == q0) ? ((r + 1) >> 1) : ((r + p + 1) >> 1);
@@ -232,8 +236,12 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     i64 *cur = smi, *nxt = smi + chunk;
     const long long base = (long long)blockIdx.x * chunk;
     const int k = a.sc->Sg0;              // f 2^-2M 2^(Sg0+2M) = f 2^Sg0
-    for (int i = threadIdx.x; i < chunk; i += blockDim.x)
-        cur[i] = a.from_f ? f64_to_fixed(a.f[base + i], k) : a.in[base + i];
+    if (a.from_f) stage_range(cur, a.f + base, chunk);
+    else stage_range(cur, a.in + base, chunk);
+    stage_wait();
+    __syncthreads();
+    if (a.from_f)
+        for (int i = threadIdx.x; i < chunk; i += blockDim.x) cur[i] = f64_to_fixed(__longlong_as_double(cur[i]), k);
     __syncthreads();
     int len = chunk;
     for (int l = a.lin; l > a.lstop && len > 1; --l) {
@@ -286,10 +294,16 @@ __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs 
     return m;
 }
 
-__device__ void load_g(LevelSmem &m, const LevelArgs &a) {
+// Issue the staging copies of G_l (or of f, converted after the wait).
+__device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
+    if (a.g) stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
+    else stage_range(m.g, a.f + m.L0, m.L1 - m.L0);
+}
+__device__ void convert_g(LevelSmem &m, const LevelArgs &a) {
+    if (a.g) return;
     const int k = a.sc->Sg0;
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-        m.g[i - m.L0] = a.g ? a.g[i] : f64_to_fixed(a.f[i], k);
+        m.g[i - m.L0] = f64_to_fixed(__longlong_as_double(m.g[i - m.L0]), k);
 }
 
 __device__ i64 *smooth_range(LevelSmem &m, int n, int nu, int gsh) {
@@ -320,16 +334,17 @@ __global__ void level_down_kernel(LevelArgs a) {
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a);
-    load_g(m, a);
+    stage_g_async(m, a);
+    if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
+    else stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_wait();
+    __syncthreads();
+    convert_g(m, a);
     if (FROM_PI) {
-        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
-            m.c[j - m.C0] = coarse_reflect(a.u_src, j, nc);
+        fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
         for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
             m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
-    } else {
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.uo[i - m.L0] = a.u_src[i];
     }
     __syncthreads();
     const i64 *u = smooth_range(m, n, a.nu, 2 * a.l - 2);
@@ -350,17 +365,21 @@ __global__ void level_up_kernel(LevelArgs a) {
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a);
-    load_g(m, a);
-    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) m.uo[i - m.L0] = a.u_src[i];
-    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) {
-        i64 v = 0;
-        if (j >= -1 && j <= nc) {
-            int jj = (j < 0) ? 0 : ((j >= nc) ? nc - 1 : j);
-            i64 cj = a.uc_src[jj] - ((a.u_src[2 * jj] + a.u_src[2 * jj + 1]) >> 1);
-            v = (j == jj) ? cj : -cj;
-        }
-        m.c[j - m.C0] = v;
+    stage_g_async(m, a);
+    stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_wait();
+    __syncthreads();
+    convert_g(m, a);
+    // c_J = U_{l-1,J} - (R U_l)_J, children from the staged tile where they lie in it
+    for (int j = max(m.C0, 0) + (int)threadIdx.x; j < min(m.C1, nc); j += (int)blockDim.x) {
+        const int i0 = 2 * j;
+        i64 r = (i0 >= m.L0 && i0 + 1 < m.L1) ? ((m.uo[i0 - m.L0] + m.uo[i0 + 1 - m.L0]) >> 1)
+                                               : ((a.u_src[i0] + a.u_src[i0 + 1]) >> 1);
+        m.c[j - m.C0] -= r;
     }
+    __syncthreads();
+    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     __syncthreads();
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
         int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
@@ -414,10 +433,13 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
 
 __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1, k = a.sc->Sg0;
-    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
-        m.c[j - m.C0] = coarse_reflect(a.uc_src, j, nc);
+    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_range(m.g, a.f + m.lo, m.hi - m.lo);
+    stage_wait();
+    __syncthreads();
+    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
-        m.g[i - m.lo] = f64_to_fixed(a.f[i], k);
+        m.g[i - m.lo] = f64_to_fixed(__longlong_as_double(m.g[i - m.lo]), k);
     __syncthreads();
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
         i64 v = fmg_interp(m.c, m.C0, i);
@@ -606,10 +628,14 @@ __global__ void tail_kernel(TailArgs a) {
     m.X = m.S + (1 << a.Mc) + 8;
     m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc, kg = a.sc->Sg0;
-    for (int i = threadIdx.x; i < nMc; i += blockDim.x) {
-        m.g[m.off(a.Mc) + i] = a.g_in ? a.g_in[i] : f64_to_fixed(a.f[i], kg);
-        if (a.mode == 1) m.u[m.off(a.Mc) + i] = a.u_in[i];
-    }
+    if (a.g_in) stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
+    else stage_range(m.g + m.off(a.Mc), a.f, nMc);
+    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
+    stage_wait();
+    __syncthreads();
+    if (!a.g_in)
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x)
+            m.g[m.off(a.Mc) + i] = f64_to_fixed(__longlong_as_double(m.g[m.off(a.Mc) + i]), kg);
     __syncthreads();
     if (a.mode == 0) {
         for (int l = a.Mc; l > a.M0; --l) {

@@ -47,6 +47,43 @@ __device__ __forceinline__ double coarse_reflect(const double *src, int base, in
     return src[j - base];
 }
 
+// Asynchronous staging of global memory into shared memory: cp.async copies of
+// 8 bytes, issued by all threads of the block and all in flight at once, then
+// one wait.  (A loop of plain loads would pay one L2 round trip per
+// iteration.)
+__device__ __forceinline__ void stage8(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    size_t g = __cvta_generic_to_global(gmem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+}
+// copy count 8-byte words src[0..count) to dst[0..count)
+__device__ __forceinline__ void stage_range(void *dst, const void *src, int count) {
+    char *d = (char *)dst;
+    const char *g = (const char *)src;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) stage8(d + 8 * (size_t)k, g + 8 * (size_t)k);
+}
+// wait for this thread's copies; follow with __syncthreads() before reading
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Stage coarse cells [C0, C1) of a level of nc cells into c[0 .. C1-C0), with
+// the odd reflection for the (at most two per side) ghost cells.  Two-phase:
+// stage_coarse_async() issues the copies of the interior part;
+// fill_coarse_ghosts() runs after the wait and a barrier.
+template <typename T>
+__device__ __forceinline__ void stage_coarse_async(T *c, const T *src, int C0, int C1, int nc) {
+    const int j0 = max(C0, 0), j1 = min(C1, nc);
+    stage_range(c + (j0 - C0), src + j0, j1 - j0);
+}
+template <typename T>
+__device__ __forceinline__ void fill_coarse_ghosts(T *c, int C0, int C1, int nc) {
+    for (int j = C0 + (int)threadIdx.x; j < C1; j += (int)blockDim.x) {
+        if (j < 0) c[j - C0] = -c[(-j - 1) - C0];
+        else if (j >= nc) c[j - C0] = -c[(2 * nc - 1 - j) - C0];
+    }
+}
+
 // Fourth order FMG interpolation Pi (Sec. 4): the left child of J takes
 // (-5, 35, 105, -7)/128 of coarse cells J-2..J+1, the right child the mirror.
 // Written as u_J plus a combination of the coarse fluxes G_{j+1/2} = u_{j+1}-u_j
@@ -122,10 +159,14 @@ __device__ void lex_sweep(const double *__restrict__ uo, double *__restrict__ un
     // phase 1: residuals and the zero-carry chain of every chunk
     for (int ch = t; ch < nch; ch += T) {
         const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        double p = 0.0;
+        double p = 0.0, ffar = 0.0;
         for (int q = q0; q < q1; ++q) {
             const int i = asc ? q : n - 1 - q;
-            double r = g[i - base] - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
+            // the face shared with the previous cell in sweep order is computed once
+            const double fnear = (q == q0) ? (asc ? flux_lo(uo, base, i) : flux_hi(uo, base, i, n)) : ffar;
+            ffar = asc ? flux_hi(uo, base, i, n) : flux_lo(uo, base, i);
+            const double d = asc ? (fnear - ffar) : (ffar - fnear);
+            double r = g[i - base] - d;
             double a = (i == start_wall || i == end_wall) ? r * (1.0 / 3.0) : scale2(r, -1);
             p = (q == q0 || i == start_wall) ? a : fma(0.5, p, a);
             un[i - base] = p;
@@ -213,8 +254,11 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     const int chunk = 1 << a.depth;
     double *cur = sm, *nxt = sm + chunk;
     const long long base = (long long)blockIdx.x * chunk;
-    for (int i = threadIdx.x; i < chunk; i += blockDim.x)
-        cur[i] = scale2(a.in[base + i], a.in_exp);
+    stage_range(cur, a.in + base, chunk);
+    stage_wait();
+    __syncthreads();
+    if (a.in_exp)
+        for (int i = threadIdx.x; i < chunk; i += blockDim.x) cur[i] = scale2(cur[i], a.in_exp);
     __syncthreads();
     int len = chunk;
     for (int l = a.lin; l > a.lstop && len > 1; --l) {
@@ -299,17 +343,19 @@ __global__ void level_down_kernel(LevelArgs a) {
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-        m.g[i - m.L0] = a.g_exp ? scale2(a.g[i], a.g_exp) : a.g[i];
+    stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
+    if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
+    else stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_wait();
+    __syncthreads();
+    if (a.g_exp)
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.g[i - m.L0] = scale2(m.g[i - m.L0], a.g_exp);
     if (FROM_PI) {
-        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
-            m.c[j - m.C0] = coarse_reflect(a.u_src, 0, j, nc);
+        fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
         for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
             m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
-    } else {
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.uo[i - m.L0] = a.u_src[i];
     }
     __syncthreads();
     const double *u = smooth_range(m, n, a.nu);
@@ -330,20 +376,24 @@ __global__ void level_up_kernel(LevelArgs a) {
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
-        m.g[i - m.L0] = a.g_exp ? scale2(a.g[i], a.g_exp) : a.g[i];
-        m.uo[i - m.L0] = a.u_src[i];
+    stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
+    stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_wait();
+    __syncthreads();
+    if (a.g_exp)
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.g[i - m.L0] = scale2(m.g[i - m.L0], a.g_exp);
+    // coarse correction c_J = u_{l-1,J} - (R u_l)_J; children from the staged
+    // tile, or from global memory for the few coarse cells at the tile ends
+    for (int j = max(m.C0, 0) + (int)threadIdx.x; j < min(m.C1, nc); j += (int)blockDim.x) {
+        const int i0 = 2 * j;
+        double r = (i0 >= m.L0 && i0 + 1 < m.L1) ? scale2(m.uo[i0 - m.L0] + m.uo[i0 + 1 - m.L0], -1)
+                                                  : scale2(a.u_src[i0] + a.u_src[i0 + 1], -1);
+        m.c[j - m.C0] -= r;
     }
-    // coarse correction c_J = u_{l-1,J} - (R u_l)_J with odd reflection
-    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) {
-        double v = 0.0;
-        if (j >= -1 && j <= nc) {
-            int jj = (j < 0) ? 0 : ((j >= nc) ? nc - 1 : j);
-            double cj = a.uc_src[jj] - scale2(a.u_src[2 * jj] + a.u_src[2 * jj + 1], -1);
-            v = (j == jj) ? cj : -cj;
-        }
-        m.c[j - m.C0] = v;
-    }
+    __syncthreads();
+    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     __syncthreads();
     // second order prolongation: child = 3/4 parent + 1/4 neighbour on its side
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
@@ -398,10 +448,13 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
 // be present in both) and the scaled rhs.
 __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1;
-    for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x)
-        m.c[j - m.C0] = coarse_reflect(a.uc_src, 0, j, nc);
+    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_range(m.g, a.f + m.lo, m.hi - m.lo);
+    stage_wait();
+    __syncthreads();
+    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
-        m.g[i - m.lo] = scale2(a.f[i], -2 * a.M);
+        m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
     __syncthreads();
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
         double v = fmg_interp(m.c, m.C0, i);
@@ -600,10 +653,12 @@ __global__ void tail_kernel(TailArgs a) {
     m.X = m.S + (1 << a.Mc) + 8;
     m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc;
-    for (int i = threadIdx.x; i < nMc; i += blockDim.x) {
-        m.g[m.off(a.Mc) + i] = a.g_exp ? scale2(a.g_in[i], a.g_exp) : a.g_in[i];
-        if (a.mode == 1) m.u[m.off(a.Mc) + i] = a.u_in[i];
-    }
+    stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
+    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
+    stage_wait();
+    __syncthreads();
+    if (a.g_exp)
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) m.g[m.off(a.Mc) + i] = scale2(m.g[m.off(a.Mc) + i], a.g_exp);
     __syncthreads();
     if (a.mode == 0) {
         for (int l = a.Mc; l > a.M0; --l) {
