@@ -21,7 +21,7 @@ using namespace srfmg;
 namespace {
 
 constexpr int kMaxTailLevel = 12;      // levels <= 12 fit one block's shared memory in FP64
-constexpr int kTailThreads = 1024;
+constexpr int kTailThreads = 512;     // one sweep chunk per thread up to 2^12 cells
 constexpr int kRhsThreads = 256;
 constexpr int kRhsDepth = 12;          // levels reduced per rhs-hierarchy launch
 constexpr int kTileMax = 2048;
@@ -143,20 +143,22 @@ std::vector<double> coarsest_inverse(int n) {
     return inv;
 }
 
-// Shared-memory layout of a block that sweeps up to `cells` cells: three
-// level buffers, the coarse cells it reads, two per-chunk carry arrays; one
-// thread per chunk (rounded up to whole warps).
+// Shared-memory layout of a block that sweeps up to `cells` cells: two level
+// buffers (solution, right-hand side), the coarse cells it reads, the
+// per-chunk carries and (fixed point) the restricted right-hand side of its
+// coarse cells; one thread per sweep chunk (rounded up to whole warps), which
+// the sweeps require.
 size_t sweep_layout(int cells, int *maxlen, int *maxc, int *maxch, int *threads) {
     *maxlen = cells + 2;
     *maxc = cells / 2 + 8;
     *maxch = (cells + kChunk - 1) / kChunk + 2;
     *threads = ((*maxch + 31) / 32) * 32;
-    return (size_t)3 * *maxlen + *maxc + 2 * *maxch;
+    return (size_t)2 * *maxlen + 2 * *maxc + *maxch;
 }
 
 size_t tail_smem_doubles(int M0, int Mc) {
     size_t tot = (1u << (Mc + 1)) - (1u << M0);
-    return 2 * tot + (1u << Mc) + 8 + 2 * kTailThreads;
+    return 2 * tot + (1u << Mc) + 8 + kTailThreads;
 }
 
 srfmg_status alloc_dev(srfmg_plan *h, double **out, size_t count) {
@@ -188,9 +190,9 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
     const int T = n < kTileMax ? n : kTileMax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
-    // after its range start (at most 6 * 17 = 102 cells, J+1 = ceil(72/17)),
-    // every sweep shrinks its range by one cell, and the tau stencil reaches
-    // 2 cells past the tile
+    // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9)), every sweep
+    // shrinks its range by one cell, and the tau stencil reaches 2 cells past
+    // the tile
     const int H = 112 * nu;
     o.lev.l = l;
     o.lev.n = n;

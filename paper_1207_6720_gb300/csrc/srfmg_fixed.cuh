@@ -89,98 +89,86 @@ __device__ __forceinline__ i64 fmg_interp(const i64 *c, int cbase, int i) {
     return (i64)((s + 64) >> 7);
 }
 
-// Fluxes F_{i-1/2}, F_{i+1/2} with the odd ghost at the walls.
-__device__ __forceinline__ i64 flux_lo(const i64 *u, int base, int i) {
-    return (i == 0) ? 2 * u[0 - base] : u[i - base] - u[i - 1 - base];
-}
-__device__ __forceinline__ i64 flux_hi(const i64 *u, int base, int i, int n) {
-    return (i == n - 1) ? -2 * u[i - base] : u[i + 1 - base] - u[i - base];
+// x / 3 rounded toward zero (C division) for |x| < 2^63: the high word of
+// x (2^64 + 2) / 3, plus one for negative x.
+__device__ __forceinline__ i64 div3(i64 x) {
+    return __mul64hi(x, 0x5555555555555556LL) + (x < 0 ? 1 : 0);
 }
 
-// Lexicographic Gauss-Seidel sweep, fixed point (same structure as the FP64
-// lex_sweep; see srfmg_kernels.cuh): residual r_i = gs_i - (F_{i-1/2} -
-// F_{i+1/2}) with the right-hand side shifted into solution units
-// (gs = G >> gsh), correction recurrence delta_i = (r_i + delta_{i-1}) / 2
-// (wall cells / 3), update U += delta.  Chunks of C cells, carries by a fixed
-// sum over the chunks that reach 64 cells back (KS = false) or a Kogge-Stone
-// scan (KS = true); a shift by 64 or more leaves nothing of a 63-bit value, so
-// dropping those terms changes nothing.
-template <bool KS>
-__device__ void lex_sweep(const i64 *__restrict__ uo, i64 *__restrict__ un, const i64 *__restrict__ g,
-                          int gsh, int base, int lo, int hi, int n, bool asc, int C, i64 *X, i64 *Y) {
-    const int t = threadIdx.x, T = blockDim.x;
+// Lexicographic Gauss-Seidel sweep in place, fixed point; the structure of the
+// FP64 lex_sweep (srfmg_kernels.cuh): residual r_i = gs_i - (F_{i-1/2} -
+// F_{i+1/2}) with the right-hand side already in solution units (gs),
+// correction recurrence delta_i = (r_i + delta_{i-1}) / 2 rounded half up
+// (wall cells / 3), update U += delta.  Chunks of C cells, one per thread
+// (the number of chunks of [lo, hi) must not exceed blockDim.x); the carry
+// into a chunk is the fixed sum over the chunks that reach 64 cells back: a
+// shift by 64 or more leaves nothing of a 63-bit value, so dropping those
+// terms changes nothing.  Integer sums are exact, so the residual is written
+// gs + u_{q-1} + u_{q+1} - 2 u_q in either direction.
+template <int C>
+__device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo, int hi, int n,
+                          bool asc, i64 *X) {
+    const int t = threadIdx.x;
     const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
     const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
-    const int start_wall = asc ? 0 : n - 1, end_wall = asc ? n - 1 : 0;
-
-    for (int ch = t; ch < nch; ch += T) {
-        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        i64 p = 0, ffar = 0;
-        for (int q = q0; q < q1; ++q) {
-            const int i = asc ? q : n - 1 - q;
-            // the face shared with the previous cell in sweep order is computed once
-            const i64 fnear = (q == q0) ? (asc ? flux_lo(uo, base, i) : flux_hi(uo, base, i, n)) : ffar;
-            ffar = asc ? flux_hi(uo, base, i, n) : flux_lo(uo, base, i);
-            const i64 d = asc ? (fnear - ffar) : (ffar - fnear);
-            i64 r = shr_round(g[i - base], gsh) - d;
-            if (i == start_wall) p = r / 3;
-            else if (i == end_wall) p = 0;           // recomputed below
-            else p = (q == q0) ? ((r + 1) >> 1) : ((r + p + 1) >> 1);
-            un[i - base] = p;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);
+    const bool wall1 = (q0 + k1 == n);
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int s = asc ? 1 : -1, a0 = asc ? -base : n - 1 - base;
+    i64 rr[C];
+    i64 p = 0, r_end = 0;
+    if (active) {
+        i64 w[C + 2];
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+        if (wall0) p = div3(gs[a0] + w[2] - 3 * w[1]);
+        if (wall1) r_end = gs[a0 + s * (n - 1)] + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const i64 r = gs[a0 + s * min(max(q0 + k, qmin), qmax)] + w[k] + w[k + 2] - 2 * w[k + 1];
+            const i64 pn = (r + p + 1) >> 1;
+            p = (k >= ka && k < kb) ? pn : p;
+            rr[k] = p;
         }
-        X[ch] = p;
+        X[t] = p;
     }
     __syncthreads();
-    const int J = (64 + C - 1) / C - 1;
-    i64 *src = X;
-    if (KS) {
-        i64 *dst = Y;
-        i64 y = (t < nch) ? X[t] : 0;
-        for (int d = 1; d * C < 64 && d < nch; d <<= 1) {
-            i64 prev = (t >= d && t < nch) ? (src[t - d] >> (C * d)) : 0;
-            y += prev;
-            if (t < nch) dst[t] = y;
-            __syncthreads();
-            i64 *tmp = src; src = dst; dst = tmp;
-        }
-    }
-    for (int ch = t; ch < nch; ch += T) {
+    if (active) {
+        constexpr int J = (64 + C - 1) / C - 1;
         i64 cin = 0;
-        if (KS) {
-            cin = (ch > 0) ? src[ch - 1] : 0;
-        } else {
-            for (int j = J; j >= 0; --j) {
-                i64 x = (ch - 1 - j >= 0) ? X[ch - 1 - j] : 0;
-                cin = (C < 64 ? (cin >> C) : 0) + x;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const i64 x = X[max(idx, 0)];
+            cin = (cin >> C) + (idx >= 0 ? x : 0);
+        }
+        i64 c = cin, dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            if (k >= k0) c >>= 1;                 // cin >> (k-k0+1)
+            if (k >= k0 && k < kb) {
+                dl = rr[k] + c;
+                u[a0 + s * (q0 + k)] += dl;
             }
         }
-        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        for (int q = q0; q < q1; ++q) {
-            const int i = asc ? q : n - 1 - q;
-            const int d = q - q0 + 1;
-            i64 dl = un[i - base];
-            if (d < 63) dl += cin >> d;
-            un[i - base] = uo[i - base] + dl;
-        }
-    }
-    __syncthreads();
-    const bool has_end = asc ? (hi == n) : (lo == 0);
-    if (has_end && t == 0) {
-        const int i = end_wall, ip = asc ? i - 1 : i + 1;
-        i64 r = shr_round(g[i - base], gsh) - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
-        i64 dprev = un[ip - base] - uo[ip - base];
-        un[i - base] = uo[i - base] + (r + dprev) / 3;
+        if (wall1) u[a0 + s * (n - 1)] += div3(r_end + dl);
     }
     __syncthreads();
 }
 
 // tau-corrected coarse right-hand side (Eqs. 6-7), exact: the tau term is a
 // combination of differences of u in solution units, moved into the coarse
-// right-hand side's units by a left shift of tsh = 2l - 4 bits; the
-// restricted right-hand side is the mean of the two children in the coarse
-// units (one rounding).  um2..u3: U at fine cells 2J-2 .. 2J+3.  tau is
-// moved by a multiplication with 2^tsh (a shift that is defined for negatives).
-__device__ __forceinline__ i64 tau_rhs(i64 g0, i64 g1, i64 um2, i64 um1, i64 u0, i64 u1, i64 u2, i64 u3,
+// right-hand side's units by a left shift of tsh = 2l - 4 bits and added to
+// gr, the restricted right-hand side (the mean of the two children in the
+// coarse units, rounded half up: restrict_rhs).  um2..u3: U at fine cells
+// 2J-2 .. 2J+3.  tau is moved by a multiplication with 2^tsh (a shift that is
+// defined for negatives).
+__device__ __forceinline__ i64 restrict_rhs(i64 g0, i64 g1) { return (g0 + g1 + 1) >> 1; }
+__device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1, i64 u2, i64 u3,
                                        int J, int nc, int tsh) {
     i64 hJ = (u0 + u1) >> 1;
     i64 Gl = (J == 0) ? 2 * hJ : hJ - ((um2 + um1) >> 1);
@@ -188,7 +176,7 @@ __device__ __forceinline__ i64 tau_rhs(i64 g0, i64 g1, i64 um2, i64 um1, i64 u0,
     i64 Fl = (J == 0) ? 2 * u0 : u0 - um1;
     i64 Fr = (J == nc - 1) ? -2 * u1 : u2 - u1;
     i64 tau = (Gl - Gr) - 2 * (Fl - Fr);
-    return ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+    return gr + tau * (1LL << tsh);
 }
 
 // --------------------------------------------------------------------------
@@ -274,8 +262,11 @@ struct LevelArgs {
     i64 *uc_out, *gc_out;      // down pass: restricted solution and tau rhs on level l-1
 };
 
+// Shared memory: u, gs (staged G or f, then the right-hand side in solution
+// units), the coarse cells, the chunk carries, gr (restricted G of the tile's
+// coarse cells, down pass): 2 maxlen + 2 maxc + maxch words.
 struct LevelSmem {
-    i64 *uo, *un, *g, *c, *X, *Y;
+    i64 *u, *gs, *c, *X, *gr;
     int L0, L1, C0, C1;
 };
 
@@ -285,41 +276,48 @@ __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs 
     m.L1 = min(a.n, s + a.tile + a.halo);
     m.C0 = (m.L0 >> 1) - 2;
     m.C1 = ((m.L1 - 1) >> 1) + 3;
-    m.uo = sm;
-    m.un = m.uo + a.maxlen;
-    m.g = m.un + a.maxlen;
-    m.c = m.g + a.maxlen;
+    m.u = sm;
+    m.gs = m.u + a.maxlen;
+    m.c = m.gs + a.maxlen;
     m.X = m.c + a.maxc;
-    m.Y = m.X + a.maxch;
+    m.gr = m.X + a.maxch;
     return m;
 }
 
-// Issue the staging copies of G_l (or of f, converted after the wait).
+// Issue the staging copies of G_l (or of f, converted by prepare_rhs).
 __device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
-    if (a.g) stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
-    else stage_range(m.g, a.f + m.L0, m.L1 - m.L0);
-}
-__device__ void convert_g(LevelSmem &m, const LevelArgs &a) {
-    if (a.g) return;
-    const int k = a.sc->Sg0;
-    for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-        m.g[i - m.L0] = f64_to_fixed(__longlong_as_double(m.g[i - m.L0]), k);
+    if (a.g) stage_range(m.gs, a.g + m.L0, m.L1 - m.L0);
+    else stage_range(m.gs, a.f + m.L0, m.L1 - m.L0);
 }
 
-__device__ i64 *smooth_range(LevelSmem &m, int n, int nu, int gsh) {
+// In place over the staged cells (pairs 2J, 2J+1; L0 and L1 are even):
+// gs = G >> gsh rounded (the right-hand side in solution units), with f
+// converted to G first on the finest level; with gr, also the restricted
+// right-hand side of the coarse cells [J0, J1).
+__device__ void prepare_rhs(LevelSmem &m, const LevelArgs &a, int gsh, i64 *gr, int J0, int J1) {
+    const bool from_f = (a.g == nullptr);
+    const int kg = a.sc->Sg0;
+    for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x) {
+        const int i = 2 * J - m.L0;
+        i64 g0 = m.gs[i], g1 = m.gs[i + 1];
+        if (from_f) {
+            g0 = f64_to_fixed(__longlong_as_double(g0), kg);
+            g1 = f64_to_fixed(__longlong_as_double(g1), kg);
+        }
+        if (gr && J >= J0 && J < J1) gr[J - J0] = restrict_rhs(g0, g1);
+        m.gs[i] = shr_round(g0, gsh);
+        m.gs[i + 1] = shr_round(g1, gsh);
+    }
+}
+
+__device__ void smooth_range(LevelSmem &m, int n, int nu) {
     int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
     int hi = (m.L1 == n) ? n : m.L1 - 1;
-    i64 *a = m.uo, *b = m.un;
     for (int k = 0; k < nu; ++k) {
-        lex_sweep<false>(a, b, m.g, gsh, m.L0, lo, hi, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            if (i < lo || i >= hi) b[i - m.L0] = a[i - m.L0];
-        __syncthreads();
-        i64 *tmp = a; a = b; b = tmp;
+        lex_sweep<kChunk>(m.u, m.gs, m.L0, lo, hi, n, (k & 1) == 0, m.X);
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
-    return a;
 }
 
 __device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
@@ -336,25 +334,27 @@ __global__ void level_down_kernel(LevelArgs a) {
     LevelSmem m = level_smem(smi, s, a);
     stage_g_async(m, a);
     if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
-    else stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    else stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
     stage_wait();
     __syncthreads();
-    convert_g(m, a);
+    const int J0 = s >> 1;
+    prepare_rhs(m, a, 2 * a.l - 2, m.gr, J0, (s + a.tile) >> 1);
     if (FROM_PI) {
         fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
         for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
+            m.u[i - m.L0] = fmg_interp(m.c, m.C0, i);
     }
     __syncthreads();
-    const i64 *u = smooth_range(m, n, a.nu, 2 * a.l - 2);
+    smooth_range(m, n, a.nu);
+    const i64 *u = m.u;
     const int tsh = 2 * a.l - 4;
-    for (int J = (s >> 1) + (int)threadIdx.x; J < ((s + a.tile) >> 1); J += (int)blockDim.x) {
+    for (int J = J0 + (int)threadIdx.x; J < ((s + a.tile) >> 1); J += (int)blockDim.x) {
         int i0 = 2 * J - m.L0;
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
         a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
-        a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+        a.gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
     }
     for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) a.u_out[i] = u[i - m.L0];
 }
@@ -366,27 +366,29 @@ __global__ void level_up_kernel(LevelArgs a) {
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a);
     stage_g_async(m, a);
-    stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
     stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
     stage_wait();
     __syncthreads();
-    convert_g(m, a);
-    // c_J = U_{l-1,J} - (R U_l)_J, children from the staged tile where they lie in it
+    prepare_rhs(m, a, 2 * a.l - 2, nullptr, 0, 0);
+    // c_J = U_{l-1,J} - (R U_l)_J from the staged tile; no correction for the
+    // coarse cells whose children lie outside it (they only reach the frozen
+    // end cells L0 and L1-1; see the FP64 kernel)
     for (int j = max(m.C0, 0) + (int)threadIdx.x; j < min(m.C1, nc); j += (int)blockDim.x) {
         const int i0 = 2 * j;
-        i64 r = (i0 >= m.L0 && i0 + 1 < m.L1) ? ((m.uo[i0 - m.L0] + m.uo[i0 + 1 - m.L0]) >> 1)
-                                               : ((a.u_src[i0] + a.u_src[i0 + 1]) >> 1);
-        m.c[j - m.C0] -= r;
+        const bool inside = i0 >= m.L0 && i0 + 1 < m.L1;
+        m.c[j - m.C0] = inside ? m.c[j - m.C0] - ((m.u[i0 - m.L0] + m.u[i0 + 1 - m.L0]) >> 1) : 0;
     }
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     __syncthreads();
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
         int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
-        m.uo[i - m.L0] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
+        m.u[i - m.L0] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
     }
     __syncthreads();
-    const i64 *u = smooth_range(m, n, a.nu, 2 * a.l - 2);
+    smooth_range(m, n, a.nu);
+    const i64 *u = m.u;
     if (a.u_out_f64) {
         const int S = a.sc->S;
         for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x)
@@ -409,8 +411,9 @@ struct SegArgs {
     double *u_out;
 };
 
+// Shared memory as LevelSmem: u, gs, c, X, gr (2 maxlen + 2 maxc + maxch words).
 struct SegSmem {
-    i64 *uo, *un, *g, *c, *X, *Y;
+    i64 *u, *gs, *c, *X, *gr;
     int e0, e1, lo, hi, C0, C1;
 };
 
@@ -422,30 +425,37 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
     m.hi = (m.e1 < a.n) ? m.e1 + 1 : a.n;
     m.C0 = (m.lo >> 1) - 2;
     m.C1 = ((m.hi - 1) >> 1) + 3;
-    m.uo = sm;
-    m.un = m.uo + a.maxlen;
-    m.g = m.un + a.maxlen;
-    m.c = m.g + a.maxlen;
+    m.u = sm;
+    m.gs = m.u + a.maxlen;
+    m.c = m.gs + a.maxlen;
     m.X = m.c + a.maxc;
-    m.Y = m.X + a.maxch;
+    m.gr = m.X + a.maxch;
     return m;
 }
 
-__device__ void seg_load(SegSmem &m, const SegArgs &a) {
-    const int nc = a.n >> 1, k = a.sc->Sg0;
+// Stage Pi U_{M-1} on [lo, hi) and the right-hand side: gs = G >> (2M-2) in
+// solution units with G converted from f; with gr, also the restricted
+// right-hand side of the segment's coarse cells [J0, J1).  The staged range
+// may start at an odd cell, so pairs are clipped to it.
+__device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) {
+    const int nc = a.n >> 1, kg = a.sc->Sg0, gsh = 2 * a.M - 2;
     stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
-    stage_range(m.g, a.f + m.lo, m.hi - m.lo);
+    stage_range(m.gs, a.f + m.lo, m.hi - m.lo);
     stage_wait();
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
-        m.g[i - m.lo] = f64_to_fixed(__longlong_as_double(m.g[i - m.lo]), k);
-    __syncthreads();
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
-        i64 v = fmg_interp(m.c, m.C0, i);
-        m.uo[i - m.lo] = v;
-        m.un[i - m.lo] = v;
+    for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
+        const int i0 = 2 * J;
+        const bool in0 = i0 >= m.lo, in1 = i0 + 1 < m.hi;
+        const i64 f0 = m.gs[max(i0 - m.lo, 0)], f1 = m.gs[min(i0 + 1 - m.lo, m.hi - 1 - m.lo)];
+        const i64 g0 = f64_to_fixed(__longlong_as_double(f0), kg);
+        const i64 g1 = f64_to_fixed(__longlong_as_double(f1), kg);
+        if (gr && J >= J0 && J < J1) gr[J - J0] = restrict_rhs(g0, g1);
+        if (in0) m.gs[i0 - m.lo] = shr_round(g0, gsh);
+        if (in1) m.gs[i0 + 1 - m.lo] = shr_round(g1, gsh);
     }
+    __syncthreads();
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) m.u[i - m.lo] = fmg_interp(m.c, m.C0, i);
     __syncthreads();
 }
 
@@ -454,15 +464,11 @@ __global__ void sr_pre_kernel(SegArgs a) {
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
     SegSmem m = seg_smem(smi, a, s);
-    seg_load(m, a);
-    const int gsh = 2 * a.M - 2, tsh = 2 * a.M - 4;
-    i64 *p = m.uo, *q = m.un;
-    for (int k = 0; k < a.nu; ++k) {
-        lex_sweep<false>(p, q, m.g, gsh, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        i64 *tmp = p; p = q; q = tmp;
-    }
-    const i64 *u = p;
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    seg_load(m, a, m.gr, J0, J1);
+    const int tsh = 2 * a.M - 4;
+    for (int k = 0; k < a.nu; ++k) lex_sweep<kChunk>(m.u, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    const i64 *u = m.u;
     for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) {
         int i0 = 2 * J - m.lo;
         a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
@@ -470,7 +476,7 @@ __global__ void sr_pre_kernel(SegArgs a) {
         if (!edge) {
             i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
             i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
-            a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+            a.gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
         }
     }
     if (threadIdx.x < 6) {
@@ -509,9 +515,8 @@ __global__ void sr_post_kernel(SegArgs a) {
     const int s = blockIdx.x * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(smi, a, s);
-    seg_load(m, a);
-    const int gsh = 2 * a.M - 2;
-    i64 *p = m.uo, *q = m.un;
+    seg_load(m, a, nullptr, 0, 0);
+    i64 *p = m.u;
     for (int k = 0; k < a.nu; ++k) {
         for (int J = (m.e0 >> 1) + (int)threadIdx.x; J < (m.e1 >> 1); J += (int)blockDim.x) {
             int i0 = 2 * J - m.lo;
@@ -520,8 +525,7 @@ __global__ void sr_post_kernel(SegArgs a) {
             p[i0 + 1] += r;
         }
         __syncthreads();
-        lex_sweep<false>(p, q, m.g, gsh, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        i64 *tmp = p; p = q; q = tmp;
+        lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
     const int S = a.sc->S;
     for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
@@ -544,20 +548,18 @@ struct TailArgs {
 };
 
 struct TailSmem {
-    i64 *u, *g, *S, *X, *Y;
+    i64 *u, *g, *S, *X;
     int M0;
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
 };
 
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
-    i64 *u = m.u + m.off(l), *g = m.g + m.off(l);
-    for (int k = 0; k < nu; ++k) {
-        lex_sweep<true>(u, m.S, g, 2 * l - 2, 0, 0, n, n, (k & 1) == 0,
-                        ((n + (int)blockDim.x - 1) / (int)blockDim.x) | 1, m.X, m.Y);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = m.S[i];
-        __syncthreads();
-    }
+    i64 *u = m.u + m.off(l);
+    const i64 *g = m.g + m.off(l);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m.S[i] = shr_round(g[i], 2 * l - 2);
+    __syncthreads();
+    for (int k = 0; k < nu; ++k) lex_sweep<kChunk>(u, m.S, 0, 0, n, n, (k & 1) == 0, m.X);
 }
 
 __device__ void tail_down(TailSmem &m, int l, int nu) {
@@ -570,7 +572,7 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
         uc[J] = (u[i0] + u[i0 + 1]) >> 1;
-        gc[J] = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4);
+        gc[J] = tau_rhs(restrict_rhs(g[i0], g[i0 + 1]), um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4);
     }
     __syncthreads();
 }
@@ -626,7 +628,6 @@ __global__ void tail_kernel(TailArgs a) {
     m.g = m.u + tot;
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
-    m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc, kg = a.sc->Sg0;
     if (a.g_in) stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
     else stage_range(m.g + m.off(a.Mc), a.f, nMc);

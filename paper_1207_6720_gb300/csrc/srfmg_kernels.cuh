@@ -20,10 +20,11 @@ namespace srfmg {
 // 2^-72 is far below the FP64 rounding of any value the recurrence produces.
 constexpr int kTrunc = 72;
 
-// Chunk length of the tiled and segment sweeps (one chunk per thread).  Odd,
-// so that the threads of a warp, each walking its own chunk, touch distinct
-// shared-memory banks (an even stride of 8-byte words serialises the warp).
-constexpr int kChunk = 17;
+// Chunk length of the sweeps (one chunk per thread).  Odd, so that the threads
+// of a warp, each reading its own chunk, touch distinct shared-memory banks
+// (an even stride of 8-byte words serialises the warp); short, so that a
+// block has many threads and each recurrence is a few dependent operations.
+constexpr int kChunk = 9;
 
 // Exact 2^k as a double, -1022 <= k <= 1023.
 __device__ __forceinline__ double exp2i(int k) {
@@ -106,10 +107,10 @@ __device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) 
 }
 
 // ---------------------------------------------------------------------------
-// Lexicographic Gauss-Seidel sweep (omega = 1) over the cells [lo, hi) of a
-// level of n cells held in shared memory (uo[i - base]: values before the
-// sweep, including the neighbours lo-1 and hi; un[i - base]: values after;
-// g[i - base]: scaled right-hand side).
+// Lexicographic Gauss-Seidel sweep (omega = 1), in place, over the cells
+// [lo, hi) of a level of n cells held in shared memory (u[i - base]; the
+// neighbours lo-1 and hi are read and left unchanged; g[i - base]: scaled
+// right-hand side over the same cells).
 //
 // Residual form.  With r_i = g_i - (F_{i-1/2} - F_{i+1/2}) the residual of the
 // old values (flux form, odd ghost at the walls), the sweep adds
@@ -120,101 +121,85 @@ __device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) 
 // a frozen patch neighbour, an approximation in a tile halo that is wider than
 // the recurrence's memory.
 //
-// delta is a first-order linear recurrence with multiplier 1/2.  Cells are
-// grouped in chunks of C consecutive cells aligned to the level (in sweep
-// order), one chunk per thread: each chunk runs the recurrence from a zero
-// carry, the carry into a chunk is then
-//   KS = false: the fixed sum  sum_{j<=J} 2^(-jC) X_{c-1-j}  of the chunk-end
-//               values of the J+1 preceding chunks, J+1 = ceil(kTrunc / C);
-//   KS = true:  a Kogge-Stone scan over all chunks of the range;
-// and every cell adds 2^-(d+1) times its chunk's carry (d: position in the
-// chunk).  Terms weighted below 2^-kTrunc are dropped, so the result is the
-// sequential sweep up to rounding.  With the fixed sum and level-aligned
-// chunks, a cell's value depends only on the data of the (J+2)C cells before
-// it, so two tiles that both hold a cell more than (J+2)C cells from their
-// range start compute bitwise the same value: tiles agree exactly with their
-// neighbours' halos, which keeps the tau correction consistent with the
-// restricted solution at tile edges.
+// delta is a first-order linear recurrence with multiplier 1/2.  In sweep
+// coordinates (q = i ascending, q = n-1-i descending) the cells are grouped in
+// chunks of C consecutive positions aligned to the level, one chunk per thread
+// (the number of chunks of [lo, hi) must not exceed blockDim.x).  Each chunk
+// runs the recurrence from a zero carry with its cells in registers; the carry
+// into a chunk is the fixed sum  sum_{j<=J} 2^(-jC) X_{c-1-j}  of the
+// chunk-end values of the J+1 preceding chunks, J+1 = ceil(kTrunc / C), and
+// the cell d places into its chunk's recurrence adds 2^-(d+1) times it.
+// Terms weighted below 2^-kTrunc are dropped, so the result is the sequential
+// sweep up to rounding.  With the fixed sum and level-aligned chunks, a cell's
+// value depends only on the data of the (J+2)C cells before it, so two tiles
+// that both hold a cell more than (J+2)C cells from their range start compute
+// bitwise the same value: tiles agree exactly with their neighbours' halos,
+// which keeps the tau correction consistent with the restricted solution at
+// tile edges.
 //
-// All threads of the block must call it.  X and Y hold one double per chunk
-// (KS = false: at least the number of chunks; KS = true: blockDim.x).
+// Every chunk runs the same unrolled code: the loads go to in-range addresses
+// (positions clamped to the staged cells) and cells outside [lo, hi) leave the
+// recurrence unchanged, so no thread of a warp waits on a divergent path; the
+// two wall cells are handled apart.  All threads of the block must call it.
+// X holds one double per thread.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double flux_lo(const double *u, int base, int i) {   // F_{i-1/2}
-    return (i == 0) ? scale2(u[0 - base], 1) : u[i - base] - u[i - 1 - base];
-}
-__device__ __forceinline__ double flux_hi(const double *u, int base, int i, int n) {   // F_{i+1/2}
-    return (i == n - 1) ? -scale2(u[i - base], 1) : u[i + 1 - base] - u[i - base];
-}
-
-template <bool KS>
-__device__ void lex_sweep(const double *__restrict__ uo, double *__restrict__ un,
-                          const double *__restrict__ g, int base, int lo, int hi, int n,
-                          bool asc, int C, double *X, double *Y) {
-    const int t = threadIdx.x, T = blockDim.x;
-    // sweep coordinate q: q = i ascending, q = n-1-i descending
+template <int C>
+__device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, int base, int lo, int hi,
+                          int n, bool asc, double *X) {
+    const int t = threadIdx.x;
     const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
     const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
-    const int start_wall = asc ? 0 : n - 1, end_wall = asc ? n - 1 : 0;
-
-    // phase 1: residuals and the zero-carry chain of every chunk
-    for (int ch = t; ch < nch; ch += T) {
-        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        double p = 0.0, ffar = 0.0;
-        for (int q = q0; q < q1; ++q) {
-            const int i = asc ? q : n - 1 - q;
-            // the face shared with the previous cell in sweep order is computed once
-            const double fnear = (q == q0) ? (asc ? flux_lo(uo, base, i) : flux_hi(uo, base, i, n)) : ffar;
-            ffar = asc ? flux_hi(uo, base, i, n) : flux_lo(uo, base, i);
-            const double d = asc ? (fnear - ffar) : (ffar - fnear);
-            double r = g[i - base] - d;
-            double a = (i == start_wall || i == end_wall) ? r * (1.0 / 3.0) : scale2(r, -1);
-            p = (q == q0 || i == start_wall) ? a : fma(0.5, p, a);
-            un[i - base] = p;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    // in-range cells [k0, k1) of the chunk; recurrence cells [ka, kb)
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);      // sweep position 0 (a wall) is swept
+    const bool wall1 = (q0 + k1 == n);               // sweep position n-1 (a wall) is swept
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    // sweep position q is u[a0 + s q]
+    const int s = asc ? 1 : -1, a0 = asc ? -base : n - 1 - base;
+    double rr[C];
+    double p = 0.0, r_end = 0.0;
+    if (active) {
+        double w[C + 2];   // u at positions q0-1 .. q0+C
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+        if (wall0) p = (g[a0] - (scale2(w[1], 1) - (w[2] - w[1]))) * (1.0 / 3.0);
+        if (wall1) {
+            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+            r_end = g[a0 + s * (n - 1)] - ((ue - um) - (-scale2(ue, 1)));
         }
-        X[ch] = p;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            const double r = gv - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
+            const double pn = fma(0.5, p, scale2(r, -1));
+            p = (k >= ka && k < kb) ? pn : p;
+            rr[k] = p;
+        }
+        X[t] = p;
     }
     __syncthreads();
-
-    // phase 2: carry into each chunk
-    const int J = (kTrunc + C - 1) / C - 1;
-    double *src = X;
-    if (KS) {
-        double *dst = Y;
-        double y = (t < nch) ? X[t] : 0.0;
-        for (int d = 1; d * C < kTrunc && d < nch; d <<= 1) {
-            double prev = (t >= d && t < nch) ? src[t - d] : 0.0;
-            y = fma(exp2i(-C * d), prev, y);
-            if (t < nch) dst[t] = y;
-            __syncthreads();
-            double *tmp = src; src = dst; dst = tmp;
-        }
-    }
-    // phase 3: fix-up and update
-    for (int ch = t; ch < nch; ch += T) {
+    if (active) {
+        constexpr int J = (kTrunc + C - 1) / C - 1;
         double cin = 0.0;
-        if (KS) {
-            cin = (ch > 0) ? src[ch - 1] : 0.0;
-        } else {
-            for (int j = J; j >= 0; --j) {
-                double x = (ch - 1 - j >= 0) ? X[ch - 1 - j] : 0.0;
-                cin = fma(exp2i(-C), cin, x);
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const double x = X[max(idx, 0)];
+            cin = fma(exp2i(-C), cin, idx >= 0 ? x : 0.0);
+        }
+        double c = cin, dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            if (k >= k0) c = scale2(c, -1);          // 2^-(k-k0+1) cin, exact
+            if (k >= k0 && k < kb) {
+                dl = rr[k] + c;
+                u[a0 + s * (q0 + k)] += dl;
             }
         }
-        const int q0 = max(qlo, (c_first + ch) * C), q1 = min(qhi, (c_first + ch + 1) * C);
-        for (int q = q0; q < q1; ++q) {
-            const int i = asc ? q : n - 1 - q;
-            double d = un[i - base];
-            if (q - q0 + 1 < kTrunc) d = fma(exp2i(-(q - q0 + 1)), cin, d);
-            un[i - base] = uo[i - base] + d;
-        }
-    }
-    __syncthreads();
-    const bool has_end = asc ? (hi == n) : (lo == 0);
-    if (has_end && t == 0) {
-        const int i = end_wall, ip = asc ? i - 1 : i + 1;
-        double r = g[i - base] - (flux_lo(uo, base, i) - flux_hi(uo, base, i, n));
-        double dprev = un[ip - base] - uo[ip - base];
-        un[i - base] = uo[i - base] + (r + dprev) * (1.0 / 3.0);
+        if (wall1) u[a0 + s * (n - 1)] += (r_end + dl) * (1.0 / 3.0);
     }
     __syncthreads();
 }
@@ -294,9 +279,11 @@ struct LevelArgs {
     double *gc_out;            // down pass: tau-corrected g_{l-1}
 };
 
-// Shared-memory layout of one stored-level block.
+// Shared-memory layout of one stored-level block (the host reserves
+// 2 maxlen + 2 maxc + maxch doubles; this path uses the first
+// 2 maxlen + maxc + maxch).
 struct LevelSmem {
-    double *uo, *un, *g, *c, *X, *Y;
+    double *u, *g, *c, *X;
     int L0, L1, C0, C1;       // fine range [L0,L1), coarse range [C0,C1)
 };
 
@@ -307,34 +294,26 @@ __device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H,
     m.L1 = min(n, s + T + H);
     m.C0 = (m.L0 >> 1) - 2;
     m.C1 = ((m.L1 - 1) >> 1) + 3;
-    m.uo = sm;
-    m.un = m.uo + maxlen;
-    m.g = m.un + maxlen;
+    m.u = sm;
+    m.g = m.u + maxlen;
     m.c = m.g + maxlen;
     m.X = m.c + maxc;
-    m.Y = m.X + maxch;
+    (void)maxch;
     return m;
 }
 
-// Smoothing of a loaded range by nu sweeps, ascending first and reversed
-// after every sweep (appendix "symmetrize").  The swept range shrinks by one
-// cell per sweep on each side that is not a wall, so that every sweep reads
-// neighbours the previous one wrote.  Returns the array holding the result.
-__device__ double *smooth_range(LevelSmem &m, int n, int nu) {
+// Smoothing of a loaded range by nu sweeps in place, ascending first and
+// reversed after every sweep (appendix "symmetrize").  The swept range
+// shrinks by one cell per sweep on each side that is not a wall, so that
+// every sweep reads neighbours the previous one wrote.
+__device__ void smooth_range(LevelSmem &m, int n, int nu) {
     int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
     int hi = (m.L1 == n) ? n : m.L1 - 1;
-    double *a = m.uo, *b = m.un;
     for (int k = 0; k < nu; ++k) {
-        lex_sweep<false>(a, b, m.g, m.L0, lo, hi, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        // cells of [L0, L1) outside the swept range keep their old values
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            if (i < lo || i >= hi) b[i - m.L0] = a[i - m.L0];
-        __syncthreads();
-        double *tmp = a; a = b; b = tmp;
+        lex_sweep<kChunk>(m.u, m.g, m.L0, lo, hi, n, (k & 1) == 0, m.X);
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
-    return a;
 }
 
 template <bool FROM_PI>
@@ -345,7 +324,7 @@ __global__ void level_down_kernel(LevelArgs a) {
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
     stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
     if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
-    else stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    else stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
     stage_wait();
     __syncthreads();
     if (a.g_exp)
@@ -355,10 +334,11 @@ __global__ void level_down_kernel(LevelArgs a) {
         fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
         for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.uo[i - m.L0] = fmg_interp(m.c, m.C0, i);
+            m.u[i - m.L0] = fmg_interp(m.c, m.C0, i);
     }
     __syncthreads();
-    const double *u = smooth_range(m, n, a.nu);
+    smooth_range(m, n, a.nu);
+    const double *u = m.u;
     // restriction of the solution and tau-corrected coarse rhs of the tile
     for (int J = (s >> 1) + threadIdx.x; J < ((s + a.tile) >> 1); J += blockDim.x) {
         int i0 = 2 * J - m.L0;
@@ -377,20 +357,21 @@ __global__ void level_up_kernel(LevelArgs a) {
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
     stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
-    stage_range(m.uo, a.u_src + m.L0, m.L1 - m.L0);
+    stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
     stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
     stage_wait();
     __syncthreads();
     if (a.g_exp)
         for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
             m.g[i - m.L0] = scale2(m.g[i - m.L0], a.g_exp);
-    // coarse correction c_J = u_{l-1,J} - (R u_l)_J; children from the staged
-    // tile, or from global memory for the few coarse cells at the tile ends
+    // coarse correction c_J = u_{l-1,J} - (R u_l)_J from the staged tile.  The
+    // coarse cells whose children lie outside it (at most two per tile end,
+    // never at a wall) get no correction: they only reach the frozen end cells
+    // L0 and L1-1, whose difference dies out inside the halo.
     for (int j = max(m.C0, 0) + (int)threadIdx.x; j < min(m.C1, nc); j += (int)blockDim.x) {
         const int i0 = 2 * j;
-        double r = (i0 >= m.L0 && i0 + 1 < m.L1) ? scale2(m.uo[i0 - m.L0] + m.uo[i0 + 1 - m.L0], -1)
-                                                  : scale2(a.u_src[i0] + a.u_src[i0 + 1], -1);
-        m.c[j - m.C0] -= r;
+        const bool inside = i0 >= m.L0 && i0 + 1 < m.L1;
+        m.c[j - m.C0] = inside ? m.c[j - m.C0] - scale2(m.u[i0 - m.L0] + m.u[i0 + 1 - m.L0], -1) : 0.0;
     }
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
@@ -399,10 +380,11 @@ __global__ void level_up_kernel(LevelArgs a) {
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
         int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
         double corr = scale2(fma(3.0, m.c[J - m.C0], m.c[nb - m.C0]), -2);
-        m.uo[i - m.L0] += corr;
+        m.u[i - m.L0] += corr;
     }
     __syncthreads();
-    const double *u = smooth_range(m, n, a.nu);
+    smooth_range(m, n, a.nu);
+    const double *u = m.u;
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
 }
 
@@ -422,8 +404,10 @@ struct SegArgs {
     double *u_out;             // post-leg: the solution
 };
 
+// (the host reserves 2 maxlen + 2 maxc + maxch doubles; this path uses the
+// first 2 maxlen + maxc + maxch)
 struct SegSmem {
-    double *uo, *un, *g, *c, *X, *Y;
+    double *u, *g, *c, *X;
     int e0, e1, lo, hi, C0, C1;
 };
 
@@ -435,17 +419,14 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
     m.hi = (m.e1 < a.n) ? m.e1 + 1 : a.n;
     m.C0 = (m.lo >> 1) - 2;
     m.C1 = ((m.hi - 1) >> 1) + 3;
-    m.uo = sm;
-    m.un = m.uo + a.maxlen;
-    m.g = m.un + a.maxlen;
+    m.u = sm;
+    m.g = m.u + a.maxlen;
     m.c = m.g + a.maxlen;
     m.X = m.c + a.maxc;
-    m.Y = m.X + a.maxch;
     return m;
 }
 
-// Load Pi u_{M-1} on [lo, hi) into both sweep buffers (the frozen cells must
-// be present in both) and the scaled rhs.
+// Load Pi u_{M-1} on [lo, hi) (patch and frozen cells) and the scaled rhs.
 __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1;
     stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
@@ -456,11 +437,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
         m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
     __syncthreads();
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
-        double v = fmg_interp(m.c, m.C0, i);
-        m.uo[i - m.lo] = v;
-        m.un[i - m.lo] = v;
-    }
+    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) m.u[i - m.lo] = fmg_interp(m.c, m.C0, i);
     __syncthreads();
 }
 
@@ -474,12 +451,8 @@ __global__ void sr_pre_kernel(SegArgs a) {
     const int n = a.n, nc = n >> 1;
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
-    double *p = m.uo, *q = m.un;
-    for (int k = 0; k < a.nu; ++k) {
-        lex_sweep<false>(p, q, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        double *tmp = p; p = q; q = tmp;
-    }
-    const double *u = p;
+    for (int k = 0; k < a.nu; ++k) lex_sweep<kChunk>(m.u, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    const double *u = m.u;
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
     for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
         int i0 = 2 * J - m.lo;
@@ -535,7 +508,7 @@ __global__ void sr_post_kernel(SegArgs a) {
     const int n = a.n;
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
-    double *p = m.uo, *q = m.un;
+    double *p = m.u;
     for (int k = 0; k < a.nu; ++k) {
         // Kaczmarz (Fig. 5): r = u^H_J - (R u)_J added to both children
         for (int J = (m.e0 >> 1) + threadIdx.x; J < (m.e1 >> 1); J += blockDim.x) {
@@ -545,8 +518,7 @@ __global__ void sr_post_kernel(SegArgs a) {
             p[i0 + 1] += r;
         }
         __syncthreads();
-        lex_sweep<false>(p, q, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, kChunk, m.X, m.Y);
-        double *tmp = p; p = q; q = tmp;
+        lex_sweep<kChunk>(p, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
     for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) a.u_out[i] = p[i - m.lo];
 }
@@ -567,7 +539,7 @@ struct TailArgs {
 };
 
 struct TailSmem {
-    double *u, *g, *S, *X, *Y;
+    double *u, *g, *S, *X;
     int M0;
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
 };
@@ -575,12 +547,7 @@ struct TailSmem {
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
-    for (int k = 0; k < nu; ++k) {
-        lex_sweep<true>(u, m.S, g, 0, 0, n, n, (k & 1) == 0, ((n + (int)blockDim.x - 1) / (int)blockDim.x) | 1,
-                        m.X, m.Y);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = m.S[i];
-        __syncthreads();
-    }
+    for (int k = 0; k < nu; ++k) lex_sweep<kChunk>(u, g, 0, 0, n, n, (k & 1) == 0, m.X);
 }
 
 // smooth level l, then restriction and tau rhs into level l-1
@@ -651,7 +618,6 @@ __global__ void tail_kernel(TailArgs a) {
     m.g = m.u + tot;
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
-    m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc;
     stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
     if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
