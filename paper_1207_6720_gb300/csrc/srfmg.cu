@@ -415,7 +415,27 @@ void build_schedule(srfmg_plan *h) {
     h->ops.insert(h->ops.begin(), sc);
 }
 
-cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t s) {
+// One kernel launch; with pdl the launch carries the programmatic-dependent-
+// launch attribute (the kernel may begin launching while the preceding
+// kernel of the stream runs; it waits for it in pdl_enter before touching
+// data).
+template <typename... KArgs, typename... Args>
+cudaError_t run(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t s, bool pdl) {
     Op o = o0;
     if (o.rhs_in == TAG_F) o.frhs.f = f;
     if (o.lev_g == TAG_F) o.flev.f = f;
@@ -424,26 +444,30 @@ cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t 
     if (o.tail_out == TAG_U) { o.ftail.u_out_f64 = u; o.ftail.u_out = nullptr; }
     if (o.seg_f == TAG_F) o.fseg.f = f;
     if (o.seg_u == TAG_U) o.fseg.u_out = u;
+    cudaError_t e = cudaSuccess;
     switch (o.kind) {
-    case OP_SCALE:
-        fx::scale_reset_kernel<<<1, 32, 0, s>>>(o.scale);
-        fx::scale_max_kernel<<<o.grid, o.block, 0, s>>>(f, (long long)o.level < 63 ? (1LL << o.level) : 0, o.scale);
-        fx::scale_finish_kernel<<<1, 32, 0, s>>>(o.scale);
+    case OP_SCALE: {
+        const long long n = (long long)o.level < 63 ? (1LL << o.level) : 0;
+        e = run(fx::scale_reset_kernel, dim3(1), dim3(32), 0, s, pdl, o.scale);
+        if (e == cudaSuccess) e = run(fx::scale_max_kernel, o.grid, o.block, 0, s, true, f, n, o.scale);
+        if (e == cudaSuccess) e = run(fx::scale_finish_kernel, dim3(1), dim3(32), 0, s, true, o.scale);
         break;
-    case OP_RHS: fx::rhs_hierarchy_kernel<<<o.grid, o.block, o.smem, s>>>(o.frhs); break;
-    case OP_TAIL: fx::tail_kernel<<<o.grid, o.block, o.smem, s>>>(o.ftail); break;
-    case OP_DOWN_PI: fx::level_down_kernel<true><<<o.grid, o.block, o.smem, s>>>(o.flev); break;
-    case OP_DOWN: fx::level_down_kernel<false><<<o.grid, o.block, o.smem, s>>>(o.flev); break;
-    case OP_UP: fx::level_up_kernel<<<o.grid, o.block, o.smem, s>>>(o.flev); break;
-    case OP_SR_PRE: fx::sr_pre_kernel<<<o.grid, o.block, o.smem, s>>>(o.fseg); break;
-    case OP_SEAM: fx::seam_tau_kernel<<<o.grid, o.block, 0, s>>>(o.fseg, o.nseg); break;
-    case OP_SR_POST: fx::sr_post_kernel<<<o.grid, o.block, o.smem, s>>>(o.fseg); break;
     }
-    return cudaGetLastError();
+    case OP_RHS: e = run(fx::rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.frhs); break;
+    case OP_TAIL: e = run(fx::tail_kernel, o.grid, o.block, o.smem, s, pdl, o.ftail); break;
+    case OP_DOWN_PI: e = run(fx::level_down_kernel<true>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_DOWN: e = run(fx::level_down_kernel<false>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_UP: e = run(fx::level_up_kernel, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_SR_PRE: e = run(fx::sr_pre_kernel, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
+    case OP_SEAM: e = run(fx::seam_tau_kernel, o.grid, o.block, 0, s, pdl, o.fseg, o.nseg); break;
+    case OP_SR_POST: e = run(fx::sr_post_kernel, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
+    }
+    return e;
 }
 
-cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s) {
-    if (o0.fixed) return launch_fixed(o0, f, u, s);
+// Enqueue one op on s; pdl as in run().
+cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s, bool pdl) {
+    if (o0.fixed) return launch_fixed(o0, f, u, s, pdl);
     Op o = o0;
     if (o.rhs_in == TAG_F) o.rhs.in = f;
     if (o.lev_g == TAG_F) o.lev.g = f;
@@ -452,17 +476,19 @@ cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s) {
     if (o.tail_out == TAG_U) o.tail.u_out = u;
     if (o.seg_f == TAG_F) o.seg.f = f;
     if (o.seg_u == TAG_U) o.seg.u_out = u;
+    cudaError_t e = cudaSuccess;
     switch (o.kind) {
-    case OP_RHS: rhs_hierarchy_kernel<<<o.grid, o.block, o.smem, s>>>(o.rhs); break;
-    case OP_TAIL: tail_kernel<<<o.grid, o.block, o.smem, s>>>(o.tail); break;
-    case OP_DOWN_PI: level_down_kernel<true><<<o.grid, o.block, o.smem, s>>>(o.lev); break;
-    case OP_DOWN: level_down_kernel<false><<<o.grid, o.block, o.smem, s>>>(o.lev); break;
-    case OP_UP: level_up_kernel<<<o.grid, o.block, o.smem, s>>>(o.lev); break;
-    case OP_SR_PRE: sr_pre_kernel<<<o.grid, o.block, o.smem, s>>>(o.seg); break;
-    case OP_SEAM: seam_tau_kernel<<<o.grid, o.block, 0, s>>>(o.seg, o.nseg); break;
-    case OP_SR_POST: sr_post_kernel<<<o.grid, o.block, o.smem, s>>>(o.seg); break;
+    case OP_RHS: e = run(rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.rhs); break;
+    case OP_TAIL: e = run(tail_kernel, o.grid, o.block, o.smem, s, pdl, o.tail); break;
+    case OP_DOWN_PI: e = run(level_down_kernel<true>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_DOWN: e = run(level_down_kernel<false>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_UP: e = run(level_up_kernel, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_SR_PRE: e = run(sr_pre_kernel, o.grid, o.block, o.smem, s, pdl, o.seg); break;
+    case OP_SEAM: e = run(seam_tau_kernel, o.grid, o.block, 0, s, pdl, o.seg, o.nseg); break;
+    case OP_SR_POST: e = run(sr_post_kernel, o.grid, o.block, o.smem, s, pdl, o.seg); break;
+    case OP_SCALE: break;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 const char *kind_name(OpKind k) {
@@ -480,10 +506,14 @@ const char *kind_name(OpKind k) {
     return "?";
 }
 
+// All launches of one solve; every launch after the first overlaps its set-up
+// with the preceding kernel (programmatic dependent launch).
 cudaError_t enqueue_all(srfmg_plan *h, const double *f, double *u, cudaStream_t s) {
+    bool first = true;
     for (const Op &o : h->ops) {
-        cudaError_t e = launch(o, f, u, s);
+        cudaError_t e = launch(o, f, u, s, !first);
         if (e != cudaSuccess) return e;
+        first = false;
     }
     return cudaSuccess;
 }
@@ -703,7 +733,7 @@ srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *str
         for (int i = 0; i < nops && e == cudaSuccess; ++i) {
             size_t idx = ((size_t)k * nops + i) * 2;
             e = cudaEventRecord(ev[idx], s);
-            if (e == cudaSuccess) e = launch(h->ops[i], f, u, s);
+            if (e == cudaSuccess) e = launch(h->ops[i], f, u, s, false);
             if (e == cudaSuccess) e = cudaEventRecord(ev[idx + 1], s);
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

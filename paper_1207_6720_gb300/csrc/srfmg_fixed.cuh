@@ -105,7 +105,7 @@ __device__ __forceinline__ i64 div3(i64 x) {
 // shift by 64 or more leaves nothing of a 63-bit value, so dropping those
 // terms changes nothing.  Integer sums are exact, so the residual is written
 // gs + u_{q-1} + u_{q+1} - 2 u_q in either direction.
-template <int C>
+template <int C, bool PRELOAD = false>
 __device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo, int hi, int n,
                           bool asc, i64 *X) {
     const int t = threadIdx.x;
@@ -127,9 +127,12 @@ __device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int b
         for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
         if (wall0) p = div3(gs[a0] + w[2] - 3 * w[1]);
         if (wall1) r_end = gs[a0 + s * (n - 1)] + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
+        i64 gv[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) gv[k] = gs[a0 + s * min(max(q0 + k, qmin), qmax)];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            const i64 r = gs[a0 + s * min(max(q0 + k, qmin), qmax)] + w[k] + w[k + 2] - 2 * w[k + 1];
+            const i64 r = gv[k] + w[k] + w[k + 2] - 2 * w[k + 1];
             const i64 pn = (r + p + 1) >> 1;
             p = (k >= ka && k < kb) ? pn : p;
             rr[k] = p;
@@ -146,16 +149,28 @@ __device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int b
             const i64 x = X[max(idx, 0)];
             cin = (cin >> C) + (idx >= 0 ? x : 0);
         }
+        // PRELOAD: all loads first, then the arithmetic, then the stores (a
+        // load after a store to a runtime-indexed address waits for the
+        // store), for latency-bound blocks; otherwise the increments are
+        // added in place, which needs fewer registers.
+        i64 uo[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0;
+        const i64 ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
         i64 c = cin, dl = cin;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             if (k >= k0) c >>= 1;                 // cin >> (k-k0+1)
-            if (k >= k0 && k < kb) {
-                dl = rr[k] + c;
-                u[a0 + s * (q0 + k)] += dl;
-            }
+            dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
+            uo[k] += dl;
         }
-        if (wall1) u[a0 + s * (n - 1)] += div3(r_end + dl);
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
+                else u[a0 + s * (q0 + k)] += uo[k];
+            }
+        if (wall1) u[a0 + s * (n - 1)] = ue + div3(r_end + dl);
     }
     __syncthreads();
 }
@@ -183,10 +198,12 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
 // Scale: E with max|f| < 2^E from the largest exponent field of f.
 // --------------------------------------------------------------------------
 __global__ void scale_reset_kernel(Scale *sc) {
+    pdl_enter();
     if (threadIdx.x == 0) { sc->E = -2000; sc->S = 0; sc->Sg0 = 0; }
 }
 
 __global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
+    pdl_enter();
     int emax = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         int e = (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff);
@@ -197,6 +214,7 @@ __global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
 }
 
 __global__ void scale_finish_kernel(Scale *sc) {
+    pdl_enter();
     if (threadIdx.x == 0) {
         int E = sc->E;
         E = E < -100 ? -100 : (E > 900 ? 900 : E);
@@ -219,6 +237,7 @@ struct RhsArgs {
 };
 
 __global__ void rhs_hierarchy_kernel(RhsArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     const int chunk = 1 << a.depth;
     i64 *cur = smi, *nxt = smi + chunk;
@@ -327,7 +346,8 @@ __device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
 }
 
 template <bool FROM_PI>
-__global__ void level_down_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -360,7 +380,8 @@ __global__ void level_down_kernel(LevelArgs a) {
 }
 
 // Up pass (Eq. 4): U_l += P (U_{l-1} - R U_l) (rounded to units), then nu sweeps.
-__global__ void level_up_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -459,7 +480,8 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
     __syncthreads();
 }
 
-__global__ void sr_pre_kernel(SegArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -489,6 +511,7 @@ __global__ void sr_pre_kernel(SegArgs a) {
 // tau rhs at the two coarse cells of each interior segment boundary from the
 // assembled fine values (seams) and the restricted solution.
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
+    pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
     const int s = (k + 1) * a.W;
@@ -510,7 +533,8 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     }
 }
 
-__global__ void sr_post_kernel(SegArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -559,7 +583,7 @@ __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const i64 *g = m.g + m.off(l);
     for (int i = threadIdx.x; i < n; i += blockDim.x) m.S[i] = shr_round(g[i], 2 * l - 2);
     __syncthreads();
-    for (int k = 0; k < nu; ++k) lex_sweep<kChunk>(u, m.S, 0, 0, n, n, (k & 1) == 0, m.X);
+    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true>(u, m.S, 0, 0, n, n, (k & 1) == 0, m.X);
 }
 
 __device__ void tail_down(TailSmem &m, int l, int nu) {
@@ -620,6 +644,7 @@ __device__ void tail_interp(TailSmem &m, int l) {
 }
 
 __global__ void tail_kernel(TailArgs a) {
+    pdl_enter();
     extern __shared__ i64 smi[];
     TailSmem m;
     m.M0 = a.M0;

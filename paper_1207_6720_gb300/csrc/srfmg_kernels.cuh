@@ -26,6 +26,21 @@ constexpr int kTrunc = 72;
 // block has many threads and each recurrence is a few dependent operations.
 constexpr int kChunk = 9;
 
+// Largest block of the level and segment kernels: one thread per chunk of at
+// most 4224 + 2 cells (a segment) or 2944 cells (a tile).  Segment kernels
+// are compiled for two such blocks per SM (at most 64 registers a thread).
+constexpr int kSweepBlockMax = 512;
+
+// Programmatic dependent launch.  Every kernel of a solve starts with this:
+// it waits until the preceding kernel in the stream has completed and its
+// writes are visible, then allows the next kernel to begin launching, so
+// that the next launch's set-up overlaps this kernel's work.  Both
+// instructions do nothing for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Exact 2^k as a double, -1022 <= k <= 1023.
 __device__ __forceinline__ double exp2i(int k) {
     return __longlong_as_double((long long)(1023 + k) << 52);
@@ -143,7 +158,7 @@ __device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) 
 // two wall cells are handled apart.  All threads of the block must call it.
 // X holds one double per thread.
 // ---------------------------------------------------------------------------
-template <int C>
+template <int C, bool PRELOAD = false>
 __device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, int base, int lo, int hi,
                           int n, bool asc, double *X) {
     const int t = threadIdx.x;
@@ -170,10 +185,12 @@ __device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, 
             const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
             r_end = g[a0 + s * (n - 1)] - ((ue - um) - (-scale2(ue, 1)));
         }
+        double gv[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) gv[k] = g[a0 + s * min(max(q0 + k, qmin), qmax)];
 #pragma unroll
         for (int k = 0; k < C; ++k) {
-            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
-            const double r = gv - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
+            const double r = gv[k] - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
             const double pn = fma(0.5, p, scale2(r, -1));
             p = (k >= ka && k < kb) ? pn : p;
             rr[k] = p;
@@ -190,16 +207,28 @@ __device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, 
             const double x = X[max(idx, 0)];
             cin = fma(exp2i(-C), cin, idx >= 0 ? x : 0.0);
         }
+        // PRELOAD: all loads first, then the arithmetic, then the stores (a
+        // load after a store to a runtime-indexed address waits for the
+        // store), for latency-bound blocks; otherwise the increments are
+        // added in place, which needs fewer registers.
+        double uo[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0.0;
+        const double ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
         double c = cin, dl = cin;
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             if (k >= k0) c = scale2(c, -1);          // 2^-(k-k0+1) cin, exact
-            if (k >= k0 && k < kb) {
-                dl = rr[k] + c;
-                u[a0 + s * (q0 + k)] += dl;
-            }
+            dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
+            uo[k] += dl;
         }
-        if (wall1) u[a0 + s * (n - 1)] += (r_end + dl) * (1.0 / 3.0);
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
+                else u[a0 + s * (q0 + k)] += uo[k];
+            }
+        if (wall1) u[a0 + s * (n - 1)] = ue + (r_end + dl) * (1.0 / 3.0);
     }
     __syncthreads();
 }
@@ -235,6 +264,7 @@ struct RhsArgs {
 };
 
 __global__ void rhs_hierarchy_kernel(RhsArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     const int chunk = 1 << a.depth;
     double *cur = sm, *nxt = sm + chunk;
@@ -317,7 +347,8 @@ __device__ void smooth_range(LevelSmem &m, int n, int nu) {
 }
 
 template <bool FROM_PI>
-__global__ void level_down_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -351,7 +382,8 @@ __global__ void level_down_kernel(LevelArgs a) {
 }
 
 // Up pass (Eq. 4): u_l += P (u_{l-1} - R u_l), then nu sweeps.
-__global__ void level_up_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -445,7 +477,8 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 // the extended patch, restricted solution on the segment's coarse cells, tau
 // rhs on the coarse cells whose stencil lies in the segment, seam values for
 // the two edge cells (formed from the assembled level by seam_tau_kernel).
-__global__ void sr_pre_kernel(SegArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -475,6 +508,7 @@ __global__ void sr_pre_kernel(SegArgs a) {
 // assembled fine values (seams) and the restricted solution (appendix down
 // leg).  Thread k handles the boundary s = (k+1) W.
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
+    pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
     const int s = (k + 1) * a.W;
@@ -502,7 +536,8 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 // K6: post-smoothing leg of the SR level (Fig. 3, Eq. 5, Fig. 5): full update
 // Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
 // Gauss-Seidel sweep), and the segment interior is written out.
-__global__ void sr_post_kernel(SegArgs a) {
+__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -547,7 +582,7 @@ struct TailSmem {
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
-    for (int k = 0; k < nu; ++k) lex_sweep<kChunk>(u, g, 0, 0, n, n, (k & 1) == 0, m.X);
+    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true>(u, g, 0, 0, n, n, (k & 1) == 0, m.X);
 }
 
 // smooth level l, then restriction and tau rhs into level l-1
@@ -610,6 +645,7 @@ __device__ void tail_interp(TailSmem &m, int l) {
 }
 
 __global__ void tail_kernel(TailArgs a) {
+    pdl_enter();
     extern __shared__ double sm[];
     TailSmem m;
     m.M0 = a.M0;
