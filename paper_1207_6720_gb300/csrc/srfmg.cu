@@ -21,7 +21,7 @@ using namespace srfmg;
 namespace {
 
 constexpr int kMaxTailLevel = 12;      // levels <= 12 fit one block's shared memory in FP64
-constexpr int kTailThreads = 512;     // one sweep chunk per thread up to 2^12 cells
+constexpr int kTailThreads = kTailBlock;
 constexpr int kRhsThreads = 256;
 constexpr int kRhsDepth = 12;          // levels reduced per rhs-hierarchy launch
 constexpr int kTileMax = 2048;

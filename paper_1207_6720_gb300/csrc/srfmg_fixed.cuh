@@ -76,17 +76,30 @@ __device__ __forceinline__ double fixed_to_f64(i64 U, int S) {
 }
 
 // Fourth order FMG interpolation Pi (Sec. 4) in fixed point: 128 Pi is the
-// integer combination (-5, 35, 105, -7) (or its mirror), formed in 128 bits
-// and rounded to the nearest unit.  c[j - cbase] holds coarse cells J-2..J+2.
-__device__ __forceinline__ i64 fmg_interp(const i64 *c, int cbase, int i) {
-    int J = i >> 1;
+// integer combination (-5, 35, 105, -7) (or its mirror) of coarse cells
+// J-2..J+1 (J-1..J+2), rounded to the nearest unit.  Both children of coarse
+// cell J are formed together, without 128-bit products: with U = 16a + b
+// (0 <= b < 16), sum w U = 16 Sa + Sb where Sa = sum w a fits 64 bits for
+// |U| < 2^59 (sum |w| = 152 < 2^8) and |Sb| <= 152 * 15; then
+//   floor((16 Sa + Sb + 64) / 128) = (Sa + ((Sb + 64) >> 4)) >> 3
+// exactly (the dropped remainder of (Sb + 64) / 16 is below 1/8 of the last
+// shift's unit).  c[j - cbase] holds coarse cells J-2..J+2.
+__device__ __forceinline__ void fmg_interp2(const i64 *c, int cbase, int J, i64 &left, i64 &right) {
     const i64 *p = c + (J - cbase);
-    __int128 s;
-    if ((i & 1) == 0)
-        s = (__int128)p[-2] * -5 + (__int128)p[-1] * 35 + (__int128)p[0] * 105 + (__int128)p[1] * -7;
-    else
-        s = (__int128)p[-1] * -7 + (__int128)p[0] * 105 + (__int128)p[1] * 35 + (__int128)p[2] * -5;
-    return (i64)((s + 64) >> 7);
+    i64 a[5];
+    int b[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const i64 v = p[j - 2];
+        a[j] = v >> 4;
+        b[j] = (int)(v & 15);
+    }
+    const i64 sal = -5 * a[0] + 35 * a[1] + 105 * a[2] - 7 * a[3];
+    const i64 sar = -7 * a[1] + 105 * a[2] + 35 * a[3] - 5 * a[4];
+    const int sbl = -5 * b[0] + 35 * b[1] + 105 * b[2] - 7 * b[3] + 64;
+    const int sbr = -7 * b[1] + 105 * b[2] + 35 * b[3] - 5 * b[4] + 64;
+    left = (sal + (i64)(sbl >> 4)) >> 3;
+    right = (sar + (i64)(sbr >> 4)) >> 3;
 }
 
 // x / 3 rounded toward zero (C division) for |x| < 2^63: the high word of
@@ -105,11 +118,12 @@ __device__ __forceinline__ i64 div3(i64 x) {
 // shift by 64 or more leaves nothing of a 63-bit value, so dropping those
 // terms changes nothing.  Integer sums are exact, so the residual is written
 // gs + u_{q-1} + u_{q+1} - 2 u_q in either direction.
-template <int C, bool PRELOAD = false>
-__device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo, int hi, int n,
-                          bool asc, i64 *X) {
+template <int C, bool PRELOAD, bool ASC>
+__device__ __noinline__ void lex_sweep_dir(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo,
+                                              int hi, int n, i64 *X) {
+    constexpr int s = ASC ? 1 : -1;                // sweep position q is u[a0 + s q]
     const int t = threadIdx.x;
-    const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
     const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
     const bool active = t < nch;
     const int q0 = (c_first + t) * C;
@@ -118,24 +132,38 @@ __device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int b
     const bool wall1 = (q0 + k1 == n);
     const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
     const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
-    const int s = asc ? 1 : -1, a0 = asc ? -base : n - 1 - base;
+    const int a0 = ASC ? -base : n - 1 - base;
+    // a warp whose chunks are all full and away from the walls takes the
+    // straight-line path (no clamps, no range selects)
+    const bool fast = __all_sync(0xffffffffu, !active || (k0 == 0 && k1 == C && !wall0 && !wall1));
     i64 rr[C];
     i64 p = 0, r_end = 0;
     if (active) {
         i64 w[C + 2];
+        if (fast) {
+            const i64 *up = u + (a0 + s * (q0 - 1)), *gp = gs + (a0 + s * q0);
 #pragma unroll
-        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
-        if (wall0) p = div3(gs[a0] + w[2] - 3 * w[1]);
-        if (wall1) r_end = gs[a0 + s * (n - 1)] + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
-        i64 gv[C];
+            for (int j = 0; j < C + 2; ++j) w[j] = up[s * j];
 #pragma unroll
-        for (int k = 0; k < C; ++k) gv[k] = gs[a0 + s * min(max(q0 + k, qmin), qmax)];
+            for (int k = 0; k < C; ++k) {
+                p = (gp[s * k] + w[k] + w[k + 2] - 2 * w[k + 1] + p + 1) >> 1;
+                rr[k] = p;
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            const i64 r = gv[k] + w[k] + w[k + 2] - 2 * w[k + 1];
-            const i64 pn = (r + p + 1) >> 1;
-            p = (k >= ka && k < kb) ? pn : p;
-            rr[k] = p;
+            for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+            if (wall0) p = div3(gs[a0] + w[2] - 3 * w[1]);
+            if (wall1) r_end = gs[a0 + s * (n - 1)] + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
+            i64 gv[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) gv[k] = gs[a0 + s * min(max(q0 + k, qmin), qmax)];
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const i64 r = gv[k] + w[k] + w[k + 2] - 2 * w[k + 1];
+                const i64 pn = (r + p + 1) >> 1;
+                p = (k >= ka && k < kb) ? pn : p;
+                rr[k] = p;
+            }
         }
         X[t] = p;
     }
@@ -153,26 +181,45 @@ __device__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int b
         // load after a store to a runtime-indexed address waits for the
         // store), for latency-bound blocks; otherwise the increments are
         // added in place, which needs fewer registers.
-        i64 uo[C];
+        if (fast) {
+            i64 *up = u + (a0 + s * q0);
+            i64 uo[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0;
-        const i64 ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
-        i64 c = cin, dl = cin;
+            for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? up[s * k] : 0;
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            if (k >= k0) c >>= 1;                 // cin >> (k-k0+1)
-            dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
-            uo[k] += dl;
-        }
-#pragma unroll
-        for (int k = 0; k < C; ++k)
-            if (k >= k0 && k < kb) {
-                if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
-                else u[a0 + s * (q0 + k)] += uo[k];
+            for (int k = 0; k < C; ++k) {
+                if (PRELOAD) up[s * k] = uo[k] + rr[k] + (cin >> (k + 1));
+                else up[s * k] += rr[k] + (cin >> (k + 1));
             }
-        if (wall1) u[a0 + s * (n - 1)] = ue + div3(r_end + dl);
+        } else {
+            i64 uo[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0;
+            const i64 ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
+            i64 c = cin, dl = cin;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                if (k >= k0) c >>= 1;                 // cin >> (k-k0+1)
+                dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
+                uo[k] += dl;
+            }
+#pragma unroll
+            for (int k = 0; k < C; ++k)
+                if (k >= k0 && k < kb) {
+                    if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
+                    else u[a0 + s * (q0 + k)] += uo[k];
+                }
+            if (wall1) u[a0 + s * (n - 1)] = ue + div3(r_end + dl);
+        }
     }
     __syncthreads();
+}
+
+template <int C, bool PRELOAD = false>
+__device__ __forceinline__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo,
+                                          int hi, int n, bool asc, i64 *X) {
+    if (asc) lex_sweep_dir<C, PRELOAD, true>(u, gs, base, lo, hi, n, X);
+    else lex_sweep_dir<C, PRELOAD, false>(u, gs, base, lo, hi, n, X);
 }
 
 // tau-corrected coarse right-hand side (Eqs. 6-7), exact: the tau term is a
@@ -362,8 +409,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     if (FROM_PI) {
         fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.u[i - m.L0] = fmg_interp(m.c, m.C0, i);
+        for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x)
+            fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
     __syncthreads();
     smooth_range(m, n, a.nu);
@@ -476,7 +523,12 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
         if (in1) m.gs[i0 + 1 - m.lo] = shr_round(g1, gsh);
     }
     __syncthreads();
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) m.u[i - m.lo] = fmg_interp(m.c, m.C0, i);
+    for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
+        i64 l, r;
+        fmg_interp2(m.c, m.C0, J, l, r);
+        if (2 * J >= m.lo) m.u[2 * J - m.lo] = l;
+        if (2 * J + 1 < m.hi) m.u[2 * J + 1 - m.lo] = r;
+    }
     __syncthreads();
 }
 
@@ -639,11 +691,11 @@ __device__ void tail_interp(TailSmem &m, int l) {
     for (int j = (int)threadIdx.x - 2; j < nc + 2; j += (int)blockDim.x)
         if (j >= -2) m.S[j + 2] = coarse_reflect(uc, j, nc);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = fmg_interp(m.S, -2, i);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x) fmg_interp2(m.S, -2, J, u[2 * J], u[2 * J + 1]);
     __syncthreads();
 }
 
-__global__ void tail_kernel(TailArgs a) {
+__global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
     TailSmem m;

@@ -31,6 +31,9 @@ constexpr int kChunk = 9;
 // are compiled for two such blocks per SM (at most 64 registers a thread).
 constexpr int kSweepBlockMax = 512;
 
+// Block size of the coarse tail: one sweep chunk per thread up to 2^12 cells.
+constexpr int kTailBlock = 512;
+
 // Programmatic dependent launch.  Every kernel of a solve starts with this:
 // it waits until the preceding kernel in the stream has completed and its
 // writes are visible, then allows the next kernel to begin launching, so
@@ -106,19 +109,15 @@ __device__ __forceinline__ void fill_coarse_ghosts(T *c, int C0, int C1, int nc)
 // (exact differences of nearby values), so the interpolated value carries a
 // single rounding:  left  = u_J + (5G_{J-3/2} - 30G_{J-1/2} - 7G_{J+1/2})/128,
 //                   right = u_J + (7G_{J-1/2} + 30G_{J+1/2} - 5G_{J+3/2})/128.
+// Both children of J are formed together (they share the fluxes).
 // c[j - cbase] must hold coarse cells J-2..J+2 (ghosts already reflected).
-__device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) {
-    int J = i >> 1;
+__device__ __forceinline__ void fmg_interp2(const double *c, int cbase, int J, double &left, double &right) {
     const double *p = c + (J - cbase);
-    double s;
-    if ((i & 1) == 0) {
-        double gm3 = p[-1] - p[-2], gm1 = p[0] - p[-1], gp1 = p[1] - p[0];
-        s = fma(5.0, gm3, fma(-30.0, gm1, -7.0 * gp1));
-    } else {
-        double gm1 = p[0] - p[-1], gp1 = p[1] - p[0], gp3 = p[2] - p[1];
-        s = fma(7.0, gm1, fma(30.0, gp1, -5.0 * gp3));
-    }
-    return p[0] + scale2(s, -7);
+    const double gm3 = p[-1] - p[-2], gm1 = p[0] - p[-1], gp1 = p[1] - p[0], gp3 = p[2] - p[1];
+    const double sl = fma(5.0, gm3, fma(-30.0, gm1, -7.0 * gp1));
+    const double sr = fma(7.0, gm1, fma(30.0, gp1, -5.0 * gp3));
+    left = p[0] + scale2(sl, -7);
+    right = p[0] + scale2(sr, -7);
 }
 
 // ---------------------------------------------------------------------------
@@ -158,11 +157,12 @@ __device__ __forceinline__ double fmg_interp(const double *c, int cbase, int i) 
 // two wall cells are handled apart.  All threads of the block must call it.
 // X holds one double per thread.
 // ---------------------------------------------------------------------------
-template <int C, bool PRELOAD = false>
-__device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, int base, int lo, int hi,
-                          int n, bool asc, double *X) {
+template <int C, bool PRELOAD, bool ASC>
+__device__ __noinline__ void lex_sweep_dir(double *__restrict__ u, const double *__restrict__ g, int base,
+                                              int lo, int hi, int n, double *X) {
+    constexpr int s = ASC ? 1 : -1;                // sweep position q is u[a0 + s q]
     const int t = threadIdx.x;
-    const int qlo = asc ? lo : n - hi, qhi = asc ? hi : n - lo;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
     const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
     const bool active = t < nch;
     const int q0 = (c_first + t) * C;
@@ -172,28 +172,42 @@ __device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, 
     const bool wall1 = (q0 + k1 == n);               // sweep position n-1 (a wall) is swept
     const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
     const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
-    // sweep position q is u[a0 + s q]
-    const int s = asc ? 1 : -1, a0 = asc ? -base : n - 1 - base;
+    const int a0 = ASC ? -base : n - 1 - base;
+    // a warp whose chunks are all full and away from the walls takes the
+    // straight-line path (no clamps, no range selects)
+    const bool fast = __all_sync(0xffffffffu, !active || (k0 == 0 && k1 == C && !wall0 && !wall1));
     double rr[C];
     double p = 0.0, r_end = 0.0;
     if (active) {
         double w[C + 2];   // u at positions q0-1 .. q0+C
+        if (fast) {
+            const double *up = u + (a0 + s * (q0 - 1)), *gp = g + (a0 + s * q0);
 #pragma unroll
-        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
-        if (wall0) p = (g[a0] - (scale2(w[1], 1) - (w[2] - w[1]))) * (1.0 / 3.0);
-        if (wall1) {
-            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
-            r_end = g[a0 + s * (n - 1)] - ((ue - um) - (-scale2(ue, 1)));
-        }
-        double gv[C];
+            for (int j = 0; j < C + 2; ++j) w[j] = up[s * j];
 #pragma unroll
-        for (int k = 0; k < C; ++k) gv[k] = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            for (int k = 0; k < C; ++k) {
+                const double r = gp[s * k] - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
+                p = fma(0.5, p, scale2(r, -1));
+                rr[k] = p;
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            const double r = gv[k] - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
-            const double pn = fma(0.5, p, scale2(r, -1));
-            p = (k >= ka && k < kb) ? pn : p;
-            rr[k] = p;
+            for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+            if (wall0) p = (g[a0] - (scale2(w[1], 1) - (w[2] - w[1]))) * (1.0 / 3.0);
+            if (wall1) {
+                const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+                r_end = g[a0 + s * (n - 1)] - ((ue - um) - (-scale2(ue, 1)));
+            }
+            double gv[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) gv[k] = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const double r = gv[k] - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
+                const double pn = fma(0.5, p, scale2(r, -1));
+                p = (k >= ka && k < kb) ? pn : p;
+                rr[k] = p;
+            }
         }
         X[t] = p;
     }
@@ -211,26 +225,47 @@ __device__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, 
         // load after a store to a runtime-indexed address waits for the
         // store), for latency-bound blocks; otherwise the increments are
         // added in place, which needs fewer registers.
-        double uo[C];
+        if (fast) {
+            double *up = u + (a0 + s * q0);
+            double uo[C];
 #pragma unroll
-        for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0.0;
-        const double ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
-        double c = cin, dl = cin;
+            for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? up[s * k] : 0.0;
+            double c = cin;
 #pragma unroll
-        for (int k = 0; k < C; ++k) {
-            if (k >= k0) c = scale2(c, -1);          // 2^-(k-k0+1) cin, exact
-            dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
-            uo[k] += dl;
-        }
-#pragma unroll
-        for (int k = 0; k < C; ++k)
-            if (k >= k0 && k < kb) {
-                if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
-                else u[a0 + s * (q0 + k)] += uo[k];
+            for (int k = 0; k < C; ++k) {
+                c = scale2(c, -1);                   // 2^-(k+1) cin, exact
+                if (PRELOAD) up[s * k] = uo[k] + (rr[k] + c);
+                else up[s * k] += rr[k] + c;
             }
-        if (wall1) u[a0 + s * (n - 1)] = ue + (r_end + dl) * (1.0 / 3.0);
+        } else {
+            double uo[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) uo[k] = PRELOAD ? u[a0 + s * min(max(q0 + k, qmin), qmax)] : 0.0;
+            const double ue = u[wall1 ? a0 + s * (n - 1) : a0 + s * min(max(q0, qmin), qmax)];   // in range
+            double c = cin, dl = cin;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                if (k >= k0) c = scale2(c, -1);          // 2^-(k-k0+1) cin, exact
+                dl = (k >= k0 && k < kb) ? rr[k] + c : dl;
+                uo[k] += dl;
+            }
+#pragma unroll
+            for (int k = 0; k < C; ++k)
+                if (k >= k0 && k < kb) {
+                    if (PRELOAD) u[a0 + s * (q0 + k)] = uo[k];
+                    else u[a0 + s * (q0 + k)] += uo[k];
+                }
+            if (wall1) u[a0 + s * (n - 1)] = ue + (r_end + dl) * (1.0 / 3.0);
+        }
     }
     __syncthreads();
+}
+
+template <int C, bool PRELOAD = false>
+__device__ __forceinline__ void lex_sweep(double *__restrict__ u, const double *__restrict__ g, int base, int lo,
+                                          int hi, int n, bool asc, double *X) {
+    if (asc) lex_sweep_dir<C, PRELOAD, true>(u, g, base, lo, hi, n, X);
+    else lex_sweep_dir<C, PRELOAD, false>(u, g, base, lo, hi, n, X);
 }
 
 // Scaled tau-corrected coarse right-hand side at coarse cell J (Eqs. 6-7,
@@ -364,8 +399,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     if (FROM_PI) {
         fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
-        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
-            m.u[i - m.L0] = fmg_interp(m.c, m.C0, i);
+        for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x)
+            fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
     __syncthreads();
     smooth_range(m, n, a.nu);
@@ -469,7 +504,12 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
         m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
     __syncthreads();
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) m.u[i - m.lo] = fmg_interp(m.c, m.C0, i);
+    for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
+        double l, r;
+        fmg_interp2(m.c, m.C0, J, l, r);
+        if (2 * J >= m.lo) m.u[2 * J - m.lo] = l;
+        if (2 * J + 1 < m.hi) m.u[2 * J + 1 - m.lo] = r;
+    }
     __syncthreads();
 }
 
@@ -640,11 +680,11 @@ __device__ void tail_interp(TailSmem &m, int l) {
     for (int j = (int)threadIdx.x - 2; j < nc + 2; j += (int)blockDim.x)
         if (j >= -2) m.S[j + 2] = coarse_reflect(uc, 0, j, nc);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = fmg_interp(m.S, -2, i);
+    for (int J = threadIdx.x; J < nc; J += blockDim.x) fmg_interp2(m.S, -2, J, u[2 * J], u[2 * J + 1]);
     __syncthreads();
 }
 
-__global__ void tail_kernel(TailArgs a) {
+__global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
     TailSmem m;
