@@ -327,6 +327,18 @@ def run_gpu(a):
         sr64 = {"value": dist.world * N / (ms64 * 1e-3), "ms_per_step": ms64,
                 "err_max_vs_exact": float(np.max(np.abs(u64 - u_exact)))}
 
+    # adjoint solve (dL/df for L = 1/2 |u - u_obs|^2, u_obs = exact + N(0, 1e-3^2))
+    rng = np.random.default_rng(7)
+    g_adj = torch.from_numpy(u - (u_exact + rng.normal(0.0, 1e-3, N))).to(dev)
+    lam = torch.empty_like(g_adj)
+
+    class _Adj:
+        def solve(self, x, y, stream=None):
+            return solver.adjoint(x, y, stream=stream)
+    ms_adj = dist.max(time_solves(_Adj(), g_adj, lam, max(10, a.steps // 4), a.warmup, dist, stream))
+    adjoint = {"value": dist.world * N / (ms_adj * 1e-3), "unit": UNIT, "ms_per_step": ms_adj,
+               "rhs": "u - u_obs, u_obs = exact + N(0, 1e-3^2), seed 7"}
+
     # end to end through the public API from pinned host buffers
     fh = torch.from_numpy(f).pin_memory()
     uh = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -388,6 +400,7 @@ def run_gpu(a):
                        "kernels_per_solve": plain_info.kernels_per_solve,
                        "speedup_over_plain": ms_plain / ms},
         "sr_fp64": sr64,
+        "adjoint": adjoint,
         "roofline": roofline,
         "kernel_share": {k: round(v / tot, 4) for k, v in sorted(by_kind.items(), key=lambda x: -x[1])},
         "clocks": clocks,

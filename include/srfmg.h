@@ -102,6 +102,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
  * and replayed afterwards.  Errors: SRFMG_EINVAL for NULL or misaligned
  * (not 16-byte aligned) pointers, SRFMG_ECUDA if a launch fails. */
 srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream);
+/* (The handle keeps the captured graphs of up to four (f, u) pointer pairs;
+ * the least recently used one is replaced.) */
 
 /* The same solve from and to HOST memory: copies f (N doubles) to a device
  * staging buffer owned by the handle, solves, copies the solution back into u
@@ -109,8 +111,20 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
  * buffers give the fastest copies; pageable ones work.  f and u may alias. */
 srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream);
 
-/* Gradient of a loss through the solve.  Reserved: returns SRFMG_EUNSUPPORTED
- * in this build (nothing is enqueued). */
+/* Gradient of a loss L(u) through the solve (the paper has no adjoint; the
+ * operator is the one of Sec. 4).  The discrete operator L of SRFMG_OP_LAPLACE
+ * (cell-centred finite volumes with odd ghosts: tridiag(-1, 2, -1)/h^2 with 3 in
+ * the wall rows) is symmetric, so the adjoint equation L^T lambda = dL/du is the
+ * forward equation with dL/du as its right-hand side, and dL/df = lambda.
+ * lambda is computed by the same FMG(-SR) solve as srfmg_solve (same plan,
+ * precision and launch schedule), so it carries that solve's algebraic error
+ * for the right-hand side dL/du (for a rough dL/du, such as a residual against
+ * noisy data, of the order of 1e-4 relative at N = 2^14 after one FMG cycle).
+ * dL_du: device pointer, N doubles (the gradient of L with respect to u at the
+ * cell centres); dL_df: device pointer, N doubles, receives dL/df.  Pointers,
+ * alignment, overlap, asynchrony and errors as in srfmg_solve (it is the same
+ * call: it has its own captured graph for its pointer pair).  Returns
+ * SRFMG_EUNSUPPORTED for an operator without a symmetric discretisation. */
 srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream);
 
 /* Plan information (workspace size, launches per solve, ...). */

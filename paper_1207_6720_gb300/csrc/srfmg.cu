@@ -73,9 +73,16 @@ struct srfmg_plan {
     std::vector<Op> ops;
     std::vector<std::string> names;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    const double *g_f = nullptr;
-    double *g_u = nullptr;
+    // captured launch sequences, one per (f, u) pointer pair (a solve and an
+    // adjoint solve on other buffers keep their own); least recently used out
+    static constexpr int kGraphSlots = 4;
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        const double *f = nullptr;
+        double *u = nullptr;
+        unsigned long long used = 0;
+    } graphs[kGraphSlots];
+    unsigned long long graph_clock = 0;
     bool use_graph = true;
     std::string err = "no error";
 };
@@ -544,7 +551,8 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
 }
 
 void release(srfmg_plan *h) {
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void *ptr : h->allocs) cudaFree(ptr);
     h->allocs.clear();
@@ -658,8 +666,14 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
         e = enqueue_all(h, f, u, s);
         return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "kernel launch");
     }
-    if (!h->gexec || h->g_f != f || h->g_u != u) {
-        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    srfmg_plan::GraphSlot *slot = nullptr;
+    for (auto &g : h->graphs)
+        if (g.exec && g.f == f && g.u == u) slot = &g;
+    if (!slot) {
+        slot = &h->graphs[0];
+        for (auto &g : h->graphs)
+            if (!g.exec || g.used < slot->used) slot = &g;
+        if (slot->exec) { cudaGraphExecDestroy(slot->exec); slot->exec = nullptr; }
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
@@ -667,13 +681,14 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
         e = cudaStreamEndCapture(h->cap_stream, &graph);
         if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, le, "kernel launch during capture"); }
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        e = cudaGraphInstantiate(&slot->exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
-        h->g_f = f;
-        h->g_u = u;
+        if (e != cudaSuccess) { slot->exec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+        slot->f = f;
+        slot->u = u;
     }
-    e = cudaGraphLaunch(h->gexec, s);
+    slot->used = ++h->graph_clock;
+    e = cudaGraphLaunch(slot->exec, s);
     return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "cudaGraphLaunch");
 }
 
@@ -699,10 +714,14 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
     return SRFMG_OK;
 }
 
+// The operator of SRFMG_OP_LAPLACE (cell-centred, odd ghosts: tridiag(-1, 2, -1)/h^2
+// with 3 in the wall rows) is symmetric, so the adjoint equation L^T lambda = dL/du is
+// the forward equation with dL/du as its right-hand side: lambda = dL/df comes from
+// the same FMG(-SR) solve.
 srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream) {
-    (void)dL_du; (void)dL_df; (void)stream;
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
-    return fail(h, SRFMG_EUNSUPPORTED, "the adjoint solve is not built yet");
+    if (h->p.op != SRFMG_OP_LAPLACE) return fail(h, SRFMG_EUNSUPPORTED, "adjoint of this operator");
+    return srfmg_solve(h, dL_du, dL_df, stream);
 }
 
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {

@@ -140,6 +140,21 @@ class Solver:
                     "solve")
         return u
 
+    def adjoint(self, dL_du, dL_df=None, stream=None):
+        """dL/df for a loss L(u) of the solution, given dL/du (CUDA float64):
+        the adjoint solve of the C ABI (the same FMG(-SR) solve applied to the
+        adjoint right-hand side; the operator is symmetric)."""
+        import torch
+        if not (dL_du.is_cuda and dL_du.dtype == torch.float64 and dL_du.is_contiguous()
+                and dL_du.numel() == self.n):
+            raise ValueError("dL_du must be a contiguous CUDA float64 tensor of 2^log2_n values")
+        if dL_df is None:
+            dL_df = torch.empty_like(dL_du)
+        self._check(self.lib.srfmg_adjoint(self.h, ctypes.c_void_p(dL_du.data_ptr()),
+                                            ctypes.c_void_p(dL_df.data_ptr()), _stream_ptr(stream)),
+                    "adjoint")
+        return dL_df
+
     def solve_host(self, f, u=None, stream=None):
         """Solve from and to host numpy arrays (copies inside; synchronises)."""
         import numpy as np
@@ -175,6 +190,36 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _solve_function():
+    import torch
+
+    class _Solve(torch.autograd.Function):
+        """u = solve(f) with dL/df = adjoint(dL/du) in the backward pass."""
+
+        @staticmethod
+        def forward(ctx, f, solver):
+            ctx.solver = solver
+            return solver.solve(f.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            return ctx.solver.adjoint(grad_u.contiguous()), None
+
+    return _Solve
+
+
+_SOLVE_FN = None
+
+
+def solve_autograd(solver, f):
+    """Differentiable solve: ``u = solve_autograd(solver, f)``; ``u.backward``
+    (or ``torch.autograd.grad``) runs the adjoint solve on the GPU."""
+    global _SOLVE_FN
+    if _SOLVE_FN is None:
+        _SOLVE_FN = _solve_function()
+    return _SOLVE_FN.apply(f, solver)
 
 
 def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None):
