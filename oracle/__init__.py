@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.  The product path never
 imports this package.  The C source (``srfmg_oracle.c``) restates the paper's
-algorithms (Figs. 1-4, Eqs. 4-7, the operators of Sec. 4) step by step; this
+algorithms (Figs. 1-4, Eqs. 1-7, the operators of Sec. 4, and the Bratu
+operator -u'' + lam e^u of the nonlinear FAS of Sec. 2.2) step by step; this
 module only marshals numpy arrays through ctypes.
 
 Parity pins: every routine is pinned by ``tests/test_oracle_pins.py`` against
@@ -28,6 +29,7 @@ class _Params(ctypes.Structure):
         ("smoother", ctypes.c_int32), ("tau_src", ctypes.c_int32),
         ("seg_w", ctypes.c_int32 * (MAXLEV + 1)),
         ("seg_b", ctypes.c_int32 * (MAXLEV + 1)),
+        ("op", ctypes.c_int32), ("lam", ctypes.c_double),
     ]
 
 
@@ -56,6 +58,8 @@ def lib():
             "or_fmg_h": [pp, dp, dp],
             "or_fmg_v": [pp, dp, dp],
             "or_vcycles_h": [pp, dp, dp, i],
+            "or_apply_N": [i, ctypes.c_double, dp, dp],
+            "or_coarsest": [pp, i, dp, dp],
         }
         for name, args in sigs.items():
             fn = getattr(_lib, name)
@@ -82,10 +86,12 @@ def _check(rc, what):
 class Params:
     """Solve parameters; ``seg[l] = (w, b)`` segments level l (w = 0: whole level)."""
 
-    def __init__(self, M, M0=2, nRS=1, nu1=1, nu2=1, smoother="lex", tau_src="assembled", seg=None):
+    def __init__(self, M, M0=2, nRS=1, nu1=1, nu2=1, smoother="lex", tau_src="assembled", seg=None,
+                 op="laplace", lam=0.0):
         self.M, self.M0, self.nRS, self.nu1, self.nu2 = M, M0, nRS, nu1, nu2
         self.smoother, self.tau_src = smoother, tau_src
         self.seg = dict(seg or {})
+        self.op, self.lam = op, lam
 
     def c(self):
         p = _Params()
@@ -95,14 +101,18 @@ class Params:
         for l, (w, b) in self.seg.items():
             p.seg_w[l] = w
             p.seg_b[l] = b
+        p.op = {"laplace": 0, "bratu": 1}[self.op]
+        p.lam = self.lam
         return p
 
     def __repr__(self):
         return (f"Params(M={self.M}, M0={self.M0}, nRS={self.nRS}, nu=({self.nu1},{self.nu2}), "
-                f"smoother={self.smoother}, tau_src={self.tau_src}, seg={self.seg})")
+                f"smoother={self.smoother}, tau_src={self.tau_src}, seg={self.seg}, op={self.op}, "
+                f"lam={self.lam})")
 
 
-def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assembled"):
+def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assembled", op="laplace",
+              lam=0.0):
     """SR levels (the finest nRS) split into segments of W >> (M-l) cells with
     b buffer cells per side; every other level is smoothed as a whole."""
     seg = {}
@@ -111,7 +121,8 @@ def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assem
         if w < 2:
             raise ValueError("segment narrower than 2 cells on an SR level")
         seg[l] = (w, b)
-    return Params(M, M0=M0, nRS=nRS, nu1=nu1, nu2=nu2, smoother=smoother, tau_src=tau_src, seg=seg)
+    return Params(M, M0=M0, nRS=nRS, nu1=nu1, nu2=nu2, smoother=smoother, tau_src=tau_src, seg=seg,
+                  op=op, lam=lam)
 
 
 def paper_params(M, nRS, halo_type, ns, M0=2):
@@ -131,6 +142,24 @@ def apply_L(u):
     out = np.empty_like(u)
     _check(lib().or_apply_L(len(u), _ptr(u), _ptr(out)), "apply_L")
     return out
+
+
+def apply_N(u, lam):
+    """N(u) = L u + lam e^u (the Bratu operator; lam = 0: L)."""
+    u = _arr(u)
+    out = np.empty_like(u)
+    _check(lib().or_apply_N(len(u), float(lam), _ptr(u), _ptr(out)), "apply_N")
+    return out
+
+
+def coarsest(params, rhs, u0):
+    """The coarsest-level solve of ``params`` (Thomas, or Newton for Bratu)
+    from the starting iterate u0."""
+    rhs = _arr(rhs)
+    u = _arr(u0).copy()
+    p = params.c()
+    _check(lib().or_coarsest(ctypes.byref(p), len(rhs), _ptr(rhs), _ptr(u)), "coarsest")
+    return u
 
 
 def restrict(uf):

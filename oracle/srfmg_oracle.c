@@ -9,7 +9,11 @@
  * shares no code, header, table or helper with the CUDA library.
  *
  * Problem (Sec. 4): -u'' = f on (0,1), u(0) = u(1) = 0, cell-centred second
- * order finite volumes.  Level l has n = 2^l cells of width h = 1/n, centres
+ * order finite volumes.  Also the nonlinear problem -u'' + lam e^u = f (the
+ * Bratu equation, lam >= 0) with the same discretisation, solved by the same
+ * FAS cycles (Sec. 2.2, Eqs. 1-2: the coarse equation of a nonlinear operator;
+ * Fig. 1: a nonlinear smoother S(L, u, f)); the paper's studies are linear,
+ * so the nonlinear pieces carry "Reading:" notes.  Level l has n = 2^l cells of width h = 1/n, centres
  * x_i = (i + 1/2) h; the Dirichlet wall is an odd ghost cell (u_{-1} = -u_0,
  * u_n = -u_{n-1}), which is where the diagonal 3/h^2 of the first and last
  * rows of the appendix operator comes from.
@@ -29,6 +33,7 @@
  * stored levels use offset 0; a segment's patch buffer uses the index of its
  * first cell.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -51,7 +56,12 @@ typedef struct {
                                   the literal reading of Fig. 3 line 4 */
     int32_t seg_w[OR_MAXLEV + 1]; /* per level: segment interior width, 0 = whole level */
     int32_t seg_b[OR_MAXLEV + 1]; /* per level: buffer cells on each side */
+    int32_t op;             /* 0: -u'' = f;  1: -u'' + lam e^u = f */
+    double lam;             /* op 1: lam >= 0 (op 0: ignored) */
 } or_params;
+
+/* lam of the operator (0 for the linear problem). */
+static double op_lam(const or_params *p) { return p->op == 1 ? p->lam : 0.0; }
 
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2 };
 
@@ -78,6 +88,12 @@ static double Lu_at(const double *u, int off, int i, int n) {
 static double Ldiag_at(int i, int n) {
     double inv_h2 = (double)n * (double)n;
     return (i == 0 || i == n - 1) ? 3.0 * inv_h2 : 2.0 * inv_h2;
+}
+
+/* Nonlinear operator N(u)_i = (L u)_i + lam e^{u_i}.  With lam = 0 the added
+ * term is an exact +0, so N is L bit for bit. */
+static double Nu_at(const double *u, int off, int i, int n, double lam) {
+    return Lu_at(u, off, i, n) + lam * exp(cell(u, off, i));
 }
 
 /* Restriction (Sec. 4, first order): mean of the two children of coarse J. */
@@ -119,7 +135,11 @@ static double prolong_fmg_at(const double *uc, int i, int nc) {
 
 /* Exact solve of L u = rhs on one level (the coarsest-grid solve of Figs. 1-2):
  * L is tridiagonal and diagonally dominant, so the Thomas algorithm. */
-static int thomas(int n, const double *rhs, double *u) {
+static int thomas_shift(int n, const double *rhs, const double *dshift, double *u);
+static int thomas(int n, const double *rhs, double *u) { return thomas_shift(n, rhs, NULL, u); }
+
+/* Thomas for the tridiagonal L + diag(dshift) (dshift = NULL: L). */
+static int thomas_shift(int n, const double *rhs, const double *dshift, double *u) {
     if (n < 1) return OR_EINVAL;
     double *cp = (double *)malloc(sizeof(double) * (size_t)n);
     double *dp = (double *)malloc(sizeof(double) * (size_t)n);
@@ -128,7 +148,8 @@ static int thomas(int n, const double *rhs, double *u) {
     for (int i = 0; i < n; i++) {
         double lower = i > 0 ? off : 0.0;
         double upper = i < n - 1 ? off : 0.0;
-        double denom = Ldiag_at(i, n) - (i > 0 ? lower * cp[i - 1] : 0.0);
+        double diag = dshift ? Ldiag_at(i, n) + dshift[i] : Ldiag_at(i, n);
+        double denom = diag - (i > 0 ? lower * cp[i - 1] : 0.0);
         cp[i] = upper / denom;
         dp[i] = (rhs[i] - (i > 0 ? lower * dp[i - 1] : 0.0)) / denom;
     }
@@ -138,13 +159,51 @@ static int thomas(int n, const double *rhs, double *u) {
     return OR_OK;
 }
 
+/* Exact solve of N(u) = rhs on the coarsest level (Figs. 1-2: "exact solve of
+ * coarsest grid").  Linear: Thomas.  Reading (nonlinear): Newton's method from
+ * the iterate passed in u (the restricted FAS iterate; zero in the first FMG
+ * step), each step a Thomas solve with the Jacobian L + diag(lam e^u), until
+ * the step is at most 4 ulp of max|u| or stops shrinking (the unique solution
+ * for lam >= 0 to rounding; at most 100 steps). */
+static int coarsest_solve(const or_params *p, int n, const double *rhs, double *u) {
+    double lam = op_lam(p);
+    if (lam == 0.0) return thomas(n, rhs, u);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double *du = (double *)malloc(sizeof(double) * (size_t)n);
+    int rc = (r && d && du) ? OR_OK : OR_ENOMEM;
+    double prev = INFINITY;
+    for (int it = 0; it < 100 && rc == OR_OK; it++) {
+        for (int i = 0; i < n; i++) {
+            r[i] = rhs[i] - Nu_at(u, 0, i, n, lam);
+            d[i] = lam * exp(u[i]);
+        }
+        rc = thomas_shift(n, r, d, du);
+        if (rc) break;
+        double step = 0.0, umax = 0.0;
+        for (int i = 0; i < n; i++) {
+            u[i] += du[i];
+            step = fmax(step, fabs(du[i]));
+            umax = fmax(umax, fabs(u[i]));
+        }
+        if (step <= 4.0 * DBL_EPSILON * umax || step >= prev) break;
+        prev = step;
+    }
+    free(r); free(d); free(du);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* The smoother S of Sec. 3 and Fig. 5 on one extended patch           */
 /* ------------------------------------------------------------------ */
 
-/* One Gauss-Seidel update (omega = 1): u_i += (f_i - (L u)_i) / L_ii. */
-static void gs_update(double *v, int voff, const double *rhs, int roff, int i, int n) {
-    v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - Lu_at(v, voff, i, n)) / Ldiag_at(i, n);
+/* One Gauss-Seidel update (omega = 1): u_i += (f_i - (L u)_i) / L_ii.
+ * Reading (nonlinear, the smoother S(L, u, f) of Fig. 1): one pointwise Newton
+ * step, u_i += (f_i - N(u)_i) / (L_ii + lam e^{u_i}); with lam = 0 both added
+ * terms are exact zeros and this is the linear update bit for bit. */
+static void gs_update(double *v, int voff, const double *rhs, int roff, int i, int n, double lam) {
+    double e = lam * exp(cell(v, voff, i));
+    v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - (Lu_at(v, voff, i, n) + e)) / (Ldiag_at(i, n) + e);
 }
 
 /* Kaczmarz pass of Fig. 5 over every coarse cell J whose children both lie in
@@ -174,17 +233,17 @@ static void kaczmarz_pass(double *v, int voff, const double *uH, int e0, int e1)
  *     this discretization its V-cycle factor grows with the depth and one FMG
  *     cycle misses discretization accuracy. */
 static void patch_sweeps(int smoother, double *v, int voff, const double *rhs, int roff,
-                         int n, int e0, int e1, int nsweeps, const double *uH) {
+                         int n, int e0, int e1, int nsweeps, const double *uH, double lam) {
     int ascending = 1;
     for (int k = 0; k < nsweeps; k++) {
         if (uH) kaczmarz_pass(v, voff, uH, e0, e1);
         if (smoother == 1) {
             for (int colour = 0; colour < 2; colour++)
                 for (int i = e0; i < e1; i++)
-                    if ((i & 1) == colour) gs_update(v, voff, rhs, roff, i, n);
+                    if ((i & 1) == colour) gs_update(v, voff, rhs, roff, i, n, lam);
         } else {
-            if (ascending) for (int i = e0; i < e1; i++) gs_update(v, voff, rhs, roff, i, n);
-            else           for (int i = e1 - 1; i >= e0; i--) gs_update(v, voff, rhs, roff, i, n);
+            if (ascending) for (int i = e0; i < e1; i++) gs_update(v, voff, rhs, roff, i, n, lam);
+            else           for (int i = e1 - 1; i >= e0; i--) gs_update(v, voff, rhs, roff, i, n, lam);
             ascending = !ascending;
         }
     }
@@ -210,15 +269,17 @@ static void extended_patch(int s, int w, int b, int n, int *e0, int *e1, int *lo
  * the role of Ihat ubar in Eq. 7 (Ihat = I here).  Reads fine cells 2J-2 ..
  * 2J+3 of ubar (fewer at a wall) and 2J, 2J+1 of rhs_f. */
 static double tau_rhs_at(const double *ubar, int uoff, const double *rhs_f, int roff,
-                         int J, int nf) {
+                         int J, int nf, double lam) {
     int nc = nf / 2;
     double Rrhs = (cell(rhs_f, roff, 2 * J) + cell(rhs_f, roff, 2 * J + 1)) * 0.5;
     double inv_H2 = (double)nc * (double)nc;
     double uJ = restrict_at(ubar, uoff, J);
     double Gl = J == 0 ? 2.0 * uJ : uJ - restrict_at(ubar, uoff, J - 1);
     double Gr = J == nc - 1 ? -2.0 * uJ : restrict_at(ubar, uoff, J + 1) - uJ;
-    double Lc = (Gl - Gr) * inv_H2;
-    double RLf = (Lu_at(ubar, uoff, 2 * J, nf) + Lu_at(ubar, uoff, 2 * J + 1, nf)) * 0.5;
+    /* nonlinear (Eq. 2 with N for L): N_c(R ubar) - R N_f(ubar); lam = 0 adds
+     * exact zeros */
+    double Lc = (Gl - Gr) * inv_H2 + lam * exp(uJ);
+    double RLf = (Nu_at(ubar, uoff, 2 * J, nf, lam) + Nu_at(ubar, uoff, 2 * J + 1, nf, lam)) * 0.5;
     return (Rrhs + Lc) - RLf;
 }
 
@@ -250,7 +311,7 @@ static void smooth_level(or_state *st, int l, const double *u_in, double *u_out,
     int n = 1 << l;
     if (!segmented(p, l)) {
         if (u_out != u_in) memcpy(u_out, u_in, sizeof(double) * (size_t)n);
-        patch_sweeps(p->smoother, u_out, 0, st->rhs[l], 0, n, 0, n, nsweeps, uH);
+        patch_sweeps(p->smoother, u_out, 0, st->rhs[l], 0, n, 0, n, nsweeps, uH, op_lam(p));
         return;
     }
     int w = p->seg_w[l];
@@ -258,7 +319,7 @@ static void smooth_level(or_state *st, int l, const double *u_in, double *u_out,
         int e0, e1, lo, hi;
         extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
         memcpy(st->patch, u_in + lo, sizeof(double) * (size_t)(hi - lo));
-        patch_sweeps(p->smoother, st->patch, lo, st->rhs[l], 0, n, e0, e1, nsweeps, uH);
+        patch_sweeps(p->smoother, st->patch, lo, st->rhs[l], 0, n, e0, e1, nsweeps, uH, op_lam(p));
         memcpy(u_out + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
     }
 }
@@ -280,7 +341,7 @@ static void presmooth_and_restrict(or_state *st, int l) {
         smooth_level(st, l, ul, st->tmp, p->nu1, NULL);
         memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
         for (int J = 0; J < nc; J++) uc[J] = restrict_at(ul, 0, J);
-        for (int J = 0; J < nc; J++) rc[J] = tau_rhs_at(ul, 0, rf, 0, J, n);
+        for (int J = 0; J < nc; J++) rc[J] = tau_rhs_at(ul, 0, rf, 0, J, n, op_lam(p));
         return;
     }
     int w = p->seg_w[l];
@@ -288,11 +349,11 @@ static void presmooth_and_restrict(or_state *st, int l) {
         int e0, e1, lo, hi;
         extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
         memcpy(st->patch, ul + lo, sizeof(double) * (size_t)(hi - lo));
-        patch_sweeps(p->smoother, st->patch, lo, rf, 0, n, e0, e1, p->nu1, NULL);
+        patch_sweeps(p->smoother, st->patch, lo, rf, 0, n, e0, e1, p->nu1, NULL, op_lam(p));
         memcpy(st->tmp + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
         for (int J = s / 2; J < (s + w) / 2; J++) {
             uc[J] = restrict_at(st->patch, lo, J);
-            rc[J] = tau_rhs_at(st->patch, lo, rf, 0, J, n);
+            rc[J] = tau_rhs_at(st->patch, lo, rf, 0, J, n, op_lam(p));
         }
     }
     memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
@@ -324,7 +385,7 @@ static void postsmooth_update(or_state *st, int l) {
 static int vcycle(or_state *st, int top) {
     const or_params *p = st->p;
     for (int l = top; l > p->M0; l--) presmooth_and_restrict(st, l);
-    int rc = thomas(1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
     if (rc) return rc;
     for (int l = p->M0 + 1; l <= top; l++) postsmooth_update(st, l);
     return OR_OK;
@@ -338,6 +399,8 @@ static void free_state(or_state *st) {
 static int check_params(const or_params *p) {
     if (p->M0 < 2 || p->M < p->M0 || p->M > 28) return OR_EINVAL;
     if (p->nRS < 0 || p->nRS > p->M - p->M0) return OR_EINVAL;
+    if (p->op != 0 && p->op != 1) return OR_EINVAL;
+    if (p->op == 1 && !(p->lam >= 0.0 && p->lam < INFINITY)) return OR_EINVAL;
     if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16) return OR_EINVAL;
     if (p->smoother < 0 || p->smoother > 1 || p->tau_src < 0 || p->tau_src > 1) return OR_EINVAL;
     for (int l = p->M0 + 1; l <= p->M; l++) {
@@ -384,7 +447,7 @@ static void rhs_hierarchy(or_state *st, int top, const double *f_top) {
  * the FMG interpolation Pi followed by one V-cycle. */
 static int fmg_up_to(or_state *st, int top) {
     const or_params *p = st->p;
-    int rc = thomas(1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
     for (int k = p->M0; k < top && !rc; k++) {
         int nc = 1 << k;
         for (int i = 0; i < 2 * nc; i++) st->u[k + 1][i] = prolong_fmg_at(st->u[k], i, nc);
@@ -418,8 +481,21 @@ int or_thomas(int n, const double *rhs, double *u) { return thomas(n, rhs, u); }
 
 /* tau-corrected coarse rhs from an assembled fine vector, every coarse cell. */
 int or_tau_rhs(int nf, const double *ubar, const double *rhs_f, double *rhs_c) {
-    for (int J = 0; J < nf / 2; J++) rhs_c[J] = tau_rhs_at(ubar, 0, rhs_f, 0, J, nf);
+    for (int J = 0; J < nf / 2; J++) rhs_c[J] = tau_rhs_at(ubar, 0, rhs_f, 0, J, nf, 0.0);
     return OR_OK;
+}
+
+/* The nonlinear operator N(u) = L u + lam e^u on one level of n cells. */
+int or_apply_N(int n, double lam, const double *u, double *out) {
+    for (int i = 0; i < n; i++) out[i] = Nu_at(u, 0, i, n, lam);
+    return OR_OK;
+}
+
+/* The coarsest-level solve of p on n cells: rhs in, u = starting iterate in,
+ * solution out. */
+int or_coarsest(const or_params *p, int n, const double *rhs, double *u) {
+    if (p->op != 0 && p->op != 1) return OR_EINVAL;
+    return coarsest_solve(p, n, rhs, u);
 }
 
 /* One application of the level smoother S (segmentation from p->seg_w[l]). */
@@ -520,13 +596,13 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
                 patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
                 frhs[i - lo] = f[i];
             }
-            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL);
+            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL, op_lam(p));
             memcpy(win + (win_hi - win_lo), patch + (s - lo), sizeof(double) * (size_t)w);
             win_hi += w;
             /* coarse cells whose fine stencil 2J-2 .. 2J+3 is now assembled */
             while (Jnext < nc && (2 * Jnext + 3 < win_hi || win_hi == n)) {
                 uc_new[Jnext] = restrict_at(win, win_lo, Jnext);
-                st.rhs[M - 1][Jnext] = tau_rhs_at(win, win_lo, f, 0, Jnext, n);
+                st.rhs[M - 1][Jnext] = tau_rhs_at(win, win_lo, f, 0, Jnext, n, op_lam(p));
                 Jnext++;
             }
             /* keep only the cells a pending coarse cell can still read */
@@ -550,7 +626,7 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
             patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
             frhs[i - lo] = f[i];
         }
-        patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, st.u[M - 1]);
+        patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, st.u[M - 1], op_lam(p));
         memcpy(u_out + s, patch + (s - lo), sizeof(double) * (size_t)w);
     }
 done:

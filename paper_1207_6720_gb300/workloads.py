@@ -12,6 +12,9 @@ x_i = (i + 1/2)/N.
   from ``numpy.random.default_rng(seed)``, so f = sum c_k (k pi)^2 sin(k pi x).
 * ``paper_series``: the appendix program's problem, f = sum over odd j below
   N/16 of sin(j pi x)/j, u = sum sin(j pi x)/(j (j pi)^2).
+* ``bratu_series``: the nonlinear problem -u'' + lam e^u = f with the
+  manufactured solution u = scale * sum c_k sin(k pi x) (default scale 1/2),
+  f = -u'' + lam e^u sampled at the centres.
 """
 import numpy as np
 
@@ -39,6 +42,20 @@ def sine_series(M, nmodes, seed, scale=1.0):
         s = np.sin(k * np.pi * x)
         f += c[k - 1] * (k * np.pi) ** 2 * s
         u += c[k - 1] * s
+    return f, u, c
+
+
+def bratu_series(M, nmodes, seed, lam, scale=0.5):
+    """(f, u_exact, c) for -u'' + lam e^u = f with u = scale * sine series."""
+    x = centres(M)
+    c = scale * sine_coefficients(nmodes, seed)
+    f = np.zeros_like(x)
+    u = np.zeros_like(x)
+    for k in range(1, nmodes + 1):
+        s = np.sin(k * np.pi * x)
+        f += c[k - 1] * (k * np.pi) ** 2 * s
+        u += c[k - 1] * s
+    f += lam * np.exp(u)
     return f, u, c
 
 
