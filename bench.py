@@ -19,6 +19,10 @@ timed region, and the accuracy of the result against the exact solution.
 --impl reference times the CPU oracle (the method's plain serial C
 restatement) on the host cores, one bounded sample of the workload per step.
 
+--workload bratu: the nonlinear -u'' + lam e^u = f (lam = 1) with the same
+discretisation and FAS cycles, N = 2^26 cells, 16384 segments of 4096 cells,
+V(2,1), FP64; u = 1/2 sum_{k=1..16} c_k sin(k pi x) (seed 1).
+
 Multi-GPU: the solve does not shard across GPUs here; with --gpus N every rank
 solves its own copy (replicas, weak scaling) and the value is the sum over
 ranks with the time taken as the maximum over ranks.
@@ -39,6 +43,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine-grid unknowns/s per FMG-FAS-SR solve at discretization accuracy vs plain FP64"
+METRIC_BRATU = ("fine-grid unknowns/s per FMG-FAS-SR solve of -u''+lam e^u=f at discretization "
+                "accuracy vs plain FP64")
 UNIT = "unknowns/s"
 NOMINAL_FP64_TFLOPS = 1.26        # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -48,6 +54,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # algorithmic DRAM bytes per cell of the level the launch sweeps.
 FLOPS_PER_CELL = {"sr_post": 13.5, "sr_pre": 15.5, "level_down_fmg": 15.5,
                   "level_down": 9.0, "level_up": 9.0}
+# Bratu, V(2,1): the nonlinear sweep adds 4 per cell (c e^u with the
+# exponential counted as one operation, the diagonal 2 + e, its reciprocal,
+# the residual term) and tau 5 (three exponentials, two combinations)
+FLOPS_PER_CELL_BRATU = {"sr_post": 6.5 + 1 * (2 + 9), "sr_pre": 6.5 + 2 * 9 + 0.5 + 6,
+                        "level_down_fmg": 6.5 + 2 * 9 + 0.5 + 6, "level_down": 2 * 9 + 0.5 + 6,
+                        "level_up": 2.0 + 1 * 9}
 BYTES_PER_CELL = {"sr_post": 20.0, "sr_pre": 20.0, "level_down_fmg": 20.0,
                   "level_down": 24.0, "level_up": 28.0}
 
@@ -58,7 +70,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["srfmg", "reference"], default="srfmg")
-    ap.add_argument("--log2n", type=int, default=24)
+    ap.add_argument("--workload", choices=["poisson", "bratu"], default="poisson")
+    ap.add_argument("--lam", type=float, default=1.0, help="Bratu: lam of -u'' + lam e^u = f")
+    ap.add_argument("--log2n", type=int, default=None, help="default 24 (poisson), 26 (bratu)")
     ap.add_argument("--segment-width", type=int, default=4096)
     ap.add_argument("--buffer-width", type=int, default=8)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
@@ -67,10 +81,25 @@ def parse_args():
     ap.add_argument("--only-solve", action="store_true",
                     help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
                          "the minimal run used for ncu captures")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.log2n is None:
+        a.log2n = 26 if a.workload == "bratu" else 24
+    if a.workload == "bratu":
+        a.precision = "fp64"
+    return a
 
 
 def workload_config(a):
+    if getattr(a, "workload", "poisson") == "bratu":
+        return {
+            "workload": f"1D -u''+lam e^u=f, lam={a.lam}, N=2^{a.log2n}, FMG-FAS V(2,1) pointwise Newton "
+                        f"lexicographic GS, 1 SR level of {(1 << a.log2n) // a.segment_width} segments x "
+                        f"{a.segment_width} cells, buffer {a.buffer_width}, FP64",
+            "precision": "fp64", "N": 1 << a.log2n, "segment_width": a.segment_width,
+            "buffer_width": a.buffer_width, "n_sr_levels": 1, "nu": [2, 1], "coarsest_level": 2,
+            "lam": a.lam, "modes": 16, "seed": 1,
+            "l2": "inputs larger than L2 (f and u 512 MiB each plus the stored coarse levels)",
+        }
     prec = ("64-bit fixed point (solution, residual, tau, interpolation) + FP64 coarsest solve"
             if getattr(a, "precision", "fp64") == "mixed" else "FP64")
     return {
@@ -233,8 +262,12 @@ def run_reference(a):
     from paper_1207_6720_gb300 import workloads
     Ms = min(a.log2n, 20)            # bounded sample per step: one solve at N = 2^20
     Ws = min(a.segment_width, (1 << Ms) // 4)
-    f, _, _ = workloads.sine_series(Ms, 32, seed=1)
-    p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
+    if a.workload == "bratu":
+        f, _, _ = workloads.bratu_series(Ms, 16, seed=1, lam=a.lam)
+        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
+    else:
+        f, _, _ = workloads.sine_series(Ms, 32, seed=1)
+        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
     for _ in range(a.warmup):
         oracle.fmg_v(p, f)
     t0 = time.perf_counter()
@@ -243,7 +276,8 @@ def run_reference(a):
     dt = time.perf_counter() - t0
     value = a.steps * (1 << Ms) / dt
     sample = f"one serial oracle solve of the same workload family at N=2^{Ms} per step"
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+    line = {"metric": METRIC_BRATU if a.workload == "bratu" else METRIC, "value": value, "unit": UNIT,
+            "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -423,10 +457,102 @@ def run_gpu(a):
     dist.close()
 
 
+def run_gpu_bratu(a):
+    """The Bratu workload: SR solve vs the plain stored solve, FP64."""
+    import torch
+    from paper_1207_6720_gb300 import srfmg, workloads
+
+    dist = Dist(a.gpus, use_cuda=True)
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    M, W, b = a.log2n, a.segment_width, a.buffer_width
+    N = 1 << M
+    f, u_exact, _ = workloads.bratu_series(M, 16, seed=1, lam=a.lam)
+    fd = torch.from_numpy(f).to(dev)
+    ud = torch.empty_like(fd)
+    kw = dict(op=srfmg.BRATU, lambda_=a.lam, nu1=2, nu2=1)
+    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, **kw)
+    info = solver.info()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ms = time_solves(solver, fd, ud, a.steps, a.warmup, dist, stream)
+    clocks = sampler.stop()
+    ms = dist.max(ms)
+    value = dist.world * N / (ms * 1e-3)
+    u = ud.cpu().numpy()
+    line = {"metric": METRIC_BRATU, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a), "gpu_launches": info.kernels_per_solve * a.steps,
+            "clocks": clocks}
+    if not a.only_solve:
+        plain = srfmg.Solver(M, device=dev, n_sr_levels=0, **kw)
+        ms_plain = dist.max(time_solves(plain, fd, ud, max(5, a.steps // 4), a.warmup, dist, stream))
+        plain.close()
+        fh = torch.from_numpy(f).pin_memory()
+        uh = torch.empty(N, dtype=torch.float64).pin_memory()
+        fh_np, uh_np = fh.numpy(), uh.numpy()
+        solver.solve_host(fh_np, uh_np, stream=stream)
+        dist.barrier()
+        e2e_steps = max(3, a.steps // 10)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            solver.solve_host(fh_np, uh_np, stream=stream)
+        dt_e2e = dist.max((time.perf_counter() - t0) / e2e_steps)
+        prof = solver.profile(fd, torch.empty_like(fd), nsolves=3, stream=stream)
+        torch.cuda.synchronize()
+        top_name, top_ms = max(prof, key=lambda x: x[1])
+        kind, lvl = top_name.split(" L")
+        cells = 1 << int(lvl)
+        flops = FLOPS_PER_CELL_BRATU.get(kind, 0.0) * cells
+        achieved_tf = flops / (top_ms * 1e-3) / 1e12
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * cells
+        line.update({
+            "e2e": {"value": dist.world * N / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
+                    "d2h_bytes_per_step": int(uh_np.nbytes)},
+            "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                           "speedup_over_plain": ms_plain / ms},
+            "roofline": {"bound": "alu", "kernel": top_name, "achieved": achieved_tf,
+                         "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": None,
+                         "peak_source": "nominal FP64 from unit counts and the maximum SM clock "
+                                        "(exponential and reciprocal counted as one operation)",
+                         "algorithmic_flops": flops, "launch_ms": top_ms,
+                         "hbm_view": {"achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                      "unit": "GB/s",
+                                      "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak}},
+        })
+    err = float(np.max(np.abs(u - u_exact)))
+    acc = {"err_max_vs_exact": err, "rel_err_max_vs_exact": err / float(np.max(np.abs(u_exact)))}
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and not a.only_solve:
+        import oracle
+        p = oracle.sr_params(M, W, b, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
+        t0 = time.perf_counter()
+        ref = oracle.fmg_v(p, f)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one serial solve of the full N=2^{M} workload (C oracle, "
+                                          f"serial SR with the finest level never stored)"}
+        err_ref = float(np.max(np.abs(ref - u_exact)))
+        acc.update({"oracle_err_max_vs_exact": err_ref,
+                    "rel_maxnorm_vs_oracle": float(np.max(np.abs(u - ref)) / np.max(np.abs(ref))),
+                    "at_discretization_accuracy": bool(err <= 1.5 * err_ref)})
+    line["accuracy"] = acc
+    solver.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "bratu":
+        run_gpu_bratu(a)
     else:
         run_gpu(a)
 

@@ -55,7 +55,12 @@ typedef enum {
     SRFMG_EUNSUPPORTED = 6     /* valid option that this build does not implement */
 } srfmg_status;
 
-typedef enum { SRFMG_OP_LAPLACE = 0 } srfmg_op;          /* -u'' = f */
+/* Operators.  SRFMG_OP_BRATU is the nonlinear -u'' + lambda e^u = f (lambda >= 0)
+ * with the same discretisation, solved by the same FAS cycles (Sec. 2.2,
+ * Eqs. 1-2: the coarse equation of a nonlinear operator; Fig. 1 with the
+ * nonlinear smoother: pointwise Newton Gauss-Seidel); FP64 only.  (The value 1
+ * is kept for a variable-coefficient operator.) */
+typedef enum { SRFMG_OP_LAPLACE = 0, SRFMG_OP_BRATU = 2 } srfmg_op;
 typedef enum { SRFMG_FP64 = 0, SRFMG_MIXED = 1 } srfmg_precision;
 typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
 
@@ -70,7 +75,8 @@ typedef struct {
     int32_t buffer_width;      /* b: buffer cells per segment side; even, 2 <= b <= 64, b <= W */
     int32_t nu1, nu2;          /* V(nu1, nu2): 1 <= nu1, nu2 <= 4 */
     int32_t smoother;          /* srfmg_smoother */
-    int32_t reserved[6];       /* must be zero */
+    double lambda;             /* SRFMG_OP_BRATU: lambda >= 0, finite; must be 0 otherwise */
+    int32_t reserved[4];       /* must be zero */
 } srfmg_params;
 
 /* Information about a created plan. */
@@ -90,7 +96,8 @@ srfmg_status srfmg_default_params(int32_t log2_n, srfmg_params *p);
 /* Create a plan on CUDA device `device`: validates *p (Sec. 3/4 parameter
  * meanings above), allocates the device workspace and records the level
  * schedule (the FMG loop of Fig. 2 with the SR steps of Fig. 3).
- * On success *out is a new handle; on failure *out is NULL. */
+ * On success *out is a new handle; on failure *out is NULL.  SRFMG_OP_BRATU
+ * with SRFMG_MIXED returns SRFMG_EUNSUPPORTED. */
 srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
 
 /* One FMG-FAS(-SR) solve (Figs. 2-4).

@@ -45,6 +45,8 @@ struct Op {
     int nseg;
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
+    // Bratu operator (FP64 kernels instantiated with the nonlinear sweep and tau)
+    bool nl;
     // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
     bool fixed;
     fx::RhsArgs frhs;
@@ -103,8 +105,11 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
-    for (int i = 0; i < 6; ++i) if (p->reserved[i]) return "reserved fields must be zero";
-    if (p->op != SRFMG_OP_LAPLACE) return "op must be SRFMG_OP_LAPLACE";
+    for (int i = 0; i < 4; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    if (p->op != SRFMG_OP_LAPLACE && p->op != SRFMG_OP_BRATU) return "op must be SRFMG_OP_LAPLACE or SRFMG_OP_BRATU";
+    if (p->op == SRFMG_OP_LAPLACE && p->lambda != 0.0) return "lambda must be 0 for SRFMG_OP_LAPLACE";
+    if (p->op == SRFMG_OP_BRATU && !(p->lambda >= 0.0 && p->lambda <= 1e300))
+        return "lambda must be finite and >= 0";
     if (p->precision != SRFMG_FP64 && p->precision != SRFMG_MIXED) return "unknown precision";
     if (p->smoother != SRFMG_SMOOTH_LEX) return "smoother must be SRFMG_SMOOTH_LEX";
     if (p->log2_n_coarsest < 2 || p->log2_n_coarsest > 6) return "log2_n_coarsest must be in [2, 6]";
@@ -165,7 +170,7 @@ size_t sweep_layout(int cells, int *maxlen, int *maxc, int *maxch, int *threads)
 
 size_t tail_smem_doubles(int M0, int Mc) {
     size_t tot = (1u << (Mc + 1)) - (1u << M0);
-    return 2 * tot + (1u << Mc) + 8 + kTailThreads;
+    return 2 * tot + (1u << Mc) + 8 + 2 * kTailThreads;
 }
 
 srfmg_status alloc_dev(srfmg_plan *h, double **out, size_t count) {
@@ -187,6 +192,8 @@ Op make_op(OpKind k) {
     o.kind = k;
     return o;
 }
+
+double op_lambda(const srfmg_plan *h) { return h->p.op == SRFMG_OP_BRATU ? h->p.lambda : 0.0; }
 
 // Level pass of a stored level (global smoothing), tile decomposition.
 Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double *uc_src,
@@ -211,6 +218,7 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     o.lev.u_out = u_out;
     o.lev.uc_out = uc_out;
     o.lev.gc_out = gc_out;
+    o.lev.lam = op_lambda(h);
     if (l == h->M) {               // finest level without SR: rhs from f
         o.lev.g = nullptr;
         o.lev_g = TAG_F;
@@ -238,6 +246,7 @@ Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, doub
     o.seg.uc_out = uc_out;
     o.seg.gc_out = gc_out;
     o.seg.seam = h->seam;
+    o.seg.lam = op_lambda(h);
     o.seg_f = TAG_F;
     if (kind == OP_SR_POST) o.seg_u = TAG_U;
     o.nseg = (int)(h->n / h->W);
@@ -269,6 +278,7 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
     o.tail.g_exp = g_exp;
     o.tail.u_out = u_out;
     o.tail.Ainv = h->Ainv;
+    o.tail.lam = op_lambda(h);
     if (g_from_f) o.tail_g = TAG_F;
     if (out_is_u) o.tail_out = TAG_U;
     o.grid = dim3(1);
@@ -411,6 +421,7 @@ void build_schedule_ops(srfmg_plan *h) {
 
 void build_schedule(srfmg_plan *h) {
     build_schedule_ops(h);
+    for (Op &o : h->ops) o.nl = (h->p.op == SRFMG_OP_BRATU);
     if (!h->fixed) return;
     for (Op &o : h->ops) to_fixed(h, o);
     Op sc = make_op(OP_SCALE);
@@ -472,6 +483,24 @@ cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t 
     return e;
 }
 
+// FP64 kernels of one op (NL: the Bratu instantiation).
+template <bool NL>
+cudaError_t launch_fp64(const Op &o, cudaStream_t s, bool pdl) {
+    cudaError_t e = cudaSuccess;
+    switch (o.kind) {
+    case OP_RHS: e = run(rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.rhs); break;
+    case OP_TAIL: e = run(tail_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.tail); break;
+    case OP_DOWN_PI: e = run(level_down_kernel<true, NL>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_DOWN: e = run(level_down_kernel<false, NL>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_UP: e = run(level_up_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
+    case OP_SR_PRE: e = run(sr_pre_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.seg); break;
+    case OP_SEAM: e = run(seam_tau_kernel<NL>, o.grid, o.block, 0, s, pdl, o.seg, o.nseg); break;
+    case OP_SR_POST: e = run(sr_post_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.seg); break;
+    case OP_SCALE: break;
+    }
+    return e;
+}
+
 // Enqueue one op on s; pdl as in run().
 cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s, bool pdl) {
     if (o0.fixed) return launch_fixed(o0, f, u, s, pdl);
@@ -483,19 +512,8 @@ cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s, boo
     if (o.tail_out == TAG_U) o.tail.u_out = u;
     if (o.seg_f == TAG_F) o.seg.f = f;
     if (o.seg_u == TAG_U) o.seg.u_out = u;
-    cudaError_t e = cudaSuccess;
-    switch (o.kind) {
-    case OP_RHS: e = run(rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.rhs); break;
-    case OP_TAIL: e = run(tail_kernel, o.grid, o.block, o.smem, s, pdl, o.tail); break;
-    case OP_DOWN_PI: e = run(level_down_kernel<true>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
-    case OP_DOWN: e = run(level_down_kernel<false>, o.grid, o.block, o.smem, s, pdl, o.lev); break;
-    case OP_UP: e = run(level_up_kernel, o.grid, o.block, o.smem, s, pdl, o.lev); break;
-    case OP_SR_PRE: e = run(sr_pre_kernel, o.grid, o.block, o.smem, s, pdl, o.seg); break;
-    case OP_SEAM: e = run(seam_tau_kernel, o.grid, o.block, 0, s, pdl, o.seg, o.nseg); break;
-    case OP_SR_POST: e = run(sr_post_kernel, o.grid, o.block, o.smem, s, pdl, o.seg); break;
-    case OP_SCALE: break;
-    }
-    return e;
+    if (o.nl) return launch_fp64<true>(o, s, pdl);
+    return launch_fp64<false>(o, s, pdl);
 }
 
 const char *kind_name(OpKind k) {
@@ -535,9 +553,12 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
     size_t need = 0;
     for (const Op &o : h->ops) need = std::max(need, o.smem);
     if (need > (size_t)optin) return fail(h, SRFMG_EUNSUPPORTED, "shared memory need exceeds the device limit");
-    const void *fns[] = {(const void *)level_down_kernel<true>, (const void *)level_down_kernel<false>,
-                         (const void *)level_up_kernel, (const void *)sr_pre_kernel,
-                         (const void *)sr_post_kernel, (const void *)tail_kernel,
+    const void *fns[] = {(const void *)level_down_kernel<true, false>, (const void *)level_down_kernel<false, false>,
+                         (const void *)level_up_kernel<false>, (const void *)sr_pre_kernel<false>,
+                         (const void *)sr_post_kernel<false>, (const void *)tail_kernel<false>,
+                         (const void *)level_down_kernel<true, true>, (const void *)level_down_kernel<false, true>,
+                         (const void *)level_up_kernel<true>, (const void *)sr_pre_kernel<true>,
+                         (const void *)sr_post_kernel<true>, (const void *)tail_kernel<true>,
                          (const void *)rhs_hierarchy_kernel,
                          (const void *)fx::level_down_kernel<true>, (const void *)fx::level_down_kernel<false>,
                          (const void *)fx::level_up_kernel, (const void *)fx::sr_pre_kernel,
@@ -585,6 +606,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     *out = nullptr;
     std::string msg = check_params(p);
     if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
+    if (p->op == SRFMG_OP_BRATU && p->precision != SRFMG_FP64)
+        return fail(nullptr, SRFMG_EUNSUPPORTED, "SRFMG_OP_BRATU runs in FP64 only");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -868,7 +891,7 @@ extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n
             }
             int optin = 0;
             if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-                cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaFuncSetAttribute(tail_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
                     cudaSuccess) {
                 cudaGetLastError();
                 return SRFMG_ECUDA;
@@ -901,7 +924,8 @@ extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n
     a.g_exp = -2 * log2_n;
     a.u_out = u;
     a.Ainv = ainv;
+    a.lam = 0.0;
     const size_t smem = tail_smem_doubles(log2_n_coarsest, log2_n) * sizeof(double);
-    tail_kernel<<<1, kTailThreads, smem, (cudaStream_t)stream>>>(a);
+    tail_kernel<false><<<1, kTailThreads, smem, (cudaStream_t)stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? SRFMG_OK : SRFMG_ECUDA;
 }

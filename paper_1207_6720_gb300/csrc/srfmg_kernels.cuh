@@ -268,6 +268,106 @@ __device__ __forceinline__ void lex_sweep(double *__restrict__ u, const double *
     else lex_sweep_dir<C, PRELOAD, false>(u, g, base, lo, hi, n, X);
 }
 
+// ---------------------------------------------------------------------------
+// Nonlinear sweep for -u'' + lam e^u = f (pointwise Newton Gauss-Seidel, the
+// nonlinear smoother S(L, u, f) of Fig. 1), in place, same layout and
+// chunking as lex_sweep.  With e_i = cl e^{u_i} (cl = lam h^2 of the level,
+// old values) one Newton step per cell gives the affine recurrence
+//   delta_i = a_i (r_i + delta_{i-1}),  a_i = 1 / (2 + e_i)  (3 + e_i at a wall),
+//   r_i = g_i - e_i - (F_{i-1/2} - F_{i+1/2})
+// in the correction.  Each chunk runs it from a zero carry and publishes its
+// end value X and the product Y of its a_i; the carry into a chunk is
+// X_{c-1} + Y_{c-1} (X_{c-2} + Y_{c-2} (...)) over the J+1 = ceil(kTrunc / C)
+// preceding chunks (every a_i <= 1/2, so the dropped terms are below 2^-72),
+// and the cell d places into its chunk's recurrence adds (a_0 ... a_d) times it.
+// X and Y hold one double per thread each.
+// ---------------------------------------------------------------------------
+template <int C, bool ASC>
+__device__ __noinline__ void lex_sweep_nl_dir(double *__restrict__ u, const double *__restrict__ g, double cl,
+                                              int base, int lo, int hi, int n, double *X, double *Y) {
+    constexpr int s = ASC ? 1 : -1;
+    const int t = threadIdx.x;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);
+    const bool wall1 = (q0 + k1 == n);
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int a0 = ASC ? -base : n - 1 - base;
+    double rr[C], aa[C];
+    double p = 0.0, A = 1.0, r_end = 0.0, a_end = 0.0;
+    if (active) {
+        double w[C + 2];
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+        if (wall0) {
+            const double e = cl * exp(w[1]);
+            const double a = 1.0 / (3.0 + e);
+            p = a * ((g[a0] - e) - (scale2(w[1], 1) - (w[2] - w[1])));
+            A = a;
+        }
+        if (wall1) {
+            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+            const double e = cl * exp(ue);
+            r_end = (g[a0 + s * (n - 1)] - e) - ((ue - um) - (-scale2(ue, 1)));
+            a_end = 1.0 / (3.0 + e);
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            const double e = cl * exp(w[k + 1]);
+            const double a = 1.0 / (2.0 + e);
+            const double r = (gv - e) - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1]));
+            const bool in = k >= ka && k < kb;
+            p = in ? a * (r + p) : p;
+            A = in ? a * A : A;
+            rr[k] = p;
+            aa[k] = A;
+        }
+        X[t] = p;
+        Y[t] = A;
+    }
+    __syncthreads();
+    if (active) {
+        constexpr int J = (kTrunc + C - 1) / C - 1;
+        double cin = 0.0;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const double x = X[max(idx, 0)], y = Y[max(idx, 0)];
+            cin = idx >= 0 ? fma(y, cin, x) : 0.0;
+        }
+        double dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                dl = fma(aa[k], cin, rr[k]);
+                u[a0 + s * (q0 + k)] += dl;
+            }
+        if (wall1) u[a0 + s * (n - 1)] += a_end * (r_end + dl);
+    }
+    __syncthreads();
+}
+
+template <int C>
+__device__ __forceinline__ void lex_sweep_nl(double *__restrict__ u, const double *__restrict__ g, double cl,
+                                             int base, int lo, int hi, int n, bool asc, double *X, double *Y) {
+    if (asc) lex_sweep_nl_dir<C, true>(u, g, cl, base, lo, hi, n, X, Y);
+    else lex_sweep_nl_dir<C, false>(u, g, cl, base, lo, hi, n, X, Y);
+}
+
+// One smoothing sweep of either operator: NL selects the Bratu sweep (cl =
+// lam h^2 of the level; Y: a second per-thread array).
+template <bool NL, bool PRELOAD = false>
+__device__ __forceinline__ void sweep_op(double *__restrict__ u, const double *__restrict__ g, double cl, int base,
+                                         int lo, int hi, int n, bool asc, double *X, double *Y) {
+    if (NL) lex_sweep_nl<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
+    else lex_sweep<kChunk, PRELOAD>(u, g, base, lo, hi, n, asc, X);
+}
+
 // Scaled tau-corrected coarse right-hand side at coarse cell J (Eqs. 6-7,
 // Fig. 3 lines 3-5): g_{l-1,J} = 2(g_{2J} + g_{2J+1}) + (G_{J-1/2} - G_{J+1/2})
 // - 2(F_{2J-1/2} - F_{2J+3/2}), where G are fluxes of uhat = R u on the coarse
@@ -283,6 +383,14 @@ __device__ __forceinline__ double tau_rhs(double g0, double g1, double um2, doub
     double Fr = (J == nc - 1) ? -scale2(u1, 1) : u2 - u1;
     double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
     return scale2(g0 + g1, 1) + tau;
+}
+
+// The nonlinear part of the scaled tau rhs (Eqs. 1-2 with N = L + lam e^u):
+// h_{l-1}^2 lam e^{uhat_J} - h_{l-1}^2 R(lam e^u)_J = cl (4 e^{uhat} - 2 (e^{u_2J} + e^{u_2J+1}))
+// with cl = lam h_l^2 of the fine level and uhat = (u_2J + u_2J+1) / 2.
+__device__ __forceinline__ double tau_nl(double cl, double u0, double u1) {
+    const double uh = scale2(u0 + u1, -1);
+    return cl * (4.0 * exp(uh) - 2.0 * (exp(u0) + exp(u1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -342,13 +450,14 @@ struct LevelArgs {
     double *u_out;             // level l after the pass (tile)
     double *uc_out;            // down pass: restricted solution on level l-1
     double *gc_out;            // down pass: tau-corrected g_{l-1}
+    double lam;                // Bratu: lam of -u'' + lam e^u = f (0 otherwise)
 };
 
 // Shared-memory layout of one stored-level block (the host reserves
 // 2 maxlen + 2 maxc + maxch doubles; this path uses the first
 // 2 maxlen + maxc + maxch).
 struct LevelSmem {
-    double *u, *g, *c, *X;
+    double *u, *g, *c, *X, *Y;   // Y: second carry array of the nonlinear sweep
     int L0, L1, C0, C1;       // fine range [L0,L1), coarse range [C0,C1)
 };
 
@@ -363,7 +472,7 @@ __device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H,
     m.g = m.u + maxlen;
     m.c = m.g + maxlen;
     m.X = m.c + maxc;
-    (void)maxch;
+    m.Y = m.X + maxch;
     return m;
 }
 
@@ -371,17 +480,18 @@ __device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H,
 // reversed after every sweep (appendix "symmetrize").  The swept range
 // shrinks by one cell per sweep on each side that is not a wall, so that
 // every sweep reads neighbours the previous one wrote.
-__device__ void smooth_range(LevelSmem &m, int n, int nu) {
+template <bool NL>
+__device__ void smooth_range(LevelSmem &m, int n, int nu, double cl) {
     int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
     int hi = (m.L1 == n) ? n : m.L1 - 1;
     for (int k = 0; k < nu; ++k) {
-        lex_sweep<kChunk>(m.u, m.g, m.L0, lo, hi, n, (k & 1) == 0, m.X);
+        sweep_op<NL>(m.u, m.g, cl, m.L0, lo, hi, n, (k & 1) == 0, m.X, m.Y);
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
 }
 
-template <bool FROM_PI>
+template <bool FROM_PI, bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -403,7 +513,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
             fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
     __syncthreads();
-    smooth_range(m, n, a.nu);
+    const double cl = scale2(a.lam, -2 * a.l);       // lam h_l^2
+    smooth_range<NL>(m, n, a.nu, cl);
     const double *u = m.u;
     // restriction of the solution and tau-corrected coarse rhs of the tile
     for (int J = (s >> 1) + threadIdx.x; J < ((s + a.tile) >> 1); J += blockDim.x) {
@@ -411,12 +522,15 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         a.uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
-        a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+        a.gc_out[J] = gc;
     }
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
 }
 
 // Up pass (Eq. 4): u_l += P (u_{l-1} - R u_l), then nu sweeps.
+template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -450,7 +564,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
         m.u[i - m.L0] += corr;
     }
     __syncthreads();
-    smooth_range(m, n, a.nu);
+    smooth_range<NL>(m, n, a.nu, scale2(a.lam, -2 * a.l));
     const double *u = m.u;
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
 }
@@ -469,12 +583,13 @@ struct SegArgs {
     double *gc_out;            // pre-leg: tau-corrected g_{M-1}
     double *seam;              // pre-leg: 6 fine values per segment
     double *u_out;             // post-leg: the solution
+    double lam;                // Bratu: lam (0 otherwise)
 };
 
 // (the host reserves 2 maxlen + 2 maxc + maxch doubles; this path uses the
 // first 2 maxlen + maxc + maxch)
 struct SegSmem {
-    double *u, *g, *c, *X;
+    double *u, *g, *c, *X, *Y;
     int e0, e1, lo, hi, C0, C1;
 };
 
@@ -490,6 +605,7 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
     m.g = m.u + a.maxlen;
     m.c = m.g + a.maxlen;
     m.X = m.c + a.maxc;
+    m.Y = m.X + a.maxch;
     return m;
 }
 
@@ -517,6 +633,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 // the extended patch, restricted solution on the segment's coarse cells, tau
 // rhs on the coarse cells whose stencil lies in the segment, seam values for
 // the two edge cells (formed from the assembled level by seam_tau_kernel).
+template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -524,7 +641,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     const int n = a.n, nc = n >> 1;
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
-    for (int k = 0; k < a.nu; ++k) lex_sweep<kChunk>(m.u, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    const double cl = scale2(a.lam, -2 * a.M);
+    for (int k = 0; k < a.nu; ++k) sweep_op<NL>(m.u, m.g, cl, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     const double *u = m.u;
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
     for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
@@ -534,7 +652,9 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
         if (!edge) {
             double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
             double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
-            a.gc_out[J] = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+            double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+            if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+            a.gc_out[J] = gc;
         }
     }
     if (threadIdx.x < 6) {
@@ -547,6 +667,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 // tau rhs of the two coarse cells at each interior segment boundary, from the
 // assembled fine values (seams) and the restricted solution (appendix down
 // leg).  Thread k handles the boundary s = (k+1) W.
+template <bool NL>
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -562,6 +683,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         double Gl = h0 - hm1, Gr = h1 - h0;
         double Fl = f2 - f3, Fr = p0 - f1;
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+        if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
         a.gc_out[J] = scale2(a.f[2 * J] + a.f[2 * J + 1], 1 - 2 * a.M) + tau;
     }
     {
@@ -569,6 +691,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         double Gl = h1 - h0, Gr = h2 - h1;
         double Fl = p0 - f1, Fr = p2 - p1;
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+        if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
         a.gc_out[J2] = scale2(a.f[2 * J2] + a.f[2 * J2 + 1], 1 - 2 * a.M) + tau;
     }
 }
@@ -576,6 +699,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 // K6: post-smoothing leg of the SR level (Fig. 3, Eq. 5, Fig. 5): full update
 // Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
 // Gauss-Seidel sweep), and the segment interior is written out.
+template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -593,7 +717,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
             p[i0 + 1] += r;
         }
         __syncthreads();
-        lex_sweep<kChunk>(p, m.g, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+        sweep_op<NL>(p, m.g, scale2(a.lam, -2 * a.M), m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     }
     for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) a.u_out[i] = p[i - m.lo];
 }
@@ -611,23 +735,28 @@ struct TailArgs {
     int g_exp;
     double *u_out;             // level Mc result
     const double *Ainv;        // inverse of the scaled coarsest operator, row-major
+    double lam;                // Bratu: lam (0 otherwise)
 };
 
 struct TailSmem {
-    double *u, *g, *S, *X;
+    double *u, *g, *S, *X, *Y;
     int M0;
+    double lam;
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
 };
 
+template <bool NL>
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
-    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true>(u, g, 0, 0, n, n, (k & 1) == 0, m.X);
+    for (int k = 0; k < nu; ++k)
+        sweep_op<NL, true>(u, g, scale2(m.lam, -2 * l), 0, 0, n, n, (k & 1) == 0, m.X, m.Y);
 }
 
 // smooth level l, then restriction and tau rhs into level l-1
+template <bool NL>
 __device__ void tail_down(TailSmem &m, int l, int nu) {
-    tail_smooth(m, l, nu);
+    tail_smooth<NL>(m, l, nu);
     const int nc = 1 << (l - 1);
     const double *u = m.u + m.off(l), *g = m.g + m.off(l);
     double *uc = m.u + m.off(l - 1), *gc = m.g + m.off(l - 1);
@@ -636,12 +765,56 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         uc[J] = scale2(u[i0] + u[i0 + 1], -1);
-        gc[J] = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        double gcv = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        if (NL) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
+        gc[J] = gcv;
     }
     __syncthreads();
 }
 
+// Coarsest level of the Bratu problem: Newton's method on the scaled system
+// T u + c e^u = g (T = h^2 L: tridiag(-1, 2, -1), 3 in the wall rows;
+// c = lam h^2) from the current iterate, each step a Thomas solve with the
+// Jacobian T + diag(c e^u), until the step is at most 4 ulp of max|u| or stops
+// shrinking (at most 100 steps).  One thread; cp and dp hold n scratch values each.
+__device__ void coarsest_newton(double *u, const double *g, int n, double c, double *cp, double *dp) {
+    double prev = __longlong_as_double(0x7ff0000000000000LL);   // +infinity
+    for (int it = 0; it < 100; ++it) {
+        // forward elimination of (T + diag(c e^u)) du = g - (T u + c e^u)
+        for (int i = 0; i < n; ++i) {
+            const double e = c * exp(u[i]);
+            const double fl = (i == 0) ? scale2(u[0], 1) : u[i] - u[i - 1];
+            const double fr = (i == n - 1) ? -scale2(u[i], 1) : u[i + 1] - u[i];
+            const double r = (g[i] - e) - (fl - fr);
+            const double diag = ((i == 0 || i == n - 1) ? 3.0 : 2.0) + e;
+            const double denom = (i > 0) ? diag + cp[i - 1] : diag;        // lower = -1
+            cp[i] = (i < n - 1) ? -1.0 / denom : 0.0;                          // upper = -1
+            dp[i] = ((i > 0) ? r + dp[i - 1] : r) / denom;
+        }
+        double step = 0.0, umax = 0.0, du = dp[n - 1];
+        u[n - 1] += du;
+        step = fabs(du);
+        umax = fabs(u[n - 1]);
+        for (int i = n - 2; i >= 0; --i) {
+            du = dp[i] - cp[i] * du;
+            u[i] += du;
+            step = fmax(step, fabs(du));
+            umax = fmax(umax, fabs(u[i]));
+        }
+        if (step <= 4.0 * 2.220446049250313e-16 * umax || step >= prev) break;
+        prev = step;
+    }
+}
+
+template <bool NL>
 __device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
+    if (NL) {
+        const int n0 = 1 << m.M0;
+        if (threadIdx.x == 0)
+            coarsest_newton(m.u + m.off(m.M0), m.g + m.off(m.M0), n0, scale2(m.lam, -2 * m.M0), m.S, m.X);
+        __syncthreads();
+        return;
+    }
     const int n0 = 1 << m.M0;
     double *u = m.u + m.off(m.M0);
     const double *g = m.g + m.off(m.M0);
@@ -656,6 +829,7 @@ __device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
 }
 
 // u_l += P (u_{l-1} - R u_l), then smoothing
+template <bool NL>
 __device__ void tail_up(TailSmem &m, int l, int nu) {
     const int n = 1 << l, nc = n >> 1;
     double *u = m.u + m.off(l);
@@ -669,7 +843,7 @@ __device__ void tail_up(TailSmem &m, int l, int nu) {
         u[i] += scale2(fma(3.0, m.S[J], cn), -2);
     }
     __syncthreads();
-    tail_smooth(m, l, nu);
+    tail_smooth<NL>(m, l, nu);
 }
 
 __device__ void tail_interp(TailSmem &m, int l) {
@@ -684,16 +858,19 @@ __device__ void tail_interp(TailSmem &m, int l) {
     __syncthreads();
 }
 
+template <bool NL>
 __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
     TailSmem m;
     m.M0 = a.M0;
+    m.lam = a.lam;
     const int tot = (1 << (a.Mc + 1)) - (1 << a.M0);
     m.u = sm;
     m.g = m.u + tot;
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
+    m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc;
     stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
     if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
@@ -710,17 +887,21 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
                 gc[J] = scale2(g[2 * J] + g[2 * J + 1], 1);
             __syncthreads();
         }
-        tail_coarsest(m, a.Ainv);
+        // the first coarsest solve of the FMG starts from zero (Newton needs a
+        // starting iterate; the linear solve ignores it)
+        for (int i = threadIdx.x; i < (1 << a.M0); i += blockDim.x) m.u[m.off(a.M0) + i] = 0.0;
+        __syncthreads();
+        tail_coarsest<NL>(m, a.Ainv);
         for (int k = a.M0; k < a.Mc; ++k) {
             tail_interp(m, k + 1);
-            for (int l = k + 1; l > a.M0; --l) tail_down(m, l, a.nu1);
-            tail_coarsest(m, a.Ainv);
-            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up(m, l, a.nu2);
+            for (int l = k + 1; l > a.M0; --l) tail_down<NL>(m, l, a.nu1);
+            tail_coarsest<NL>(m, a.Ainv);
+            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up<NL>(m, l, a.nu2);
         }
     } else {
-        for (int l = a.Mc; l > a.M0; --l) tail_down(m, l, a.nu1);
-        tail_coarsest(m, a.Ainv);
-        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up(m, l, a.nu2);
+        for (int l = a.Mc; l > a.M0; --l) tail_down<NL>(m, l, a.nu1);
+        tail_coarsest<NL>(m, a.Ainv);
+        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up<NL>(m, l, a.nu2);
     }
     for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out[i] = m.u[m.off(a.Mc) + i];
 }

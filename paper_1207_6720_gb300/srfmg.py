@@ -14,6 +14,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_ECUDA",
                 4: "SRFMG_ETIMEOUT", 5: "SRFMG_ENONFINITE", 6: "SRFMG_EUNSUPPORTED"}
 FP64, MIXED = 0, 1
+LAPLACE, BRATU = 0, 2
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
@@ -23,7 +24,8 @@ EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_h
 class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "op", "precision", "log2_n", "log2_n_coarsest", "n_sr_levels", "segment_width",
-        "buffer_width", "nu1", "nu2", "smoother")] + [("reserved", ctypes.c_int32 * 6)]
+        "buffer_width", "nu1", "nu2", "smoother")] + [("lambda_", ctypes.c_double),
+                                                      ("reserved", ctypes.c_int32 * 4)]
 
 
 class Info(ctypes.Structure):
@@ -91,7 +93,7 @@ def default_params(log2_n, **overrides):
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise KeyError(k)
-        setattr(p, k, int(v))
+        setattr(p, k, float(v) if k == "lambda_" else int(v))
     return p
 
 
