@@ -19,6 +19,12 @@ timed region, and the accuracy of the result against the exact solution.
 --impl reference times the CPU oracle (the method's plain serial C
 restatement) on the host cores, one bounded sample of the workload per step.
 
+--workload batch: 8192 independent problems of N = 2^m cells, m ~ U{10..20}
+(seed 11; about 1.55e9 unknowns in all), each a 32-mode sine series with its
+own seed; one batched plan per size (segments of min(4096, N/4) cells, 8
+buffer cells), all sizes on their own streams at once; 64-bit fixed point.
+value = all problems' unknowns / time of one pass over all sizes.
+
 --workload bratu: the nonlinear -u'' + lam e^u = f (lam = 1) with the same
 discretisation and FAS cycles, N = 2^26 cells, 16384 segments of 4096 cells,
 V(2,1), FP64; u = 1/2 sum_{k=1..16} c_k sin(k pi x) (seed 1).
@@ -43,6 +49,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine-grid unknowns/s per FMG-FAS-SR solve at discretization accuracy vs plain FP64"
+METRIC_BATCH = ("fine-grid unknowns/s over a batch of independent FMG-FAS-SR solves at "
+                "discretization accuracy vs plain FP64")
 METRIC_BRATU = ("fine-grid unknowns/s per FMG-FAS-SR solve of -u''+lam e^u=f at discretization "
                 "accuracy vs plain FP64")
 UNIT = "unknowns/s"
@@ -61,7 +69,7 @@ FLOPS_PER_CELL_BRATU = {"sr_post": 6.5 + 1 * (2 + 9), "sr_pre": 6.5 + 2 * 9 + 0.
                         "level_down_fmg": 6.5 + 2 * 9 + 0.5 + 6, "level_down": 2 * 9 + 0.5 + 6,
                         "level_up": 2.0 + 1 * 9}
 BYTES_PER_CELL = {"sr_post": 20.0, "sr_pre": 20.0, "level_down_fmg": 20.0,
-                  "level_down": 24.0, "level_up": 28.0}
+                  "level_down": 24.0, "level_up": 28.0, "rhs_hierarchy": 16.0}
 
 
 def parse_args():
@@ -70,7 +78,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["srfmg", "reference"], default="srfmg")
-    ap.add_argument("--workload", choices=["poisson", "bratu"], default="poisson")
+    ap.add_argument("--workload", choices=["poisson", "bratu", "batch"], default="poisson")
+    ap.add_argument("--nprob", type=int, default=8192, help="batch: number of problems")
     ap.add_argument("--lam", type=float, default=1.0, help="Bratu: lam of -u'' + lam e^u = f")
     ap.add_argument("--log2n", type=int, default=None, help="default 24 (poisson), 26 (bratu)")
     ap.add_argument("--segment-width", type=int, default=4096)
@@ -90,6 +99,15 @@ def parse_args():
 
 
 def workload_config(a):
+    if getattr(a, "workload", "poisson") == "batch":
+        return {
+            "workload": f"{a.nprob} independent 1D -u''=f problems, N=2^m with m ~ U{{10..20}} (seed 11), "
+                        f"FMG-FAS V(1,1) lexicographic GS, 1 SR level of min(4096, N/4)-cell segments, "
+                        f"buffer 8, 64-bit fixed point; one batched plan per size, sizes on concurrent streams",
+            "precision": "mixed", "nprob": a.nprob, "m_range": [10, 20], "size_seed": 11,
+            "modes": 32, "buffer_width": 8, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
+            "l2": "inputs larger than L2 (about 12 GB of f and 12 GB of u)",
+        }
     if getattr(a, "workload", "poisson") == "bratu":
         return {
             "workload": f"1D -u''+lam e^u=f, lam={a.lam}, N=2^{a.log2n}, FMG-FAS V(2,1) pointwise Newton "
@@ -547,10 +565,154 @@ def run_gpu_bratu(a):
     dist.close()
 
 
+def run_gpu_batch(a):
+    """Many independent problems: one batched plan per size, sizes concurrent."""
+    import torch
+    from paper_1207_6720_gb300 import srfmg, workloads
+
+    dist = Dist(a.gpus, use_cuda=True)
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    master = torch.cuda.current_stream()
+    sizes = workloads.batch_sizes(a.nprob, 10, 20, seed=11)
+    classes = {}
+    for k, m in enumerate(sizes):
+        classes.setdefault(int(m), []).append(k + 1000)       # problem k's series seed
+    total = int(sum(len(v) << m for m, v in classes.items()))
+    fs, us, streams = {}, {}, {}
+    for m, seeds in sorted(classes.items()):
+        fs[m], _ = workloads.sine_series_batch(m, seeds, 32, dev)
+        us[m] = torch.empty_like(fs[m])
+        streams[m] = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+
+    def make(prec, nRS):
+        out = {}
+        for m, seeds in classes.items():
+            kw = dict(batch=len(seeds), precision=prec, n_sr_levels=nRS)
+            if nRS:
+                kw.update(segment_width=min(4096, (1 << m) // 4), buffer_width=8)
+            out[m] = srfmg.Solver(m, device=dev, **kw)
+        return out
+
+    def one_pass(solvers):
+        e0 = torch.cuda.Event()
+        e0.record(master)
+        done = []
+        for m, sv in solvers.items():
+            st = streams[m]
+            st.wait_event(e0)
+            sv.solve(fs[m], us[m], stream=st)
+            done.append(st.record_event())
+        for ev in done:
+            master.wait_event(ev)
+
+    def timed(solvers, steps, warmup):
+        for _ in range(warmup):
+            one_pass(solvers)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(master)
+        for _ in range(steps):
+            one_pass(solvers)
+        t1.record(master)
+        t1.synchronize()
+        torch.cuda.synchronize()
+        dist.barrier()
+        return t0.elapsed_time(t1) / steps
+
+    solvers = make(srfmg.MIXED, 1)
+    launches = sum(sv.info().kernels_per_solve for sv in solvers.values())
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ms = dist.max(timed(solvers, a.steps, a.warmup))
+    clocks = sampler.stop()
+    value = dist.world * total / (ms * 1e-3)
+    line = {"metric": METRIC_BATCH, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": workload_config(a), "gpu_launches": launches * a.steps, "clocks": clocks,
+            "unknowns_per_step": total}
+    # accuracy on a sample: the first problem of every size against its exact solution
+    worst = 0.0
+    samples = {}
+    for m, seeds in classes.items():
+        u0 = us[m][: 1 << m].cpu().numpy()
+        f0, ue, _ = workloads.sine_series(m, 32, seeds[0])
+        samples[m] = (fs[m][: 1 << m].cpu().numpy(), ue, u0)
+        worst = max(worst, float(np.max(np.abs(u0 - ue))))
+    if not a.only_solve:
+        # end to end: every size through srfmg_solve_host from pinned host buffers, in turn
+        hosts = {m: (fs[m].cpu().pin_memory(), torch.empty(fs[m].numel(), dtype=torch.float64).pin_memory())
+                 for m in classes}
+        for m, sv in solvers.items():
+            sv.solve_host(hosts[m][0].numpy(), hosts[m][1].numpy(), stream=master)
+        t0 = time.perf_counter()
+        for m, sv in solvers.items():
+            sv.solve_host(hosts[m][0].numpy(), hosts[m][1].numpy(), stream=master)
+        dt_e2e = dist.max(time.perf_counter() - t0)
+        hb = int(sum(h[0].numel() for h in hosts.values()) * 8)
+        line["e2e"] = {"value": dist.world * total / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": hb,
+                       "d2h_bytes_per_step": hb}
+        # roofline: the longest launch of the largest size's batch
+        mbig = max(classes)
+        prof = solvers[mbig].profile(fs[mbig], torch.empty_like(fs[mbig]), nsolves=2, stream=master)
+        torch.cuda.synchronize()
+        top_name, top_ms = max(prof, key=lambda x: x[1])
+        kind, lvl = top_name.split(" L")
+        kind = kind.replace("fx.", "")
+        bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * len(classes[mbig]) * (1 << int(lvl))
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        line["roofline"] = {"bound": "hbm", "kernel": f"{top_name} (batch of {len(classes[mbig])})",
+                            "achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                            "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
+                            "launch_ms": top_ms}
+    for sv in solvers.values():
+        sv.close()
+    if not a.only_solve:
+        plain = make(srfmg.FP64, 0)
+        ms_plain = dist.max(timed(plain, max(3, a.steps // 2), 1))
+        for sv in plain.values():
+            sv.close()
+        line["plain_fp64"] = {"value": dist.world * total / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                              "speedup_over_plain": ms_plain / ms}
+    acc = {"err_max_vs_exact_sample": worst, "sample": "first problem of each size"}
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and not a.only_solve:
+        import oracle
+        refs = {}
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            for m, (f0, ue, u0) in samples.items():
+                refs[m] = oracle.fmg_v(oracle.sr_params(m, min(4096, (1 << m) // 4), 8), f0)
+            reps += 1
+            if time.perf_counter() - t0 > 10.0 or reps >= 20:
+                break
+        dt = time.perf_counter() - t0
+        n_sample = sum(1 << m for m in samples)
+        line["cpu_baseline"] = {"value": reps * n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{reps} x one problem of each size ({n_sample} unknowns) "
+                                          f"with the serial C oracle"}
+        ok = all(np.max(np.abs(u0 - ue)) <= 1.5 * np.max(np.abs(refs[m] - ue))
+                 for m, (f0, ue, u0) in samples.items())
+        acc.update({"rel_maxnorm_vs_oracle_sample": max(
+            float(np.max(np.abs(u0 - refs[m])) / np.max(np.abs(refs[m]))) for m, (f0, ue, u0) in samples.items()),
+            "at_discretization_accuracy_sample": bool(ok)})
+    line["accuracy"] = acc
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_gpu_batch(a)
     elif a.workload == "bratu":
         run_gpu_bratu(a)
     else:

@@ -76,7 +76,9 @@ typedef struct {
     int32_t nu1, nu2;          /* V(nu1, nu2): 1 <= nu1, nu2 <= 4 */
     int32_t smoother;          /* srfmg_smoother */
     double lambda;             /* SRFMG_OP_BRATU: lambda >= 0, finite; must be 0 otherwise */
-    int32_t reserved[4];       /* must be zero */
+    int32_t batch;             /* independent problems of this size solved together, in
+                                  [0, 65535] (0 means 1); see srfmg_solve */
+    int32_t reserved[3];       /* must be zero */
 } srfmg_params;
 
 /* Information about a created plan. */
@@ -103,6 +105,9 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
 /* One FMG-FAS(-SR) solve (Figs. 2-4).
  * f: device pointer, N doubles, the right-hand side at the cell centres.
  * u: device pointer, N doubles, receives the solution at the cell centres.
+ * With batch = B > 1 the plan solves B independent problems of N cells with
+ * the same launches (each kernel's grid has one row per problem): f and u
+ * then hold B * N doubles, problem k at offset k * N.
  * f and u must not overlap and must stay valid until the stream reaches the
  * end of the solve.  Enqueued asynchronously on `stream`; the launch sequence
  * is captured into a CUDA graph the first time a (f, u, stream) triple is seen
@@ -112,9 +117,9 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
 /* (The handle keeps the captured graphs of up to four (f, u) pointer pairs;
  * the least recently used one is replaced.) */
 
-/* The same solve from and to HOST memory: copies f (N doubles) to a device
- * staging buffer owned by the handle, solves, copies the solution back into u
- * (N doubles) and synchronises `stream` before returning.  Pinned host
+/* The same solve from and to HOST memory: copies f (N doubles, B * N for a
+ * batch) to a device staging buffer owned by the handle, solves, copies the
+ * solution back into u and synchronises `stream` before returning.  Pinned host
  * buffers give the fastest copies; pageable ones work.  f and u may alias. */
 srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream);
 

@@ -62,7 +62,8 @@ struct srfmg_plan {
     srfmg_params p;
     int device;
     int M, M0, Mc, nRS, W, b;
-    size_t n;
+    int batch;                     // independent problems solved together (>= 1)
+    size_t n;                      // cells per problem
     std::vector<void *> allocs;
     double *ulev[32][2] = {};
     double *glev[32] = {};
@@ -105,7 +106,8 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
-    for (int i = 0; i < 4; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    for (int i = 0; i < 3; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    if (p->batch < 0 || p->batch > 65535) return "batch must be in [0, 65535] (0 means 1)";
     if (p->op != SRFMG_OP_LAPLACE && p->op != SRFMG_OP_BRATU) return "op must be SRFMG_OP_LAPLACE or SRFMG_OP_BRATU";
     if (p->op == SRFMG_OP_LAPLACE && p->lambda != 0.0) return "lambda must be 0 for SRFMG_OP_LAPLACE";
     if (p->op == SRFMG_OP_BRATU && !(p->lambda >= 0.0 && p->lambda <= 1e300))
@@ -301,6 +303,7 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.frhs.lin = o.rhs.lin;
         o.frhs.lstop = o.rhs.lstop;
         o.frhs.depth = o.rhs.depth;
+        o.frhs.chunk_log = o.rhs.chunk_log;
         for (int l = 0; l < 32; ++l) o.frhs.out[l] = (i64 *)o.rhs.out[l];
         break;
     case OP_DOWN_PI: case OP_DOWN: case OP_UP:
@@ -355,12 +358,15 @@ void build_schedule_ops(srfmg_plan *h) {
             o.rhs.lin = lin;
             o.rhs.lstop = lin - depth;
             o.rhs.depth = depth;
+            // at least 4096 cells per block: a shallow reduction (few levels
+            // above the tail) would otherwise launch one tiny block per 2^depth cells
+            o.rhs.chunk_log = std::max(depth, std::min(lin, 12));
             if (lin == M) { o.rhs_in = TAG_F; o.rhs.in_exp = -2 * M; }
             else { o.rhs.in = h->glev[lin]; o.rhs.in_exp = 0; }
             for (int l = lin - depth; l < lin; ++l) o.rhs.out[l] = h->glev[l];
-            o.grid = dim3((unsigned)((1ULL << lin) >> depth));
+            o.grid = dim3((unsigned)((1ULL << lin) >> o.rhs.chunk_log));
             o.block = dim3(kRhsThreads);
-            o.smem = (size_t)(1 << depth) * 3 / 2 * sizeof(double);
+            o.smem = (size_t)(1 << o.rhs.chunk_log) * 3 / 2 * sizeof(double);
             h->ops.push_back(o);
             lin -= depth;
         }
@@ -421,14 +427,19 @@ void build_schedule_ops(srfmg_plan *h) {
 
 void build_schedule(srfmg_plan *h) {
     build_schedule_ops(h);
-    for (Op &o : h->ops) o.nl = (h->p.op == SRFMG_OP_BRATU);
+    for (Op &o : h->ops) {
+        o.nl = (h->p.op == SRFMG_OP_BRATU);
+        o.grid.y = (unsigned)h->batch;           // one grid row per problem of the batch
+    }
     if (!h->fixed) return;
     for (Op &o : h->ops) to_fixed(h, o);
     Op sc = make_op(OP_SCALE);
     sc.fixed = true;
     sc.scale = h->scale;
     sc.level = h->M;
-    sc.grid = dim3(608);
+    // max|f| of each problem: one block per 4096 cells (at most 4 x 152)
+    const size_t sblocks = std::min<size_t>(608, std::max<size_t>(1, h->n / 4096));
+    sc.grid = dim3((unsigned)sblocks, (unsigned)h->batch);
     sc.block = dim3(256);
     h->ops.insert(h->ops.begin(), sc);
 }
@@ -466,9 +477,10 @@ cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t 
     switch (o.kind) {
     case OP_SCALE: {
         const long long n = (long long)o.level < 63 ? (1LL << o.level) : 0;
-        e = run(fx::scale_reset_kernel, dim3(1), dim3(32), 0, s, pdl, o.scale);
+        const dim3 one(1, o.grid.y);
+        e = run(fx::scale_reset_kernel, one, dim3(32), 0, s, pdl, o.scale);
         if (e == cudaSuccess) e = run(fx::scale_max_kernel, o.grid, o.block, 0, s, true, f, n, o.scale);
-        if (e == cudaSuccess) e = run(fx::scale_finish_kernel, dim3(1), dim3(32), 0, s, true, o.scale);
+        if (e == cudaSuccess) e = run(fx::scale_finish_kernel, one, dim3(32), 0, s, true, o.scale);
         break;
     }
     case OP_RHS: e = run(fx::rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.frhs); break;
@@ -627,6 +639,7 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     h->W = p->segment_width;
     h->b = p->buffer_width;
     h->n = (size_t)1 << h->M;
+    h->batch = p->batch > 0 ? p->batch : 1;
     int top_stored = h->M - h->nRS;
     h->Mc = top_stored < kMaxTailLevel ? top_stored : kMaxTailLevel;
     if (h->Mc < h->M0) h->Mc = h->M0;
@@ -635,19 +648,20 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     h->use_graph = !(env && env[0] == '1');
 
     srfmg_status st = SRFMG_OK;
+    const size_t B = (size_t)h->batch;   // every per-problem array holds B problems back to back
     for (int l = h->Mc; l <= h->M && st == SRFMG_OK; ++l) {
         if (l == h->M) {
-            if (h->nRS == 0 && h->Mc < h->M) st = alloc_dev(h, &h->ulev[l][0], (size_t)1 << l);
+            if (h->nRS == 0 && h->Mc < h->M) st = alloc_dev(h, &h->ulev[l][0], B << l);
             break;
         }
-        st = alloc_dev(h, &h->ulev[l][0], (size_t)1 << l);
-        if (st == SRFMG_OK) st = alloc_dev(h, &h->ulev[l][1], (size_t)1 << l);
-        if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], (size_t)1 << l);
+        st = alloc_dev(h, &h->ulev[l][0], B << l);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->ulev[l][1], B << l);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], B << l);
     }
-    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, (h->n / h->W) * 6);
+    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, B * (h->n / h->W) * 6);
     if (st == SRFMG_OK && h->fixed) {
         double *sc = nullptr;
-        st = alloc_dev(h, &sc, 2);
+        st = alloc_dev(h, &sc, 2 * B);
         h->scale = (fx::Scale *)sc;
     }
     const int n0 = 1 << h->M0;
@@ -681,7 +695,8 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
     if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be device pointers");
     if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned");
-    if ((const double *)u < f + h->n && f < (const double *)u + h->n) return fail(h, SRFMG_EINVAL, "f and u overlap");
+    const size_t total = h->n * (size_t)h->batch;
+    if ((const double *)u < f + total && f < (const double *)u + total) return fail(h, SRFMG_EINVAL, "f and u overlap");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
@@ -720,17 +735,18 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
     if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be host pointers");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t total = h->n * (size_t)h->batch;
     if (!h->f_stage) {
-        srfmg_status st = alloc_dev(h, &h->f_stage, h->n);
-        if (st == SRFMG_OK) st = alloc_dev(h, &h->u_stage, h->n);
+        srfmg_status st = alloc_dev(h, &h->f_stage, total);
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->u_stage, total);
         if (st != SRFMG_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(h->f_stage, f, h->n * sizeof(double), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(h->f_stage, f, total * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(f)");
     srfmg_status st = srfmg_solve(h, h->f_stage, h->u_stage, stream);
     if (st != SRFMG_OK) return st;
-    e = cudaMemcpyAsync(u, h->u_stage, h->n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(u, h->u_stage, total * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync(u)");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");

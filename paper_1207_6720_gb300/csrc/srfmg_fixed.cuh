@@ -244,13 +244,17 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
 // --------------------------------------------------------------------------
 // Scale: E with max|f| < 2^E from the largest exponent field of f.
 // --------------------------------------------------------------------------
+// (one Scale per problem of a batch: sc[blockIdx.y])
 __global__ void scale_reset_kernel(Scale *sc) {
     pdl_enter();
+    sc += blockIdx.y;
     if (threadIdx.x == 0) { sc->E = -2000; sc->S = 0; sc->Sg0 = 0; }
 }
 
 __global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
     pdl_enter();
+    f = batch_at(f, n);
+    sc += blockIdx.y;
     int emax = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         int e = (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff);
@@ -262,6 +266,7 @@ __global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
 
 __global__ void scale_finish_kernel(Scale *sc) {
     pdl_enter();
+    sc += blockIdx.y;
     if (threadIdx.x == 0) {
         int E = sc->E;
         E = E < -100 ? -100 : (E > 900 ? 900 : E);
@@ -280,15 +285,19 @@ struct RhsArgs {
     const i64 *in;
     const Scale *sc;
     int from_f, lin, lstop, depth;
+    int chunk_log;             // log2 of the cells each block reduces (>= depth)
     i64 *out[32];
 };
 
 __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
-    const int chunk = 1 << a.depth;
+    const int chunk = 1 << a.chunk_log;       // cells of level lin per block (>= 2^depth)
     i64 *cur = smi, *nxt = smi + chunk;
     const long long base = (long long)blockIdx.x * chunk;
+    a.sc += blockIdx.y;
+    a.f = batch_at(a.f, 1LL << a.lin);
+    a.in = batch_at(a.in, 1LL << a.lin);
     const int k = a.sc->Sg0;              // f 2^-2M 2^(Sg0+2M) = f 2^Sg0
     if (a.from_f) stage_range(cur, a.f + base, chunk);
     else stage_range(cur, a.in + base, chunk);
@@ -300,7 +309,7 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     int len = chunk;
     for (int l = a.lin; l > a.lstop && len > 1; --l) {
         const int half = len >> 1;
-        i64 *dst = a.out[l - 1] + (base >> (a.lin - l + 1));
+        i64 *dst = batch_at(a.out[l - 1], 1LL << (l - 1)) + (base >> (a.lin - l + 1));
         for (int J = threadIdx.x; J < half; J += blockDim.x) {
             i64 x = (cur[2 * J] + cur[2 * J + 1] + 1) >> 1;
             nxt[J] = x;
@@ -335,6 +344,21 @@ struct LevelSmem {
     i64 *u, *gs, *c, *X, *gr;
     int L0, L1, C0, C1;
 };
+
+// The arrays of one problem of the batch (see batch_at); u_src is on level
+// l-1 when it feeds the FMG interpolation.
+__device__ __forceinline__ void level_batch(LevelArgs &a, bool u_src_coarse) {
+    const long long n = a.n;
+    a.sc += blockIdx.y;
+    a.u_src = batch_at(a.u_src, u_src_coarse ? n / 2 : n);
+    a.g = batch_at(a.g, n);
+    a.f = batch_at(a.f, n);
+    a.uc_src = batch_at(a.uc_src, n / 2);
+    a.u_out = batch_at(a.u_out, n);
+    a.u_out_f64 = batch_at(a.u_out_f64, n);
+    a.uc_out = batch_at(a.uc_out, n / 2);
+    a.gc_out = batch_at(a.gc_out, n / 2);
+}
 
 __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs &a) {
     LevelSmem m;
@@ -395,6 +419,7 @@ __device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
 template <bool FROM_PI>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
     pdl_enter();
+    level_batch(a, FROM_PI);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -429,6 +454,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
 // Up pass (Eq. 4): U_l += P (U_{l-1} - R U_l) (rounded to units), then nu sweeps.
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
     pdl_enter();
+    level_batch(a, false);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
@@ -485,6 +511,18 @@ struct SegSmem {
     int e0, e1, lo, hi, C0, C1;
 };
 
+// The arrays of one problem of the batch (see batch_at).
+__device__ __forceinline__ void seg_batch(SegArgs &a) {
+    const long long n = a.n;
+    a.sc += blockIdx.y;
+    a.f = batch_at(a.f, n);
+    a.uc_src = batch_at(a.uc_src, n / 2);
+    a.uc_out = batch_at(a.uc_out, n / 2);
+    a.gc_out = batch_at(a.gc_out, n / 2);
+    a.seam = batch_at(a.seam, 6 * (n / a.W));
+    a.u_out = batch_at(a.u_out, n);
+}
+
 __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
     SegSmem m;
     m.e0 = max(0, s - a.b);
@@ -534,6 +572,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
 
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
+    seg_batch(a);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -564,6 +603,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 // assembled fine values (seams) and the restricted solution.
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
+    seg_batch(a);
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
     const int s = (k + 1) * a.W;
@@ -587,6 +627,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
+    seg_batch(a);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -705,7 +746,14 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     m.g = m.u + tot;
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
-    const int nMc = 1 << a.Mc, kg = a.sc->Sg0;
+    const int nMc = 1 << a.Mc;
+    a.sc += blockIdx.y;
+    a.u_in = batch_at(a.u_in, nMc);
+    a.g_in = batch_at(a.g_in, nMc);
+    a.f = batch_at(a.f, nMc);
+    a.u_out = batch_at(a.u_out, nMc);
+    a.u_out_f64 = batch_at(a.u_out_f64, nMc);
+    const int kg = a.sc->Sg0;
     if (a.g_in) stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
     else stage_range(m.g + m.off(a.Mc), a.f, nMc);
     if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);

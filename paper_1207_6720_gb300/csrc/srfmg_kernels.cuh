@@ -44,6 +44,14 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// Batched solves: a block serves problem blockIdx.y of the batch.  Every array
+// of a level holds the problems one after another, so a pointer into an array
+// of `cells` cells per problem moves by blockIdx.y * cells.
+template <typename T>
+__device__ __forceinline__ T *batch_at(T *p, long long cells) {
+    return p ? p + (long long)blockIdx.y * cells : p;
+}
+
 // Exact 2^k as a double, -1022 <= k <= 1023.
 __device__ __forceinline__ double exp2i(int k) {
     return __longlong_as_double((long long)(1023 + k) << 52);
@@ -403,15 +411,17 @@ struct RhsArgs {
     const double *in;
     int in_exp;
     int lin, lstop, depth;
+    int chunk_log;             // log2 of the cells each block reduces (>= depth)
     double *out[32];           // out[l] for the written levels
 };
 
 __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
-    const int chunk = 1 << a.depth;
+    const int chunk = 1 << a.chunk_log;       // cells of level lin per block (>= 2^depth)
     double *cur = sm, *nxt = sm + chunk;
     const long long base = (long long)blockIdx.x * chunk;
+    a.in = batch_at(a.in, 1LL << a.lin);
     stage_range(cur, a.in + base, chunk);
     stage_wait();
     __syncthreads();
@@ -421,7 +431,7 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     int len = chunk;
     for (int l = a.lin; l > a.lstop && len > 1; --l) {
         const int half = len >> 1;
-        double *dst = a.out[l - 1] + (base >> (a.lin - l + 1));
+        double *dst = batch_at(a.out[l - 1], 1LL << (l - 1)) + (base >> (a.lin - l + 1));
         for (int J = threadIdx.x; J < half; J += blockDim.x) {
             double x = scale2(cur[2 * J] + cur[2 * J + 1], 1);
             nxt[J] = x;
@@ -497,6 +507,11 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
+    a.u_src = batch_at(a.u_src, FROM_PI ? nc : n);
+    a.g = batch_at(a.g, n);
+    a.u_out = batch_at(a.u_out, n);
+    a.uc_out = batch_at(a.uc_out, nc);
+    a.gc_out = batch_at(a.gc_out, nc);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
     stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
     if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
@@ -536,6 +551,10 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
+    a.u_src = batch_at(a.u_src, n);
+    a.g = batch_at(a.g, n);
+    a.uc_src = batch_at(a.uc_src, nc);
+    a.u_out = batch_at(a.u_out, n);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
     stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
     stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
@@ -593,6 +612,17 @@ struct SegSmem {
     int e0, e1, lo, hi, C0, C1;
 };
 
+// The arrays of one problem of the batch (see batch_at).
+__device__ __forceinline__ void seg_batch(SegArgs &a) {
+    const long long n = a.n;
+    a.f = batch_at(a.f, n);
+    a.uc_src = batch_at(a.uc_src, n / 2);
+    a.uc_out = batch_at(a.uc_out, n / 2);
+    a.gc_out = batch_at(a.gc_out, n / 2);
+    a.seam = batch_at(a.seam, 6 * (n / a.W));
+    a.u_out = batch_at(a.u_out, n);
+}
+
 __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s) {
     SegSmem m;
     m.e0 = max(0, s - a.b);
@@ -636,6 +666,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
+    seg_batch(a);
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -670,6 +701,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 template <bool NL>
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
+    seg_batch(a);
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
     const int s = (k + 1) * a.W;
@@ -702,6 +734,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
+    seg_batch(a);
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -872,6 +905,9 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     m.X = m.S + (1 << a.Mc) + 8;
     m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc;
+    a.u_in = batch_at(a.u_in, nMc);
+    a.g_in = batch_at(a.g_in, nMc);
+    a.u_out = batch_at(a.u_out, nMc);
     stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
     if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
     stage_wait();

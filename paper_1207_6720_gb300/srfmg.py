@@ -25,7 +25,8 @@ class Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int32) for name in (
         "op", "precision", "log2_n", "log2_n_coarsest", "n_sr_levels", "segment_width",
         "buffer_width", "nu1", "nu2", "smoother")] + [("lambda_", ctypes.c_double),
-                                                      ("reserved", ctypes.c_int32 * 4)]
+                                                      ("batch", ctypes.c_int32),
+                                                      ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -115,6 +116,7 @@ class Solver:
         self.lib = load()
         self.params = params if params is not None else default_params(log2_n, **overrides)
         self.n = 1 << self.params.log2_n
+        self.batch = max(1, self.params.batch)
         self.device = device
         h = ctypes.c_void_p()
         st = self.lib.srfmg_create(ctypes.byref(self.params), device, ctypes.byref(h))
@@ -133,8 +135,9 @@ class Solver:
 
     def solve(self, f, u=None, stream=None):
         import torch
-        if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.numel() == self.n):
-            raise ValueError("f must be a contiguous CUDA float64 tensor of 2^log2_n values")
+        if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous()
+                and f.numel() == self.n * self.batch):
+            raise ValueError("f must be a contiguous CUDA float64 tensor of batch * 2^log2_n values")
         if u is None:
             u = torch.empty_like(f)
         self._check(self.lib.srfmg_solve(self.h, ctypes.c_void_p(f.data_ptr()),
@@ -148,8 +151,8 @@ class Solver:
         adjoint right-hand side; the operator is symmetric)."""
         import torch
         if not (dL_du.is_cuda and dL_du.dtype == torch.float64 and dL_du.is_contiguous()
-                and dL_du.numel() == self.n):
-            raise ValueError("dL_du must be a contiguous CUDA float64 tensor of 2^log2_n values")
+                and dL_du.numel() == self.n * self.batch):
+            raise ValueError("dL_du must be a contiguous CUDA float64 tensor of batch * 2^log2_n values")
         if dL_df is None:
             dL_df = torch.empty_like(dL_du)
         self._check(self.lib.srfmg_adjoint(self.h, ctypes.c_void_p(dL_du.data_ptr()),
@@ -161,8 +164,8 @@ class Solver:
         """Solve from and to host numpy arrays (copies inside; synchronises)."""
         import numpy as np
         f = np.ascontiguousarray(f, dtype=np.float64)
-        if f.size != self.n:
-            raise ValueError("f must hold 2^log2_n values")
+        if f.size != self.n * self.batch:
+            raise ValueError("f must hold batch * 2^log2_n values")
         if u is None:
             u = np.empty_like(f)
         dp = ctypes.POINTER(ctypes.c_double)

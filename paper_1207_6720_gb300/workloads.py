@@ -12,6 +12,10 @@ x_i = (i + 1/2)/N.
   from ``numpy.random.default_rng(seed)``, so f = sum c_k (k pi)^2 sin(k pi x).
 * ``paper_series``: the appendix program's problem, f = sum over odd j below
   N/16 of sin(j pi x)/j, u = sum sin(j pi x)/(j (j pi)^2).
+* ``batch_sizes`` / ``sine_series_batch``: many independent problems (sizes
+  2^m with m drawn uniformly; each problem a sine series with its own seed),
+  generated on the device as one matrix product of the coefficients with the
+  sampled sines.
 * ``bratu_series``: the nonlinear problem -u'' + lam e^u = f with the
   manufactured solution u = scale * sum c_k sin(k pi x) (default scale 1/2),
   f = -u'' + lam e^u sampled at the centres.
@@ -43,6 +47,25 @@ def sine_series(M, nmodes, seed, scale=1.0):
         f += c[k - 1] * (k * np.pi) ** 2 * s
         u += c[k - 1] * s
     return f, u, c
+
+
+def batch_sizes(nprob, mmin, mmax, seed):
+    """log2 sizes m ~ U{mmin .. mmax} of nprob problems (default_rng(seed))."""
+    return np.random.default_rng(seed).integers(mmin, mmax + 1, size=nprob)
+
+
+def sine_series_batch(M, seeds, nmodes, device):
+    """(f, c): float64 tensor of len(seeds) * 2^M right-hand-side values on
+    `device`, problem k holding sine_series(M, nmodes, seeds[k]), and the
+    coefficient array (len(seeds), nmodes)."""
+    import torch
+    c = np.stack([sine_coefficients(nmodes, int(s)) for s in seeds])
+    k = np.arange(1, nmodes + 1, dtype=np.float64)
+    x = torch.from_numpy(centres(M)).to(device)
+    kt = torch.from_numpy(k).to(device)
+    S = torch.sin(torch.pi * kt[:, None] * x[None, :])                 # (nmodes, 2^M)
+    cf = torch.from_numpy(c * (k * np.pi) ** 2).to(device)             # (B, nmodes)
+    return (cf @ S).reshape(-1).contiguous(), c
 
 
 def bratu_series(M, nmodes, seed, lam, scale=0.5):
