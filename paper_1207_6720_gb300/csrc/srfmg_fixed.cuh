@@ -295,12 +295,12 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     const int chunk = 1 << a.chunk_log;       // cells of level lin per block (>= 2^depth)
     i64 *cur = smi, *nxt = smi + chunk;
     const long long base = (long long)blockIdx.x * chunk;
-    a.sc += blockIdx.y;
-    a.f = batch_at(a.f, 1LL << a.lin);
-    a.in = batch_at(a.in, 1LL << a.lin);
-    const int k = a.sc->Sg0;              // f 2^-2M 2^(Sg0+2M) = f 2^Sg0
-    if (a.from_f) stage_range(cur, a.f + base, chunk);
-    else stage_range(cur, a.in + base, chunk);
+    const Scale *sc = a.sc + blockIdx.y;
+    const double *f = batch_at(a.f, 1LL << a.lin);
+    const i64 *in = batch_at(a.in, 1LL << a.lin);
+    const int k = sc->Sg0;                // f 2^-2M 2^(Sg0+2M) = f 2^Sg0
+    if (a.from_f) stage_range(cur, f + base, chunk);
+    else stage_range(cur, in + base, chunk);
     stage_wait();
     __syncthreads();
     if (a.from_f)
@@ -343,24 +343,17 @@ struct LevelArgs {
 struct LevelSmem {
     i64 *u, *gs, *c, *X, *gr;
     int L0, L1, C0, C1;
+    // this problem's arrays (see batch_at)
+    const Scale *sc;
+    const i64 *usrc, *gin, *ucsrc;
+    const double *fin;
+    i64 *uout, *ucout, *gcout;
+    double *uout64;
 };
 
-// The arrays of one problem of the batch (see batch_at); u_src is on level
-// l-1 when it feeds the FMG interpolation.
-__device__ __forceinline__ void level_batch(LevelArgs &a, bool u_src_coarse) {
-    const long long n = a.n;
-    a.sc += blockIdx.y;
-    a.u_src = batch_at(a.u_src, u_src_coarse ? n / 2 : n);
-    a.g = batch_at(a.g, n);
-    a.f = batch_at(a.f, n);
-    a.uc_src = batch_at(a.uc_src, n / 2);
-    a.u_out = batch_at(a.u_out, n);
-    a.u_out_f64 = batch_at(a.u_out_f64, n);
-    a.uc_out = batch_at(a.uc_out, n / 2);
-    a.gc_out = batch_at(a.gc_out, n / 2);
-}
-
-__device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs &a) {
+// Layout and this problem's arrays (see batch_at); u_src is on level l-1
+// when it feeds the FMG interpolation.
+__device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs &a, bool u_src_coarse) {
     LevelSmem m;
     m.L0 = max(0, s - a.halo);
     m.L1 = min(a.n, s + a.tile + a.halo);
@@ -371,13 +364,24 @@ __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs 
     m.c = m.gs + a.maxlen;
     m.X = m.c + a.maxc;
     m.gr = m.X + a.maxch;
+    const long long n = a.n;
+    m.sc = a.sc + blockIdx.y;
+    m.usrc = batch_at(a.u_src, u_src_coarse ? n / 2 : n);
+    m.gin = batch_at(a.g, n);
+    m.fin = batch_at(a.f, n);
+    m.ucsrc = batch_at(a.uc_src, n / 2);
+    m.uout = batch_at(a.u_out, n);
+    m.uout64 = batch_at(a.u_out_f64, n);
+    m.ucout = batch_at(a.uc_out, n / 2);
+    m.gcout = batch_at(a.gc_out, n / 2);
     return m;
 }
 
 // Issue the staging copies of G_l (or of f, converted by prepare_rhs).
 __device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
-    if (a.g) stage_range(m.gs, a.g + m.L0, m.L1 - m.L0);
-    else stage_range(m.gs, a.f + m.L0, m.L1 - m.L0);
+    (void)a;
+    if (m.gin) stage_range(m.gs, m.gin + m.L0, m.L1 - m.L0);
+    else stage_range(m.gs, m.fin + m.L0, m.L1 - m.L0);
 }
 
 // In place over the staged cells (pairs 2J, 2J+1; L0 and L1 are even):
@@ -385,8 +389,9 @@ __device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
 // converted to G first on the finest level; with gr, also the restricted
 // right-hand side of the coarse cells [J0, J1).
 __device__ void prepare_rhs(LevelSmem &m, const LevelArgs &a, int gsh, i64 *gr, int J0, int J1) {
-    const bool from_f = (a.g == nullptr);
-    const int kg = a.sc->Sg0;
+    (void)a;
+    const bool from_f = (m.gin == nullptr);
+    const int kg = m.sc->Sg0;
     for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x) {
         const int i = 2 * J - m.L0;
         i64 g0 = m.gs[i], g1 = m.gs[i + 1];
@@ -419,14 +424,14 @@ __device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
 template <bool FROM_PI>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
     pdl_enter();
-    level_batch(a, FROM_PI);
+
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
-    LevelSmem m = level_smem(smi, s, a);
+    LevelSmem m = level_smem(smi, s, a, FROM_PI);
     stage_g_async(m, a);
-    if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
-    else stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
+    if (FROM_PI) stage_coarse_async(m.c, m.usrc, m.C0, m.C1, nc);
+    else stage_range(m.u, m.usrc + m.L0, m.L1 - m.L0);
     stage_wait();
     __syncthreads();
     const int J0 = s >> 1;
@@ -445,23 +450,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         int i0 = 2 * J - m.L0;
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
-        a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
-        a.gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+        m.ucout[J] = (u[i0] + u[i0 + 1]) >> 1;
+        m.gcout[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
     }
-    for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) a.u_out[i] = u[i - m.L0];
+    for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) m.uout[i] = u[i - m.L0];
 }
 
 // Up pass (Eq. 4): U_l += P (U_{l-1} - R U_l) (rounded to units), then nu sweeps.
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
     pdl_enter();
-    level_batch(a, false);
+
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
-    LevelSmem m = level_smem(smi, s, a);
+    LevelSmem m = level_smem(smi, s, a, false);
     stage_g_async(m, a);
-    stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
-    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_range(m.u, m.usrc + m.L0, m.L1 - m.L0);
+    stage_coarse_async(m.c, m.ucsrc, m.C0, m.C1, nc);
     stage_wait();
     __syncthreads();
     prepare_rhs(m, a, 2 * a.l - 2, nullptr, 0, 0);
@@ -483,12 +488,12 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     __syncthreads();
     smooth_range(m, n, a.nu);
     const i64 *u = m.u;
-    if (a.u_out_f64) {
-        const int S = a.sc->S;
+    if (m.uout64) {
+        const int S = m.sc->S;
         for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x)
-            a.u_out_f64[i] = fixed_to_f64(u[i - m.L0], S);
+            m.uout64[i] = fixed_to_f64(u[i - m.L0], S);
     } else {
-        for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) a.u_out[i] = u[i - m.L0];
+        for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) m.uout[i] = u[i - m.L0];
     }
 }
 
@@ -511,17 +516,8 @@ struct SegSmem {
     int e0, e1, lo, hi, C0, C1;
 };
 
-// The arrays of one problem of the batch (see batch_at).
-__device__ __forceinline__ void seg_batch(SegArgs &a) {
-    const long long n = a.n;
-    a.sc += blockIdx.y;
-    a.f = batch_at(a.f, n);
-    a.uc_src = batch_at(a.uc_src, n / 2);
-    a.uc_out = batch_at(a.uc_out, n / 2);
-    a.gc_out = batch_at(a.gc_out, n / 2);
-    a.seam = batch_at(a.seam, 6 * (n / a.W));
-    a.u_out = batch_at(a.u_out, n);
-}
+// (The arrays of problem blockIdx.y are formed where they are used, see
+// batch_at, so that their pointers do not stay live across the sweeps.)
 
 __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
     SegSmem m;
@@ -544,9 +540,9 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
 // right-hand side of the segment's coarse cells [J0, J1).  The staged range
 // may start at an odd cell, so pairs are clipped to it.
 __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) {
-    const int nc = a.n >> 1, kg = a.sc->Sg0, gsh = 2 * a.M - 2;
-    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
-    stage_range(m.gs, a.f + m.lo, m.hi - m.lo);
+    const int nc = a.n >> 1, kg = (a.sc + blockIdx.y)->Sg0, gsh = 2 * a.M - 2;
+    stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
+    stage_range(m.gs, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
     stage_wait();
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
@@ -572,7 +568,6 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
 
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
-    seg_batch(a);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -582,20 +577,21 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     const int tsh = 2 * a.M - 4;
     for (int k = 0; k < a.nu; ++k) lex_sweep<kChunk>(m.u, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     const i64 *u = m.u;
+    i64 *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) {
         int i0 = 2 * J - m.lo;
-        a.uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
+        uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
         bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
         if (!edge) {
             i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
             i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
-            a.gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+            gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
         }
     }
     if (threadIdx.x < 6) {
         int k = threadIdx.x;
         int i = (k < 3) ? s + k : s + a.W - 6 + k;
-        a.seam[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
+        batch_at(a.seam, 6LL * (n / a.W))[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
     }
 }
 
@@ -603,31 +599,32 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 // assembled fine values (seams) and the restricted solution.
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
-    seg_batch(a);
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
     const int s = (k + 1) * a.W;
-    const int kg = a.sc->Sg0, tsh = 2 * a.M - 4;
-    const i64 *L = a.seam + (size_t)k * 6, *R = a.seam + (size_t)(k + 1) * 6;
+    const int kg = (a.sc + blockIdx.y)->Sg0, tsh = 2 * a.M - 4;
+    const i64 *seam = batch_at(a.seam, 6LL * nseg);
+    const double *f = batch_at(a.f, a.n);
+    i64 *uc_out = batch_at(a.uc_out, a.n / 2), *gc_out = batch_at(a.gc_out, a.n / 2);
+    const i64 *L = seam + (size_t)k * 6, *R = seam + (size_t)(k + 1) * 6;
     const i64 f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
     const int J = (s >> 1) - 1;
-    const i64 hm1 = a.uc_out[J - 1], h0 = a.uc_out[J], h1 = a.uc_out[J + 1], h2 = a.uc_out[J + 2];
+    const i64 hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
     {
         i64 tau = ((h0 - hm1) - (h1 - h0)) - 2 * ((f2 - f3) - (p0 - f1));
-        i64 g0 = f64_to_fixed(a.f[2 * J], kg), g1 = f64_to_fixed(a.f[2 * J + 1], kg);
-        a.gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        i64 g0 = f64_to_fixed(f[2 * J], kg), g1 = f64_to_fixed(f[2 * J + 1], kg);
+        gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
     }
     {
         const int J2 = J + 1;
         i64 tau = ((h1 - h0) - (h2 - h1)) - 2 * ((p0 - f1) - (p2 - p1));
-        i64 g0 = f64_to_fixed(a.f[2 * J2], kg), g1 = f64_to_fixed(a.f[2 * J2 + 1], kg);
-        a.gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        i64 g0 = f64_to_fixed(f[2 * J2], kg), g1 = f64_to_fixed(f[2 * J2 + 1], kg);
+        gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
     }
 }
 
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
-    seg_batch(a);
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -644,9 +641,10 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
         __syncthreads();
         lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
-    const int S = a.sc->S;
+    const int S = (a.sc + blockIdx.y)->S;
+    double *u_out = batch_at(a.u_out, a.n);
     for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
-        a.u_out[i] = fixed_to_f64(p[i - m.lo], S);
+        u_out[i] = fixed_to_f64(p[i - m.lo], S);
 }
 
 // --------------------------------------------------------------------------
@@ -747,19 +745,18 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
     const int nMc = 1 << a.Mc;
-    a.sc += blockIdx.y;
-    a.u_in = batch_at(a.u_in, nMc);
-    a.g_in = batch_at(a.g_in, nMc);
-    a.f = batch_at(a.f, nMc);
-    a.u_out = batch_at(a.u_out, nMc);
-    a.u_out_f64 = batch_at(a.u_out_f64, nMc);
-    const int kg = a.sc->Sg0;
-    if (a.g_in) stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
-    else stage_range(m.g + m.off(a.Mc), a.f, nMc);
-    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
+    const Scale *sc = a.sc + blockIdx.y;
+    const i64 *u_in = batch_at(a.u_in, nMc), *g_in = batch_at(a.g_in, nMc);
+    const double *f = batch_at(a.f, nMc);
+    i64 *u_out = batch_at(a.u_out, nMc);
+    double *u_out_f64 = batch_at(a.u_out_f64, nMc);
+    const int kg = sc->Sg0;
+    if (g_in) stage_range(m.g + m.off(a.Mc), g_in, nMc);
+    else stage_range(m.g + m.off(a.Mc), f, nMc);
+    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), u_in, nMc);
     stage_wait();
     __syncthreads();
-    if (!a.g_in)
+    if (!g_in)
         for (int i = threadIdx.x; i < nMc; i += blockDim.x)
             m.g[m.off(a.Mc) + i] = f64_to_fixed(__longlong_as_double(m.g[m.off(a.Mc) + i]), kg);
     __syncthreads();
@@ -770,23 +767,23 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
             for (int J = threadIdx.x; J < (1 << (l - 1)); J += blockDim.x) gc[J] = (g[2 * J] + g[2 * J + 1] + 1) >> 1;
             __syncthreads();
         }
-        tail_coarsest(m, a.Ainv, a.sc);
+        tail_coarsest(m, a.Ainv, sc);
         for (int k = a.M0; k < a.Mc; ++k) {
             tail_interp(m, k + 1);
             for (int l = k + 1; l > a.M0; --l) tail_down(m, l, a.nu1);
-            tail_coarsest(m, a.Ainv, a.sc);
+            tail_coarsest(m, a.Ainv, sc);
             for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up(m, l, a.nu2);
         }
     } else {
         for (int l = a.Mc; l > a.M0; --l) tail_down(m, l, a.nu1);
-        tail_coarsest(m, a.Ainv, a.sc);
+        tail_coarsest(m, a.Ainv, sc);
         for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up(m, l, a.nu2);
     }
-    if (a.u_out_f64) {
-        const int S = a.sc->S;
-        for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out_f64[i] = fixed_to_f64(m.u[m.off(a.Mc) + i], S);
+    if (u_out_f64) {
+        const int S = sc->S;
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) u_out_f64[i] = fixed_to_f64(m.u[m.off(a.Mc) + i], S);
     } else {
-        for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out[i] = m.u[m.off(a.Mc) + i];
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) u_out[i] = m.u[m.off(a.Mc) + i];
     }
 }
 

@@ -46,7 +46,9 @@ __device__ __forceinline__ void pdl_enter() {
 
 // Batched solves: a block serves problem blockIdx.y of the batch.  Every array
 // of a level holds the problems one after another, so a pointer into an array
-// of `cells` cells per problem moves by blockIdx.y * cells.
+// of `cells` cells per problem moves by blockIdx.y * cells.  (The kernels keep
+// the moved pointers in locals: writing a field of a kernel's parameter
+// struct would make every thread copy the whole struct to local memory.)
 template <typename T>
 __device__ __forceinline__ T *batch_at(T *p, long long cells) {
     return p ? p + (long long)blockIdx.y * cells : p;
@@ -421,8 +423,8 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     const int chunk = 1 << a.chunk_log;       // cells of level lin per block (>= 2^depth)
     double *cur = sm, *nxt = sm + chunk;
     const long long base = (long long)blockIdx.x * chunk;
-    a.in = batch_at(a.in, 1LL << a.lin);
-    stage_range(cur, a.in + base, chunk);
+    const double *in = batch_at(a.in, 1LL << a.lin);
+    stage_range(cur, in + base, chunk);
     stage_wait();
     __syncthreads();
     if (a.in_exp)
@@ -507,15 +509,12 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
-    a.u_src = batch_at(a.u_src, FROM_PI ? nc : n);
-    a.g = batch_at(a.g, n);
-    a.u_out = batch_at(a.u_out, n);
-    a.uc_out = batch_at(a.uc_out, nc);
-    a.gc_out = batch_at(a.gc_out, nc);
+    const double *u_src = batch_at(a.u_src, FROM_PI ? nc : n), *g = batch_at(a.g, n);
+    double *u_out = batch_at(a.u_out, n), *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
-    if (FROM_PI) stage_coarse_async(m.c, a.u_src, m.C0, m.C1, nc);
-    else stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
+    stage_range(m.g, g + m.L0, m.L1 - m.L0);
+    if (FROM_PI) stage_coarse_async(m.c, u_src, m.C0, m.C1, nc);
+    else stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
     stage_wait();
     __syncthreads();
     if (a.g_exp)
@@ -536,12 +535,12 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         int i0 = 2 * J - m.L0;
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
-        a.uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
+        uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
         double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
         if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
-        a.gc_out[J] = gc;
+        gc_out[J] = gc;
     }
-    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
+    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
 }
 
 // Up pass (Eq. 4): u_l += P (u_{l-1} - R u_l), then nu sweeps.
@@ -551,14 +550,12 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
-    a.u_src = batch_at(a.u_src, n);
-    a.g = batch_at(a.g, n);
-    a.uc_src = batch_at(a.uc_src, nc);
-    a.u_out = batch_at(a.u_out, n);
+    const double *u_src = batch_at(a.u_src, n), *g = batch_at(a.g, n), *uc_src = batch_at(a.uc_src, nc);
+    double *u_out = batch_at(a.u_out, n);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    stage_range(m.g, a.g + m.L0, m.L1 - m.L0);
-    stage_range(m.u, a.u_src + m.L0, m.L1 - m.L0);
-    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
+    stage_range(m.g, g + m.L0, m.L1 - m.L0);
+    stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
+    stage_coarse_async(m.c, uc_src, m.C0, m.C1, nc);
     stage_wait();
     __syncthreads();
     if (a.g_exp)
@@ -585,7 +582,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     __syncthreads();
     smooth_range<NL>(m, n, a.nu, scale2(a.lam, -2 * a.l));
     const double *u = m.u;
-    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) a.u_out[i] = u[i - m.L0];
+    for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
 }
 
 // ---------------------------------------------------------------------------
@@ -612,17 +609,6 @@ struct SegSmem {
     int e0, e1, lo, hi, C0, C1;
 };
 
-// The arrays of one problem of the batch (see batch_at).
-__device__ __forceinline__ void seg_batch(SegArgs &a) {
-    const long long n = a.n;
-    a.f = batch_at(a.f, n);
-    a.uc_src = batch_at(a.uc_src, n / 2);
-    a.uc_out = batch_at(a.uc_out, n / 2);
-    a.gc_out = batch_at(a.gc_out, n / 2);
-    a.seam = batch_at(a.seam, 6 * (n / a.W));
-    a.u_out = batch_at(a.u_out, n);
-}
-
 __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s) {
     SegSmem m;
     m.e0 = max(0, s - a.b);
@@ -642,8 +628,8 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
 // Load Pi u_{M-1} on [lo, hi) (patch and frozen cells) and the scaled rhs.
 __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1;
-    stage_coarse_async(m.c, a.uc_src, m.C0, m.C1, nc);
-    stage_range(m.g, a.f + m.lo, m.hi - m.lo);
+    stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
+    stage_range(m.g, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
     stage_wait();
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
@@ -666,7 +652,6 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
-    seg_batch(a);
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
@@ -676,22 +661,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     for (int k = 0; k < a.nu; ++k) sweep_op<NL>(m.u, m.g, cl, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     const double *u = m.u;
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    double *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
         int i0 = 2 * J - m.lo;
-        a.uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
+        uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
         bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
         if (!edge) {
             double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
             double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
             double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
             if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
-            a.gc_out[J] = gc;
+            gc_out[J] = gc;
         }
     }
     if (threadIdx.x < 6) {
         int k = threadIdx.x;
         int i = (k < 3) ? s + k : s + a.W - 6 + k;
-        a.seam[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
+        batch_at(a.seam, 6LL * (a.n / a.W))[(size_t)blockIdx.x * 6 + k] = u[i - m.lo];
     }
 }
 
@@ -701,22 +687,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 template <bool NL>
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
-    seg_batch(a);
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
+    const double *seam = batch_at(a.seam, 6LL * nseg), *f = batch_at(a.f, a.n);
+    double *uc_out = batch_at(a.uc_out, a.n / 2), *gc_out = batch_at(a.gc_out, a.n / 2);
     const int s = (k + 1) * a.W;
-    const double *L = a.seam + (size_t)k * 6, *R = a.seam + (size_t)(k + 1) * 6;
+    const double *L = seam + (size_t)k * 6, *R = seam + (size_t)(k + 1) * 6;
     // fine cells s-3 .. s+2 of the assembled level
     double f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
     const int J = (s >> 1) - 1;         // last coarse cell of the left segment
     // coarse fluxes G from the restricted solution, fine fluxes F from the seams
-    const double hm1 = a.uc_out[J - 1], h0 = a.uc_out[J], h1 = a.uc_out[J + 1], h2 = a.uc_out[J + 2];
+    const double hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
     {
         double Gl = h0 - hm1, Gr = h1 - h0;
         double Fl = f2 - f3, Fr = p0 - f1;
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
         if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
-        a.gc_out[J] = scale2(a.f[2 * J] + a.f[2 * J + 1], 1 - 2 * a.M) + tau;
+        gc_out[J] = scale2(f[2 * J] + f[2 * J + 1], 1 - 2 * a.M) + tau;
     }
     {
         int J2 = J + 1;
@@ -724,7 +711,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         double Fl = p0 - f1, Fr = p2 - p1;
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
         if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
-        a.gc_out[J2] = scale2(a.f[2 * J2] + a.f[2 * J2 + 1], 1 - 2 * a.M) + tau;
+        gc_out[J2] = scale2(f[2 * J2] + f[2 * J2 + 1], 1 - 2 * a.M) + tau;
     }
 }
 
@@ -734,7 +721,6 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 template <bool NL>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
-    seg_batch(a);
     extern __shared__ double sm[];
     const int s = blockIdx.x * a.W;
     const int n = a.n;
@@ -752,7 +738,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
         __syncthreads();
         sweep_op<NL>(p, m.g, scale2(a.lam, -2 * a.M), m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     }
-    for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) a.u_out[i] = p[i - m.lo];
+    double *u_out = batch_at(a.u_out, a.n);
+    for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) u_out[i] = p[i - m.lo];
 }
 
 // ---------------------------------------------------------------------------
@@ -905,11 +892,10 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     m.X = m.S + (1 << a.Mc) + 8;
     m.Y = m.X + blockDim.x;
     const int nMc = 1 << a.Mc;
-    a.u_in = batch_at(a.u_in, nMc);
-    a.g_in = batch_at(a.g_in, nMc);
-    a.u_out = batch_at(a.u_out, nMc);
-    stage_range(m.g + m.off(a.Mc), a.g_in, nMc);
-    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), a.u_in, nMc);
+    const double *u_in = batch_at(a.u_in, nMc), *g_in = batch_at(a.g_in, nMc);
+    double *u_out = batch_at(a.u_out, nMc);
+    stage_range(m.g + m.off(a.Mc), g_in, nMc);
+    if (a.mode == 1) stage_range(m.u + m.off(a.Mc), u_in, nMc);
     stage_wait();
     __syncthreads();
     if (a.g_exp)
@@ -939,7 +925,7 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
         tail_coarsest<NL>(m, a.Ainv);
         for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up<NL>(m, l, a.nu2);
     }
-    for (int i = threadIdx.x; i < nMc; i += blockDim.x) a.u_out[i] = m.u[m.off(a.Mc) + i];
+    for (int i = threadIdx.x; i < nMc; i += blockDim.x) u_out[i] = m.u[m.off(a.Mc) + i];
 }
 
 }  // namespace srfmg
