@@ -379,6 +379,12 @@ def run_gpu(a):
         sr64 = {"value": dist.world * N / (ms64 * 1e-3), "ms_per_step": ms64,
                 "err_max_vs_exact": float(np.max(np.abs(u64 - u_exact)))}
 
+    # autotuner (row f1): the fastest admissible segment layout for this solve
+    best, table = srfmg.autotune(M, device=dev, reps=5, precision=prec)
+    autotune = {"choice": {"segment_width": best.segment_width, "buffer_width": best.buffer_width},
+                "candidates_ms": {f"W{w}_b{bb}": round(t, 4) for w, bb, t in table},
+                "benchmarked_layout": {"segment_width": W, "buffer_width": b}}
+
     # adjoint solve (dL/df for L = 1/2 |u - u_obs|^2, u_obs = exact + N(0, 1e-3^2))
     rng = np.random.default_rng(7)
     g_adj = torch.from_numpy(u - (u_exact + rng.normal(0.0, 1e-3, N))).to(dev)
@@ -453,6 +459,7 @@ def run_gpu(a):
                        "speedup_over_plain": ms_plain / ms},
         "sr_fp64": sr64,
         "adjoint": adjoint,
+        "autotune": autotune,
         "roofline": roofline,
         "kernel_share": {k: round(v / tot, 4) for k, v in sorted(by_kind.items(), key=lambda x: -x[1])},
         "clocks": clocks,

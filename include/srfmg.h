@@ -183,6 +183,27 @@ const char *srfmg_launch_name(srfmg_handle h, int32_t i);
 srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n_coarsest, int32_t nu1,
                                        int32_t nu2, const double *f, double *u, void *stream);
 
+/* Autotuner for the SR segment layout (the paper leaves W and b free; Sec. 4
+ * finds four buffer cells enough for one FMG cycle to stay at discretization
+ * accuracy in every configuration studied, so only b >= 4 is admissible).
+ * For the solve described by *base (n_sr_levels must be 1; segment_width and
+ * buffer_width are ignored) it times every candidate (W, b) with W in
+ * {256, 512, 1024, 2048, 4096}, W <= N/2, and b in {4, 8}, b <= W (candidate
+ * k in that order; srfmg_autotune_candidate names it): a plan per candidate,
+ * two warm-up solves of a zero right-hand side (the kernels have no data-
+ * dependent control flow) and `reps` timed solves with CUDA events on a
+ * stream of its own; it allocates and frees its own f and u.  *best receives
+ * *base with the fastest (W, b); the result of a solve depends on (W, b), so a
+ * caller that checks it replays the oracle with the same pair.  ms (optional,
+ * capacity entries) receives the average milliseconds per solve of each
+ * candidate; *ncand (optional) the number of candidates.  Synchronous.
+ * Errors: SRFMG_EINVAL for NULL or invalid arguments (before any device
+ * work), as srfmg_create/srfmg_solve otherwise. */
+srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
+                            float *ms, int32_t capacity, int32_t *ncand);
+srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32_t *segment_width,
+                                      int32_t *buffer_width);
+
 /* Release the device workspace and graphs.  Synchronises the device first.
  * Accepts NULL (returns SRFMG_OK). */
 srfmg_status srfmg_destroy(srfmg_handle h);

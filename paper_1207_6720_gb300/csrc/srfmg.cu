@@ -827,6 +827,76 @@ const char *srfmg_last_error(srfmg_handle h) {
     return h ? h->err.c_str() : g_create_error.c_str();
 }
 
+srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
+                            float *ms, int32_t capacity, int32_t *ncand) {
+    if (!base || !best || reps < 1 || (ms && capacity < 0)) return fail(nullptr, SRFMG_EINVAL, "bad arguments to srfmg_autotune");
+    std::string msg = check_params(base);
+    if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
+    if (base->n_sr_levels != 1) return fail(nullptr, SRFMG_EINVAL, "srfmg_autotune tunes the SR segment layout (n_sr_levels = 1)");
+    const long long N = 1LL << base->log2_n;
+    std::vector<std::pair<int, int>> cand;
+    for (int W = 256; W <= 4096; W *= 2)
+        for (int b : {4, 8})
+            if (W <= N / 2 && b <= W) cand.push_back({W, b});
+    if (cand.empty()) cand.push_back({(int)std::max<long long>(16, N), 4});
+    if (ncand) *ncand = (int32_t)cand.size();
+    const size_t B = (size_t)(base->batch > 0 ? base->batch : 1);
+    double *f = nullptr, *u = nullptr;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&f, B * (size_t)N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&u, B * (size_t)N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(f, 0, B * (size_t)N * sizeof(double));   // no data-dependent control flow
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    srfmg_status st = (e == cudaSuccess) ? SRFMG_OK : fail(nullptr, SRFMG_ECUDA, std::string("autotune set-up: ") + cudaGetErrorString(e));
+    float best_ms = 0.f;
+    for (size_t k = 0; k < cand.size() && st == SRFMG_OK; ++k) {
+        srfmg_params p = *base;
+        p.segment_width = cand[k].first;
+        p.buffer_width = cand[k].second;
+        srfmg_handle h = nullptr;
+        st = srfmg_create(&p, device, &h);
+        for (int w = 0; w < 2 && st == SRFMG_OK; ++w) st = srfmg_solve(h, f, u, s);
+        if (st == SRFMG_OK && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = SRFMG_ECUDA;
+        for (int r = 0; r < reps && st == SRFMG_OK; ++r) st = srfmg_solve(h, f, u, s);
+        float t = 0.f;
+        if (st == SRFMG_OK && ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                               (e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess))
+            st = fail(nullptr, SRFMG_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+        if (st != SRFMG_OK && h) g_create_error = h->err;
+        srfmg_destroy(h);
+        t /= (float)reps;
+        if (st == SRFMG_OK) {
+            if (ms && (int32_t)k < capacity) ms[k] = t;
+            if (k == 0 || t < best_ms) { best_ms = t; *best = p; }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(f);
+    cudaFree(u);
+    return st;
+}
+
+srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32_t *segment_width,
+                                      int32_t *buffer_width) {
+    if (!base || !segment_width || !buffer_width || k < 0) return fail(nullptr, SRFMG_EINVAL, "bad arguments");
+    const long long N = 1LL << base->log2_n;
+    int32_t i = 0;
+    for (int W = 256; W <= 4096; W *= 2)
+        for (int b : {4, 8})
+            if (W <= N / 2 && b <= W) {
+                if (i == k) { *segment_width = W; *buffer_width = b; return SRFMG_OK; }
+                ++i;
+            }
+    if (i == 0 && k == 0) { *segment_width = (int32_t)std::max<long long>(16, N); *buffer_width = 4; return SRFMG_OK; }
+    return fail(nullptr, SRFMG_EINVAL, "candidate index out of range");
+}
+
 const char *srfmg_version(void) { return "srfmg 0.1 sm_103a"; }
 
 }  // extern "C"

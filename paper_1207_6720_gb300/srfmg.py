@@ -18,7 +18,8 @@ LAPLACE, BRATU = 0, 2
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
-           "srfmg_solve_small_noalloc", "srfmg_destroy", "srfmg_last_error", "srfmg_version")
+           "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
+           "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
 class Params(ctypes.Structure):
@@ -77,10 +78,15 @@ def load(build_if_missing=True):
     lib.srfmg_solve_small_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, vp, vp, vp]
     lib.srfmg_solve_small_noalloc.restype = ctypes.c_int
+    lib.srfmg_autotune.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_int32, ctypes.POINTER(Params),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.srfmg_autotune_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
-                 "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy"):
+                 "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
+                 "srfmg_autotune_candidate"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -246,6 +252,26 @@ def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None)
     if st != OK:
         raise SrfmgError(st, "srfmg_solve_small_noalloc (status code only)")
     return u
+
+
+def autotune(log2_n, device=0, reps=5, **overrides):
+    """Time the admissible SR segment layouts (W, b >= 4) for this solve and
+    return (best Params, [(W, b, ms per solve), ...])."""
+    lib = load()
+    base = default_params(log2_n, **overrides)
+    best = Params()
+    cap = 16
+    ms = (ctypes.c_float * cap)()
+    n = ctypes.c_int32()
+    st = lib.srfmg_autotune(ctypes.byref(base), device, reps, ctypes.byref(best), ms, cap, ctypes.byref(n))
+    if st != OK:
+        raise SrfmgError(st, lib.srfmg_last_error(None).decode())
+    table = []
+    for k in range(min(n.value, cap)):
+        W, b = ctypes.c_int32(), ctypes.c_int32()
+        lib.srfmg_autotune_candidate(ctypes.byref(base), k, ctypes.byref(W), ctypes.byref(b))
+        table.append((W.value, b.value, float(ms[k])))
+    return best, table
 
 
 def version():

@@ -73,3 +73,39 @@ def test_batch_equals_single_solves_gpu(M, kw):
         p = oracle.Params(M, nRS=0, nu2=kw.get("nu2", 1))
     r = oracle.fmg_h(p, fs[3])
     assert np.max(np.abs(ub[3] - r)) <= 1e-10 * np.max(np.abs(r))
+
+
+# ---------------------------------------------------------------- autotuner (row f1)
+
+def test_autotune_checks_arguments_on_the_host():
+    lib = srfmg.load()
+    p = srfmg.default_params(16)
+    best = srfmg.Params()
+    assert lib.srfmg_autotune(None, 0, 3, ctypes.byref(best), None, 0, None) == srfmg.EINVAL
+    assert lib.srfmg_autotune(ctypes.byref(p), 0, 0, ctypes.byref(best), None, 0, None) == srfmg.EINVAL
+    p0 = srfmg.default_params(16, n_sr_levels=0)
+    assert lib.srfmg_autotune(ctypes.byref(p0), 0, 3, ctypes.byref(best), None, 0, None) == srfmg.EINVAL
+    W, b = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.srfmg_autotune_candidate(ctypes.byref(p), 0, ctypes.byref(W), ctypes.byref(b)) == srfmg.OK
+    assert (W.value, b.value) == (256, 4)
+    assert lib.srfmg_autotune_candidate(ctypes.byref(p), 10, ctypes.byref(W), ctypes.byref(b)) == srfmg.EINVAL
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_choice_replays_on_the_oracle_gpu(precision):
+    torch = pytest.importorskip("torch")
+    M = 16
+    best, table = srfmg.autotune(M, reps=3, precision=precision)
+    assert len(table) == 10 and all(b >= 4 for _, b, _ in table)
+    W, b = best.segment_width, best.buffer_width
+    assert (W, b) in [(w, bb) for w, bb, _ in table]
+    assert min(t for _, _, t in table) == [t for w, bb, t in table if (w, bb) == (W, b)][0]
+    f, _, _ = workloads.sine_series(M, 32, seed=9)
+    s = srfmg.Solver(M, params=best)
+    try:
+        u = s.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    finally:
+        s.close()
+    ref = oracle.fmg_h(oracle.sr_params(M, W, b), f)
+    assert np.max(np.abs(u - ref)) <= 1e-10 * np.max(np.abs(ref))
