@@ -30,6 +30,7 @@ class _Params(ctypes.Structure):
         ("seg_w", ctypes.c_int32 * (MAXLEV + 1)),
         ("seg_b", ctypes.c_int32 * (MAXLEV + 1)),
         ("op", ctypes.c_int32), ("lam", ctypes.c_double),
+        ("coef", ctypes.POINTER(ctypes.c_double)), ("coef_level", ctypes.c_int32),
     ]
 
 
@@ -59,6 +60,7 @@ def lib():
             "or_fmg_v": [pp, dp, dp],
             "or_vcycles_h": [pp, dp, dp, i],
             "or_apply_N": [i, ctypes.c_double, dp, dp],
+            "or_apply_La": [i, dp, dp, dp],
             "or_coarsest": [pp, i, dp, dp],
         }
         for name, args in sigs.items():
@@ -87,11 +89,13 @@ class Params:
     """Solve parameters; ``seg[l] = (w, b)`` segments level l (w = 0: whole level)."""
 
     def __init__(self, M, M0=2, nRS=1, nu1=1, nu2=1, smoother="lex", tau_src="assembled", seg=None,
-                 op="laplace", lam=0.0):
+                 op="laplace", lam=0.0, coef=None):
         self.M, self.M0, self.nRS, self.nu1, self.nu2 = M, M0, nRS, nu1, nu2
         self.smoother, self.tau_src = smoother, tau_src
         self.seg = dict(seg or {})
         self.op, self.lam = op, lam
+        # op "varcoef": the face coefficients a_j, j = 0..2^L, of the finest level L
+        self.coef = None if coef is None else _arr(coef)
 
     def c(self):
         p = _Params()
@@ -101,8 +105,11 @@ class Params:
         for l, (w, b) in self.seg.items():
             p.seg_w[l] = w
             p.seg_b[l] = b
-        p.op = {"laplace": 0, "bratu": 1}[self.op]
+        p.op = {"laplace": 0, "bratu": 1, "varcoef": 2}[self.op]
         p.lam = self.lam
+        if self.coef is not None:
+            p.coef = _ptr(self.coef)          # self.coef keeps the array alive
+            p.coef_level = int(np.log2(len(self.coef) - 1))
         return p
 
     def __repr__(self):
@@ -112,7 +119,7 @@ class Params:
 
 
 def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assembled", op="laplace",
-              lam=0.0):
+              lam=0.0, coef=None):
     """SR levels (the finest nRS) split into segments of W >> (M-l) cells with
     b buffer cells per side; every other level is smoothed as a whole."""
     seg = {}
@@ -122,7 +129,7 @@ def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assem
             raise ValueError("segment narrower than 2 cells on an SR level")
         seg[l] = (w, b)
     return Params(M, M0=M0, nRS=nRS, nu1=nu1, nu2=nu2, smoother=smoother, tau_src=tau_src, seg=seg,
-                  op=op, lam=lam)
+                  op=op, lam=lam, coef=coef)
 
 
 def paper_params(M, nRS, halo_type, ns, M0=2):
@@ -149,6 +156,15 @@ def apply_N(u, lam):
     u = _arr(u)
     out = np.empty_like(u)
     _check(lib().or_apply_N(len(u), float(lam), _ptr(u), _ptr(out)), "apply_N")
+    return out
+
+
+def apply_La(u, a):
+    """-(a u')' on one level with the face coefficients a (len(u) + 1 values)."""
+    u, a = _arr(u), _arr(a)
+    assert len(a) == len(u) + 1
+    out = np.empty_like(u)
+    _check(lib().or_apply_La(len(u), _ptr(a), _ptr(u), _ptr(out)), "apply_La")
     return out
 
 

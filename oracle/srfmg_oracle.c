@@ -13,7 +13,10 @@
  * Bratu equation, lam >= 0) with the same discretisation, solved by the same
  * FAS cycles (Sec. 2.2, Eqs. 1-2: the coarse equation of a nonlinear operator;
  * Fig. 1: a nonlinear smoother S(L, u, f)); the paper's studies are linear,
- * so the nonlinear pieces carry "Reading:" notes.  Level l has n = 2^l cells of width h = 1/n, centres
+ * so the nonlinear pieces carry "Reading:" notes.  And -(a u')' = f with a
+ * coefficient a > 0 given at the cell faces of the finest level (the paper's
+ * studies have a = 1): fluxes F_{i+1/2} = a_{i+1/2} (u_{i+1} - u_i), the same
+ * cycles; "Reading:" notes mark its pieces.  Level l has n = 2^l cells of width h = 1/n, centres
  * x_i = (i + 1/2) h; the Dirichlet wall is an odd ghost cell (u_{-1} = -u_0,
  * u_n = -u_{n-1}), which is where the diagonal 3/h^2 of the first and last
  * rows of the appendix operator comes from.
@@ -56,8 +59,10 @@ typedef struct {
                                   the literal reading of Fig. 3 line 4 */
     int32_t seg_w[OR_MAXLEV + 1]; /* per level: segment interior width, 0 = whole level */
     int32_t seg_b[OR_MAXLEV + 1]; /* per level: buffer cells on each side */
-    int32_t op;             /* 0: -u'' = f;  1: -u'' + lam e^u = f */
+    int32_t op;             /* 0: -u'' = f;  1: -u'' + lam e^u = f;  2: -(a u')' = f */
     double lam;             /* op 1: lam >= 0 (op 0: ignored) */
+    const double *coef;     /* op 2: a at the 2^coef_level + 1 faces x = j 2^-coef_level */
+    int32_t coef_level;     /* op 2: the level coef is given on (the finest) */
 } or_params;
 
 /* lam of the operator (0 for the linear problem). */
@@ -71,29 +76,36 @@ static double cell(const double *a, int off, int i) { return a[i - off]; }
 /* Operators of Sec. 4 (one level of n cells, h = 1/n)                 */
 /* ------------------------------------------------------------------ */
 
-/* F_{i-1/2}; at the left wall F_{-1/2} = u_0 - (-u_0). */
-static double flux_left(const double *u, int off, int i) {
-    return i == 0 ? 2.0 * cell(u, off, 0) : cell(u, off, i) - cell(u, off, i - 1);
+/* Face coefficient a_j of a level (faces x = j h, j = 0..n); a = NULL is the
+ * constant coefficient 1 (every product with it is then exact, so the
+ * constant-coefficient results are unchanged bit for bit). */
+static double coef(const double *a, int j) { return a ? a[j] : 1.0; }
+
+/* F_{i-1/2} = a_i (u_i - u_{i-1}); at the left wall F_{-1/2} = a_0 (u_0 - (-u_0)). */
+static double flux_left(const double *u, int off, int i, const double *a) {
+    return coef(a, i) * (i == 0 ? 2.0 * cell(u, off, 0) : cell(u, off, i) - cell(u, off, i - 1));
 }
-/* F_{i+1/2}; at the right wall F_{n-1/2} = (-u_{n-1}) - u_{n-1}. */
-static double flux_right(const double *u, int off, int i, int n) {
-    return i == n - 1 ? -2.0 * cell(u, off, n - 1) : cell(u, off, i + 1) - cell(u, off, i);
+/* F_{i+1/2} = a_{i+1} (u_{i+1} - u_i); at the right wall F_{n-1/2} = a_n ((-u_{n-1}) - u_{n-1}). */
+static double flux_right(const double *u, int off, int i, int n, const double *a) {
+    return coef(a, i + 1) * (i == n - 1 ? -2.0 * cell(u, off, n - 1) : cell(u, off, i + 1) - cell(u, off, i));
 }
 /* (L u)_i = (F_{i-1/2} - F_{i+1/2}) / h^2, with 1/h^2 = n^2 exactly. */
-static double Lu_at(const double *u, int off, int i, int n) {
+static double Lu_at(const double *u, int off, int i, int n, const double *a) {
     double inv_h2 = (double)n * (double)n;
-    return (flux_left(u, off, i) - flux_right(u, off, i, n)) * inv_h2;
+    return (flux_left(u, off, i, a) - flux_right(u, off, i, n, a)) * inv_h2;
 }
-/* Diagonal of L: 2/h^2 inside, 3/h^2 in the two wall cells. */
-static double Ldiag_at(int i, int n) {
+/* Diagonal of L: (a_i + a_{i+1}) / h^2, with 2 a at a wall face (2/h^2 inside
+ * and 3/h^2 in the two wall cells for a = 1). */
+static double Ldiag_at(int i, int n, const double *a) {
     double inv_h2 = (double)n * (double)n;
-    return (i == 0 || i == n - 1) ? 3.0 * inv_h2 : 2.0 * inv_h2;
+    double al = coef(a, i) * (i == 0 ? 2.0 : 1.0), ar = coef(a, i + 1) * (i == n - 1 ? 2.0 : 1.0);
+    return (al + ar) * inv_h2;
 }
 
 /* Nonlinear operator N(u)_i = (L u)_i + lam e^{u_i}.  With lam = 0 the added
  * term is an exact +0, so N is L bit for bit. */
-static double Nu_at(const double *u, int off, int i, int n, double lam) {
-    return Lu_at(u, off, i, n) + lam * exp(cell(u, off, i));
+static double Nu_at(const double *u, int off, int i, int n, double lam, const double *a) {
+    return Lu_at(u, off, i, n, a) + lam * exp(cell(u, off, i));
 }
 
 /* Restriction (Sec. 4, first order): mean of the two children of coarse J. */
@@ -135,20 +147,21 @@ static double prolong_fmg_at(const double *uc, int i, int nc) {
 
 /* Exact solve of L u = rhs on one level (the coarsest-grid solve of Figs. 1-2):
  * L is tridiagonal and diagonally dominant, so the Thomas algorithm. */
-static int thomas_shift(int n, const double *rhs, const double *dshift, double *u);
-static int thomas(int n, const double *rhs, double *u) { return thomas_shift(n, rhs, NULL, u); }
+static int thomas_shift(int n, const double *rhs, const double *dshift, double *u, const double *a);
+static int thomas(int n, const double *rhs, double *u) { return thomas_shift(n, rhs, NULL, u, NULL); }
 
-/* Thomas for the tridiagonal L + diag(dshift) (dshift = NULL: L). */
-static int thomas_shift(int n, const double *rhs, const double *dshift, double *u) {
+/* Thomas for the tridiagonal L + diag(dshift) (dshift = NULL: L); the
+ * coefficient a of the level (NULL: 1). */
+static int thomas_shift(int n, const double *rhs, const double *dshift, double *u, const double *a) {
     if (n < 1) return OR_EINVAL;
     double *cp = (double *)malloc(sizeof(double) * (size_t)n);
     double *dp = (double *)malloc(sizeof(double) * (size_t)n);
     if (!cp || !dp) { free(cp); free(dp); return OR_ENOMEM; }
     double off = -((double)n * (double)n);
     for (int i = 0; i < n; i++) {
-        double lower = i > 0 ? off : 0.0;
-        double upper = i < n - 1 ? off : 0.0;
-        double diag = dshift ? Ldiag_at(i, n) + dshift[i] : Ldiag_at(i, n);
+        double lower = i > 0 ? coef(a, i) * off : 0.0;
+        double upper = i < n - 1 ? coef(a, i + 1) * off : 0.0;
+        double diag = dshift ? Ldiag_at(i, n, a) + dshift[i] : Ldiag_at(i, n, a);
         double denom = diag - (i > 0 ? lower * cp[i - 1] : 0.0);
         cp[i] = upper / denom;
         dp[i] = (rhs[i] - (i > 0 ? lower * dp[i - 1] : 0.0)) / denom;
@@ -165,9 +178,9 @@ static int thomas_shift(int n, const double *rhs, const double *dshift, double *
  * step), each step a Thomas solve with the Jacobian L + diag(lam e^u), until
  * the step is at most 4 ulp of max|u| or stops shrinking (the unique solution
  * for lam >= 0 to rounding; at most 100 steps). */
-static int coarsest_solve(const or_params *p, int n, const double *rhs, double *u) {
+static int coarsest_solve(const or_params *p, int n, const double *rhs, double *u, const double *a) {
     double lam = op_lam(p);
-    if (lam == 0.0) return thomas(n, rhs, u);
+    if (lam == 0.0) return thomas_shift(n, rhs, NULL, u, a);
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
     double *d = (double *)malloc(sizeof(double) * (size_t)n);
     double *du = (double *)malloc(sizeof(double) * (size_t)n);
@@ -175,10 +188,10 @@ static int coarsest_solve(const or_params *p, int n, const double *rhs, double *
     double prev = INFINITY;
     for (int it = 0; it < 100 && rc == OR_OK; it++) {
         for (int i = 0; i < n; i++) {
-            r[i] = rhs[i] - Nu_at(u, 0, i, n, lam);
+            r[i] = rhs[i] - Nu_at(u, 0, i, n, lam, a);
             d[i] = lam * exp(u[i]);
         }
-        rc = thomas_shift(n, r, d, du);
+        rc = thomas_shift(n, r, d, du, a);
         if (rc) break;
         double step = 0.0, umax = 0.0;
         for (int i = 0; i < n; i++) {
@@ -201,9 +214,10 @@ static int coarsest_solve(const or_params *p, int n, const double *rhs, double *
  * Reading (nonlinear, the smoother S(L, u, f) of Fig. 1): one pointwise Newton
  * step, u_i += (f_i - N(u)_i) / (L_ii + lam e^{u_i}); with lam = 0 both added
  * terms are exact zeros and this is the linear update bit for bit. */
-static void gs_update(double *v, int voff, const double *rhs, int roff, int i, int n, double lam) {
+static void gs_update(double *v, int voff, const double *rhs, int roff, int i, int n, double lam,
+                      const double *a) {
     double e = lam * exp(cell(v, voff, i));
-    v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - (Lu_at(v, voff, i, n) + e)) / (Ldiag_at(i, n) + e);
+    v[i - voff] = cell(v, voff, i) + (cell(rhs, roff, i) - (Lu_at(v, voff, i, n, a) + e)) / (Ldiag_at(i, n, a) + e);
 }
 
 /* Kaczmarz pass of Fig. 5 over every coarse cell J whose children both lie in
@@ -233,17 +247,17 @@ static void kaczmarz_pass(double *v, int voff, const double *uH, int e0, int e1)
  *     this discretization its V-cycle factor grows with the depth and one FMG
  *     cycle misses discretization accuracy. */
 static void patch_sweeps(int smoother, double *v, int voff, const double *rhs, int roff,
-                         int n, int e0, int e1, int nsweeps, const double *uH, double lam) {
+                         int n, int e0, int e1, int nsweeps, const double *uH, double lam, const double *a) {
     int ascending = 1;
     for (int k = 0; k < nsweeps; k++) {
         if (uH) kaczmarz_pass(v, voff, uH, e0, e1);
         if (smoother == 1) {
             for (int colour = 0; colour < 2; colour++)
                 for (int i = e0; i < e1; i++)
-                    if ((i & 1) == colour) gs_update(v, voff, rhs, roff, i, n, lam);
+                    if ((i & 1) == colour) gs_update(v, voff, rhs, roff, i, n, lam, a);
         } else {
-            if (ascending) for (int i = e0; i < e1; i++) gs_update(v, voff, rhs, roff, i, n, lam);
-            else           for (int i = e1 - 1; i >= e0; i--) gs_update(v, voff, rhs, roff, i, n, lam);
+            if (ascending) for (int i = e0; i < e1; i++) gs_update(v, voff, rhs, roff, i, n, lam, a);
+            else           for (int i = e1 - 1; i >= e0; i--) gs_update(v, voff, rhs, roff, i, n, lam, a);
             ascending = !ascending;
         }
     }
@@ -269,17 +283,19 @@ static void extended_patch(int s, int w, int b, int n, int *e0, int *e1, int *lo
  * the role of Ihat ubar in Eq. 7 (Ihat = I here).  Reads fine cells 2J-2 ..
  * 2J+3 of ubar (fewer at a wall) and 2J, 2J+1 of rhs_f. */
 static double tau_rhs_at(const double *ubar, int uoff, const double *rhs_f, int roff,
-                         int J, int nf, double lam) {
+                         int J, int nf, double lam, const double *af, const double *ac) {
     int nc = nf / 2;
     double Rrhs = (cell(rhs_f, roff, 2 * J) + cell(rhs_f, roff, 2 * J + 1)) * 0.5;
     double inv_H2 = (double)nc * (double)nc;
     double uJ = restrict_at(ubar, uoff, J);
-    double Gl = J == 0 ? 2.0 * uJ : uJ - restrict_at(ubar, uoff, J - 1);
-    double Gr = J == nc - 1 ? -2.0 * uJ : restrict_at(ubar, uoff, J + 1) - uJ;
+    /* Reading (variable coefficient): the coarse operator has the coefficients
+     * of the coinciding fine faces (coarse face J is fine face 2J) */
+    double Gl = coef(ac, J) * (J == 0 ? 2.0 * uJ : uJ - restrict_at(ubar, uoff, J - 1));
+    double Gr = coef(ac, J + 1) * (J == nc - 1 ? -2.0 * uJ : restrict_at(ubar, uoff, J + 1) - uJ);
     /* nonlinear (Eq. 2 with N for L): N_c(R ubar) - R N_f(ubar); lam = 0 adds
      * exact zeros */
     double Lc = (Gl - Gr) * inv_H2 + lam * exp(uJ);
-    double RLf = (Nu_at(ubar, uoff, 2 * J, nf, lam) + Nu_at(ubar, uoff, 2 * J + 1, nf, lam)) * 0.5;
+    double RLf = (Nu_at(ubar, uoff, 2 * J, nf, lam, af) + Nu_at(ubar, uoff, 2 * J + 1, nf, lam, af)) * 0.5;
     return (Rrhs + Lc) - RLf;
 }
 
@@ -294,7 +310,20 @@ typedef struct {
     double *tmp;      /* scratch, 2^M doubles */
     double *tmp2;     /* scratch, 2^M doubles */
     double *patch;    /* one extended patch incl. frozen cells */
+    double *a[OR_MAXLEV + 1];   /* op 2: face coefficients of each level, else NULL */
 } or_state;
+
+/* Face coefficients of level l (2^l + 1 values) for op 2, else NULL.
+ * Reading (variable coefficient): every face of level l coincides with a face
+ * of the finest level, whose coefficient it takes (injection). */
+static double *level_coef(const or_params *p, int l) {
+    if (p->op != 2) return NULL;
+    int n = 1 << l, sh = p->coef_level - l;
+    double *a = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    if (a)
+        for (int j = 0; j <= n; j++) a[j] = p->coef[(size_t)j << sh];
+    return a;
+}
 
 static int is_sr_level(const or_params *p, int l) { return l > p->M - p->nRS; }
 static int segmented(const or_params *p, int l) {
@@ -311,7 +340,7 @@ static void smooth_level(or_state *st, int l, const double *u_in, double *u_out,
     int n = 1 << l;
     if (!segmented(p, l)) {
         if (u_out != u_in) memcpy(u_out, u_in, sizeof(double) * (size_t)n);
-        patch_sweeps(p->smoother, u_out, 0, st->rhs[l], 0, n, 0, n, nsweeps, uH, op_lam(p));
+        patch_sweeps(p->smoother, u_out, 0, st->rhs[l], 0, n, 0, n, nsweeps, uH, op_lam(p), st->a[l]);
         return;
     }
     int w = p->seg_w[l];
@@ -319,7 +348,7 @@ static void smooth_level(or_state *st, int l, const double *u_in, double *u_out,
         int e0, e1, lo, hi;
         extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
         memcpy(st->patch, u_in + lo, sizeof(double) * (size_t)(hi - lo));
-        patch_sweeps(p->smoother, st->patch, lo, st->rhs[l], 0, n, e0, e1, nsweeps, uH, op_lam(p));
+        patch_sweeps(p->smoother, st->patch, lo, st->rhs[l], 0, n, e0, e1, nsweeps, uH, op_lam(p), st->a[l]);
         memcpy(u_out + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
     }
 }
@@ -341,7 +370,7 @@ static void presmooth_and_restrict(or_state *st, int l) {
         smooth_level(st, l, ul, st->tmp, p->nu1, NULL);
         memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
         for (int J = 0; J < nc; J++) uc[J] = restrict_at(ul, 0, J);
-        for (int J = 0; J < nc; J++) rc[J] = tau_rhs_at(ul, 0, rf, 0, J, n, op_lam(p));
+        for (int J = 0; J < nc; J++) rc[J] = tau_rhs_at(ul, 0, rf, 0, J, n, op_lam(p), st->a[l], st->a[l - 1]);
         return;
     }
     int w = p->seg_w[l];
@@ -349,11 +378,11 @@ static void presmooth_and_restrict(or_state *st, int l) {
         int e0, e1, lo, hi;
         extended_patch(s, w, p->seg_b[l], n, &e0, &e1, &lo, &hi);
         memcpy(st->patch, ul + lo, sizeof(double) * (size_t)(hi - lo));
-        patch_sweeps(p->smoother, st->patch, lo, rf, 0, n, e0, e1, p->nu1, NULL, op_lam(p));
+        patch_sweeps(p->smoother, st->patch, lo, rf, 0, n, e0, e1, p->nu1, NULL, op_lam(p), st->a[l]);
         memcpy(st->tmp + s, st->patch + (s - lo), sizeof(double) * (size_t)w);
         for (int J = s / 2; J < (s + w) / 2; J++) {
             uc[J] = restrict_at(st->patch, lo, J);
-            rc[J] = tau_rhs_at(st->patch, lo, rf, 0, J, n, op_lam(p));
+            rc[J] = tau_rhs_at(st->patch, lo, rf, 0, J, n, op_lam(p), st->a[l], st->a[l - 1]);
         }
     }
     memcpy(ul, st->tmp, sizeof(double) * (size_t)n);
@@ -385,22 +414,27 @@ static void postsmooth_update(or_state *st, int l) {
 static int vcycle(or_state *st, int top) {
     const or_params *p = st->p;
     for (int l = top; l > p->M0; l--) presmooth_and_restrict(st, l);
-    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0], st->a[p->M0]);
     if (rc) return rc;
     for (int l = p->M0 + 1; l <= top; l++) postsmooth_update(st, l);
     return OR_OK;
 }
 
 static void free_state(or_state *st) {
-    for (int l = 0; l <= OR_MAXLEV; l++) { free(st->u[l]); free(st->rhs[l]); }
+    for (int l = 0; l <= OR_MAXLEV; l++) { free(st->u[l]); free(st->rhs[l]); free(st->a[l]); }
     free(st->tmp); free(st->tmp2); free(st->patch);
 }
 
 static int check_params(const or_params *p) {
     if (p->M0 < 2 || p->M < p->M0 || p->M > 28) return OR_EINVAL;
     if (p->nRS < 0 || p->nRS > p->M - p->M0) return OR_EINVAL;
-    if (p->op != 0 && p->op != 1) return OR_EINVAL;
+    if (p->op != 0 && p->op != 1 && p->op != 2) return OR_EINVAL;
     if (p->op == 1 && !(p->lam >= 0.0 && p->lam < INFINITY)) return OR_EINVAL;
+    if (p->op == 2) {
+        if (!p->coef || p->coef_level < p->M || p->coef_level > 28) return OR_EINVAL;
+        for (long long j = 0; j <= (1LL << p->coef_level); j++)
+            if (!(p->coef[j] > 0.0 && p->coef[j] < INFINITY)) return OR_EINVAL;
+    }
     if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16) return OR_EINVAL;
     if (p->smoother < 0 || p->smoother > 1 || p->tau_src < 0 || p->tau_src > 1) return OR_EINVAL;
     for (int l = p->M0 + 1; l <= p->M; l++) {
@@ -425,7 +459,8 @@ static int alloc_state(or_state *st, const or_params *p) {
     for (int l = p->M0; l <= p->M; l++) {
         st->u[l] = (double *)calloc((size_t)1 << l, sizeof(double));
         st->rhs[l] = (double *)calloc((size_t)1 << l, sizeof(double));
-        if (!st->u[l] || !st->rhs[l]) { free_state(st); return OR_ENOMEM; }
+        st->a[l] = level_coef(p, l);
+        if (!st->u[l] || !st->rhs[l] || (p->op == 2 && !st->a[l])) { free_state(st); return OR_ENOMEM; }
     }
     st->tmp = (double *)calloc((size_t)1 << p->M, sizeof(double));
     st->tmp2 = (double *)calloc((size_t)1 << p->M, sizeof(double));
@@ -447,7 +482,7 @@ static void rhs_hierarchy(or_state *st, int top, const double *f_top) {
  * the FMG interpolation Pi followed by one V-cycle. */
 static int fmg_up_to(or_state *st, int top) {
     const or_params *p = st->p;
-    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0]);
+    int rc = coarsest_solve(p, 1 << p->M0, st->rhs[p->M0], st->u[p->M0], st->a[p->M0]);
     for (int k = p->M0; k < top && !rc; k++) {
         int nc = 1 << k;
         for (int i = 0; i < 2 * nc; i++) st->u[k + 1][i] = prolong_fmg_at(st->u[k], i, nc);
@@ -461,7 +496,7 @@ static int fmg_up_to(or_state *st, int top) {
 /* ------------------------------------------------------------------ */
 
 int or_apply_L(int n, const double *u, double *out) {
-    for (int i = 0; i < n; i++) out[i] = Lu_at(u, 0, i, n);
+    for (int i = 0; i < n; i++) out[i] = Lu_at(u, 0, i, n, NULL);
     return OR_OK;
 }
 int or_restrict(int nc, const double *uf, double *uc) {
@@ -481,21 +516,35 @@ int or_thomas(int n, const double *rhs, double *u) { return thomas(n, rhs, u); }
 
 /* tau-corrected coarse rhs from an assembled fine vector, every coarse cell. */
 int or_tau_rhs(int nf, const double *ubar, const double *rhs_f, double *rhs_c) {
-    for (int J = 0; J < nf / 2; J++) rhs_c[J] = tau_rhs_at(ubar, 0, rhs_f, 0, J, nf, 0.0);
+    for (int J = 0; J < nf / 2; J++) rhs_c[J] = tau_rhs_at(ubar, 0, rhs_f, 0, J, nf, 0.0, NULL, NULL);
     return OR_OK;
 }
 
 /* The nonlinear operator N(u) = L u + lam e^u on one level of n cells. */
 int or_apply_N(int n, double lam, const double *u, double *out) {
-    for (int i = 0; i < n; i++) out[i] = Nu_at(u, 0, i, n, lam);
+    for (int i = 0; i < n; i++) out[i] = Nu_at(u, 0, i, n, lam, NULL);
+    return OR_OK;
+}
+
+/* The variable-coefficient operator -(a u')' on one level of n cells with the
+ * face coefficients a[0..n]. */
+int or_apply_La(int n, const double *a, const double *u, double *out) {
+    for (int i = 0; i < n; i++) out[i] = Lu_at(u, 0, i, n, a);
     return OR_OK;
 }
 
 /* The coarsest-level solve of p on n cells: rhs in, u = starting iterate in,
  * solution out. */
 int or_coarsest(const or_params *p, int n, const double *rhs, double *u) {
-    if (p->op != 0 && p->op != 1) return OR_EINVAL;
-    return coarsest_solve(p, n, rhs, u);
+    if (p->op != 0 && p->op != 1 && p->op != 2) return OR_EINVAL;
+    int l = 0;
+    while ((1 << l) < n) l++;
+    if ((1 << l) != n || (p->op == 2 && (!p->coef || p->coef_level < l))) return OR_EINVAL;
+    double *a = level_coef(p, l);
+    if (p->op == 2 && !a) return OR_ENOMEM;
+    int rc = coarsest_solve(p, n, rhs, u, a);
+    free(a);
+    return rc;
 }
 
 /* One application of the level smoother S (segmentation from p->seg_w[l]). */
@@ -507,9 +556,11 @@ int or_smooth(const or_params *p, int l, const double *u_in, const double *rhs,
     st.p = p;
     st.rhs[l] = (double *)rhs;
     st.patch = (double *)calloc((size_t)max_patch(p), sizeof(double));
-    if (!st.patch) return OR_ENOMEM;
+    st.a[l] = level_coef(p, l);
+    if (!st.patch || (p->op == 2 && !st.a[l])) { free(st.patch); free(st.a[l]); return OR_ENOMEM; }
     smooth_level(&st, l, u_in, u_out, nsweeps, uH);
     free(st.patch);
+    free(st.a[l]);
     return OR_OK;
 }
 
@@ -577,7 +628,8 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
     double *frhs = (double *)malloc(sizeof(double) * (size_t)cap);
     double *win = (double *)malloc(sizeof(double) * (size_t)wcap);
     double *uc_new = (double *)malloc(sizeof(double) * (size_t)nc);
-    if (!patch || !frhs || !win || !uc_new) { rc = OR_ENOMEM; goto done; }
+    double *aM = level_coef(p, M);
+    if (!patch || !frhs || !win || !uc_new || (p->op == 2 && !aM)) { rc = OR_ENOMEM; goto done; }
 
     /* right-hand sides of levels M-1 .. M0 (restriction of f), FMG to M-1 */
     for (int J = 0; J < nc; J++) uc_new[J] = restrict_at(f, 0, J);
@@ -596,13 +648,13 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
                 patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
                 frhs[i - lo] = f[i];
             }
-            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL, op_lam(p));
+            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL, op_lam(p), aM);
             memcpy(win + (win_hi - win_lo), patch + (s - lo), sizeof(double) * (size_t)w);
             win_hi += w;
             /* coarse cells whose fine stencil 2J-2 .. 2J+3 is now assembled */
             while (Jnext < nc && (2 * Jnext + 3 < win_hi || win_hi == n)) {
                 uc_new[Jnext] = restrict_at(win, win_lo, Jnext);
-                st.rhs[M - 1][Jnext] = tau_rhs_at(win, win_lo, f, 0, Jnext, n, op_lam(p));
+                st.rhs[M - 1][Jnext] = tau_rhs_at(win, win_lo, f, 0, Jnext, n, op_lam(p), aM, st.a[M - 1]);
                 Jnext++;
             }
             /* keep only the cells a pending coarse cell can still read */
@@ -626,11 +678,11 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
             patch[i - lo] = prolong_fmg_at(st.u[M - 1], i, nc);
             frhs[i - lo] = f[i];
         }
-        patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, st.u[M - 1], op_lam(p));
+        patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, st.u[M - 1], op_lam(p), aM);
         memcpy(u_out + s, patch + (s - lo), sizeof(double) * (size_t)w);
     }
 done:
-    free(patch); free(frhs); free(win); free(uc_new);
+    free(patch); free(frhs); free(win); free(uc_new); free(aM);
     free_state(&st);
     return rc;
 }

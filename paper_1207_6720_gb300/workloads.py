@@ -16,6 +16,9 @@ x_i = (i + 1/2)/N.
   2^m with m drawn uniformly; each problem a sine series with its own seed),
   generated on the device as one matrix product of the coefficients with the
   sampled sines.
+* ``varcoef_series``: -(a u')' = f with a = exp(g/2) at the faces,
+  g = amp * sum_{k=1..K} d_k cos(k pi x) (d_k ~ N(0,1)/k), the manufactured
+  u = sine series, f = -(a u')' = -(a' u' + a u'') at the centres.
 * ``bratu_series``: the nonlinear problem -u'' + lam e^u = f with the
   manufactured solution u = scale * sum c_k sin(k pi x) (default scale 1/2),
   f = -u'' + lam e^u sampled at the centres.
@@ -66,6 +69,35 @@ def sine_series_batch(M, seeds, nmodes, device):
     S = torch.sin(torch.pi * kt[:, None] * x[None, :])                 # (nmodes, 2^M)
     cf = torch.from_numpy(c * (k * np.pi) ** 2).to(device)             # (B, nmodes)
     return (cf @ S).reshape(-1).contiguous(), c
+
+
+def varcoef_series(M, nmodes, seed, amp=1.0, gmodes=8):
+    """(f, u_exact, log_a) for -(a u')' = f: log_a at the 2^M + 1 faces
+    x_j = j / 2^M, f and u_exact at the cell centres."""
+    n = 1 << M
+    rng = np.random.default_rng(seed + 7919)
+    d = amp * rng.standard_normal(gmodes) / np.arange(1, gmodes + 1)
+    c = sine_coefficients(nmodes, seed)
+    faces = np.arange(n + 1, dtype=np.float64) / n
+    x = centres(M)
+    log_a = np.zeros(n + 1)
+    g = np.zeros_like(x)
+    gp = np.zeros_like(x)
+    for k in range(1, gmodes + 1):
+        log_a += 0.5 * d[k - 1] * np.cos(k * np.pi * faces)
+        g += 0.5 * d[k - 1] * np.cos(k * np.pi * x)
+        gp -= 0.5 * d[k - 1] * k * np.pi * np.sin(k * np.pi * x)
+    a = np.exp(g)
+    ap = gp * a
+    u = np.zeros_like(x)
+    up = np.zeros_like(x)
+    upp = np.zeros_like(x)
+    for k in range(1, nmodes + 1):
+        u += c[k - 1] * np.sin(k * np.pi * x)
+        up += c[k - 1] * k * np.pi * np.cos(k * np.pi * x)
+        upp -= c[k - 1] * (k * np.pi) ** 2 * np.sin(k * np.pi * x)
+    f = -(ap * up + a * upp)
+    return f, u, log_a
 
 
 def bratu_series(M, nmodes, seed, lam, scale=0.5):
