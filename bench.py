@@ -25,6 +25,10 @@ own seed; one batched plan per size (segments of min(4096, N/4) cells, 8
 buffer cells), all sizes on their own streams at once; 64-bit fixed point.
 value = all problems' unknowns / time of one pass over all sizes.
 
+--workload varcoef: -(a u')' = f, a = exp(g/2) at the faces with g a seeded
+8-mode cosine series, N = 2^24 cells, 4096 segments of 4096 cells, V(1,1), FP64;
+u = sum_{k=1..16} c_k sin(k pi x) (seed 1).
+
 --workload bratu: the nonlinear -u'' + lam e^u = f (lam = 1) with the same
 discretisation and FAS cycles, N = 2^26 cells, 16384 segments of 4096 cells,
 V(2,1), FP64; u = 1/2 sum_{k=1..16} c_k sin(k pi x) (seed 1).
@@ -51,6 +55,8 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-grid unknowns/s per FMG-FAS-SR solve at discretization accuracy vs plain FP64"
 METRIC_BATCH = ("fine-grid unknowns/s over a batch of independent FMG-FAS-SR solves at "
                 "discretization accuracy vs plain FP64")
+METRIC_VARCOEF = ("fine-grid unknowns/s per FMG-FAS-SR solve of -(a u')'=f at discretization accuracy "
+                  "vs plain FP64")
 METRIC_BRATU = ("fine-grid unknowns/s per FMG-FAS-SR solve of -u''+lam e^u=f at discretization "
                 "accuracy vs plain FP64")
 UNIT = "unknowns/s"
@@ -65,6 +71,11 @@ FLOPS_PER_CELL = {"sr_post": 13.5, "sr_pre": 15.5, "level_down_fmg": 15.5,
 # Bratu, V(2,1): the nonlinear sweep adds 4 per cell (c e^u with the
 # exponential counted as one operation, the diagonal 2 + e, its reciprocal,
 # the residual term) and tau 5 (three exponentials, two combinations)
+# variable coefficient, V(1,1): every flux and diagonal weighted (sweep 5 + 3:
+# two products and the reciprocal of the diagonal; tau 3 more)
+FLOPS_PER_CELL_VARCOEF = {"sr_post": 6.5 + 1 * (2 + 8), "sr_pre": 6.5 + 8 + 0.5 + 6.5,
+                          "level_down_fmg": 6.5 + 8 + 0.5 + 6.5, "level_down": 8 + 0.5 + 6.5,
+                          "level_up": 2.0 + 8}
 FLOPS_PER_CELL_BRATU = {"sr_post": 6.5 + 1 * (2 + 9), "sr_pre": 6.5 + 2 * 9 + 0.5 + 6,
                         "level_down_fmg": 6.5 + 2 * 9 + 0.5 + 6, "level_down": 2 * 9 + 0.5 + 6,
                         "level_up": 2.0 + 1 * 9}
@@ -78,7 +89,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["srfmg", "reference"], default="srfmg")
-    ap.add_argument("--workload", choices=["poisson", "bratu", "batch"], default="poisson")
+    ap.add_argument("--workload", choices=["poisson", "bratu", "varcoef", "batch"], default="poisson")
     ap.add_argument("--nprob", type=int, default=8192, help="batch: number of problems")
     ap.add_argument("--lam", type=float, default=1.0, help="Bratu: lam of -u'' + lam e^u = f")
     ap.add_argument("--log2n", type=int, default=None, help="default 24 (poisson), 26 (bratu)")
@@ -93,12 +104,22 @@ def parse_args():
     a = ap.parse_args()
     if a.log2n is None:
         a.log2n = 26 if a.workload == "bratu" else 24
-    if a.workload == "bratu":
+    if a.workload in ("bratu", "varcoef"):
         a.precision = "fp64"
     return a
 
 
 def workload_config(a):
+    if getattr(a, "workload", "poisson") == "varcoef":
+        return {
+            "workload": f"1D -(a u')'=f, a=exp(g/2) (8-mode cosine series g, seed 1), N=2^{a.log2n}, FMG-FAS "
+                        f"V(1,1) lexicographic GS, 1 SR level of {(1 << a.log2n) // a.segment_width} segments x "
+                        f"{a.segment_width} cells, buffer {a.buffer_width}, FP64",
+            "precision": "fp64", "N": 1 << a.log2n, "segment_width": a.segment_width,
+            "buffer_width": a.buffer_width, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
+            "modes": 16, "seed": 1,
+            "l2": "inputs larger than L2 (f and u 128 MiB each, log a 128 MiB, the stored levels)",
+        }
     if getattr(a, "workload", "poisson") == "batch":
         return {
             "workload": f"{a.nprob} independent 1D -u''=f problems, N=2^m with m ~ U{{10..20}} (seed 11), "
@@ -283,6 +304,9 @@ def run_reference(a):
     if a.workload == "bratu":
         f, _, _ = workloads.bratu_series(Ms, 16, seed=1, lam=a.lam)
         p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
+    elif a.workload == "varcoef":
+        f, _, log_a = workloads.varcoef_series(Ms, 16, seed=1)
+        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, op="varcoef", coef=np.exp(log_a))
     else:
         f, _, _ = workloads.sine_series(Ms, 32, seed=1)
         p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
@@ -294,7 +318,8 @@ def run_reference(a):
     dt = time.perf_counter() - t0
     value = a.steps * (1 << Ms) / dt
     sample = f"one serial oracle solve of the same workload family at N=2^{Ms} per step"
-    line = {"metric": METRIC_BRATU if a.workload == "bratu" else METRIC, "value": value, "unit": UNIT,
+    line = {"metric": {"bratu": METRIC_BRATU, "varcoef": METRIC_VARCOEF}.get(a.workload, METRIC),
+            "value": value, "unit": UNIT,
             "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -483,7 +508,8 @@ def run_gpu(a):
 
 
 def run_gpu_bratu(a):
-    """The Bratu workload: SR solve vs the plain stored solve, FP64."""
+    """The Bratu or variable-coefficient workload: SR solve vs the plain stored
+    solve, FP64."""
     import torch
     from paper_1207_6720_gb300 import srfmg, workloads
 
@@ -493,11 +519,21 @@ def run_gpu_bratu(a):
     stream = torch.cuda.current_stream()
     M, W, b = a.log2n, a.segment_width, a.buffer_width
     N = 1 << M
-    f, u_exact, _ = workloads.bratu_series(M, 16, seed=1, lam=a.lam)
+    vcoef = a.workload == "varcoef"
+    if vcoef:
+        f, u_exact, log_a = workloads.varcoef_series(M, 16, seed=1)
+        kw = dict(op=srfmg.VARCOEF, nu1=1, nu2=1)
+        metric, flops_table = METRIC_VARCOEF, FLOPS_PER_CELL_VARCOEF
+    else:
+        f, u_exact, _ = workloads.bratu_series(M, 16, seed=1, lam=a.lam)
+        kw = dict(op=srfmg.BRATU, lambda_=a.lam, nu1=2, nu2=1)
+        metric, flops_table = METRIC_BRATU, FLOPS_PER_CELL_BRATU
     fd = torch.from_numpy(f).to(dev)
     ud = torch.empty_like(fd)
-    kw = dict(op=srfmg.BRATU, lambda_=a.lam, nu1=2, nu2=1)
     solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, **kw)
+    if vcoef:
+        log_a_d = torch.from_numpy(log_a).to(dev)
+        solver.set_coefficient(log_a_d, stream=stream)
     info = solver.info()
     sampler = ClockSampler(dev)
     sampler.start()
@@ -506,13 +542,15 @@ def run_gpu_bratu(a):
     ms = dist.max(ms)
     value = dist.world * N / (ms * 1e-3)
     u = ud.cpu().numpy()
-    line = {"metric": METRIC_BRATU, "value": value, "unit": UNIT, "n_gpus": dist.world,
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(a), "gpu_launches": info.kernels_per_solve * a.steps,
             "clocks": clocks}
     if not a.only_solve:
         plain = srfmg.Solver(M, device=dev, n_sr_levels=0, **kw)
+        if vcoef:
+            plain.set_coefficient(log_a_d, stream=stream)
         ms_plain = dist.max(time_solves(plain, fd, ud, max(5, a.steps // 4), a.warmup, dist, stream))
         plain.close()
         fh = torch.from_numpy(f).pin_memory()
@@ -530,7 +568,7 @@ def run_gpu_bratu(a):
         top_name, top_ms = max(prof, key=lambda x: x[1])
         kind, lvl = top_name.split(" L")
         cells = 1 << int(lvl)
-        flops = FLOPS_PER_CELL_BRATU.get(kind, 0.0) * cells
+        flops = flops_table.get(kind, 0.0) * cells
         achieved_tf = flops / (top_ms * 1e-3) / 1e12
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -554,7 +592,10 @@ def run_gpu_bratu(a):
     acc = {"err_max_vs_exact": err, "rel_err_max_vs_exact": err / float(np.max(np.abs(u_exact)))}
     if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and not a.only_solve:
         import oracle
-        p = oracle.sr_params(M, W, b, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
+        if vcoef:
+            p = oracle.sr_params(M, W, b, nRS=1, op="varcoef", coef=np.exp(log_a))
+        else:
+            p = oracle.sr_params(M, W, b, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
         t0 = time.perf_counter()
         ref = oracle.fmg_v(p, f)
         dt = time.perf_counter() - t0
@@ -720,7 +761,7 @@ def main():
         run_reference(a)
     elif a.workload == "batch":
         run_gpu_batch(a)
-    elif a.workload == "bratu":
+    elif a.workload in ("bratu", "varcoef"):
         run_gpu_bratu(a)
     else:
         run_gpu(a)

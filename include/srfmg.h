@@ -58,9 +58,12 @@ typedef enum {
 /* Operators.  SRFMG_OP_BRATU is the nonlinear -u'' + lambda e^u = f (lambda >= 0)
  * with the same discretisation, solved by the same FAS cycles (Sec. 2.2,
  * Eqs. 1-2: the coarse equation of a nonlinear operator; Fig. 1 with the
- * nonlinear smoother: pointwise Newton Gauss-Seidel); FP64 only.  (The value 1
- * is kept for a variable-coefficient operator.) */
-typedef enum { SRFMG_OP_LAPLACE = 0, SRFMG_OP_BRATU = 2 } srfmg_op;
+ * nonlinear smoother: pointwise Newton Gauss-Seidel).  SRFMG_OP_VARCOEF is
+ * -(a u')' = f with a > 0 at the cell faces (fluxes a_{i+1/2} (u_{i+1} - u_i),
+ * a wall face counted twice by the odd ghost; coarse faces take the
+ * coefficient of the coinciding fine face), set by srfmg_set_coefficient.
+ * Both run in FP64 only. */
+typedef enum { SRFMG_OP_LAPLACE = 0, SRFMG_OP_VARCOEF = 1, SRFMG_OP_BRATU = 2 } srfmg_op;
 typedef enum { SRFMG_FP64 = 0, SRFMG_MIXED = 1 } srfmg_precision;
 typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
 
@@ -135,9 +138,21 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
  * dL_du: device pointer, N doubles (the gradient of L with respect to u at the
  * cell centres); dL_df: device pointer, N doubles, receives dL/df.  Pointers,
  * alignment, overlap, asynchrony and errors as in srfmg_solve (it is the same
- * call: it has its own captured graph for its pointer pair).  Returns
- * SRFMG_EUNSUPPORTED for an operator without a symmetric discretisation. */
+ * call: it has its own captured graph for its pointer pair).  SRFMG_OP_VARCOEF
+ * is symmetric as well (dL/df only: the gradient with respect to the
+ * coefficient is not provided).  Returns SRFMG_EUNSUPPORTED for
+ * SRFMG_OP_BRATU. */
 srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream);
+
+/* SRFMG_OP_VARCOEF: set the coefficient for the following solves.  log_a:
+ * device pointer, 2^M + 1 doubles per problem (B * (2^M + 1) for a batch), the
+ * natural logarithm of a at the faces x_j = j / N, j = 0..N.  Fills the plan's
+ * face coefficients of every level (a = exp(log_a); coarse faces coincide
+ * with fine faces and take their value) with one kernel on `stream`,
+ * asynchronously; log_a may be freed once the stream has passed it.  Until
+ * the first call a = 1.  Errors: SRFMG_EINVAL for a NULL handle or pointer or
+ * a plan of another operator. */
+srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *stream);
 
 /* Plan information (workspace size, launches per solve, ...). */
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info);

@@ -45,8 +45,8 @@ struct Op {
     int nseg;
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
-    // Bratu operator (FP64 kernels instantiated with the nonlinear sweep and tau)
-    bool nl;
+    // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu)
+    int opk;
     // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
     bool fixed;
     fx::RhsArgs frhs;
@@ -69,6 +69,7 @@ struct srfmg_plan {
     double *glev[32] = {};
     double *seam = nullptr;
     double *Ainv = nullptr;
+    double *coef[32] = {};         // variable coefficient: face coefficients of levels M0..M
     fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
     bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
@@ -108,8 +109,9 @@ std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
     for (int i = 0; i < 3; ++i) if (p->reserved[i]) return "reserved fields must be zero";
     if (p->batch < 0 || p->batch > 65535) return "batch must be in [0, 65535] (0 means 1)";
-    if (p->op != SRFMG_OP_LAPLACE && p->op != SRFMG_OP_BRATU) return "op must be SRFMG_OP_LAPLACE or SRFMG_OP_BRATU";
-    if (p->op == SRFMG_OP_LAPLACE && p->lambda != 0.0) return "lambda must be 0 for SRFMG_OP_LAPLACE";
+    if (p->op != SRFMG_OP_LAPLACE && p->op != SRFMG_OP_BRATU && p->op != SRFMG_OP_VARCOEF)
+        return "op must be SRFMG_OP_LAPLACE, SRFMG_OP_VARCOEF or SRFMG_OP_BRATU";
+    if (p->op != SRFMG_OP_BRATU && p->lambda != 0.0) return "lambda must be 0 unless op is SRFMG_OP_BRATU";
     if (p->op == SRFMG_OP_BRATU && !(p->lambda >= 0.0 && p->lambda <= 1e300))
         return "lambda must be finite and >= 0";
     if (p->precision != SRFMG_FP64 && p->precision != SRFMG_MIXED) return "unknown precision";
@@ -221,6 +223,7 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     o.lev.uc_out = uc_out;
     o.lev.gc_out = gc_out;
     o.lev.lam = op_lambda(h);
+    o.lev.coef = h->coef[l];
     if (l == h->M) {               // finest level without SR: rhs from f
         o.lev.g = nullptr;
         o.lev_g = TAG_F;
@@ -249,6 +252,7 @@ Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, doub
     o.seg.gc_out = gc_out;
     o.seg.seam = h->seam;
     o.seg.lam = op_lambda(h);
+    o.seg.coef = h->coef[h->M];
     o.seg_f = TAG_F;
     if (kind == OP_SR_POST) o.seg_u = TAG_U;
     o.nseg = (int)(h->n / h->W);
@@ -281,6 +285,7 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
     o.tail.u_out = u_out;
     o.tail.Ainv = h->Ainv;
     o.tail.lam = op_lambda(h);
+    for (int l = 0; l < 32; ++l) o.tail.coef[l] = h->coef[l];
     if (g_from_f) o.tail_g = TAG_F;
     if (out_is_u) o.tail_out = TAG_U;
     o.grid = dim3(1);
@@ -428,7 +433,12 @@ void build_schedule_ops(srfmg_plan *h) {
 void build_schedule(srfmg_plan *h) {
     build_schedule_ops(h);
     for (Op &o : h->ops) {
-        o.nl = (h->p.op == SRFMG_OP_BRATU);
+        o.opk = (h->p.op == SRFMG_OP_BRATU) ? kOpBratu : (h->p.op == SRFMG_OP_VARCOEF) ? kOpVarcoef : kOpLaplace;
+        // the variable-coefficient kernels stage their face coefficients
+        if (o.opk == kOpVarcoef && (o.kind == OP_DOWN || o.kind == OP_DOWN_PI || o.kind == OP_UP ||
+                                    o.kind == OP_SR_PRE || o.kind == OP_SR_POST))
+            o.smem += (size_t)((o.kind == OP_SR_PRE || o.kind == OP_SR_POST) ? o.seg.maxlen : o.lev.maxlen) *
+                      sizeof(double) + 2 * sizeof(double);
         o.grid.y = (unsigned)h->batch;           // one grid row per problem of the batch
     }
     if (!h->fixed) return;
@@ -496,7 +506,7 @@ cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t 
 }
 
 // FP64 kernels of one op (NL: the Bratu instantiation).
-template <bool NL>
+template <int NL>
 cudaError_t launch_fp64(const Op &o, cudaStream_t s, bool pdl) {
     cudaError_t e = cudaSuccess;
     switch (o.kind) {
@@ -524,8 +534,9 @@ cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s, boo
     if (o.tail_out == TAG_U) o.tail.u_out = u;
     if (o.seg_f == TAG_F) o.seg.f = f;
     if (o.seg_u == TAG_U) o.seg.u_out = u;
-    if (o.nl) return launch_fp64<true>(o, s, pdl);
-    return launch_fp64<false>(o, s, pdl);
+    if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
+    if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
+    return launch_fp64<kOpLaplace>(o, s, pdl);
 }
 
 const char *kind_name(OpKind k) {
@@ -541,6 +552,20 @@ const char *kind_name(OpKind k) {
     case OP_SCALE: return "fixed_scale";
     }
     return "?";
+}
+
+// Face coefficients of every level from log a (NULL: a = 1), on stream s.
+cudaError_t launch_coef(srfmg_plan *h, const double *log_a, cudaStream_t s) {
+    CoefArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.log_a = log_a;
+    a.M = h->M;
+    a.M0 = h->M0;
+    for (int l = 0; l < 32; ++l) a.out[l] = h->coef[l];
+    const size_t nf = ((size_t)1 << h->M) + 1;
+    const unsigned blocks = (unsigned)std::min<size_t>(4 * 152, (nf + 255) / 256);
+    coef_hierarchy_kernel<<<dim3(blocks, (unsigned)h->batch), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // All launches of one solve; every launch after the first overlaps its set-up
@@ -565,12 +590,11 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
     size_t need = 0;
     for (const Op &o : h->ops) need = std::max(need, o.smem);
     if (need > (size_t)optin) return fail(h, SRFMG_EUNSUPPORTED, "shared memory need exceeds the device limit");
-    const void *fns[] = {(const void *)level_down_kernel<true, false>, (const void *)level_down_kernel<false, false>,
-                         (const void *)level_up_kernel<false>, (const void *)sr_pre_kernel<false>,
-                         (const void *)sr_post_kernel<false>, (const void *)tail_kernel<false>,
-                         (const void *)level_down_kernel<true, true>, (const void *)level_down_kernel<false, true>,
-                         (const void *)level_up_kernel<true>, (const void *)sr_pre_kernel<true>,
-                         (const void *)sr_post_kernel<true>, (const void *)tail_kernel<true>,
+#define SRFMG_FP64_KERNELS(OPK)                                                                            \
+    (const void *)level_down_kernel<true, OPK>, (const void *)level_down_kernel<false, OPK>,                   \
+        (const void *)level_up_kernel<OPK>, (const void *)sr_pre_kernel<OPK>, (const void *)sr_post_kernel<OPK>, \
+        (const void *)tail_kernel<OPK>
+    const void *fns[] = {SRFMG_FP64_KERNELS(kOpLaplace), SRFMG_FP64_KERNELS(kOpVarcoef), SRFMG_FP64_KERNELS(kOpBratu),
                          (const void *)rhs_hierarchy_kernel,
                          (const void *)fx::level_down_kernel<true>, (const void *)fx::level_down_kernel<false>,
                          (const void *)fx::level_up_kernel, (const void *)fx::sr_pre_kernel,
@@ -618,8 +642,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     *out = nullptr;
     std::string msg = check_params(p);
     if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
-    if (p->op == SRFMG_OP_BRATU && p->precision != SRFMG_FP64)
-        return fail(nullptr, SRFMG_EUNSUPPORTED, "SRFMG_OP_BRATU runs in FP64 only");
+    if (p->op != SRFMG_OP_LAPLACE && p->precision != SRFMG_FP64)
+        return fail(nullptr, SRFMG_EUNSUPPORTED, "SRFMG_OP_BRATU and SRFMG_OP_VARCOEF run in FP64 only");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -664,6 +688,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         st = alloc_dev(h, &sc, 2 * B);
         h->scale = (fx::Scale *)sc;
     }
+    if (p->op == SRFMG_OP_VARCOEF)
+        for (int l = h->M0; l <= h->M && st == SRFMG_OK; ++l) st = alloc_dev(h, &h->coef[l], B * (((size_t)1 << l) + 1));
     const int n0 = 1 << h->M0;
     if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
     if (st == SRFMG_OK) {
@@ -680,6 +706,11 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     if (st == SRFMG_OK) {
         e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamCreate");
+    }
+    if (st == SRFMG_OK && p->op == SRFMG_OP_VARCOEF) {          // a = 1 until srfmg_set_coefficient
+        e = launch_coef(h, nullptr, h->cap_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "coefficient initialisation");
     }
     if (st != SRFMG_OK) {
         g_create_error = h->err;
@@ -759,8 +790,18 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
 // the same FMG(-SR) solve.
 srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream) {
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
-    if (h->p.op != SRFMG_OP_LAPLACE) return fail(h, SRFMG_EUNSUPPORTED, "adjoint of this operator");
+    // -(a u')' is symmetric as well; the Bratu operator is nonlinear
+    if (h->p.op == SRFMG_OP_BRATU) return fail(h, SRFMG_EUNSUPPORTED, "adjoint of this operator");
     return srfmg_solve(h, dL_du, dL_df, stream);
+}
+
+srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (h->p.op != SRFMG_OP_VARCOEF) return fail(h, SRFMG_EINVAL, "the plan's operator has no coefficient");
+    if (!log_a || ((uintptr_t)log_a & 7)) return fail(h, SRFMG_EINVAL, "log_a must be an 8-byte aligned device pointer");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = launch_coef(h, log_a, (cudaStream_t)stream);
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "coefficient kernel");
 }
 
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {
@@ -977,7 +1018,7 @@ extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n
             }
             int optin = 0;
             if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-                cudaFuncSetAttribute(tail_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaFuncSetAttribute(tail_kernel<kOpLaplace>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
                     cudaSuccess) {
                 cudaGetLastError();
                 return SRFMG_ECUDA;
@@ -1012,6 +1053,6 @@ extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n
     a.Ainv = ainv;
     a.lam = 0.0;
     const size_t smem = tail_smem_doubles(log2_n_coarsest, log2_n) * sizeof(double);
-    tail_kernel<false><<<1, kTailThreads, smem, (cudaStream_t)stream>>>(a);
+    tail_kernel<kOpLaplace><<<1, kTailThreads, smem, (cudaStream_t)stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? SRFMG_OK : SRFMG_ECUDA;
 }

@@ -26,6 +26,10 @@ constexpr int kTrunc = 72;
 // block has many threads and each recurrence is a few dependent operations.
 constexpr int kChunk = 9;
 
+// Operators of the FP64 kernels (template parameter OP): -u'' = f, the
+// variable-coefficient -(a u')' = f, and the Bratu problem -u'' + lam e^u = f.
+constexpr int kOpLaplace = 0, kOpVarcoef = 1, kOpBratu = 2;
+
 // Largest block of the level and segment kernels: one thread per chunk of at
 // most 4224 + 2 cells (a segment) or 2944 cells (a tile).  Segment kernels
 // are compiled for two such blocks per SM (at most 64 registers a thread).
@@ -369,12 +373,119 @@ __device__ __forceinline__ void lex_sweep_nl(double *__restrict__ u, const doubl
     else lex_sweep_nl_dir<C, false>(u, g, cl, base, lo, hi, n, X, Y);
 }
 
-// One smoothing sweep of either operator: NL selects the Bratu sweep (cl =
-// lam h^2 of the level; Y: a second per-thread array).
-template <bool NL, bool PRELOAD = false>
-__device__ __forceinline__ void sweep_op(double *__restrict__ u, const double *__restrict__ g, double cl, int base,
-                                         int lo, int hi, int n, bool asc, double *X, double *Y) {
-    if (NL) lex_sweep_nl<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
+// ---------------------------------------------------------------------------
+// Variable-coefficient sweep for -(a u')' = f (Gauss-Seidel, omega = 1), in
+// place, same layout and chunking as lex_sweep.  With the face coefficients
+// a_near (between the previous cell in sweep order and this one) and a_far
+// (between this cell and the next), the update of a cell is
+//   delta_q = (r_q + a_near delta_{q-1}) / (a_near + a_far),
+//   r_q = g_q - (a_near (u_q - u_{q-1}) - a_far (u_{q+1} - u_q))
+// (a wall face counts twice: odd ghost), an affine recurrence evaluated as in
+// lex_sweep_nl with the multiplier a_near / (a_near + a_far).  For a
+// coefficient that varies slowly between faces the multiplier stays near 1/2;
+// the carry sum covers 11 chunks (99 cells), enough for multipliers up to 0.6
+// (0.6^99 < 2^-72).  a[f - abase] is the coefficient of face f (faces f = 0..n,
+// face f between cells f-1 and f); X and Y hold one double per thread.
+// ---------------------------------------------------------------------------
+constexpr int kTruncVc = 96;
+
+template <int C, bool ASC>
+__device__ __noinline__ void lex_sweep_vc_dir(double *__restrict__ u, const double *__restrict__ g,
+                                              const double *__restrict__ a, int abase, int base, int lo, int hi,
+                                              int n, double *X, double *Y) {
+    constexpr int s = ASC ? 1 : -1;
+    const int t = threadIdx.x;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);
+    const bool wall1 = (q0 + k1 == n);
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int a0 = ASC ? -base : n - 1 - base;
+    // near face of sweep position q: face q ascending, face n - q descending;
+    // the faces a chunk reads lie in [lo, hi] (clamped for the unused ones)
+    const int fb0 = ASC ? 0 : n, fmin = lo, fmax = hi;
+    double rr[C], aa[C];
+    double p = 0.0, A = 1.0, r_end = 0.0, b_end = 0.0, al_end = 0.0;
+    if (active) {
+        double w[C + 2], an[C + 1];
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+#pragma unroll
+        for (int j = 0; j <= C; ++j) an[j] = a[min(max(fb0 + s * (q0 + j), fmin), fmax) - abase];
+        if (wall0) {
+            const double aw = an[0], af = an[1];
+            const double D = scale2(aw, 1) + af;
+            p = ((g[a0] - (aw * scale2(w[1], 1) - af * (w[2] - w[1])))) / D;
+            A = 0.0;
+        }
+        if (wall1) {
+            const int kw = k1 - 1;                      // the wall cell's place in the chunk
+            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+            const double anr = a[fb0 + s * (n - 1) - abase], aw = a[fb0 + s * n - abase];
+            const double D = anr + scale2(aw, 1);
+            r_end = g[a0 + s * (n - 1)] - (anr * (ue - um) - aw * (-scale2(ue, 1)));
+            b_end = 1.0 / D;
+            al_end = anr * b_end;
+            (void)kw;
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            const double anr = an[k], afr = an[k + 1];
+            const double b = 1.0 / (anr + afr);
+            const double r = gv - (anr * (w[k + 1] - w[k]) - afr * (w[k + 2] - w[k + 1]));
+            const bool in = k >= ka && k < kb;
+            p = in ? fma(anr * b, p, r * b) : p;
+            A = in ? (anr * b) * A : A;
+            rr[k] = p;
+            aa[k] = A;
+        }
+        X[t] = p;
+        Y[t] = A;
+    }
+    __syncthreads();
+    if (active) {
+        constexpr int J = (kTruncVc + C - 1) / C - 1;
+        double cin = 0.0;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const double x = X[max(idx, 0)], y = Y[max(idx, 0)];
+            cin = idx >= 0 ? fma(y, cin, x) : 0.0;
+        }
+        double dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                dl = fma(aa[k], cin, rr[k]);
+                u[a0 + s * (q0 + k)] += dl;
+            }
+        if (wall1) u[a0 + s * (n - 1)] += fma(al_end, dl, b_end * r_end);
+    }
+    __syncthreads();
+}
+
+template <int C>
+__device__ __forceinline__ void lex_sweep_vc(double *__restrict__ u, const double *__restrict__ g,
+                                             const double *__restrict__ a, int abase, int base, int lo, int hi, int n,
+                                             bool asc, double *X, double *Y) {
+    if (asc) lex_sweep_vc_dir<C, true>(u, g, a, abase, base, lo, hi, n, X, Y);
+    else lex_sweep_vc_dir<C, false>(u, g, a, abase, base, lo, hi, n, X, Y);
+}
+
+// One smoothing sweep of the operator OP (cl = lam h^2 of the level for the
+// Bratu problem; a, abase: the face coefficients for the variable-coefficient
+// problem; Y: a second per-thread array).
+template <int OP, bool PRELOAD = false>
+__device__ __forceinline__ void sweep_op(double *__restrict__ u, const double *__restrict__ g, double cl,
+                                         const double *a, int abase, int base, int lo, int hi, int n, bool asc,
+                                         double *X, double *Y) {
+    if (OP == kOpBratu) lex_sweep_nl<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
+    else if (OP == kOpVarcoef) lex_sweep_vc<kChunk>(u, g, a, abase, base, lo, hi, n, asc, X, Y);
     else lex_sweep<kChunk, PRELOAD>(u, g, base, lo, hi, n, asc, X);
 }
 
@@ -393,6 +504,37 @@ __device__ __forceinline__ double tau_rhs(double g0, double g1, double um2, doub
     double Fr = (J == nc - 1) ? -scale2(u1, 1) : u2 - u1;
     double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
     return scale2(g0 + g1, 1) + tau;
+}
+
+// Scaled tau-corrected coarse rhs for -(a u')' = f: as tau_rhs with every flux
+// weighted by its face coefficient; the coarse faces J and J+1 are the fine
+// faces 2J and 2J+2, whose coefficients a2J and a2J2 they take (injection).
+__device__ __forceinline__ double tau_rhs_vc(double g0, double g1, double um2, double um1, double u0, double u1,
+                                             double u2, double u3, int J, int nc, double a2J, double a2J2) {
+    double hJ = scale2(u0 + u1, -1);
+    double Gl = a2J * ((J == 0) ? scale2(hJ, 1) : hJ - scale2(um2 + um1, -1));
+    double Gr = a2J2 * ((J == nc - 1) ? -scale2(hJ, 1) : scale2(u2 + u3, -1) - hJ);
+    double Fl = a2J * ((J == 0) ? scale2(u0, 1) : u0 - um1);
+    double Fr = a2J2 * ((J == nc - 1) ? -scale2(u1, 1) : u2 - u1);
+    double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
+    return scale2(g0 + g1, 1) + tau;
+}
+
+// Coarsest level of -(a u')' = f: Thomas on h^2 L_a u = g (row i: -a_i u_{i-1}
+// + (a_i + a_{i+1}) u_i - a_{i+1} u_{i+1}, a wall face counted twice), with
+// the level's face coefficients a[0..n].  One thread; cp, dp hold n values.
+__device__ void coarsest_thomas_vc(double *u, const double *g, int n, const double *a, double *cp, double *dp) {
+    for (int i = 0; i < n; ++i) {
+        const double al = (i == 0) ? scale2(a[0], 1) : a[i];
+        const double ar = (i == n - 1) ? scale2(a[n], 1) : a[i + 1];
+        const double diag = al + ar;
+        const double lower = (i > 0) ? -a[i] : 0.0, upper = (i < n - 1) ? -a[i + 1] : 0.0;
+        const double denom = (i > 0) ? diag - lower * cp[i - 1] : diag;
+        cp[i] = upper / denom;
+        dp[i] = ((i > 0) ? g[i] - lower * dp[i - 1] : g[i]) / denom;
+    }
+    u[n - 1] = dp[n - 1];
+    for (int i = n - 2; i >= 0; --i) u[i] = dp[i] - cp[i] * u[i + 1];
 }
 
 // The nonlinear part of the scaled tau rhs (Eqs. 1-2 with N = L + lam e^u):
@@ -446,6 +588,32 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Face coefficients of every level for -(a u')' = f from log a at the 2^M + 1
+// faces of the finest level (NULL: a = 1): a_l[j] = exp(log_a[j 2^(M-l)]), the
+// coarse faces taking the coefficient of the coinciding fine face.  out[l]
+// holds 2^l + 1 values per problem (problem blockIdx.y).
+// ---------------------------------------------------------------------------
+struct CoefArgs {
+    const double *log_a;
+    int M, M0;
+    double *out[32];
+};
+
+__global__ void coef_hierarchy_kernel(CoefArgs a) {
+    pdl_enter();
+    const long long nf = (1LL << a.M) + 1;
+    const double *la = batch_at(a.log_a, nf);
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf; j += (long long)gridDim.x * blockDim.x) {
+        const double v = la ? exp(la[j]) : 1.0;
+        for (int l = a.M; l >= a.M0; --l) {
+            const int sh = a.M - l;
+            if (j & ((1LL << sh) - 1)) break;
+            batch_at(a.out[l], (1LL << l) + 1)[j >> sh] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stored-level passes (global lexicographic smoothing).  A block owns the
 // tile [s, s+T) of level l and loads it with a halo of H cells per side; the
 // halo is wider than the Gauss-Seidel carry horizon, so the tile's values are
@@ -463,13 +631,15 @@ struct LevelArgs {
     double *uc_out;            // down pass: restricted solution on level l-1
     double *gc_out;            // down pass: tau-corrected g_{l-1}
     double lam;                // Bratu: lam of -u'' + lam e^u = f (0 otherwise)
+    const double *coef;        // variable coefficient: face coefficients of level l (2^l + 1)
 };
 
 // Shared-memory layout of one stored-level block (the host reserves
 // 2 maxlen + 2 maxc + maxch doubles; this path uses the first
 // 2 maxlen + maxc + maxch).
 struct LevelSmem {
-    double *u, *g, *c, *X, *Y;   // Y: second carry array of the nonlinear sweep
+    double *u, *g, *c, *X, *Y;   // Y: second carry array of the nonlinear sweeps
+    double *a;                // variable coefficient: faces [L0, L1] (the host adds maxlen words)
     int L0, L1, C0, C1;       // fine range [L0,L1), coarse range [C0,C1)
 };
 
@@ -485,6 +655,7 @@ __device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H,
     m.c = m.g + maxlen;
     m.X = m.c + maxc;
     m.Y = m.X + maxch;
+    m.a = m.c + 2 * maxc;     // past the whole X/Y region (maxc words)
     return m;
 }
 
@@ -492,18 +663,18 @@ __device__ __forceinline__ LevelSmem level_smem(double *sm, int s, int T, int H,
 // reversed after every sweep (appendix "symmetrize").  The swept range
 // shrinks by one cell per sweep on each side that is not a wall, so that
 // every sweep reads neighbours the previous one wrote.
-template <bool NL>
+template <int OP>
 __device__ void smooth_range(LevelSmem &m, int n, int nu, double cl) {
     int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
     int hi = (m.L1 == n) ? n : m.L1 - 1;
     for (int k = 0; k < nu; ++k) {
-        sweep_op<NL>(m.u, m.g, cl, m.L0, lo, hi, n, (k & 1) == 0, m.X, m.Y);
+        sweep_op<OP>(m.u, m.g, cl, m.a, m.L0, m.L0, lo, hi, n, (k & 1) == 0, m.X, m.Y);
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
 }
 
-template <bool FROM_PI, bool NL>
+template <bool FROM_PI, int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -512,6 +683,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     const double *u_src = batch_at(a.u_src, FROM_PI ? nc : n), *g = batch_at(a.g, n);
     double *u_out = batch_at(a.u_out, n), *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
+    if (OP == kOpVarcoef) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
     stage_range(m.g, g + m.L0, m.L1 - m.L0);
     if (FROM_PI) stage_coarse_async(m.c, u_src, m.C0, m.C1, nc);
     else stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
@@ -528,7 +700,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     }
     __syncthreads();
     const double cl = scale2(a.lam, -2 * a.l);       // lam h_l^2
-    smooth_range<NL>(m, n, a.nu, cl);
+    smooth_range<OP>(m, n, a.nu, cl);
     const double *u = m.u;
     // restriction of the solution and tau-corrected coarse rhs of the tile
     for (int J = (s >> 1) + threadIdx.x; J < ((s + a.tile) >> 1); J += blockDim.x) {
@@ -536,15 +708,18 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
-        double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-        if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+        double gc = (OP == kOpVarcoef)
+                        ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
+                                     m.a[i0 + 2])
+                        : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        if (OP == kOpBratu) gc += tau_nl(cl, u[i0], u[i0 + 1]);
         gc_out[J] = gc;
     }
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
 }
 
 // Up pass (Eq. 4): u_l += P (u_{l-1} - R u_l), then nu sweeps.
-template <bool NL>
+template <int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -553,6 +728,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     const double *u_src = batch_at(a.u_src, n), *g = batch_at(a.g, n), *uc_src = batch_at(a.uc_src, nc);
     double *u_out = batch_at(a.u_out, n);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
+    if (OP == kOpVarcoef) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
     stage_range(m.g, g + m.L0, m.L1 - m.L0);
     stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
     stage_coarse_async(m.c, uc_src, m.C0, m.C1, nc);
@@ -580,7 +756,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
         m.u[i - m.L0] += corr;
     }
     __syncthreads();
-    smooth_range<NL>(m, n, a.nu, scale2(a.lam, -2 * a.l));
+    smooth_range<OP>(m, n, a.nu, scale2(a.lam, -2 * a.l));
     const double *u = m.u;
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
 }
@@ -600,12 +776,14 @@ struct SegArgs {
     double *seam;              // pre-leg: 6 fine values per segment
     double *u_out;             // post-leg: the solution
     double lam;                // Bratu: lam (0 otherwise)
+    const double *coef;        // variable coefficient: face coefficients of level M (2^M + 1)
 };
 
 // (the host reserves 2 maxlen + 2 maxc + maxch doubles; this path uses the
 // first 2 maxlen + maxc + maxch)
 struct SegSmem {
     double *u, *g, *c, *X, *Y;
+    double *a;                 // variable coefficient: faces [lo, hi]
     int e0, e1, lo, hi, C0, C1;
 };
 
@@ -622,6 +800,7 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
     m.c = m.g + a.maxlen;
     m.X = m.c + a.maxc;
     m.Y = m.X + a.maxch;
+    m.a = m.c + 2 * a.maxc;
     return m;
 }
 
@@ -630,6 +809,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1;
     stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
     stage_range(m.g, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
+    if (a.coef) stage_range(m.a, batch_at(a.coef, a.n + 1) + m.lo, m.hi - m.lo + 1);
     stage_wait();
     __syncthreads();
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
@@ -649,7 +829,7 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 // the extended patch, restricted solution on the segment's coarse cells, tau
 // rhs on the coarse cells whose stencil lies in the segment, seam values for
 // the two edge cells (formed from the assembled level by seam_tau_kernel).
-template <bool NL>
+template <int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -658,7 +838,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
     const double cl = scale2(a.lam, -2 * a.M);
-    for (int k = 0; k < a.nu; ++k) sweep_op<NL>(m.u, m.g, cl, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+    for (int k = 0; k < a.nu; ++k)
+        sweep_op<OP>(m.u, m.g, cl, m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     const double *u = m.u;
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
     double *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
@@ -669,8 +850,11 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
         if (!edge) {
             double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
             double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
-            double gc = tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-            if (NL) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+            double gc = (OP == kOpVarcoef)
+                            ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
+                                         m.a[i0 + 2])
+                            : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+            if (OP == kOpBratu) gc += tau_nl(cl, u[i0], u[i0 + 1]);
             gc_out[J] = gc;
         }
     }
@@ -684,7 +868,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 // tau rhs of the two coarse cells at each interior segment boundary, from the
 // assembled fine values (seams) and the restricted solution (appendix down
 // leg).  Thread k handles the boundary s = (k+1) W.
-template <bool NL>
+template <int OP>
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -698,19 +882,29 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     const int J = (s >> 1) - 1;         // last coarse cell of the left segment
     // coarse fluxes G from the restricted solution, fine fluxes F from the seams
     const double hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
+    // variable coefficient: faces s-2, s, s+2 (coarse faces J, J+1, J+2 coincide with them)
+    double am = 1.0, a0 = 1.0, ap = 1.0;
+    if (OP == kOpVarcoef) {
+        const double *co = batch_at(a.coef, a.n + 1);
+        am = co[s - 2];
+        a0 = co[s];
+        ap = co[s + 2];
+    }
     {
         double Gl = h0 - hm1, Gr = h1 - h0;
         double Fl = f2 - f3, Fr = p0 - f1;
+        if (OP == kOpVarcoef) { Gl *= am; Fl *= am; Gr *= a0; Fr *= a0; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
+        if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
         gc_out[J] = scale2(f[2 * J] + f[2 * J + 1], 1 - 2 * a.M) + tau;
     }
     {
         int J2 = J + 1;
         double Gl = h1 - h0, Gr = h2 - h1;
         double Fl = p0 - f1, Fr = p2 - p1;
+        if (OP == kOpVarcoef) { Gl *= a0; Fl *= a0; Gr *= ap; Fr *= ap; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (NL) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
+        if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
         gc_out[J2] = scale2(f[2 * J2] + f[2 * J2 + 1], 1 - 2 * a.M) + tau;
     }
 }
@@ -718,7 +912,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 // K6: post-smoothing leg of the SR level (Fig. 3, Eq. 5, Fig. 5): full update
 // Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
 // Gauss-Seidel sweep), and the segment interior is written out.
-template <bool NL>
+template <int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
@@ -736,7 +930,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
             p[i0 + 1] += r;
         }
         __syncthreads();
-        sweep_op<NL>(p, m.g, scale2(a.lam, -2 * a.M), m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+        sweep_op<OP>(p, m.g, scale2(a.lam, -2 * a.M), m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     }
     double *u_out = batch_at(a.u_out, a.n);
     for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) u_out[i] = p[i - m.lo];
@@ -756,27 +950,32 @@ struct TailArgs {
     double *u_out;             // level Mc result
     const double *Ainv;        // inverse of the scaled coarsest operator, row-major
     double lam;                // Bratu: lam (0 otherwise)
+    const double *coef[32];    // variable coefficient: face coefficients of level l (2^l + 1 per problem)
 };
 
 struct TailSmem {
     double *u, *g, *S, *X, *Y;
     int M0;
     double lam;
+    const double *const *coef;  // per-level face coefficients (global), before the batch offset
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
+    // this problem's face coefficients of level l
+    __device__ const double *a(int l) const { return coef[l] ? batch_at(coef[l], (1LL << l) + 1) : nullptr; }
 };
 
-template <bool NL>
+template <int OP>
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
+    const double *a = (OP == kOpVarcoef) ? m.a(l) : nullptr;
     for (int k = 0; k < nu; ++k)
-        sweep_op<NL, true>(u, g, scale2(m.lam, -2 * l), 0, 0, n, n, (k & 1) == 0, m.X, m.Y);
+        sweep_op<OP, true>(u, g, scale2(m.lam, -2 * l), a, 0, 0, 0, n, n, (k & 1) == 0, m.X, m.Y);
 }
 
 // smooth level l, then restriction and tau rhs into level l-1
-template <bool NL>
+template <int OP>
 __device__ void tail_down(TailSmem &m, int l, int nu) {
-    tail_smooth<NL>(m, l, nu);
+    tail_smooth<OP>(m, l, nu);
     const int nc = 1 << (l - 1);
     const double *u = m.u + m.off(l), *g = m.g + m.off(l);
     double *uc = m.u + m.off(l - 1), *gc = m.g + m.off(l - 1);
@@ -785,8 +984,14 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         uc[J] = scale2(u[i0] + u[i0 + 1], -1);
-        double gcv = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-        if (NL) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
+        double gcv;
+        if (OP == kOpVarcoef) {
+            const double *a = m.a(l);
+            gcv = tau_rhs_vc(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, a[i0], a[i0 + 2]);
+        } else {
+            gcv = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
+        }
+        if (OP == kOpBratu) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
         gc[J] = gcv;
     }
     __syncthreads();
@@ -826,12 +1031,19 @@ __device__ void coarsest_newton(double *u, const double *g, int n, double c, dou
     }
 }
 
-template <bool NL>
+template <int OP>
 __device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
-    if (NL) {
+    if (OP == kOpBratu) {
         const int n0 = 1 << m.M0;
         if (threadIdx.x == 0)
             coarsest_newton(m.u + m.off(m.M0), m.g + m.off(m.M0), n0, scale2(m.lam, -2 * m.M0), m.S, m.X);
+        __syncthreads();
+        return;
+    }
+    if (OP == kOpVarcoef) {
+        const int n0 = 1 << m.M0;
+        if (threadIdx.x == 0)
+            coarsest_thomas_vc(m.u + m.off(m.M0), m.g + m.off(m.M0), n0, m.a(m.M0), m.S, m.X);
         __syncthreads();
         return;
     }
@@ -849,7 +1061,7 @@ __device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
 }
 
 // u_l += P (u_{l-1} - R u_l), then smoothing
-template <bool NL>
+template <int OP>
 __device__ void tail_up(TailSmem &m, int l, int nu) {
     const int n = 1 << l, nc = n >> 1;
     double *u = m.u + m.off(l);
@@ -863,7 +1075,7 @@ __device__ void tail_up(TailSmem &m, int l, int nu) {
         u[i] += scale2(fma(3.0, m.S[J], cn), -2);
     }
     __syncthreads();
-    tail_smooth<NL>(m, l, nu);
+    tail_smooth<OP>(m, l, nu);
 }
 
 __device__ void tail_interp(TailSmem &m, int l) {
@@ -878,13 +1090,14 @@ __device__ void tail_interp(TailSmem &m, int l) {
     __syncthreads();
 }
 
-template <bool NL>
-__global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
+template <int OP>
+__global__ void __launch_bounds__(kTailBlock) tail_kernel(const __grid_constant__ TailArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
     TailSmem m;
     m.M0 = a.M0;
     m.lam = a.lam;
+    m.coef = a.coef;
     const int tot = (1 << (a.Mc + 1)) - (1 << a.M0);
     m.u = sm;
     m.g = m.u + tot;
@@ -913,17 +1126,17 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
         // starting iterate; the linear solve ignores it)
         for (int i = threadIdx.x; i < (1 << a.M0); i += blockDim.x) m.u[m.off(a.M0) + i] = 0.0;
         __syncthreads();
-        tail_coarsest<NL>(m, a.Ainv);
+        tail_coarsest<OP>(m, a.Ainv);
         for (int k = a.M0; k < a.Mc; ++k) {
             tail_interp(m, k + 1);
-            for (int l = k + 1; l > a.M0; --l) tail_down<NL>(m, l, a.nu1);
-            tail_coarsest<NL>(m, a.Ainv);
-            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up<NL>(m, l, a.nu2);
+            for (int l = k + 1; l > a.M0; --l) tail_down<OP>(m, l, a.nu1);
+            tail_coarsest<OP>(m, a.Ainv);
+            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up<OP>(m, l, a.nu2);
         }
     } else {
-        for (int l = a.Mc; l > a.M0; --l) tail_down<NL>(m, l, a.nu1);
-        tail_coarsest<NL>(m, a.Ainv);
-        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up<NL>(m, l, a.nu2);
+        for (int l = a.Mc; l > a.M0; --l) tail_down<OP>(m, l, a.nu1);
+        tail_coarsest<OP>(m, a.Ainv);
+        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up<OP>(m, l, a.nu2);
     }
     for (int i = threadIdx.x; i < nMc; i += blockDim.x) u_out[i] = m.u[m.off(a.Mc) + i];
 }

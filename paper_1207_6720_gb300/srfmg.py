@@ -14,11 +14,12 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_ECUDA",
                 4: "SRFMG_ETIMEOUT", 5: "SRFMG_ENONFINITE", 6: "SRFMG_EUNSUPPORTED"}
 FP64, MIXED = 0, 1
-LAPLACE, BRATU = 0, 2
+LAPLACE, VARCOEF, BRATU = 0, 1, 2
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
+           "srfmg_set_coefficient",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
@@ -82,11 +83,12 @@ def load(build_if_missing=True):
                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_autotune_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.srfmg_set_coefficient.argtypes = [H, vp, vp]
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
-                 "srfmg_autotune_candidate"):
+                 "srfmg_autotune_candidate", "srfmg_set_coefficient"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -165,6 +167,15 @@ class Solver:
                                             ctypes.c_void_p(dL_df.data_ptr()), _stream_ptr(stream)),
                     "adjoint")
         return dL_df
+
+    def set_coefficient(self, log_a, stream=None):
+        """SRFMG_OP_VARCOEF: a = exp(log_a) at the 2^log2_n + 1 faces (per problem)."""
+        import torch
+        if not (log_a.is_cuda and log_a.dtype == torch.float64 and log_a.is_contiguous()
+                and log_a.numel() == (self.n + 1) * self.batch):
+            raise ValueError("log_a must be a contiguous CUDA float64 tensor of batch * (2^log2_n + 1) values")
+        self._check(self.lib.srfmg_set_coefficient(self.h, ctypes.c_void_p(log_a.data_ptr()), _stream_ptr(stream)),
+                    "set_coefficient")
 
     def solve_host(self, f, u=None, stream=None):
         """Solve from and to host numpy arrays (copies inside; synchronises)."""

@@ -43,7 +43,7 @@ def test_default_params():
     ("log2_n", 2), ("log2_n", 29), ("log2_n_coarsest", 1), ("log2_n_coarsest", 7),
     ("n_sr_levels", 2), ("n_sr_levels", -1), ("segment_width", 24), ("segment_width", 8),
     ("segment_width", 8192), ("buffer_width", 3), ("buffer_width", 0), ("buffer_width", 66),
-    ("nu1", 0), ("nu2", 5), ("op", 1), ("smoother", 1), ("precision", 7),
+    ("nu1", 0), ("nu2", 5), ("op", 3), ("smoother", 1), ("precision", 7),
 ])
 def test_create_rejects_bad_params_before_cuda(field, value):
     lib = srfmg.load()

@@ -34,7 +34,7 @@ def test_bratu_parameters_are_checked_on_the_host():
     assert _create(op=srfmg.BRATU, lambda_=-1.0) == srfmg.EINVAL
     assert _create(op=srfmg.BRATU, lambda_=float("inf")) == srfmg.EINVAL
     assert _create(op=srfmg.BRATU, lambda_=float("nan")) == srfmg.EINVAL
-    assert _create(op=1) == srfmg.EINVAL
+    assert _create(op=3) == srfmg.EINVAL
 
 
 CASES = [

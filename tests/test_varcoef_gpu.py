@@ -1,0 +1,126 @@
+"""The variable-coefficient problem -(a u')' = f on the GPU (FP64 kernels with
+the coefficient-weighted sweep, tau and coarsest solve) against the oracle on
+the same seeded inputs; tolerance 1e-10 relative max-norm.  The host-side
+argument checks run without a GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1207_6720_gb300 import srfmg, workloads
+
+TOL = 1e-10
+
+
+def rel_maxnorm(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _create(**kw):
+    lib = srfmg.load()
+    p = srfmg.default_params(12)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    return lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h))
+
+
+def test_varcoef_parameters_are_checked_on_the_host():
+    assert _create(op=srfmg.VARCOEF, precision=srfmg.MIXED) == srfmg.EUNSUPPORTED
+    assert _create(op=srfmg.VARCOEF, lambda_=1.0) == srfmg.EINVAL
+    lib = srfmg.load()
+    assert lib.srfmg_set_coefficient(None, None, None) == srfmg.EINVAL
+
+
+CASES = [
+    # (M, nRS, W, b, nu1, nu2, M0)
+    (6, 1, 16, 2, 1, 1, 2),
+    (10, 1, 256, 4, 1, 1, 2),
+    (12, 1, 64, 8, 1, 1, 2),
+    (13, 1, 128, 8, 2, 1, 2),
+    (14, 1, 4096, 8, 2, 2, 3),
+    (16, 1, 4096, 64, 1, 1, 6),
+    (17, 1, 2048, 8, 1, 1, 2),
+    (8, 0, 0, 0, 1, 1, 2),
+    (15, 0, 0, 0, 1, 2, 2),
+]
+
+
+def oracle_params(M, nRS, W, b, nu1, nu2, M0, log_a):
+    a = np.exp(log_a)
+    if nRS == 0:
+        return oracle.Params(M, M0=M0, nRS=0, nu1=nu1, nu2=nu2, op="varcoef", coef=a)
+    return oracle.sr_params(M, W, b, nRS=1, nu1=nu1, nu2=nu2, M0=M0, op="varcoef", coef=a)
+
+
+def _kw(nRS, W, b, nu1, nu2, M0):
+    kw = dict(op=srfmg.VARCOEF, n_sr_levels=nRS, nu1=nu1, nu2=nu2, log2_n_coarsest=M0)
+    if nRS:
+        kw.update(segment_width=W, buffer_width=b)
+    return kw
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M,nRS,W,b,nu1,nu2,M0", CASES)
+def test_varcoef_parity_gpu(M, nRS, W, b, nu1, nu2, M0):
+    torch = pytest.importorskip("torch")
+    f, _, log_a = workloads.varcoef_series(M, 16, seed=M)
+    s = srfmg.Solver(M, **_kw(nRS, W, b, nu1, nu2, M0))
+    try:
+        s.set_coefficient(torch.from_numpy(log_a).cuda())
+        u = s.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    finally:
+        s.close()
+    ref = oracle.fmg_h(oracle_params(M, nRS, W, b, nu1, nu2, M0, log_a), f)
+    assert rel_maxnorm(u, ref) <= TOL
+
+
+@pytest.mark.gpu
+def test_coefficient_can_change_between_replayed_solves_gpu():
+    torch = pytest.importorskip("torch")
+    M, W, b = 14, 1024, 8
+    f, _, la1 = workloads.varcoef_series(M, 16, seed=1)
+    _, _, la2 = workloads.varcoef_series(M, 16, seed=2, amp=2.0)
+    s = srfmg.Solver(M, **_kw(1, W, b, 1, 1, 2))
+    try:
+        fd = torch.from_numpy(f).cuda()
+        u = torch.empty_like(fd)
+        s.solve(fd, u)                                   # a = 1 until set
+        u_one = u.cpu().numpy()
+        for la in (la1, la2, la1):                       # the same graph replays
+            s.set_coefficient(torch.from_numpy(la).cuda())
+            s.solve(fd, u)
+            ref = oracle.fmg_h(oracle.sr_params(M, W, b, op="varcoef", coef=np.exp(la)), f)
+            assert rel_maxnorm(u.cpu().numpy(), ref) <= TOL
+    finally:
+        s.close()
+    ref1 = oracle.fmg_h(oracle.sr_params(M, W, b), f)    # a = 1 is the constant-coefficient solve
+    assert rel_maxnorm(u_one, ref1) <= TOL
+
+
+@pytest.mark.gpu
+def test_varcoef_batch_gpu():
+    torch = pytest.importorskip("torch")
+    M, W, b, B = 13, 512, 8, 3
+    data = [workloads.varcoef_series(M, 16, seed=10 + k) for k in range(B)]
+    s = srfmg.Solver(M, batch=B, **_kw(1, W, b, 1, 1, 2))
+    try:
+        s.set_coefficient(torch.from_numpy(np.concatenate([d[2] for d in data])).cuda())
+        ub = s.solve(torch.from_numpy(np.concatenate([d[0] for d in data])).cuda()).cpu().numpy().reshape(B, -1)
+    finally:
+        s.close()
+    for k, (f, _, la) in enumerate(data):
+        ref = oracle.fmg_h(oracle.sr_params(M, W, b, op="varcoef", coef=np.exp(la)), f)
+        assert rel_maxnorm(ub[k], ref) <= TOL
+
+
+@pytest.mark.gpu
+def test_set_coefficient_needs_a_varcoef_plan_gpu():
+    torch = pytest.importorskip("torch")
+    s = srfmg.Solver(12)
+    try:
+        with pytest.raises(srfmg.SrfmgError):
+            s.set_coefficient(torch.zeros((1 << 12) + 1, dtype=torch.float64, device="cuda"))
+    finally:
+        s.close()
