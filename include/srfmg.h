@@ -148,10 +148,16 @@ srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, v
  * device pointer, 2^M + 1 doubles per problem (B * (2^M + 1) for a batch), the
  * natural logarithm of a at the faces x_j = j / N, j = 0..N.  Fills the plan's
  * face coefficients of every level (a = exp(log_a); coarse faces coincide
- * with fine faces and take their value) with one kernel on `stream`,
- * asynchronously; log_a may be freed once the stream has passed it.  Until
- * the first call a = 1.  Errors: SRFMG_EINVAL for a NULL handle or pointer or
- * a plan of another operator. */
+ * with fine faces and take their value) with one kernel on `stream`, and
+ * checks on the device that the sweeps can take it exactly: every log_a finite
+ * with |log_a| <= 700, and on every level of 128 or more cells adjacent faces
+ * within a factor 1.5 of each other (|log a_{j+1} - log a_j| <= ln 1.5; the
+ * Gauss-Seidel carry over 99 cells is exact to 2^-72 for multipliers
+ * a_near / (a_near + a_far) <= 0.6).  The call synchronises `stream` to read
+ * the check; log_a may be freed when it returns.  Until the first call a = 1.
+ * Errors: SRFMG_EINVAL for a NULL handle or pointer, a plan of another
+ * operator, or a coefficient that fails the check (the plan's coefficient is
+ * then reset to a = 1). */
 srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *stream);
 
 /* Plan information (workspace size, launches per solve, ...). */

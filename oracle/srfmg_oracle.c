@@ -154,8 +154,8 @@ static int thomas(int n, const double *rhs, double *u) { return thomas_shift(n, 
  * coefficient a of the level (NULL: 1). */
 static int thomas_shift(int n, const double *rhs, const double *dshift, double *u, const double *a) {
     if (n < 1) return OR_EINVAL;
-    double *cp = (double *)malloc(sizeof(double) * (size_t)n);
-    double *dp = (double *)malloc(sizeof(double) * (size_t)n);
+    double *cp = (double *)calloc((size_t)n, sizeof(double));
+    double *dp = (double *)calloc((size_t)n, sizeof(double));
     if (!cp || !dp) { free(cp); free(dp); return OR_ENOMEM; }
     double off = -((double)n * (double)n);
     for (int i = 0; i < n; i++) {

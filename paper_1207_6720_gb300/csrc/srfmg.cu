@@ -70,6 +70,7 @@ struct srfmg_plan {
     double *seam = nullptr;
     double *Ainv = nullptr;
     double *coef[32] = {};         // variable coefficient: face coefficients of levels M0..M
+    int *coef_bad = nullptr;       // variable coefficient: set by the coefficient kernel's check
     fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
     bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
@@ -208,9 +209,9 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
     const int T = n < kTileMax ? n : kTileMax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
-    // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9)), every sweep
-    // shrinks its range by one cell, and the tau stencil reaches 2 cells past
-    // the tile
+    // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9); 12 * 9 = 108
+    // for the variable coefficient's 11 carry chunks), every sweep shrinks its
+    // range by one cell, and the tau stencil reaches 2 cells past the tile
     const int H = 112 * nu;
     o.lev.l = l;
     o.lev.n = n;
@@ -561,6 +562,7 @@ cudaError_t launch_coef(srfmg_plan *h, const double *log_a, cudaStream_t s) {
     a.log_a = log_a;
     a.M = h->M;
     a.M0 = h->M0;
+    a.bad = h->coef_bad;
     for (int l = 0; l < 32; ++l) a.out[l] = h->coef[l];
     const size_t nf = ((size_t)1 << h->M) + 1;
     const unsigned blocks = (unsigned)std::min<size_t>(4 * 152, (nf + 255) / 256);
@@ -688,8 +690,12 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         st = alloc_dev(h, &sc, 2 * B);
         h->scale = (fx::Scale *)sc;
     }
-    if (p->op == SRFMG_OP_VARCOEF)
+    if (p->op == SRFMG_OP_VARCOEF) {
         for (int l = h->M0; l <= h->M && st == SRFMG_OK; ++l) st = alloc_dev(h, &h->coef[l], B * (((size_t)1 << l) + 1));
+        double *flag = nullptr;
+        if (st == SRFMG_OK) st = alloc_dev(h, &flag, 1);
+        h->coef_bad = (int *)flag;
+    }
     const int n0 = 1 << h->M0;
     if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
     if (st == SRFMG_OK) {
@@ -799,9 +805,22 @@ srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *st
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
     if (h->p.op != SRFMG_OP_VARCOEF) return fail(h, SRFMG_EINVAL, "the plan's operator has no coefficient");
     if (!log_a || ((uintptr_t)log_a & 7)) return fail(h, SRFMG_EINVAL, "log_a must be an 8-byte aligned device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(h->device);
-    if (e == cudaSuccess) e = launch_coef(h, log_a, (cudaStream_t)stream);
-    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "coefficient kernel");
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->coef_bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_coef(h, log_a, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->coef_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "coefficient kernel");
+    if (!bad) return SRFMG_OK;
+    // rejected: back to a = 1, so that no solve runs on a coefficient the sweeps cannot take
+    e = launch_coef(h, nullptr, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "coefficient reset");
+    return fail(h, SRFMG_EINVAL,
+                "log_a: a value is not finite or beyond +-700, or adjacent faces of a level of 128 or more "
+                "cells differ by more than a factor 1.5 (ln 1.5 in log a); the coefficient was reset to a = 1");
 }
 
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {

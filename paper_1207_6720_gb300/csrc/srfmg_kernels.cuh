@@ -592,25 +592,46 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
 // faces of the finest level (NULL: a = 1): a_l[j] = exp(log_a[j 2^(M-l)]), the
 // coarse faces taking the coefficient of the coinciding fine face.  out[l]
 // holds 2^l + 1 values per problem (problem blockIdx.y).
+//
+// The kernel also sets *bad when the sweeps could not take the coefficient
+// exactly: a log a that is not finite or lies beyond +-700 (a would overflow or
+// vanish), or two adjacent faces of a level of 2^7 cells or more whose
+// coefficients differ by more than a factor 1.5.  The variable-coefficient
+// sweep carries over 99 cells, which is exact to 2^-72 for multipliers
+// a_near / (a_near + a_far) <= 0.6, i.e. for a contrast of at most 1.5
+// between neighbouring faces; levels of at most 64 cells carry over the whole
+// level and need no bound.
 // ---------------------------------------------------------------------------
 struct CoefArgs {
     const double *log_a;
     int M, M0;
+    int *bad;
     double *out[32];
 };
+
+constexpr int kCoefCheckLevel = 7;
+constexpr double kLogContrastMax = 0.405465108108164382;   // ln 1.5
+constexpr double kLogAMax = 700.0;
 
 __global__ void coef_hierarchy_kernel(CoefArgs a) {
     pdl_enter();
     const long long nf = (1LL << a.M) + 1;
     const double *la = batch_at(a.log_a, nf);
+    bool ok = true;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nf; j += (long long)gridDim.x * blockDim.x) {
-        const double v = la ? exp(la[j]) : 1.0;
+        const double lv = la ? la[j] : 0.0;
+        const double v = la ? exp(lv) : 1.0;
+        ok = ok && fabs(lv) <= kLogAMax;                 // false for NaN
         for (int l = a.M; l >= a.M0; --l) {
             const int sh = a.M - l;
             if (j & ((1LL << sh) - 1)) break;
             batch_at(a.out[l], (1LL << l) + 1)[j >> sh] = v;
+            const long long jn = j + (1LL << sh);        // the next face of level l
+            if (la && l >= kCoefCheckLevel && jn < nf)
+                ok = ok && fabs(la[jn] - lv) <= kLogContrastMax;
         }
     }
+    if (!ok) atomicOr(a.bad, 1);
 }
 
 // ---------------------------------------------------------------------------

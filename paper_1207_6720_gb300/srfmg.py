@@ -169,7 +169,11 @@ class Solver:
         return dL_df
 
     def set_coefficient(self, log_a, stream=None):
-        """SRFMG_OP_VARCOEF: a = exp(log_a) at the 2^log2_n + 1 faces (per problem)."""
+        """SRFMG_OP_VARCOEF: a = exp(log_a) at the 2^log2_n + 1 faces (per problem).
+        The library checks the coefficient on the device and synchronises the
+        stream; a coefficient the sweeps cannot take exactly (log_a not finite
+        or beyond +-700, or neighbouring faces of a level of 128 or more cells
+        more than a factor 1.5 apart) raises SrfmgError and resets a to 1."""
         import torch
         if not (log_a.is_cuda and log_a.dtype == torch.float64 and log_a.is_contiguous()
                 and log_a.numel() == (self.n + 1) * self.batch):

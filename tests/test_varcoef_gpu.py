@@ -124,3 +124,40 @@ def test_set_coefficient_needs_a_varcoef_plan_gpu():
             s.set_coefficient(torch.zeros((1 << 12) + 1, dtype=torch.float64, device="cuda"))
     finally:
         s.close()
+
+
+@pytest.mark.gpu
+def test_rough_coefficient_is_rejected_and_reset_gpu():
+    # the sweep's 99-cell carry is exact for neighbouring faces within a factor
+    # 1.5 on every level of 128 or more cells; a rougher coefficient is refused
+    # and the plan falls back to a = 1
+    torch = pytest.importorskip("torch")
+    M, W, b = 12, 512, 8
+    n = 1 << M
+    f, _, _ = workloads.sine_series(M, 16, seed=3)
+    s = srfmg.Solver(M, **_kw(1, W, b, 1, 1, 2))
+    fd = torch.from_numpy(f).cuda()
+    jump_ok = np.zeros(n + 1)
+    jump_ok[n // 2:] = np.log(1.45)                      # one jump by 1.45: accepted
+    jump_bad = np.zeros(n + 1)
+    jump_bad[n // 2 + 3:] = np.log(1.6)                  # one jump by 1.6 on the finest level
+    ramp = np.zeros(n + 1)                               # smooth on the finest level (1.6^(1/32) per face),
+    ramp[2048:2081] = np.linspace(0.0, np.log(1.6), 33)  # but faces 2048 and 2080 of level 7 differ by 1.6
+    ramp[2081:] = np.log(1.6)
+    nan = np.zeros(n + 1)
+    nan[17] = np.nan
+    big = np.zeros(n + 1)
+    big[5] = 800.0
+    try:
+        s.set_coefficient(torch.from_numpy(jump_ok).cuda())
+        u = s.solve(fd).cpu().numpy()
+        ref = oracle.fmg_h(oracle.sr_params(M, W, b, op="varcoef", coef=np.exp(jump_ok)), f)
+        assert rel_maxnorm(u, ref) <= TOL
+        ref1 = oracle.fmg_h(oracle.sr_params(M, W, b), f)
+        for la in (jump_bad, ramp, nan, big):
+            with pytest.raises(srfmg.SrfmgError):
+                s.set_coefficient(torch.from_numpy(la).cuda())
+            u = s.solve(fd).cpu().numpy()                # a = 1 after the refusal
+            assert rel_maxnorm(u, ref1) <= TOL
+    finally:
+        s.close()
