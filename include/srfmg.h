@@ -139,8 +139,8 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
  * cell centres); dL_df: device pointer, N doubles, receives dL/df.  Pointers,
  * alignment, overlap, asynchrony and errors as in srfmg_solve (it is the same
  * call: it has its own captured graph for its pointer pair).  SRFMG_OP_VARCOEF
- * is symmetric as well (dL/df only: the gradient with respect to the
- * coefficient is not provided).  Returns SRFMG_EUNSUPPORTED for
+ * is symmetric as well; its gradient with respect to the coefficient follows
+ * from u and dL/df by srfmg_coef_gradient.  Returns SRFMG_EUNSUPPORTED for
  * SRFMG_OP_BRATU. */
 srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, void *stream);
 
@@ -159,6 +159,24 @@ srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, v
  * operator, or a coefficient that fails the check (the plan's coefficient is
  * then reset to a = 1). */
 srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *stream);
+
+/* SRFMG_OP_VARCOEF: gradient of a loss L with respect to the coefficient,
+ * dL/dlog a, from the solution u of srfmg_solve and the adjoint state
+ * lam = dL/df of srfmg_adjoint (the operator is symmetric, so lam solves
+ * A lam = dL/du).  The derivative of the variable-coefficient operator of the
+ * paper's Sec. 4 discretisation (the paper itself has no gradient): face f,
+ * between cells f-1 and f, gives
+ *   dL/dlog a_f = -a_f (u_f - u_{f-1}) (lam_f - lam_{f-1}) N^2,
+ * the wall faces -2 a_0 u_0 lam_0 N^2 and -2 a_N u_{N-1} lam_{N-1} N^2, with
+ * the plan's current coefficient (the one the solve used).  It is the gradient
+ * of the discrete problem evaluated at the FMG-SR u and lam, so it carries
+ * their algebraic error.  u, lam: device pointers, N doubles per problem;
+ * dL_dloga: device pointer, N + 1 doubles per problem (B * (N + 1) for a
+ * batch), not overlapping u or lam; all 8-byte aligned.  One kernel on
+ * `stream`, asynchronous.  Errors: SRFMG_EINVAL for a NULL handle or pointer,
+ * misalignment, overlap, or a plan of another operator. */
+srfmg_status srfmg_coef_gradient(srfmg_handle h, const double *u, const double *lam, double *dL_dloga,
+                                 void *stream);
 
 /* Plan information (workspace size, launches per solve, ...). */
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info);

@@ -61,6 +61,7 @@ def lib():
             "or_vcycles_h": [pp, dp, dp, i],
             "or_apply_N": [i, ctypes.c_double, dp, dp],
             "or_apply_La": [i, dp, dp, dp],
+            "or_coef_gradient": [i, dp, dp, dp, dp],
             "or_coarsest": [pp, i, dp, dp],
         }
         for name, args in sigs.items():
@@ -165,6 +166,16 @@ def apply_La(u, a):
     assert len(a) == len(u) + 1
     out = np.empty_like(u)
     _check(lib().or_apply_La(len(u), _ptr(a), _ptr(u), _ptr(out)), "apply_La")
+    return out
+
+
+def coef_gradient(a, u, lam):
+    """dL/dlog a at the len(u) + 1 faces from the solution u and the adjoint
+    state lam = A^{-1} dL/du of -(a u')' = f (face coefficients a)."""
+    a, u, lam = _arr(a), _arr(u), _arr(lam)
+    assert len(a) == len(u) + 1 and len(lam) == len(u)
+    out = np.empty_like(a)
+    _check(lib().or_coef_gradient(len(u), _ptr(a), _ptr(u), _ptr(lam), _ptr(out)), "coef_gradient")
     return out
 
 

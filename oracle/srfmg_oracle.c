@@ -533,6 +533,24 @@ int or_apply_La(int n, const double *a, const double *u, double *out) {
     return OR_OK;
 }
 
+/* Gradient of a loss L through the solution of A(a) u = f with respect to the
+ * logarithm of the face coefficients, by the adjoint state (the paper has no
+ * gradient; this is the derivative of the variable-coefficient operator of the
+ * Sec. 4 discretisation).  lam = A^{-T} dL/du = A^{-1} dL/du (A is symmetric).
+ * Face f (between cells f-1 and f) carries the flux a_f (u_f - u_{f-1}) n^2,
+ * which enters (A u)_f with + and (A u)_{f-1} with -, so
+ *   dL/da_f = -lam^T (dA/da_f) u = -(u_f - u_{f-1}) (lam_f - lam_{f-1}) n^2;
+ * the wall faces enter one cell only, through the odd ghost: 2 a_0 u_0 n^2 in
+ * (A u)_0 and 2 a_n u_{n-1} n^2 in (A u)_{n-1}.  out[f] = a_f dL/da_f, f = 0..n. */
+int or_coef_gradient(int n, const double *a, const double *u, const double *lam, double *out) {
+    if (n < 1) return OR_EINVAL;
+    const double n2 = (double)n * (double)n;
+    out[0] = -(a[0] * (2.0 * u[0]) * lam[0]) * n2;
+    for (int f = 1; f < n; f++) out[f] = -(a[f] * (u[f] - u[f - 1]) * (lam[f] - lam[f - 1])) * n2;
+    out[n] = -(a[n] * (2.0 * u[n - 1]) * lam[n - 1]) * n2;
+    return OR_OK;
+}
+
 /* The coarsest-level solve of p on n cells: rhs in, u = starting iterate in,
  * solution out. */
 int or_coarsest(const or_params *p, int n, const double *rhs, double *u) {

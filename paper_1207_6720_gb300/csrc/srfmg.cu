@@ -801,6 +801,26 @@ srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, v
     return srfmg_solve(h, dL_du, dL_df, stream);
 }
 
+srfmg_status srfmg_coef_gradient(srfmg_handle h, const double *u, const double *lam, double *dL_dloga,
+                                 void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (h->p.op != SRFMG_OP_VARCOEF) return fail(h, SRFMG_EINVAL, "the plan's operator has no coefficient");
+    if (!u || !lam || !dL_dloga) return fail(h, SRFMG_EINVAL, "u, lam and dL_dloga must be device pointers");
+    if (((uintptr_t)u | (uintptr_t)lam | (uintptr_t)dL_dloga) & 7)
+        return fail(h, SRFMG_EINVAL, "u, lam and dL_dloga must be 8-byte aligned");
+    const size_t cells = h->n * (size_t)h->batch, faces = (h->n + 1) * (size_t)h->batch;
+    const double *o = dL_dloga;
+    if ((o < u + cells && u < o + faces) || (o < lam + cells && lam < o + faces))
+        return fail(h, SRFMG_EINVAL, "dL_dloga overlaps u or lam");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const unsigned blocks = (unsigned)std::min<size_t>(4 * 152, (h->n + 1 + 255) / 256);
+    coef_gradient_kernel<<<dim3(blocks, (unsigned)h->batch), 256, 0, (cudaStream_t)stream>>>(
+        u, lam, h->coef[h->M], dL_dloga, h->M);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "coefficient gradient kernel");
+}
+
 srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *stream) {
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
     if (h->p.op != SRFMG_OP_VARCOEF) return fail(h, SRFMG_EINVAL, "the plan's operator has no coefficient");

@@ -635,6 +635,38 @@ __global__ void coef_hierarchy_kernel(CoefArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// dL/dlog a at the 2^M + 1 faces of the finest level from the solution u and
+// the adjoint state lam = A^{-1} dL/du of -(a u')' = f (the derivative of the
+// variable-coefficient operator): face f, between cells f-1 and f, carries the
+// flux a_f (u_f - u_{f-1}) n^2 into cell f (+) and cell f-1 (-), so
+//   dL/dlog a_f = -a_f (u_f - u_{f-1}) (lam_f - lam_{f-1}) n^2,
+// and the wall faces, through the odd ghost, -a (2 u) lam n^2 with their one
+// cell.  One thread per face (grid-stride), problem blockIdx.y.
+// ---------------------------------------------------------------------------
+__global__ void coef_gradient_kernel(const double *__restrict__ u, const double *__restrict__ lam,
+                                     const double *__restrict__ a, double *__restrict__ out, int M) {
+    pdl_enter();
+    const long long n = 1LL << M;
+    const double n2 = (double)n * (double)n;
+    const double *up = batch_at(u, n), *lp = batch_at(lam, n), *ap = batch_at(a, n + 1);
+    double *op = batch_at(out, n + 1);
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f <= n; f += (long long)gridDim.x * blockDim.x) {
+        double du, dl;
+        if (f == 0) {
+            du = 2.0 * up[0];
+            dl = lp[0];
+        } else if (f == n) {
+            du = 2.0 * up[n - 1];
+            dl = lp[n - 1];
+        } else {
+            du = up[f] - up[f - 1];
+            dl = lp[f] - lp[f - 1];
+        }
+        op[f] = -(ap[f] * du * dl) * n2;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stored-level passes (global lexicographic smoothing).  A block owns the
 // tile [s, s+T) of level l and loads it with a halo of H cells per side; the
 // halo is wider than the Gauss-Seidel carry horizon, so the tile's values are

@@ -19,7 +19,7 @@ LAPLACE, VARCOEF, BRATU = 0, 1, 2
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
-           "srfmg_set_coefficient",
+           "srfmg_set_coefficient", "srfmg_coef_gradient",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
@@ -84,11 +84,12 @@ def load(build_if_missing=True):
     lib.srfmg_autotune_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_set_coefficient.argtypes = [H, vp, vp]
+    lib.srfmg_coef_gradient.argtypes = [H, vp, vp, vp, vp]
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
-                 "srfmg_autotune_candidate", "srfmg_set_coefficient"):
+                 "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -181,6 +182,20 @@ class Solver:
         self._check(self.lib.srfmg_set_coefficient(self.h, ctypes.c_void_p(log_a.data_ptr()), _stream_ptr(stream)),
                     "set_coefficient")
 
+    def coef_gradient(self, u, lam, out=None, stream=None):
+        """SRFMG_OP_VARCOEF: dL/dlog a at the 2^log2_n + 1 faces (per problem)
+        from the solution u and the adjoint state lam = adjoint(dL/du)."""
+        import torch
+        for name, t in (("u", u), ("lam", lam)):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == self.n * self.batch):
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of batch * 2^log2_n values")
+        if out is None:
+            out = torch.empty((self.n + 1) * self.batch, dtype=torch.float64, device=u.device)
+        self._check(self.lib.srfmg_coef_gradient(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+                    "coef_gradient")
+        return out
+
     def solve_host(self, f, u=None, stream=None):
         """Solve from and to host numpy arrays (copies inside; synchronises)."""
         import numpy as np
@@ -218,7 +233,7 @@ class Solver:
             pass
 
 
-def _solve_function():
+def _solve_functions():
     import torch
 
     class _Solve(torch.autograd.Function):
@@ -233,19 +248,43 @@ def _solve_function():
         def backward(ctx, grad_u):
             return ctx.solver.adjoint(grad_u.contiguous()), None
 
-    return _Solve
+    class _SolveCoef(torch.autograd.Function):
+        """u = solve(f; a = exp(log_a)) with dL/df = lam = adjoint(dL/du) and
+        dL/dlog a = coef_gradient(u, lam) in the backward pass."""
+
+        @staticmethod
+        def forward(ctx, f, log_a, solver):
+            solver.set_coefficient(log_a.detach().contiguous())
+            u = solver.solve(f.contiguous())
+            ctx.solver = solver
+            ctx.save_for_backward(u)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            (u,) = ctx.saved_tensors
+            lam = ctx.solver.adjoint(grad_u.contiguous())
+            g = ctx.solver.coef_gradient(u, lam) if ctx.needs_input_grad[1] else None
+            return lam, g, None
+
+    return _Solve, _SolveCoef
 
 
-_SOLVE_FN = None
+_SOLVE_FNS = None
 
 
-def solve_autograd(solver, f):
+def solve_autograd(solver, f, log_a=None):
     """Differentiable solve: ``u = solve_autograd(solver, f)``; ``u.backward``
-    (or ``torch.autograd.grad``) runs the adjoint solve on the GPU."""
-    global _SOLVE_FN
-    if _SOLVE_FN is None:
-        _SOLVE_FN = _solve_function()
-    return _SOLVE_FN.apply(f, solver)
+    (or ``torch.autograd.grad``) runs the adjoint solve on the GPU.  For a
+    SRFMG_OP_VARCOEF plan, ``log_a`` (the log of the face coefficients) sets the
+    coefficient and receives dL/dlog a; the backward pass uses the plan's
+    coefficient, so it must run before the plan's coefficient is set again."""
+    global _SOLVE_FNS
+    if _SOLVE_FNS is None:
+        _SOLVE_FNS = _solve_functions()
+    if log_a is None:
+        return _SOLVE_FNS[0].apply(f, solver)
+    return _SOLVE_FNS[1].apply(f, log_a, solver)
 
 
 def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None):

@@ -31,6 +31,7 @@ def test_varcoef_parameters_are_checked_on_the_host():
     assert _create(op=srfmg.VARCOEF, lambda_=1.0) == srfmg.EINVAL
     lib = srfmg.load()
     assert lib.srfmg_set_coefficient(None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_coef_gradient(None, None, None, None, None) == srfmg.EINVAL
 
 
 CASES = [
