@@ -117,6 +117,50 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
  * and replayed afterwards.  Errors: SRFMG_EINVAL for NULL or misaligned
  * (not 16-byte aligned) pointers, SRFMG_ECUDA if a launch fails. */
 srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream);
+
+/* Number of functionals srfmg_solve_functionals returns per problem. */
+#define SRFMG_NUM_FUNCTIONALS 5
+
+/* An SR solve (n_sr_levels = 1) that collects functionals of the fine-grid
+ * solution while its segments are swept (Fig. 3 computes a functional of the
+ * fine grid in the post-smoothing leg; the paper's section on obtaining the
+ * solution names this as one way to get quantities of interest without
+ * storing the fine grid).  For each problem k, functionals[5 k ..] receives
+ *   [0] h sum_i u_i          (the integral of u, midpoint rule, h = 1/N)
+ *   [1] h sum_i u_i^2        (the squared L2 norm)
+ *   [2] max_i |u_i|
+ *   [3] h sum_i (u_i - u_ref_i)^2   (0 without u_ref)
+ *   [4] max_i |u_i - u_ref_i|       (0 without u_ref)
+ * each segment reducing its interior and one kernel reducing the segments,
+ * both in a fixed order (the same bits on every run).
+ * u: device pointer as in srfmg_solve, or NULL: the fine solution is then
+ * never written to memory (the solve moves 8 bytes per cell less); the plan
+ * still keeps the coarse solution for srfmg_reconstruct.  u_ref: device
+ * pointer, N doubles per problem, or NULL.  functionals: device pointer,
+ * 5 doubles per problem.  Alignment as in srfmg_solve for f and u, 8 bytes for
+ * u_ref and functionals; no output may overlap another argument.
+ * Asynchronous on `stream`, captured and replayed per pointer set like
+ * srfmg_solve.  Errors: SRFMG_EUNSUPPORTED without an SR level; SRFMG_EINVAL
+ * for NULL f or functionals, misalignment or overlap; SRFMG_ECUDA. */
+srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u, const double *u_ref,
+                                     double *functionals, void *stream);
+
+/* PDE decompression on demand (the paper's section on obtaining the
+ * solution): expand fine-grid segments [seg_begin, seg_begin + seg_count)
+ * from the coarse solution u_{M-1} that the plan keeps after its last solve
+ * (srfmg_solve, srfmg_solve_functionals or srfmg_adjoint), by that solve's
+ * post-leg: the full update Pi u_{M-1} and the nu2 compatible-relaxation
+ * iterations on each segment's extended patch.  The result equals, bit for
+ * bit, the same cells of that solve's u.  f: device pointer, the right-hand
+ * side of that solve (N doubles per problem).  u_seg: device pointer,
+ * seg_count * W doubles per problem (problem k at offset k * seg_count * W),
+ * receives cells [seg_begin W, (seg_begin + seg_count) W).  One kernel on
+ * `stream`, ordered after the solve by the caller (same stream or an event).
+ * Errors: SRFMG_EUNSUPPORTED without an SR level; SRFMG_EINVAL for a plan that
+ * has not solved yet, a segment range outside [0, n_segments), NULL or
+ * misaligned pointers (f 16 bytes, u_seg 8 bytes) or overlap; SRFMG_ECUDA. */
+srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begin, int32_t seg_count,
+                               double *u_seg, void *stream);
 /* (The handle keeps the captured graphs of up to four (f, u) pointer pairs;
  * the least recently used one is replaced.) */
 

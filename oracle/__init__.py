@@ -179,6 +179,23 @@ def coef_gradient(a, u, lam):
     return out
 
 
+def functionals(u, u_ref=None):
+    """The five functionals of a fine-grid solution of N cells (h = 1/N) that
+    the SR solve collects while it sweeps the fine grid (Fig. 3 computes a
+    functional of the fine grid in the post-smoothing leg):
+    [h sum u, h sum u^2, max|u|, h sum (u - u_ref)^2, max|u - u_ref|], the last
+    two 0 without a reference.  Plain definitions; sums by math.fsum."""
+    import math
+    u = _arr(u)
+    h = 1.0 / len(u)
+    out = [h * math.fsum(u), h * math.fsum(u * u), float(np.max(np.abs(u))), 0.0, 0.0]
+    if u_ref is not None:
+        d = u - _arr(u_ref)
+        out[3] = h * math.fsum(d * d)
+        out[4] = float(np.max(np.abs(d)))
+    return np.array(out)
+
+
 def coarsest(params, rhs, u0):
     """The coarsest-level solve of ``params`` (Thomas, or Newton for Bratu)
     from the starting iterate u0."""

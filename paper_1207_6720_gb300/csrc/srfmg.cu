@@ -56,6 +56,15 @@ struct Op {
     fx::Scale *scale;
 };
 
+// The caller's pointers of one solve, patched into the tagged op fields.
+struct Io {
+    const double *f;
+    double *u;                 // the solution (NULL: not written; functionals only)
+    const double *u_ref;       // reference of the functionals, or NULL
+    double *fout;              // functionals, kNumFunc per problem, or NULL
+    double *fpart;             // the plan's segment partials when fout is set
+};
+
 }  // namespace
 
 struct srfmg_plan {
@@ -72,19 +81,24 @@ struct srfmg_plan {
     double *coef[32] = {};         // variable coefficient: face coefficients of levels M0..M
     int *coef_bad = nullptr;       // variable coefficient: set by the coefficient kernel's check
     fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
+    double *fpart = nullptr;       // SR plans: functional partials, kNumFunc per segment and problem
+    bool solved = false;           // a solve has been enqueued (its coarse solution is kept)
     bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
     size_t ws_bytes = 0;
     std::vector<Op> ops;
     std::vector<std::string> names;
     cudaStream_t cap_stream = nullptr;
-    // captured launch sequences, one per (f, u) pointer pair (a solve and an
-    // adjoint solve on other buffers keep their own); least recently used out
+    // captured launch sequences, one per (f, u, u_ref, functionals) pointer set
+    // (a solve and an adjoint solve on other buffers keep their own); least
+    // recently used out
     static constexpr int kGraphSlots = 4;
     struct GraphSlot {
         cudaGraphExec_t exec = nullptr;
         const double *f = nullptr;
         double *u = nullptr;
+        const double *u_ref = nullptr;
+        double *fout = nullptr;
         unsigned long long used = 0;
     } graphs[kGraphSlots];
     unsigned long long graph_clock = 0;
@@ -475,15 +489,21 @@ cudaError_t run(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-cudaError_t launch_fixed(const Op &o0, const double *f, double *u, cudaStream_t s, bool pdl) {
+cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     Op o = o0;
+    const double *f = io.f;
+    double *u = io.u;
     if (o.rhs_in == TAG_F) o.frhs.f = f;
     if (o.lev_g == TAG_F) o.flev.f = f;
     if (o.lev_out == TAG_U) { o.flev.u_out_f64 = u; o.flev.u_out = nullptr; }
     if (o.tail_g == TAG_F) o.ftail.f = f;
     if (o.tail_out == TAG_U) { o.ftail.u_out_f64 = u; o.ftail.u_out = nullptr; }
     if (o.seg_f == TAG_F) o.fseg.f = f;
-    if (o.seg_u == TAG_U) o.fseg.u_out = u;
+    if (o.seg_u == TAG_U) {
+        o.fseg.u_out = u;
+        o.fseg.u_ref = io.u_ref;
+        o.fseg.fpart = io.fout ? io.fpart : nullptr;
+    }
     cudaError_t e = cudaSuccess;
     switch (o.kind) {
     case OP_SCALE: {
@@ -525,16 +545,22 @@ cudaError_t launch_fp64(const Op &o, cudaStream_t s, bool pdl) {
 }
 
 // Enqueue one op on s; pdl as in run().
-cudaError_t launch(const Op &o0, const double *f, double *u, cudaStream_t s, bool pdl) {
-    if (o0.fixed) return launch_fixed(o0, f, u, s, pdl);
+cudaError_t launch(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
+    if (o0.fixed) return launch_fixed(o0, io, s, pdl);
     Op o = o0;
+    const double *f = io.f;
+    double *u = io.u;
     if (o.rhs_in == TAG_F) o.rhs.in = f;
     if (o.lev_g == TAG_F) o.lev.g = f;
     if (o.lev_out == TAG_U) o.lev.u_out = u;
     if (o.tail_g == TAG_F) o.tail.g_in = f;
     if (o.tail_out == TAG_U) o.tail.u_out = u;
     if (o.seg_f == TAG_F) o.seg.f = f;
-    if (o.seg_u == TAG_U) o.seg.u_out = u;
+    if (o.seg_u == TAG_U) {
+        o.seg.u_out = u;
+        o.seg.u_ref = io.u_ref;
+        o.seg.fpart = io.fout ? io.fpart : nullptr;
+    }
     if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
     if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
     return launch_fp64<kOpLaplace>(o, s, pdl);
@@ -572,13 +598,16 @@ cudaError_t launch_coef(srfmg_plan *h, const double *log_a, cudaStream_t s) {
 
 // All launches of one solve; every launch after the first overlaps its set-up
 // with the preceding kernel (programmatic dependent launch).
-cudaError_t enqueue_all(srfmg_plan *h, const double *f, double *u, cudaStream_t s) {
+cudaError_t enqueue_all(srfmg_plan *h, const Io &io, cudaStream_t s) {
     bool first = true;
     for (const Op &o : h->ops) {
-        cudaError_t e = launch(o, f, u, s, !first);
+        cudaError_t e = launch(o, io, s, !first);
         if (e != cudaSuccess) return e;
         first = false;
     }
+    if (io.fout)    // the segments' partials -> the functionals of each problem
+        return run(functionals_finish_kernel, dim3(1, (unsigned)h->batch), dim3(256), 0, s, true,
+                   (const double *)io.fpart, (int)(h->n / h->W), h->M, io.fout);
     return cudaSuccess;
 }
 
@@ -603,7 +632,11 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
                          (const void *)fx::sr_post_kernel, (const void *)fx::tail_kernel,
                          (const void *)fx::rhs_hierarchy_kernel};
     for (const void *fn : fns) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        // the opt-in limit covers static and dynamic shared memory together
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncGetAttributes");
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
     }
     return SRFMG_OK;
@@ -685,6 +718,7 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], B << l);
     }
     if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, B * (h->n / h->W) * 6);
+    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->fpart, B * (h->n / h->W) * kNumFunc);
     if (st == SRFMG_OK && h->fixed) {
         double *sc = nullptr;
         st = alloc_dev(h, &sc, 2 * B);
@@ -728,22 +762,24 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     return SRFMG_OK;
 }
 
-srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream) {
-    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
-    if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be device pointers");
-    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned");
-    const size_t total = h->n * (size_t)h->batch;
-    if ((const double *)u < f + total && f < (const double *)u + total) return fail(h, SRFMG_EINVAL, "f and u overlap");
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Enqueue one solve with the caller's pointers io (checked by the caller):
+// replay the captured graph of this pointer set, capturing it first.
+srfmg_status solve_io(srfmg_handle h, const Io &io, cudaStream_t s) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     if (!h->use_graph) {
-        e = enqueue_all(h, f, u, s);
-        return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "kernel launch");
+        e = enqueue_all(h, io, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+        h->solved = true;
+        return SRFMG_OK;
     }
     srfmg_plan::GraphSlot *slot = nullptr;
     for (auto &g : h->graphs)
-        if (g.exec && g.f == f && g.u == u) slot = &g;
+        if (g.exec && g.f == io.f && g.u == io.u && g.u_ref == io.u_ref && g.fout == io.fout) slot = &g;
     if (!slot) {
         slot = &h->graphs[0];
         for (auto &g : h->graphs)
@@ -752,19 +788,86 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
-        cudaError_t le = enqueue_all(h, f, u, h->cap_stream);
+        cudaError_t le = enqueue_all(h, io, h->cap_stream);
         e = cudaStreamEndCapture(h->cap_stream, &graph);
         if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(h, le, "kernel launch during capture"); }
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&slot->exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { slot->exec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
-        slot->f = f;
-        slot->u = u;
+        slot->f = io.f;
+        slot->u = io.u;
+        slot->u_ref = io.u_ref;
+        slot->fout = io.fout;
     }
     slot->used = ++h->graph_clock;
     e = cudaGraphLaunch(slot->exec, s);
-    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "cudaGraphLaunch");
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+    h->solved = true;
+    return SRFMG_OK;
+}
+
+// [p, p + n) and [q, q + m) share memory
+bool overlap(const void *p, size_t pn, const void *q, size_t qn) {
+    const char *a = (const char *)p, *b = (const char *)q;
+    return a < b + qn && b < a + pn;
+}
+
+}  // namespace
+
+extern "C" {
+
+srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be device pointers");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned");
+    const size_t bytes = h->n * (size_t)h->batch * sizeof(double);
+    if (overlap(f, bytes, u, bytes)) return fail(h, SRFMG_EINVAL, "f and u overlap");
+    return solve_io(h, Io{f, u, nullptr, nullptr, nullptr}, (cudaStream_t)stream);
+}
+
+srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u, const double *u_ref,
+                                     double *functionals, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (h->nRS != 1)
+        return fail(h, SRFMG_EUNSUPPORTED, "functionals are collected by the SR post-leg: the plan needs n_sr_levels = 1");
+    if (!f || !functionals) return fail(h, SRFMG_EINVAL, "f and functionals must be device pointers");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15) || ((uintptr_t)u_ref & 7) || ((uintptr_t)functionals & 7))
+        return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned, u_ref and functionals 8-byte aligned");
+    const size_t bytes = h->n * (size_t)h->batch * sizeof(double);
+    const size_t fbytes = (size_t)kNumFunc * h->batch * sizeof(double);
+    if ((u && overlap(f, bytes, u, bytes)) || (u && u_ref && overlap(u, bytes, u_ref, bytes)) ||
+        overlap(functionals, fbytes, f, bytes) || (u && overlap(functionals, fbytes, u, bytes)) ||
+        (u_ref && overlap(functionals, fbytes, u_ref, bytes)))
+        return fail(h, SRFMG_EINVAL, "an output overlaps another argument");
+    return solve_io(h, Io{f, u, u_ref, functionals, h->fpart}, (cudaStream_t)stream);
+}
+
+srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begin, int32_t seg_count,
+                               double *u_seg, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (h->nRS != 1) return fail(h, SRFMG_EUNSUPPORTED, "reconstruction expands SR segments: the plan needs n_sr_levels = 1");
+    if (!h->solved) return fail(h, SRFMG_EINVAL, "no solve has been enqueued on this plan");
+    const int nseg = (int)(h->n / h->W);
+    if (seg_begin < 0 || seg_count < 1 || seg_begin > nseg - seg_count)
+        return fail(h, SRFMG_EINVAL, "segments [seg_begin, seg_begin + seg_count) must lie in [0, n_segments)");
+    if (!f || !u_seg) return fail(h, SRFMG_EINVAL, "f and u_seg must be device pointers");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u_seg & 7))
+        return fail(h, SRFMG_EINVAL, "f must be 16-byte aligned, u_seg 8-byte aligned");
+    const size_t fb = h->n * (size_t)h->batch * sizeof(double);
+    const size_t ub = (size_t)seg_count * h->W * h->batch * sizeof(double);
+    if (overlap(f, fb, u_seg, ub)) return fail(h, SRFMG_EINVAL, "f and u_seg overlap");
+    const Op *post = nullptr;
+    for (const Op &o : h->ops)
+        if (o.kind == OP_SR_POST) post = &o;
+    if (!post) return fail(h, SRFMG_EUNSUPPORTED, "the plan has no SR post-leg");
+    Op o = *post;
+    o.grid.x = (unsigned)seg_count;
+    o.seg.seg0 = seg_begin;
+    o.fseg.seg0 = seg_begin;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = launch(o, Io{f, u_seg, nullptr, nullptr, nullptr}, (cudaStream_t)stream, false);
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "reconstruction kernel");
 }
 
 srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream) {
@@ -871,7 +974,7 @@ srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *str
         for (int i = 0; i < nops && e == cudaSuccess; ++i) {
             size_t idx = ((size_t)k * nops + i) * 2;
             e = cudaEventRecord(ev[idx], s);
-            if (e == cudaSuccess) e = launch(h->ops[i], f, u, s, false);
+            if (e == cudaSuccess) e = launch(h->ops[i], Io{f, u, nullptr, nullptr, nullptr}, s, false);
             if (e == cudaSuccess) e = cudaEventRecord(ev[idx + 1], s);
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

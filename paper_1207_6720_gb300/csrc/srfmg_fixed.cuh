@@ -503,11 +503,14 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
 struct SegArgs {
     int M, n, W, b, nu;
     int maxlen, maxc, maxch;
+    int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
     const Scale *sc;
     const double *f;
     const i64 *uc_src;
     i64 *uc_out, *gc_out, *seam;
-    double *u_out;
+    double *u_out;             // post-leg: FP64 solution of segments seg0.. (NULL: not written)
+    const double *u_ref;       // post-leg: reference for the functionals (NULL: none)
+    double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
 };
 
 // Shared memory as LevelSmem: u, gs, c, X, gr (2 maxlen + 2 maxc + maxch words).
@@ -623,10 +626,11 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     }
 }
 
+// K6 in fixed point; output and functionals as in the FP64 kernel.
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
-    const int s = blockIdx.x * a.W;
+    const int s = (a.seg0 + (int)blockIdx.x) * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(smi, a, s);
     seg_load(m, a, nullptr, 0, 0);
@@ -642,9 +646,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
         lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
     const int S = (a.sc + blockIdx.y)->S;
-    double *u_out = batch_at(a.u_out, a.n);
-    for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
-        u_out[i] = fixed_to_f64(p[i - m.lo], S);
+    const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
+    double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;
+    const double *ref = a.u_ref ? batch_at(a.u_ref, a.n) : nullptr;
+    FuncAcc q;
+    for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x) {
+        const double v = fixed_to_f64(p[i - m.lo], S);
+        if (u_out) u_out[i - s0] = v;
+        if (a.fpart) q.add(v, ref, i);
+    }
+    if (a.fpart) {
+        func_block_reduce(q);
+        if (threadIdx.x == 0) {
+            double *dst = batch_at(a.fpart, (long long)gridDim.x * kNumFunc) + (long long)blockIdx.x * kNumFunc;
+#pragma unroll
+            for (int k = 0; k < kNumFunc; ++k) dst[k] = q.v[k];
+        }
+    }
 }
 
 // --------------------------------------------------------------------------

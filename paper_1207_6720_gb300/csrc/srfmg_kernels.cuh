@@ -819,15 +819,104 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
 // E = [s-b, s+W+b) clipped to the domain and one frozen cell on each side.
 // The fine level exists only in shared memory.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Functionals of the fine-grid solution, collected while the segments are swept
+// (Fig. 3 computes a functional of the fine grid in the post-smoothing leg; the
+// paper's closing section names such functionals as one way to get quantities
+// of interest out of a solution that is never stored).  Per problem:
+//   F0 = h sum u_i, F1 = h sum u_i^2, F2 = max |u_i|,
+//   F3 = h sum (u_i - r_i)^2, F4 = max |u_i - r_i|  (r a reference; 0 without one).
+// Each post-leg block reduces its segment interior into kNumFunc partials in a
+// fixed order, and functionals_finish_kernel reduces the segments in a fixed
+// order, so a solve gives the same bits on every run.
+// ---------------------------------------------------------------------------
+constexpr int kNumFunc = 5;
+
+struct FuncAcc {
+    double v[kNumFunc];
+    __device__ FuncAcc() {
+#pragma unroll
+        for (int k = 0; k < kNumFunc; ++k) v[k] = 0.0;
+    }
+    __device__ __forceinline__ void add(double x, const double *ref, long long i) {
+        v[0] += x;
+        v[1] = fma(x, x, v[1]);
+        v[2] = fmax(v[2], fabs(x));
+        if (ref) {
+            const double d = x - ref[i];
+            v[3] = fma(d, d, v[3]);
+            v[4] = fmax(v[4], fabs(d));
+        }
+    }
+    __device__ __forceinline__ void merge(const double *e) {
+        v[0] += e[0];
+        v[1] += e[1];
+        v[2] = fmax(v[2], e[2]);
+        v[3] += e[3];
+        v[4] = fmax(v[4], e[4]);
+    }
+};
+
+// Reduce the block's accumulators (sums F0, F1, F3; maxima F2, F4) in a fixed
+// order; the result is valid in thread 0.  blockDim.x is a multiple of 32 and
+// every thread of the block calls it once.
+__device__ __forceinline__ void func_block_reduce(FuncAcc &q) {
+    __shared__ double red[kNumFunc][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kNumFunc; ++k) {
+        double x = q.v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (k == 2 || k == 4) ? fmax(x, y) : x + y;
+        }
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < kNumFunc; ++k) {
+            double x = lane < nw ? red[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = (k == 2 || k == 4) ? fmax(x, y) : x + y;
+            }
+            q.v[k] = x;
+        }
+    }
+}
+
+// Segment partials (nseg per problem, problem blockIdx.y) -> out[kNumFunc] per
+// problem; one block of 256 threads per problem.
+__global__ void functionals_finish_kernel(const double *fpart, int nseg, int M, double *out) {
+    pdl_enter();
+    const double *src = batch_at(fpart, (long long)nseg * kNumFunc);
+    FuncAcc q;
+    for (int j = threadIdx.x; j < nseg; j += blockDim.x) q.merge(src + (long long)j * kNumFunc);
+    func_block_reduce(q);
+    if (threadIdx.x == 0) {
+        const double h = scale2(1.0, -M);
+        double *o = batch_at(out, kNumFunc);
+        o[0] = q.v[0] * h;
+        o[1] = q.v[1] * h;
+        o[2] = q.v[2];
+        o[3] = q.v[3] * h;
+        o[4] = q.v[4];
+    }
+}
+
 struct SegArgs {
     int M, n, W, b, nu;
     int maxlen, maxc, maxch;   // shared-memory layout sizes (doubles)
+    int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
     const double *f;           // right-hand side, unscaled
     const double *uc_src;      // level M-1
     double *uc_out;            // pre-leg: restricted solution on level M-1
     double *gc_out;            // pre-leg: tau-corrected g_{M-1}
     double *seam;              // pre-leg: 6 fine values per segment
-    double *u_out;             // post-leg: the solution
+    double *u_out;             // post-leg: the solution of segments seg0.. (NULL: not written)
+    const double *u_ref;       // post-leg: reference for the functionals (NULL: none)
+    double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
     double lam;                // Bratu: lam (0 otherwise)
     const double *coef;        // variable coefficient: face coefficients of level M (2^M + 1)
 };
@@ -964,12 +1053,14 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
 
 // K6: post-smoothing leg of the SR level (Fig. 3, Eq. 5, Fig. 5): full update
 // Pi u_{M-1}, then nu2 times (Kaczmarz over the patch's sibling pairs,
-// Gauss-Seidel sweep), and the segment interior is written out.
+// Gauss-Seidel sweep); the segment interior is written out and/or reduced into
+// the functionals.  Block x handles segment seg0 + x (seg0 > 0 expands chosen
+// segments from the stored coarse solution: PDE decompression on demand).
 template <int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ double sm[];
-    const int s = blockIdx.x * a.W;
+    const int s = (a.seg0 + blockIdx.x) * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
@@ -985,8 +1076,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
         __syncthreads();
         sweep_op<OP>(p, m.g, scale2(a.lam, -2 * a.M), m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     }
-    double *u_out = batch_at(a.u_out, a.n);
-    for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) u_out[i] = p[i - m.lo];
+    const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
+    double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;
+    const double *ref = a.u_ref ? batch_at(a.u_ref, a.n) : nullptr;
+    FuncAcc q;
+    for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) {
+        const double v = p[i - m.lo];
+        if (u_out) u_out[i - s0] = v;
+        if (a.fpart) q.add(v, ref, i);
+    }
+    if (a.fpart) {
+        func_block_reduce(q);
+        if (threadIdx.x == 0) {
+            double *dst = batch_at(a.fpart, (long long)gridDim.x * kNumFunc) + (long long)blockIdx.x * kNumFunc;
+#pragma unroll
+            for (int k = 0; k < kNumFunc; ++k) dst[k] = q.v[k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -15,11 +15,12 @@ STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_E
                 4: "SRFMG_ETIMEOUT", 5: "SRFMG_ENONFINITE", 6: "SRFMG_EUNSUPPORTED"}
 FP64, MIXED = 0, 1
 LAPLACE, VARCOEF, BRATU = 0, 1, 2
+NUM_FUNCTIONALS = 5          # functionals per problem of srfmg_solve_functionals
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
-           "srfmg_set_coefficient", "srfmg_coef_gradient",
+           "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
@@ -85,11 +86,14 @@ def load(build_if_missing=True):
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_set_coefficient.argtypes = [H, vp, vp]
     lib.srfmg_coef_gradient.argtypes = [H, vp, vp, vp, vp]
+    lib.srfmg_solve_functionals.argtypes = [H, vp, vp, vp, vp, vp]
+    lib.srfmg_reconstruct.argtypes = [H, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
-                 "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient"):
+                 "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
+                 "srfmg_solve_functionals", "srfmg_reconstruct"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -181,6 +185,42 @@ class Solver:
             raise ValueError("log_a must be a contiguous CUDA float64 tensor of batch * (2^log2_n + 1) values")
         self._check(self.lib.srfmg_set_coefficient(self.h, ctypes.c_void_p(log_a.data_ptr()), _stream_ptr(stream)),
                     "set_coefficient")
+
+    def solve_functionals(self, f, u=None, u_ref=None, out=None, stream=None):
+        """SR solve that returns the functionals of the fine solution, NUM_FUNCTIONALS
+        per problem: [h sum u, h sum u^2, max|u|, h sum (u - u_ref)^2, max|u - u_ref|]
+        (the last two 0 without u_ref).  u: CUDA float64 tensor to receive the
+        solution, or None to leave the fine grid unwritten."""
+        import torch
+        self._check_vec("f", f)
+        for name, t in (("u", u), ("u_ref", u_ref)):
+            if t is not None:
+                self._check_vec(name, t)
+        if out is None:
+            out = torch.empty(NUM_FUNCTIONALS * self.batch, dtype=torch.float64, device=f.device)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)
+        self._check(self.lib.srfmg_solve_functionals(self.h, ptr(f), ptr(u), ptr(u_ref), ptr(out),
+                                                     _stream_ptr(stream)), "solve_functionals")
+        return out
+
+    def reconstruct(self, f, seg_begin, seg_count, out=None, stream=None):
+        """Fine-grid segments [seg_begin, seg_begin + seg_count) expanded from the
+        coarse solution of the last solve (f: that solve's right-hand side);
+        returns seg_count * segment_width values per problem."""
+        import torch
+        self._check_vec("f", f)
+        n_out = seg_count * self.params.segment_width * self.batch
+        if out is None:
+            out = torch.empty(n_out, dtype=torch.float64, device=f.device)
+        self._check(self.lib.srfmg_reconstruct(self.h, ctypes.c_void_p(f.data_ptr()), seg_begin, seg_count,
+                                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+                    "reconstruct")
+        return out
+
+    def _check_vec(self, name, t):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == self.n * self.batch):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of batch * 2^log2_n values")
 
     def coef_gradient(self, u, lam, out=None, stream=None):
         """SRFMG_OP_VARCOEF: dL/dlog a at the 2^log2_n + 1 faces (per problem)
