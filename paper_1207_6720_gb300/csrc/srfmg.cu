@@ -606,7 +606,7 @@ cudaError_t enqueue_all(srfmg_plan *h, const Io &io, cudaStream_t s) {
         first = false;
     }
     if (io.fout)    // the segments' partials -> the functionals of each problem
-        return run(functionals_finish_kernel, dim3(1, (unsigned)h->batch), dim3(256), 0, s, true,
+        return run(functionals_finish_kernel, dim3(1, (unsigned)h->batch), dim3(kFinishThreads), 0, s, true,
                    (const double *)io.fpart, (int)(h->n / h->W), h->M, io.fout);
     return cudaSuccess;
 }

@@ -626,6 +626,95 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     }
 }
 
+// Sum of squares of non-negative fixed-point values A < 2^59 in integers:
+// V = A >> 8 split as V = 2^26 va + vb, V^2 = 2^52 va^2 + 2^27 va vb + vb^2 in
+// three 64-bit sums.  A thread adds at most 16 values (va^2 < 2^50 each);
+// norm() carries q0 into q1 and q1 into q2 (weights 2^27 and 2^25 apart), after
+// which 512 threads' sums stay below 2^63.  A^2 ~ 2^16 V^2: dropping 8 of A's
+// bits moves a square by at most 2^-50 of the largest.  value(S) is the sum of
+// (A 2^-S)^2 as a double.
+struct FxSquares {
+    u64 q0 = 0, q1 = 0, q2 = 0;
+    __device__ __forceinline__ void add(u64 A) {
+        const u64 V = A >> 8, va = V >> 26, vb = V & 0x3ffffffULL;
+        q2 += va * va;
+        q1 += va * vb;
+        q0 += vb * vb;
+    }
+    __device__ __forceinline__ void norm() {
+        q1 += q0 >> 27;
+        q0 &= (1ULL << 27) - 1;
+        q2 += q1 >> 25;
+        q1 &= (1ULL << 25) - 1;
+    }
+    __device__ __forceinline__ double value(int S) const {
+        return scale2(fma((double)q2, 4503599627370496.0, fma((double)q1, 134217728.0, (double)q0)), 16 - 2 * S);
+    }
+};
+
+// The functional state of one thread in integers: sum U in 128 bits (hi, lo),
+// max |U|, the squares; against the reference, max |D| and the squares of D;
+// e3, e4 the FP64 terms of references beyond the integer grid's range.
+struct FxFunc {
+    u64 lo = 0, mx = 0, mxd = 0;
+    i64 hi = 0;
+    FxSquares su, sd;
+    double e3 = 0.0, e4 = 0.0;
+};
+
+// Warp butterfly over the ten integer words of FxFunc (128-bit add with carry,
+// maxima, limb sums): exact, the same in every lane.
+__device__ __forceinline__ void fx_warp_reduce(u64 v[10]) {
+    for (int o = 16; o > 0; o >>= 1) {
+        u64 y[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) y[k] = __shfl_xor_sync(0xffffffffu, v[k], o);
+        const u64 lo = v[0] + y[0];
+        v[1] = v[1] + y[1] + (lo < v[0] ? 1ULL : 0ULL);
+        v[0] = lo;
+        v[2] = y[2] > v[2] ? y[2] : v[2];
+        v[6] = y[6] > v[6] ? y[6] : v[6];
+        v[3] += y[3]; v[4] += y[4]; v[5] += y[5];
+        v[7] += y[7]; v[8] += y[8]; v[9] += y[9];
+    }
+}
+
+// Reduce the block's FxFunc in integers (FP64 only for e3, e4, through the
+// integer-grid warp sums) and write the segment's kNumFunc partials from
+// thread 0.  Every thread of the block calls it once; blockDim.x <= 512.
+__device__ __forceinline__ void fx_block_functionals(FxFunc &t, int S, double *dst) {
+    __shared__ u64 red[10][16];
+    __shared__ double red64[2][16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    t.su.norm();
+    t.sd.norm();
+    u64 v[10] = {t.lo, (u64)t.hi, t.mx, t.su.q0, t.su.q1, t.su.q2, t.mxd, t.sd.q0, t.sd.q1, t.sd.q2};
+    fx_warp_reduce(v);
+    const double w3 = warp_sum(t.e3), w4 = warp_max_nonneg(t.e4);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) red[k][w] = v[k];
+        red64[0][w] = w3;
+        red64[1][w] = w4;
+    }
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) v[k] = lane < nw ? red[k][lane] : 0ULL;
+    fx_warp_reduce(v);
+    const double e3 = warp_sum(lane < nw ? red64[0][lane] : 0.0);
+    const double e4 = warp_max_nonneg(lane < nw ? red64[1][lane] : 0.0);
+    if (lane != 0) return;
+    FxSquares su, sd;
+    su.q0 = v[3]; su.q1 = v[4]; su.q2 = v[5];
+    sd.q0 = v[7]; sd.q1 = v[8]; sd.q2 = v[9];
+    dst[0] = scale2(fma((double)(i64)v[1], 18446744073709551616.0, (double)v[0]), -S);   // hi 2^64 + lo
+    dst[1] = su.value(S);
+    dst[2] = scale2((double)v[2], -S);
+    dst[3] = e3 + sd.value(S);
+    dst[4] = fmax(e4, scale2((double)v[6], -S));
+}
+
 // K6 in fixed point; output and functionals as in the FP64 kernel.
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
@@ -648,20 +737,45 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     const int S = (a.sc + blockIdx.y)->S;
     const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
     double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;
-    const double *ref = a.u_ref ? batch_at(a.u_ref, a.n) : nullptr;
-    FuncAcc q;
-    for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x) {
-        const double v = fixed_to_f64(p[i - m.lo], S);
-        if (u_out) u_out[i - s0] = v;
-        if (a.fpart) q.add(v, ref, i);
-    }
+    if (u_out)
+        for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
+            u_out[i - s0] = fixed_to_f64(p[i - m.lo], S);
     if (a.fpart) {
-        func_block_reduce(q);
-        if (threadIdx.x == 0) {
-            double *dst = batch_at(a.fpart, (long long)gridDim.x * kNumFunc) + (long long)blockIdx.x * kNumFunc;
-#pragma unroll
-            for (int k = 0; k < kNumFunc; ++k) dst[k] = q.v[k];
+        // The functionals in integer arithmetic (FxFunc): against a reference r,
+        // D = U - round(r 2^S) exactly on the fixed-point grid; a reference beyond
+        // that grid's range (|r| 2^S >= 2^59, or not finite) or a |D| >= 2^59
+        // takes FP64.
+        const bool ref = a.u_ref != nullptr;
+        if (ref) {   // the reference of the interior into the rhs array, which the sweeps are done with
+            __syncthreads();
+            stage_range(m.gs + (s - m.lo), batch_at(a.u_ref, a.n) + s, a.W);
+            stage_wait();
+            __syncthreads();
         }
+        FxFunc t;
+        for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x) {
+            const i64 U = p[i - m.lo];
+            t.lo += (u64)U;
+            t.hi += (U >> 63) + (t.lo < (u64)U ? 1 : 0);
+            const u64 A = (u64)(U < 0 ? -U : U);
+            t.mx = A > t.mx ? A : t.mx;
+            t.su.add(A);
+            if (ref) {
+                const double r = __longlong_as_double(m.gs[i - m.lo]);
+                const int e = (int)((__double_as_longlong(r) >> 52) & 0x7ff) - 1023;   // |r| < 2^(e+1)
+                const i64 D = (e + S <= 57) ? U - f64_to_fixed(r, S) : 0;
+                const u64 AD = (u64)(D < 0 ? -D : D);
+                if (e + S <= 57 && AD < (1ULL << 59)) {
+                    t.mxd = AD > t.mxd ? AD : t.mxd;
+                    t.sd.add(AD);
+                } else {
+                    const double d = fixed_to_f64(U, S) - r;
+                    t.e3 = fma(d, d, t.e3);
+                    t.e4 = fmax(t.e4, fabs(d));
+                }
+            }
+        }
+        fx_block_functionals(t, S, batch_at(a.fpart, (long long)gridDim.x * kNumFunc) + (long long)blockIdx.x * kNumFunc);
     }
 }
 

@@ -831,6 +831,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
 // order, so a solve gives the same bits on every run.
 // ---------------------------------------------------------------------------
 constexpr int kNumFunc = 5;
+constexpr int kFinishThreads = 1024;
 
 struct FuncAcc {
     double v[kNumFunc];
@@ -857,38 +858,80 @@ struct FuncAcc {
     }
 };
 
+// The reductions below keep FP64 instructions out of the shuffle trees: an FP64
+// warp instruction occupies this GPU's narrow FP64 pipe for many cycles, and a
+// butterfly over five values in every warp of every segment block cost more
+// than the post-leg itself.
+//
+// Maximum over the warp of non-negative doubles (or NaN) by their bit patterns,
+// which order like the values; NaN (above every finite value and inf) wins.
+__device__ __forceinline__ double warp_max_nonneg(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+        b = y > b ? y : b;
+    }
+    return __longlong_as_double((long long)b);
+}
+
+// round(x 2^k) of the bits b of a double, for |x| 2^k < 2^60 (zero and
+// subnormals give 0).
+__device__ __forceinline__ long long round_scaled_bits(long long b, int k) {
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = e - 1075 + k;
+    long long v;
+    if (sh >= 0) v = m << sh;
+    else if (sh > -63) v = (m + (1LL << (-sh - 1))) >> (-sh);
+    else v = 0;
+    return b < 0 ? -v : v;
+}
+
+// Sum over the warp: every lane's value on the integer grid 2^-k of the warp's
+// largest exponent (|v| < 2^56, so the 32-lane sum stays below 2^61), summed
+// exactly, one conversion back.  The rounding moves each term by at most
+// 2^-56 of the largest; the result (in every lane) does not depend on which
+// lane holds which term's neighbours.  A non-finite lane takes FP64 sums.
+__device__ __forceinline__ double warp_sum(double x) {
+    const long long b = __double_as_longlong(x);
+    const unsigned emax = __reduce_max_sync(0xffffffffu, (unsigned)((b >> 52) & 0x7ff));
+    if (emax == 0x7ff) {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    }
+    const int k = 1078 - (int)emax;                 // |x| < 2^(emax - 1022)
+    long long v = round_scaled_bits(b, k);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v == 0 ? 0.0 : scale2((double)v, -k);
+}
+
 // Reduce the block's accumulators (sums F0, F1, F3; maxima F2, F4) in a fixed
-// order; the result is valid in thread 0.  blockDim.x is a multiple of 32 and
-// every thread of the block calls it once.
+// order; the result is valid in thread 0.  blockDim.x is a multiple of 32, at
+// most 1024, and every thread of the block calls it once.
 __device__ __forceinline__ void func_block_reduce(FuncAcc &q) {
     __shared__ double red[kNumFunc][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < kNumFunc; ++k) {
-        double x = q.v[k];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = (k == 2 || k == 4) ? fmax(x, y) : x + y;
-        }
+        const double x = (k == 2 || k == 4) ? warp_max_nonneg(q.v[k]) : warp_sum(q.v[k]);
         if (lane == 0) red[k][w] = x;
     }
     __syncthreads();
     if (w == 0) {
 #pragma unroll
         for (int k = 0; k < kNumFunc; ++k) {
-            double x = lane < nw ? red[k][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double y = __shfl_xor_sync(0xffffffffu, x, o);
-                x = (k == 2 || k == 4) ? fmax(x, y) : x + y;
-            }
-            q.v[k] = x;
+            const double x = lane < nw ? red[k][lane] : 0.0;
+            q.v[k] = (k == 2 || k == 4) ? warp_max_nonneg(x) : warp_sum(x);
         }
     }
 }
 
 // Segment partials (nseg per problem, problem blockIdx.y) -> out[kNumFunc] per
-// problem; one block of 256 threads per problem.
-__global__ void functionals_finish_kernel(const double *fpart, int nseg, int M, double *out) {
+// problem; one block of kFinishThreads threads per problem (a few segments per
+// thread, so the chain of dependent loads and adds stays short).
+__global__ void __launch_bounds__(kFinishThreads) functionals_finish_kernel(const double *fpart, int nseg, int M,
+                                                                        double *out) {
     pdl_enter();
     const double *src = batch_at(fpart, (long long)nseg * kNumFunc);
     FuncAcc q;
@@ -1078,12 +1121,18 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     }
     const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
     double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;
-    const double *ref = a.u_ref ? batch_at(a.u_ref, a.n) : nullptr;
+    const bool ref = a.fpart && a.u_ref;
+    if (ref) {   // the reference of the interior into the rhs array, which the sweeps are done with
+        __syncthreads();
+        stage_range(m.g + (s - m.lo), batch_at(a.u_ref, a.n) + s, a.W);
+        stage_wait();
+        __syncthreads();
+    }
     FuncAcc q;
     for (int i = s + threadIdx.x; i < s + a.W; i += blockDim.x) {
         const double v = p[i - m.lo];
         if (u_out) u_out[i - s0] = v;
-        if (a.fpart) q.add(v, ref, i);
+        if (a.fpart) q.add(v, ref ? m.g : nullptr, i - m.lo);
     }
     if (a.fpart) {
         func_block_reduce(q);

@@ -104,6 +104,26 @@ def test_functionals_parity_gpu(M, W, b, precision):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", [srfmg.FP64, srfmg.MIXED])
+def test_functionals_with_a_reference_out_of_range_gpu(precision):
+    # the fixed-point path forms u - u_ref on its integer grid and takes FP64 for
+    # reference values beyond that grid's range: both kinds in one solve
+    pytest.importorskip("torch")
+    M, W, b = 12, 512, 8
+    f, ue, _ = workloads.sine_series(M, 16, seed=5)
+    ref = ue.copy()
+    ref[[3, 700, 2049, 4095]] = [1e20, -3e15, 7e100, 2.5]      # squares stay finite
+    s = srfmg.Solver(M, segment_width=W, buffer_width=b, precision=precision)
+    try:
+        F = s.solve_functionals(_dev(f), None, _dev(ref)).cpu().numpy()
+    finally:
+        s.close()
+    Fo = oracle.functionals(oracle.fmg_h(oracle.sr_params(M, W, b), f), ref)
+    assert abs(F[3] - Fo[3]) <= 1e-12 * Fo[3]
+    assert abs(F[4] - Fo[4]) <= 1e-12 * Fo[4]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [srfmg.FP64, srfmg.MIXED])
 def test_functionals_of_a_batch_equal_single_solves_gpu(precision):
     torch = pytest.importorskip("torch")
     M, W, b, B = 13, 512, 8, 3
