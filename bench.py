@@ -404,6 +404,14 @@ def run_gpu(a):
         sr64 = {"value": dist.world * N / (ms64 * 1e-3), "ms_per_step": ms64,
                 "err_max_vs_exact": float(np.max(np.abs(u64 - u_exact)))}
 
+    # two SR levels (levels M and M-1 segmented; Fig. 3 with a deeper SR set)
+    s2 = srfmg.Solver(M, device=dev, n_sr_levels=2, segment_width=W, buffer_width=b, precision=prec)
+    ms2 = dist.max(time_solves(s2, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
+    u2 = ud.cpu().numpy()
+    s2.close()
+    sr2 = {"value": dist.world * N / (ms2 * 1e-3), "ms_per_step": ms2,
+           "err_max_vs_exact": float(np.max(np.abs(u2 - u_exact)))}
+
     # autotuner (row f1): the fastest admissible segment layout for this solve
     best, table = srfmg.autotune(M, device=dev, reps=5, precision=prec)
     autotune = {"choice": {"segment_width": best.segment_width, "buffer_width": best.buffer_width},
@@ -507,6 +515,7 @@ def run_gpu(a):
                        "kernels_per_solve": plain_info.kernels_per_solve,
                        "speedup_over_plain": ms_plain / ms},
         "sr_fp64": sr64,
+        "sr_levels_2": sr2,
         "adjoint": adjoint,
         "functionals_only": functionals,
         "autotune": autotune,

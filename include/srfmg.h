@@ -73,7 +73,8 @@ typedef struct {
     int32_t precision;         /* srfmg_precision */
     int32_t log2_n;            /* M: N = 2^M fine cells, M0 < M <= 28 */
     int32_t log2_n_coarsest;   /* M0: coarsest level, solved exactly; 2 <= M0 <= 6 (default 2) */
-    int32_t n_sr_levels;       /* number of SR levels: 0 (plain stored FMG-FAS) or 1 */
+    int32_t n_sr_levels;       /* number of SR levels: 0 (plain stored FMG-FAS), 1 or 2 (the finest
+                                  levels; level M - l has segments of W >> l cells) */
     int32_t segment_width;     /* W: finest-level cells per segment; power of two, 16 <= W <= 4096, W <= N */
     int32_t buffer_width;      /* b: buffer cells per segment side; even, 2 <= b <= 64, b <= W */
     int32_t nu1, nu2;          /* V(nu1, nu2): 1 <= nu1, nu2 <= 4 */

@@ -133,16 +133,19 @@ std::string check_params(const srfmg_params *p) {
     if (p->smoother != SRFMG_SMOOTH_LEX) return "smoother must be SRFMG_SMOOTH_LEX";
     if (p->log2_n_coarsest < 2 || p->log2_n_coarsest > 6) return "log2_n_coarsest must be in [2, 6]";
     if (p->log2_n <= p->log2_n_coarsest || p->log2_n > 28) return "log2_n must be in (log2_n_coarsest, 28]";
-    if (p->n_sr_levels < 0 || p->n_sr_levels > 1) return "n_sr_levels must be 0 or 1";
+    if (p->n_sr_levels < 0 || p->n_sr_levels > 2) return "n_sr_levels must be 0, 1 or 2";
+    if (p->n_sr_levels == 2 && p->log2_n < p->log2_n_coarsest + 2)
+        return "two SR levels need log2_n >= log2_n_coarsest + 2 (a stored level below them)";
     if (p->nu1 < 1 || p->nu1 > 4 || p->nu2 < 1 || p->nu2 > 4) return "nu1 and nu2 must be in [1, 4]";
-    if (p->n_sr_levels == 1) {
+    if (p->n_sr_levels >= 1) {
         long long N = 1LL << p->log2_n;
         if (!pow2(p->segment_width) || p->segment_width < 16 || p->segment_width > 4096 ||
             p->segment_width > N)
             return "segment_width must be a power of two in [16, min(4096, N)]";
-        if (p->buffer_width < 2 || p->buffer_width > 64 || (p->buffer_width & 1) ||
-            p->buffer_width > p->segment_width)
-            return "buffer_width must be even, in [2, 64] and <= segment_width";
+        // the deepest SR level's segments are segment_width >> (n_sr_levels - 1) cells
+        const int wmin = p->segment_width >> (p->n_sr_levels - 1);
+        if (p->buffer_width < 2 || p->buffer_width > 64 || (p->buffer_width & 1) || p->buffer_width > wmin)
+            return "buffer_width must be even, in [2, 64] and <= the segment width of every SR level";
     }
     return "";
 }
@@ -254,22 +257,34 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     return o;
 }
 
-Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, double *gc_out) {
+// A segment pass on the SR level L (segments of W >> (M - L) cells with b
+// buffer cells).  On the finest level the rhs is f and the post-leg writes the
+// caller's u; below it the rhs is the stored g_in = glev[L] and the post-leg
+// writes the level array u_out.  u_in: the assembled iterate of a down-leg
+// pre-pass (no FMG interpolation).
+Op seg_op(srfmg_plan *h, OpKind kind, int L, const double *uc_src, double *uc_out, double *gc_out,
+          const double *g_in, const double *u_in, double *u_out) {
     Op o = make_op(kind);
-    o.level = h->M;
-    o.seg.M = h->M;
-    o.seg.n = 1 << h->M;
-    o.seg.W = h->W;
+    const int W = h->W >> (h->M - L);
+    o.level = L;
+    o.seg.M = L;
+    o.seg.n = 1 << L;
+    o.seg.W = W;
     o.seg.b = h->b;
     o.seg.nu = (kind == OP_SR_POST) ? h->p.nu2 : h->p.nu1;
     o.seg.uc_src = uc_src;
     o.seg.uc_out = uc_out;
     o.seg.gc_out = gc_out;
+    o.seg.g_in = g_in;
+    o.seg.u_in = u_in;
+    o.seg.u_out = u_out;
     o.seg.seam = h->seam;
     o.seg.lam = op_lambda(h);
-    o.seg.coef = h->coef[h->M];
-    o.seg_f = TAG_F;
-    if (kind == OP_SR_POST) o.seg_u = TAG_U;
+    o.seg.coef = h->coef[L];
+    if (L == h->M) {
+        o.seg_f = TAG_F;
+        if (kind == OP_SR_POST) o.seg_u = TAG_U;
+    }
     o.nseg = (int)(h->n / h->W);
     if (kind == OP_SEAM) {
         o.grid = dim3((o.nseg + 127) / 128);
@@ -278,8 +293,7 @@ Op seg_op(srfmg_plan *h, OpKind kind, const double *uc_src, double *uc_out, doub
     } else {
         int threads;
         o.grid = dim3(o.nseg);
-        o.smem = sweep_layout(h->W + 2 * h->b, &o.seg.maxlen, &o.seg.maxc, &o.seg.maxch, &threads) *
-                 sizeof(double);
+        o.smem = sweep_layout(W + 2 * h->b, &o.seg.maxlen, &o.seg.maxc, &o.seg.maxch, &threads) * sizeof(double);
         o.block = dim3(threads);
     }
     return o;
@@ -345,6 +359,9 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.fseg.uc_out = (i64 *)o.seg.uc_out;
         o.fseg.gc_out = (i64 *)o.seg.gc_out;
         o.fseg.seam = (i64 *)o.seg.seam;
+        o.fseg.g_in = (const i64 *)o.seg.g_in;
+        o.fseg.u_in = (const i64 *)o.seg.u_in;
+        o.fseg.u_out_fx = (i64 *)o.seg.u_out;   // a level below the finest (the finest: patched per solve)
         break;
     case OP_TAIL:
         o.ftail.M0 = o.tail.M0; o.ftail.Mc = o.tail.Mc; o.ftail.nu1 = o.tail.nu1; o.ftail.nu2 = o.tail.nu2;
@@ -414,9 +431,9 @@ void build_schedule_ops(srfmg_plan *h) {
         }
     };
 
-    const int last_stored = (h->nRS == 1) ? M - 1 : M;
+    const int R = M - h->nRS;          // the highest stored level below the SR levels
     // FMG steps whose top level is a stored level below the finest
-    for (int k = Mc; k < M - 1; ++k) {
+    for (int k = Mc; k < (h->nRS ? R : M - 1); ++k) {
         int top = k + 1;
         h->ops.push_back(level_op(h, OP_DOWN_PI, top, U(k), nullptr, Unext(top), Unext(k), h->glev[k]));
         cur[top] ^= 1;
@@ -425,13 +442,34 @@ void build_schedule_ops(srfmg_plan *h) {
         h->ops.push_back(level_op(h, OP_UP, top, U(top), U(k), Unext(top), nullptr, nullptr));
         cur[top] ^= 1;
     }
-    // last step: top level M
-    if (h->nRS == 1) {
-        h->ops.push_back(seg_op(h, OP_SR_PRE, U(M - 1), Unext(M - 1), h->glev[M - 1]));
-        cur[M - 1] ^= 1;
-        h->ops.push_back(seg_op(h, OP_SEAM, nullptr, U(M - 1), h->glev[M - 1]));
-        vcycle_below(M - 1);
-        h->ops.push_back(seg_op(h, OP_SR_POST, U(M - 1), nullptr, nullptr));
+    if (h->nRS >= 1) {
+        // FMG steps whose top T is an SR level (Fig. 3): the top's pre-leg from
+        // Pi u_{T-1}; the SR levels below it from their assembled iterates; the
+        // stored V-cycle; the post-legs (full update + compatible relaxation)
+        // of the SR levels from the bottom up, the finest writing the caller's u
+        for (int T = R + 1; T <= M; ++T) {
+            const double *gT = (T == M) ? nullptr : h->glev[T];
+            h->ops.push_back(seg_op(h, OP_SR_PRE, T, U(T - 1), Unext(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
+            cur[T - 1] ^= 1;
+            h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, U(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
+            for (int L = T - 1; L > R; --L) {
+                h->ops.push_back(seg_op(h, OP_SR_PRE, L, nullptr, Unext(L - 1), h->glev[L - 1], h->glev[L], U(L),
+                                        nullptr));
+                cur[L - 1] ^= 1;
+                h->ops.push_back(seg_op(h, OP_SEAM, L, nullptr, U(L - 1), h->glev[L - 1], h->glev[L], nullptr, nullptr));
+            }
+            vcycle_below(R);
+            for (int L = R + 1; L < T; ++L) {
+                h->ops.push_back(seg_op(h, OP_SR_POST, L, U(L - 1), nullptr, nullptr, h->glev[L], nullptr, Unext(L)));
+                cur[L] ^= 1;
+            }
+            if (T == M) {
+                h->ops.push_back(seg_op(h, OP_SR_POST, M, U(M - 1), nullptr, nullptr, nullptr, nullptr, nullptr));
+            } else {
+                h->ops.push_back(seg_op(h, OP_SR_POST, T, U(T - 1), nullptr, nullptr, h->glev[T], nullptr, Unext(T)));
+                cur[T] ^= 1;
+            }
+        }
     } else {
         // level M stored in ulev[M][0]; the up pass writes the user's u
         h->ops.push_back(level_op(h, OP_DOWN_PI, M, U(M - 1), nullptr, h->ulev[M][0], Unext(M - 1),
@@ -442,7 +480,6 @@ void build_schedule_ops(srfmg_plan *h) {
         o.lev_out = TAG_U;
         h->ops.push_back(o);
     }
-    (void)last_stored;
 }
 
 void build_schedule(srfmg_plan *h) {
@@ -717,8 +754,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         if (st == SRFMG_OK) st = alloc_dev(h, &h->ulev[l][1], B << l);
         if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], B << l);
     }
-    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->seam, B * (h->n / h->W) * 6);
-    if (st == SRFMG_OK && h->nRS == 1) st = alloc_dev(h, &h->fpart, B * (h->n / h->W) * kNumFunc);
+    if (st == SRFMG_OK && h->nRS >= 1) st = alloc_dev(h, &h->seam, B * (h->n / h->W) * 6);
+    if (st == SRFMG_OK && h->nRS >= 1) st = alloc_dev(h, &h->fpart, B * (h->n / h->W) * kNumFunc);
     if (st == SRFMG_OK && h->fixed) {
         double *sc = nullptr;
         st = alloc_dev(h, &sc, 2 * B);
@@ -829,8 +866,8 @@ srfmg_status srfmg_solve(srfmg_handle h, const double *f, double *u, void *strea
 srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u, const double *u_ref,
                                      double *functionals, void *stream) {
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
-    if (h->nRS != 1)
-        return fail(h, SRFMG_EUNSUPPORTED, "functionals are collected by the SR post-leg: the plan needs n_sr_levels = 1");
+    if (h->nRS < 1)
+        return fail(h, SRFMG_EUNSUPPORTED, "functionals are collected by the SR post-leg: the plan needs an SR level");
     if (!f || !functionals) return fail(h, SRFMG_EINVAL, "f and functionals must be device pointers");
     if (((uintptr_t)f & 15) || ((uintptr_t)u & 15) || ((uintptr_t)u_ref & 7) || ((uintptr_t)functionals & 7))
         return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned, u_ref and functionals 8-byte aligned");
@@ -846,7 +883,7 @@ srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u,
 srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begin, int32_t seg_count,
                                double *u_seg, void *stream) {
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
-    if (h->nRS != 1) return fail(h, SRFMG_EUNSUPPORTED, "reconstruction expands SR segments: the plan needs n_sr_levels = 1");
+    if (h->nRS < 1) return fail(h, SRFMG_EUNSUPPORTED, "reconstruction expands SR segments: the plan needs an SR level");
     if (!h->solved) return fail(h, SRFMG_EINVAL, "no solve has been enqueued on this plan");
     const int nseg = (int)(h->n / h->W);
     if (seg_begin < 0 || seg_count < 1 || seg_begin > nseg - seg_count)

@@ -505,9 +505,12 @@ struct SegArgs {
     int maxlen, maxc, maxch;
     int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
     const Scale *sc;
-    const double *f;
+    const double *f;           // the finest level's rhs
+    const i64 *g_in;           // SR level below the finest: its rhs G_M (then f is unused)
+    const i64 *u_in;           // pre-leg of an SR level below the top: its assembled iterate (no Pi)
     const i64 *uc_src;
     i64 *uc_out, *gc_out, *seam;
+    i64 *u_out_fx;             // post-leg of an SR level below the finest: U of the level
     double *u_out;             // post-leg: FP64 solution of segments seg0.. (NULL: not written)
     const double *u_ref;       // post-leg: reference for the functionals (NULL: none)
     double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
@@ -538,28 +541,34 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
     return m;
 }
 
-// Stage Pi U_{M-1} on [lo, hi) and the right-hand side: gs = G >> (2M-2) in
-// solution units with G converted from f; with gr, also the restricted
+// Stage the patch [lo, hi) of an SR level M: the iterate Pi U_{M-1} (or, with
+// u_in, the assembled iterate of a level below the top, in the down leg) and
+// the right-hand side gs = G >> (2M-2) in solution units, G converted from f
+// on the finest level or read from g_in below it; with gr, also the restricted
 // right-hand side of the segment's coarse cells [J0, J1).  The staged range
 // may start at an odd cell, so pairs are clipped to it.
 __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) {
     const int nc = a.n >> 1, kg = (a.sc + blockIdx.y)->Sg0, gsh = 2 * a.M - 2;
-    stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
-    stage_range(m.gs, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
+    const bool from_f = (a.g_in == nullptr);
+    if (a.u_in) stage_range(m.u, batch_at(a.u_in, a.n) + m.lo, m.hi - m.lo);
+    else stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
+    if (from_f) stage_range(m.gs, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
+    else stage_range(m.gs, batch_at(a.g_in, a.n) + m.lo, m.hi - m.lo);
     stage_wait();
     __syncthreads();
-    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
+    if (!a.u_in) fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         const int i0 = 2 * J;
         const bool in0 = i0 >= m.lo, in1 = i0 + 1 < m.hi;
         const i64 f0 = m.gs[max(i0 - m.lo, 0)], f1 = m.gs[min(i0 + 1 - m.lo, m.hi - 1 - m.lo)];
-        const i64 g0 = f64_to_fixed(__longlong_as_double(f0), kg);
-        const i64 g1 = f64_to_fixed(__longlong_as_double(f1), kg);
+        const i64 g0 = from_f ? f64_to_fixed(__longlong_as_double(f0), kg) : f0;
+        const i64 g1 = from_f ? f64_to_fixed(__longlong_as_double(f1), kg) : f1;
         if (gr && J >= J0 && J < J1) gr[J - J0] = restrict_rhs(g0, g1);
         if (in0) m.gs[i0 - m.lo] = shr_round(g0, gsh);
         if (in1) m.gs[i0 + 1 - m.lo] = shr_round(g1, gsh);
     }
     __syncthreads();
+    if (a.u_in) return;
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         i64 l, r;
         fmg_interp2(m.c, m.C0, J, l, r);
@@ -608,6 +617,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     const int kg = (a.sc + blockIdx.y)->Sg0, tsh = 2 * a.M - 4;
     const i64 *seam = batch_at(a.seam, 6LL * nseg);
     const double *f = batch_at(a.f, a.n);
+    const i64 *gl = a.g_in ? batch_at(a.g_in, a.n) : nullptr;      // G of a level below the finest
     i64 *uc_out = batch_at(a.uc_out, a.n / 2), *gc_out = batch_at(a.gc_out, a.n / 2);
     const i64 *L = seam + (size_t)k * 6, *R = seam + (size_t)(k + 1) * 6;
     const i64 f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
@@ -615,13 +625,13 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     const i64 hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
     {
         i64 tau = ((h0 - hm1) - (h1 - h0)) - 2 * ((f2 - f3) - (p0 - f1));
-        i64 g0 = f64_to_fixed(f[2 * J], kg), g1 = f64_to_fixed(f[2 * J + 1], kg);
+        i64 g0 = gl ? gl[2 * J] : f64_to_fixed(f[2 * J], kg), g1 = gl ? gl[2 * J + 1] : f64_to_fixed(f[2 * J + 1], kg);
         gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
     }
     {
         const int J2 = J + 1;
         i64 tau = ((h1 - h0) - (h2 - h1)) - 2 * ((p0 - f1) - (p2 - p1));
-        i64 g0 = f64_to_fixed(f[2 * J2], kg), g1 = f64_to_fixed(f[2 * J2 + 1], kg);
+        i64 g0 = gl ? gl[2 * J2] : f64_to_fixed(f[2 * J2], kg), g1 = gl ? gl[2 * J2 + 1] : f64_to_fixed(f[2 * J2 + 1], kg);
         gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
     }
 }
@@ -740,6 +750,10 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     if (u_out)
         for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
             u_out[i - s0] = fixed_to_f64(p[i - m.lo], S);
+    if (a.u_out_fx) {
+        i64 *uo = batch_at(a.u_out_fx, a.n);
+        for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x) uo[i] = p[i - m.lo];
+    }
     if (a.fpart) {
         // The functionals in integer arithmetic (FxFunc): against a reference r,
         // D = U - round(r 2^S) exactly on the fixed-point grid; a reference beyond

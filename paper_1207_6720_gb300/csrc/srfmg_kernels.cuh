@@ -952,7 +952,9 @@ struct SegArgs {
     int M, n, W, b, nu;
     int maxlen, maxc, maxch;   // shared-memory layout sizes (doubles)
     int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
-    const double *f;           // right-hand side, unscaled
+    const double *f;           // right-hand side, unscaled (the finest level)
+    const double *g_in;        // SR level below the finest: its scaled rhs g_M (then f is unused)
+    const double *u_in;        // pre-leg of an SR level below the top: its assembled iterate (no Pi)
     const double *uc_src;      // level M-1
     double *uc_out;            // pre-leg: restricted solution on level M-1
     double *gc_out;            // pre-leg: tau-corrected g_{M-1}
@@ -989,17 +991,24 @@ __device__ __forceinline__ SegSmem seg_smem(double *sm, const SegArgs &a, int s)
     return m;
 }
 
-// Load Pi u_{M-1} on [lo, hi) (patch and frozen cells) and the scaled rhs.
+// Load the patch [lo, hi) (patch and frozen cells) of an SR level M: the
+// iterate Pi u_{M-1} (or, with u_in, the assembled iterate of a level below
+// the top, in the down leg) and the scaled rhs (f 2^-2M on the finest level,
+// g_in on the levels below it).
 __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     const int nc = a.n >> 1;
-    stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
-    stage_range(m.g, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
+    if (a.u_in) stage_range(m.u, batch_at(a.u_in, a.n) + m.lo, m.hi - m.lo);
+    else stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
+    if (a.g_in) stage_range(m.g, batch_at(a.g_in, a.n) + m.lo, m.hi - m.lo);
+    else stage_range(m.g, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
     if (a.coef) stage_range(m.a, batch_at(a.coef, a.n + 1) + m.lo, m.hi - m.lo + 1);
     stage_wait();
     __syncthreads();
+    if (a.u_in) return;
     fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
-    for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
-        m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
+    if (!a.g_in)
+        for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
+            m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
     __syncthreads();
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         double l, r;
@@ -1058,7 +1067,10 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg - 1) return;
-    const double *seam = batch_at(a.seam, 6LL * nseg), *f = batch_at(a.f, a.n);
+    const double *seam = batch_at(a.seam, 6LL * nseg);
+    // restricted rhs R g of the coarse cell J' from the level's rhs (f 2^-2M, or g_in)
+    const double *rf = a.g_in ? batch_at(a.g_in, a.n) : batch_at(a.f, a.n);
+    const int rexp = a.g_in ? 1 : 1 - 2 * a.M;
     double *uc_out = batch_at(a.uc_out, a.n / 2), *gc_out = batch_at(a.gc_out, a.n / 2);
     const int s = (k + 1) * a.W;
     const double *L = seam + (size_t)k * 6, *R = seam + (size_t)(k + 1) * 6;
@@ -1081,7 +1093,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         if (OP == kOpVarcoef) { Gl *= am; Fl *= am; Gr *= a0; Fr *= a0; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
         if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
-        gc_out[J] = scale2(f[2 * J] + f[2 * J + 1], 1 - 2 * a.M) + tau;
+        gc_out[J] = scale2(rf[2 * J] + rf[2 * J + 1], rexp) + tau;
     }
     {
         int J2 = J + 1;
@@ -1090,7 +1102,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         if (OP == kOpVarcoef) { Gl *= a0; Fl *= a0; Gr *= ap; Fr *= ap; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
         if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
-        gc_out[J2] = scale2(f[2 * J2] + f[2 * J2 + 1], 1 - 2 * a.M) + tau;
+        gc_out[J2] = scale2(rf[2 * J2] + rf[2 * J2 + 1], rexp) + tau;
     }
 }
 

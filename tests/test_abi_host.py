@@ -41,7 +41,7 @@ def test_default_params():
 
 @pytest.mark.parametrize("field,value", [
     ("log2_n", 2), ("log2_n", 29), ("log2_n_coarsest", 1), ("log2_n_coarsest", 7),
-    ("n_sr_levels", 2), ("n_sr_levels", -1), ("segment_width", 24), ("segment_width", 8),
+    ("n_sr_levels", 3), ("n_sr_levels", -1), ("segment_width", 24), ("segment_width", 8),
     ("segment_width", 8192), ("buffer_width", 3), ("buffer_width", 0), ("buffer_width", 66),
     ("nu1", 0), ("nu2", 5), ("op", 3), ("smoother", 1), ("precision", 7),
 ])
@@ -54,6 +54,20 @@ def test_create_rejects_bad_params_before_cuda(field, value):
     assert st == srfmg.EINVAL
     assert h.value is None
     assert lib.srfmg_last_error(None)
+
+
+@pytest.mark.parametrize("overrides", [
+    dict(n_sr_levels=2, log2_n=5, log2_n_coarsest=4),              # no stored level below the SR levels
+    dict(n_sr_levels=2, segment_width=16, buffer_width=10),        # buffer wider than level M-1's 8-cell segments
+])
+def test_two_sr_levels_are_checked_before_cuda(overrides):
+    lib = srfmg.load()
+    p = srfmg.default_params(12)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p(1)
+    assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL
+    assert h.value is None
 
 
 def test_create_rejects_reserved_and_null():
