@@ -117,10 +117,14 @@ __device__ __forceinline__ i64 div3(i64 x) {
 // into a chunk is the fixed sum over the chunks that reach 64 cells back: a
 // shift by 64 or more leaves nothing of a 63-bit value, so dropping those
 // terms changes nothing.  Integer sums are exact, so the residual is written
-// gs + u_{q-1} + u_{q+1} - 2 u_q in either direction.
-template <int C, bool PRELOAD, bool ASC>
+// gs + u_{q-1} + u_{q+1} - 2 u_q in either direction.  SHIFT: gs holds the
+// level's G and each value is moved into solution units on load,
+// shr_round(G, gsh) (the same values as a pre-shifted array, without the pass
+// that would form it).
+template <int C, bool PRELOAD, bool ASC, bool SHIFT = false>
 __device__ __noinline__ void lex_sweep_dir(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo,
-                                              int hi, int n, i64 *X) {
+                                              int hi, int n, i64 *X, int gsh = 0) {
+    auto G = [gsh](i64 x) { return SHIFT ? shr_round(x, gsh) : x; };
     constexpr int s = ASC ? 1 : -1;                // sweep position q is u[a0 + s q]
     const int t = threadIdx.x;
     const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
@@ -146,17 +150,17 @@ __device__ __noinline__ void lex_sweep_dir(i64 *__restrict__ u, const i64 *__res
             for (int j = 0; j < C + 2; ++j) w[j] = up[s * j];
 #pragma unroll
             for (int k = 0; k < C; ++k) {
-                p = (gp[s * k] + w[k] + w[k + 2] - 2 * w[k + 1] + p + 1) >> 1;
+                p = (G(gp[s * k]) + w[k] + w[k + 2] - 2 * w[k + 1] + p + 1) >> 1;
                 rr[k] = p;
             }
         } else {
 #pragma unroll
             for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
-            if (wall0) p = div3(gs[a0] + w[2] - 3 * w[1]);
-            if (wall1) r_end = gs[a0 + s * (n - 1)] + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
+            if (wall0) p = div3(G(gs[a0]) + w[2] - 3 * w[1]);
+            if (wall1) r_end = G(gs[a0 + s * (n - 1)]) + u[a0 + s * (n - 2)] - 3 * u[a0 + s * (n - 1)];
             i64 gv[C];
 #pragma unroll
-            for (int k = 0; k < C; ++k) gv[k] = gs[a0 + s * min(max(q0 + k, qmin), qmax)];
+            for (int k = 0; k < C; ++k) gv[k] = G(gs[a0 + s * min(max(q0 + k, qmin), qmax)]);
 #pragma unroll
             for (int k = 0; k < C; ++k) {
                 const i64 r = gv[k] + w[k] + w[k + 2] - 2 * w[k + 1];
@@ -215,11 +219,11 @@ __device__ __noinline__ void lex_sweep_dir(i64 *__restrict__ u, const i64 *__res
     __syncthreads();
 }
 
-template <int C, bool PRELOAD = false>
+template <int C, bool PRELOAD = false, bool SHIFT = false>
 __device__ __forceinline__ void lex_sweep(i64 *__restrict__ u, const i64 *__restrict__ gs, int base, int lo,
-                                          int hi, int n, bool asc, i64 *X) {
-    if (asc) lex_sweep_dir<C, PRELOAD, true>(u, gs, base, lo, hi, n, X);
-    else lex_sweep_dir<C, PRELOAD, false>(u, gs, base, lo, hi, n, X);
+                                          int hi, int n, bool asc, i64 *X, int gsh = 0) {
+    if (asc) lex_sweep_dir<C, PRELOAD, true, SHIFT>(u, gs, base, lo, hi, n, X, gsh);
+    else lex_sweep_dir<C, PRELOAD, false, SHIFT>(u, gs, base, lo, hi, n, X, gsh);
 }
 
 // tau-corrected coarse right-hand side (Eqs. 6-7), exact: the tau term is a
@@ -814,13 +818,12 @@ struct TailSmem {
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
 };
 
+// nu sweeps of level l on G_l directly (the sweep shifts it into solution units)
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     i64 *u = m.u + m.off(l);
     const i64 *g = m.g + m.off(l);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m.S[i] = shr_round(g[i], 2 * l - 2);
-    __syncthreads();
-    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true>(u, m.S, 0, 0, n, n, (k & 1) == 0, m.X);
+    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true, true>(u, g, 0, 0, n, n, (k & 1) == 0, m.X, 2 * l - 2);
 }
 
 __device__ void tail_down(TailSmem &m, int l, int nu) {
