@@ -66,6 +66,15 @@ typedef enum {
 typedef enum { SRFMG_OP_LAPLACE = 0, SRFMG_OP_VARCOEF = 1, SRFMG_OP_BRATU = 2 } srfmg_op;
 typedef enum { SRFMG_FP64 = 0, SRFMG_MIXED = 1 } srfmg_precision;
 typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
+/* Where the tau correction of a segment's two edge coarse cells comes from
+ * (SR levels; Fig. 3 forms tau from each segment's smoothed extended patch,
+ * the paper's program from the assembled level, which the paper states has
+ * the same semantics): SRFMG_TAU_ASSEMBLED (default) uses the neighbouring
+ * segments' interior values, exchanged through a seam pass;
+ * SRFMG_TAU_SEGMENT uses the segment's own buffer cells (fully local, no
+ * exchange; at large N its rounding-level mismatch with the assembled
+ * restriction grows like N^2). */
+typedef enum { SRFMG_TAU_ASSEMBLED = 0, SRFMG_TAU_SEGMENT = 1 } srfmg_tau_edge;
 
 /* Solve parameters (the paper's problem statement and cycle type). */
 typedef struct {
@@ -82,7 +91,8 @@ typedef struct {
     double lambda;             /* SRFMG_OP_BRATU: lambda >= 0, finite; must be 0 otherwise */
     int32_t batch;             /* independent problems of this size solved together, in
                                   [0, 65535] (0 means 1); see srfmg_solve */
-    int32_t reserved[3];       /* must be zero */
+    int32_t tau_edge;          /* srfmg_tau_edge (SR levels only; 0 without SR) */
+    int32_t reserved[2];       /* must be zero */
 } srfmg_params;
 
 /* Information about a created plan. */

@@ -122,7 +122,10 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
-    for (int i = 0; i < 3; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    for (int i = 0; i < 2; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->tau_edge != SRFMG_TAU_SEGMENT)
+        return "tau_edge must be SRFMG_TAU_ASSEMBLED or SRFMG_TAU_SEGMENT";
+    if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->n_sr_levels == 0) return "tau_edge applies to SR levels only";
     if (p->batch < 0 || p->batch > 65535) return "batch must be in [0, 65535] (0 means 1)";
     if (p->op != SRFMG_OP_LAPLACE && p->op != SRFMG_OP_BRATU && p->op != SRFMG_OP_VARCOEF)
         return "op must be SRFMG_OP_LAPLACE, SRFMG_OP_VARCOEF or SRFMG_OP_BRATU";
@@ -281,6 +284,7 @@ Op seg_op(srfmg_plan *h, OpKind kind, int L, const double *uc_src, double *uc_ou
     o.seg.seam = h->seam;
     o.seg.lam = op_lambda(h);
     o.seg.coef = h->coef[L];
+    o.seg.local_tau = (h->p.tau_edge == SRFMG_TAU_SEGMENT);
     if (L == h->M) {
         o.seg_f = TAG_F;
         if (kind == OP_SR_POST) o.seg_u = TAG_U;
@@ -362,6 +366,7 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.fseg.g_in = (const i64 *)o.seg.g_in;
         o.fseg.u_in = (const i64 *)o.seg.u_in;
         o.fseg.u_out_fx = (i64 *)o.seg.u_out;   // a level below the finest (the finest: patched per solve)
+        o.fseg.local_tau = o.seg.local_tau;
         break;
     case OP_TAIL:
         o.ftail.M0 = o.tail.M0; o.ftail.Mc = o.tail.Mc; o.ftail.nu1 = o.tail.nu1; o.ftail.nu2 = o.tail.nu2;
@@ -451,12 +456,15 @@ void build_schedule_ops(srfmg_plan *h) {
             const double *gT = (T == M) ? nullptr : h->glev[T];
             h->ops.push_back(seg_op(h, OP_SR_PRE, T, U(T - 1), Unext(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
             cur[T - 1] ^= 1;
-            h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, U(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
+            if (h->p.tau_edge == SRFMG_TAU_ASSEMBLED)
+                h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, U(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
             for (int L = T - 1; L > R; --L) {
                 h->ops.push_back(seg_op(h, OP_SR_PRE, L, nullptr, Unext(L - 1), h->glev[L - 1], h->glev[L], U(L),
                                         nullptr));
                 cur[L - 1] ^= 1;
-                h->ops.push_back(seg_op(h, OP_SEAM, L, nullptr, U(L - 1), h->glev[L - 1], h->glev[L], nullptr, nullptr));
+                if (h->p.tau_edge == SRFMG_TAU_ASSEMBLED)
+                    h->ops.push_back(seg_op(h, OP_SEAM, L, nullptr, U(L - 1), h->glev[L - 1], h->glev[L], nullptr,
+                                            nullptr));
             }
             vcycle_below(R);
             for (int L = R + 1; L < T; ++L) {

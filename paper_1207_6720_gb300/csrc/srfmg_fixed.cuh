@@ -508,6 +508,7 @@ struct SegArgs {
     int M, n, W, b, nu;
     int maxlen, maxc, maxch;
     int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
+    int local_tau;             // pre-leg: tau of the edge coarse cells from the own patch (no seam pass)
     const Scale *sc;
     const double *f;           // the finest level's rhs
     const i64 *g_in;           // SR level below the finest: its rhs G_M (then f is unused)
@@ -597,7 +598,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) {
         int i0 = 2 * J - m.lo;
         uc_out[J] = (u[i0] + u[i0 + 1]) >> 1;
-        bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
+        bool edge = !a.local_tau && ((J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1));
         if (!edge) {
             i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
             i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;

@@ -952,6 +952,7 @@ struct SegArgs {
     int M, n, W, b, nu;
     int maxlen, maxc, maxch;   // shared-memory layout sizes (doubles)
     int seg0;                  // post-leg: first segment (block x handles segment seg0 + x)
+    int local_tau;             // pre-leg: tau of the edge coarse cells from the own patch (no seam pass)
     const double *f;           // right-hand side, unscaled (the finest level)
     const double *g_in;        // SR level below the finest: its scaled rhs g_M (then f is unused)
     const double *u_in;        // pre-leg of an SR level below the top: its assembled iterate (no Pi)
@@ -1022,7 +1023,9 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
 // K5: pre-smoothing leg of the SR level (Fig. 3 lines 1-5): Pi, nu1 sweeps on
 // the extended patch, restricted solution on the segment's coarse cells, tau
 // rhs on the coarse cells whose stencil lies in the segment, seam values for
-// the two edge cells (formed from the assembled level by seam_tau_kernel).
+// the two edge cells (formed from the assembled level by seam_tau_kernel);
+// with local_tau the edge cells' tau too, from the patch's own buffer cells
+// (Fig. 3 line 4 read literally; b >= 2 keeps their stencil in the patch).
 template <int OP>
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
@@ -1040,7 +1043,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
         int i0 = 2 * J - m.lo;
         uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
-        bool edge = (J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1);
+        bool edge = !a.local_tau && ((J == J0 && J > 0) || (J == J1 - 1 && J < nc - 1));
         if (!edge) {
             double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
             double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;

@@ -15,6 +15,7 @@ STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_E
                 4: "SRFMG_ETIMEOUT", 5: "SRFMG_ENONFINITE", 6: "SRFMG_EUNSUPPORTED"}
 FP64, MIXED = 0, 1
 LAPLACE, VARCOEF, BRATU = 0, 1, 2
+TAU_ASSEMBLED, TAU_SEGMENT = 0, 1
 NUM_FUNCTIONALS = 5          # functionals per problem of srfmg_solve_functionals
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
@@ -29,7 +30,8 @@ class Params(ctypes.Structure):
         "op", "precision", "log2_n", "log2_n_coarsest", "n_sr_levels", "segment_width",
         "buffer_width", "nu1", "nu2", "smoother")] + [("lambda_", ctypes.c_double),
                                                       ("batch", ctypes.c_int32),
-                                                      ("reserved", ctypes.c_int32 * 3)]
+                                                      ("tau_edge", ctypes.c_int32),
+                                                      ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):

@@ -59,6 +59,8 @@ def test_create_rejects_bad_params_before_cuda(field, value):
 @pytest.mark.parametrize("overrides", [
     dict(n_sr_levels=2, log2_n=5, log2_n_coarsest=4),              # no stored level below the SR levels
     dict(n_sr_levels=2, segment_width=16, buffer_width=10),        # buffer wider than level M-1's 8-cell segments
+    dict(tau_edge=2),                                               # no such edge-tau reading
+    dict(tau_edge=1, n_sr_levels=0),                                # edge tau without SR segments
 ])
 def test_two_sr_levels_are_checked_before_cuda(overrides):
     lib = srfmg.load()

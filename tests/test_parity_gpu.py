@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1207_6720_gb300 import workloads
+from paper_1207_6720_gb300 import srfmg, workloads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -113,3 +113,47 @@ def test_launch_count_reported():
         assert inf.kernels_per_solve > 20
     finally:
         s.close()
+
+
+# SRFMG_TAU_SEGMENT: the edge coarse cells' tau from each segment's own buffer
+# (Fig. 3 line 4 read literally) against the oracle's tau_src="segment"
+SEGMENT_TAU_CASES = [
+    # (M, nRS, W, b, op)
+    (10, 1, 256, 4, "laplace"),
+    (14, 1, 1024, 8, "laplace"),
+    (17, 1, 4096, 2, "laplace"),
+    (13, 2, 512, 8, "laplace"),
+    (13, 1, 512, 8, "bratu"),
+    (13, 2, 512, 8, "varcoef"),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [srfmg.FP64, srfmg.MIXED])
+@pytest.mark.parametrize("M,nRS,W,b,op", SEGMENT_TAU_CASES)
+def test_segment_local_tau_parity_gpu(M, nRS, W, b, op, precision):
+    torch = pytest.importorskip("torch")
+    if op != "laplace" and precision == srfmg.MIXED:
+        pytest.skip("Bratu and the variable coefficient run in FP64 only")
+    kw, okw, log_a = {}, {}, None
+    if op == "bratu":
+        f, _, _ = workloads.bratu_series(M, 16, seed=M, lam=1.0)
+        kw, okw = dict(op=srfmg.BRATU, lambda_=1.0), dict(op="bratu", lam=1.0)
+    elif op == "varcoef":
+        f, _, log_a = workloads.varcoef_series(M, 16, seed=M)
+        kw, okw = dict(op=srfmg.VARCOEF), dict(op="varcoef", coef=np.exp(log_a))
+    else:
+        f, _, _ = workloads.sine_series(M, 16, seed=M)
+    s = srfmg.Solver(M, n_sr_levels=nRS, segment_width=W, buffer_width=b, tau_edge=srfmg.TAU_SEGMENT,
+                     precision=precision, **kw)
+    try:
+        if log_a is not None:
+            s.set_coefficient(torch.from_numpy(log_a).cuda())
+        u = s.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    finally:
+        s.close()
+    ref = oracle.fmg_h(oracle.sr_params(M, W, b, nRS=nRS, tau_src="segment", **okw), f)
+    assert np.max(np.abs(u - ref)) <= TOL * np.max(np.abs(ref))
+    # and it is a different reading from the assembled one
+    ref_asm = oracle.fmg_h(oracle.sr_params(M, W, b, nRS=nRS, **okw), f)
+    assert np.max(np.abs(ref - ref_asm)) > 0.0
