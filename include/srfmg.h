@@ -92,7 +92,10 @@ typedef struct {
     int32_t batch;             /* independent problems of this size solved together, in
                                   [0, 65535] (0 means 1); see srfmg_solve */
     int32_t tau_edge;          /* srfmg_tau_edge (SR levels only; 0 without SR) */
-    int32_t reserved[2];       /* must be zero */
+    int32_t n_vcycles;         /* FAS V-cycles (Fig. 1, with the SR steps of Fig. 3 on the SR levels)
+                                  after the FMG cycle, each from the current fine solution:
+                                  0..16 (default 0); plans with an SR level only */
+    int32_t reserved[1];       /* must be zero */
 } srfmg_params;
 
 /* Information about a created plan. */

@@ -31,7 +31,7 @@ thread_local std::string g_create_error = "no error";
 enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST, OP_SCALE };
 
 // Pointers that are only known at solve time are patched through these tags.
-enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };
+enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };   // f, u: the caller's pointers of a solve
 
 struct Op {
     OpKind kind;
@@ -45,6 +45,7 @@ struct Op {
     int nseg;
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
+    PtrTag seg_uin;   // a V-cycle's pre-leg from the caller's current fine solution
     // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu)
     int opk;
     // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
@@ -122,7 +123,9 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
-    for (int i = 0; i < 2; ++i) if (p->reserved[i]) return "reserved fields must be zero";
+    if (p->reserved[0]) return "reserved fields must be zero";
+    if (p->n_vcycles < 0 || p->n_vcycles > 16) return "n_vcycles must be in [0, 16]";
+    if (p->n_vcycles > 0 && p->n_sr_levels == 0) return "n_vcycles applies to plans with an SR level";
     if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->tau_edge != SRFMG_TAU_SEGMENT)
         return "tau_edge must be SRFMG_TAU_ASSEMBLED or SRFMG_TAU_SEGMENT";
     if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->n_sr_levels == 0) return "tau_edge applies to SR levels only";
@@ -452,9 +455,13 @@ void build_schedule_ops(srfmg_plan *h) {
         // Pi u_{T-1}; the SR levels below it from their assembled iterates; the
         // stored V-cycle; the post-legs (full update + compatible relaxation)
         // of the SR levels from the bottom up, the finest writing the caller's u
-        for (int T = R + 1; T <= M; ++T) {
+        // from_u: a further V-cycle on level M from the caller's current u
+        auto sr_step = [&](int T, bool from_u) {
             const double *gT = (T == M) ? nullptr : h->glev[T];
-            h->ops.push_back(seg_op(h, OP_SR_PRE, T, U(T - 1), Unext(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
+            Op pre = seg_op(h, OP_SR_PRE, T, from_u ? nullptr : U(T - 1), Unext(T - 1), h->glev[T - 1], gT, nullptr,
+                            nullptr);
+            if (from_u) pre.seg_uin = TAG_U;
+            h->ops.push_back(pre);
             cur[T - 1] ^= 1;
             if (h->p.tau_edge == SRFMG_TAU_ASSEMBLED)
                 h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, U(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
@@ -477,7 +484,9 @@ void build_schedule_ops(srfmg_plan *h) {
                 h->ops.push_back(seg_op(h, OP_SR_POST, T, U(T - 1), nullptr, nullptr, h->glev[T], nullptr, Unext(T)));
                 cur[T] ^= 1;
             }
-        }
+        };
+        for (int T = R + 1; T <= M; ++T) sr_step(T, false);
+        for (int c = 0; c < h->p.n_vcycles; ++c) sr_step(M, true);
     } else {
         // level M stored in ulev[M][0]; the up pass writes the user's u
         h->ops.push_back(level_op(h, OP_DOWN_PI, M, U(M - 1), nullptr, h->ulev[M][0], Unext(M - 1),
@@ -549,6 +558,7 @@ cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
         o.fseg.u_ref = io.u_ref;
         o.fseg.fpart = io.fout ? io.fpart : nullptr;
     }
+    if (o.seg_uin == TAG_U) o.fseg.u_in_f64 = u;
     cudaError_t e = cudaSuccess;
     switch (o.kind) {
     case OP_SCALE: {
@@ -606,6 +616,7 @@ cudaError_t launch(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
         o.seg.u_ref = io.u_ref;
         o.seg.fpart = io.fout ? io.fpart : nullptr;
     }
+    if (o.seg_uin == TAG_U) o.seg.u_in = u;
     if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
     if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
     return launch_fp64<kOpLaplace>(o, s, pdl);
@@ -877,6 +888,8 @@ srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u,
     if (h->nRS < 1)
         return fail(h, SRFMG_EUNSUPPORTED, "functionals are collected by the SR post-leg: the plan needs an SR level");
     if (!f || !functionals) return fail(h, SRFMG_EINVAL, "f and functionals must be device pointers");
+    if (!u && h->p.n_vcycles > 0)
+        return fail(h, SRFMG_EINVAL, "a plan with n_vcycles > 0 needs u: each V-cycle starts from the fine solution");
     if (((uintptr_t)f & 15) || ((uintptr_t)u & 15) || ((uintptr_t)u_ref & 7) || ((uintptr_t)functionals & 7))
         return fail(h, SRFMG_EINVAL, "f and u must be 16-byte aligned, u_ref and functionals 8-byte aligned");
     const size_t bytes = h->n * (size_t)h->batch * sizeof(double);

@@ -513,6 +513,7 @@ struct SegArgs {
     const double *f;           // the finest level's rhs
     const i64 *g_in;           // SR level below the finest: its rhs G_M (then f is unused)
     const i64 *u_in;           // pre-leg of an SR level below the top: its assembled iterate (no Pi)
+    const double *u_in_f64;    // pre-leg of a further V-cycle: the current FP64 fine solution (no Pi)
     const i64 *uc_src;
     i64 *uc_out, *gc_out, *seam;
     i64 *u_out_fx;             // post-leg of an SR level below the finest: U of the level
@@ -556,12 +557,14 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
     const int nc = a.n >> 1, kg = (a.sc + blockIdx.y)->Sg0, gsh = 2 * a.M - 2;
     const bool from_f = (a.g_in == nullptr);
     if (a.u_in) stage_range(m.u, batch_at(a.u_in, a.n) + m.lo, m.hi - m.lo);
+    else if (a.u_in_f64) stage_range(m.u, batch_at(a.u_in_f64, a.n) + m.lo, m.hi - m.lo);
     else stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
     if (from_f) stage_range(m.gs, batch_at(a.f, a.n) + m.lo, m.hi - m.lo);
     else stage_range(m.gs, batch_at(a.g_in, a.n) + m.lo, m.hi - m.lo);
     stage_wait();
     __syncthreads();
-    if (!a.u_in) fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
+    if (!a.u_in && !a.u_in_f64) fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
+    const int S = (a.sc + blockIdx.y)->S;
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         const int i0 = 2 * J;
         const bool in0 = i0 >= m.lo, in1 = i0 + 1 < m.hi;
@@ -571,9 +574,13 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
         if (gr && J >= J0 && J < J1) gr[J - J0] = restrict_rhs(g0, g1);
         if (in0) m.gs[i0 - m.lo] = shr_round(g0, gsh);
         if (in1) m.gs[i0 + 1 - m.lo] = shr_round(g1, gsh);
+        if (a.u_in_f64) {   // the FP64 solution onto the fixed-point grid
+            if (in0) m.u[i0 - m.lo] = f64_to_fixed(__longlong_as_double(m.u[i0 - m.lo]), S);
+            if (in1) m.u[i0 + 1 - m.lo] = f64_to_fixed(__longlong_as_double(m.u[i0 + 1 - m.lo]), S);
+        }
     }
     __syncthreads();
-    if (a.u_in) return;
+    if (a.u_in || a.u_in_f64) return;
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         i64 l, r;
         fmg_interp2(m.c, m.C0, J, l, r);

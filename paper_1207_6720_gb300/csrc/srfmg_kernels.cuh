@@ -1005,11 +1005,14 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a) {
     if (a.coef) stage_range(m.a, batch_at(a.coef, a.n + 1) + m.lo, m.hi - m.lo + 1);
     stage_wait();
     __syncthreads();
-    if (a.u_in) return;
-    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     if (!a.g_in)
         for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
             m.g[i - m.lo] = scale2(m.g[i - m.lo], -2 * a.M);
+    if (a.u_in) {
+        __syncthreads();
+        return;
+    }
+    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
     __syncthreads();
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         double l, r;

@@ -31,7 +31,8 @@ class Params(ctypes.Structure):
         "buffer_width", "nu1", "nu2", "smoother")] + [("lambda_", ctypes.c_double),
                                                       ("batch", ctypes.c_int32),
                                                       ("tau_edge", ctypes.c_int32),
-                                                      ("reserved", ctypes.c_int32 * 2)]
+                                                      ("n_vcycles", ctypes.c_int32),
+                                                      ("reserved", ctypes.c_int32 * 1)]
 
 
 class Info(ctypes.Structure):
