@@ -236,6 +236,14 @@ srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *st
 srfmg_status srfmg_coef_gradient(srfmg_handle h, const double *u, const double *lam, double *dL_dloga,
                                  void *stream);
 
+/* Non-finite detection: the kernels that read f record an inf or NaN in it,
+ * and a functionals solve records non-finite functionals, in the plan's
+ * status word.  srfmg_check synchronises `stream`, reads and clears that word,
+ * and returns SRFMG_ENONFINITE if anything was recorded since the last check
+ * (the solves themselves run on and return SRFMG_OK), else SRFMG_OK.
+ * Errors: SRFMG_EINVAL for a NULL handle; SRFMG_ECUDA. */
+srfmg_status srfmg_check(srfmg_handle h, void *stream);
+
 /* Plan information (workspace size, launches per solve, ...). */
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info);
 

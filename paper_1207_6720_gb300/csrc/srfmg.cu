@@ -55,6 +55,7 @@ struct Op {
     fx::SegArgs fseg;
     fx::TailArgs ftail;
     fx::Scale *scale;
+    int *status;      // OP_SCALE: the plan's status word
 };
 
 // The caller's pointers of one solve, patched into the tagged op fields.
@@ -83,6 +84,7 @@ struct srfmg_plan {
     int *coef_bad = nullptr;       // variable coefficient: set by the coefficient kernel's check
     fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
     double *fpart = nullptr;       // SR plans: functional partials, kNumFunc per segment and problem
+    int *status = nullptr;         // device status word (kStatusNonFinite), read by srfmg_check
     bool solved = false;           // a solve has been enqueued (its coarse solution is kept)
     bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
@@ -318,6 +320,7 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
     o.tail.u_in = u_in;
     o.tail.g_in = g_in;
     o.tail.g_exp = g_exp;
+    o.tail.status = h->status;
     o.tail.u_out = u_out;
     o.tail.Ainv = h->Ainv;
     o.tail.lam = op_lambda(h);
@@ -406,7 +409,7 @@ void build_schedule_ops(srfmg_plan *h) {
             // at least 4096 cells per block: a shallow reduction (few levels
             // above the tail) would otherwise launch one tiny block per 2^depth cells
             o.rhs.chunk_log = std::max(depth, std::min(lin, 12));
-            if (lin == M) { o.rhs_in = TAG_F; o.rhs.in_exp = -2 * M; }
+            if (lin == M) { o.rhs_in = TAG_F; o.rhs.in_exp = -2 * M; o.rhs.status = h->status; }
             else { o.rhs.in = h->glev[lin]; o.rhs.in_exp = 0; }
             for (int l = lin - depth; l < lin; ++l) o.rhs.out[l] = h->glev[l];
             o.grid = dim3((unsigned)((1ULL << lin) >> o.rhs.chunk_log));
@@ -515,6 +518,7 @@ void build_schedule(srfmg_plan *h) {
     Op sc = make_op(OP_SCALE);
     sc.fixed = true;
     sc.scale = h->scale;
+    sc.status = h->status;
     sc.level = h->M;
     // max|f| of each problem: one block per 4096 cells (at most 4 x 152)
     const size_t sblocks = std::min<size_t>(608, std::max<size_t>(1, h->n / 4096));
@@ -565,7 +569,7 @@ cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
         const long long n = (long long)o.level < 63 ? (1LL << o.level) : 0;
         const dim3 one(1, o.grid.y);
         e = run(fx::scale_reset_kernel, one, dim3(32), 0, s, pdl, o.scale);
-        if (e == cudaSuccess) e = run(fx::scale_max_kernel, o.grid, o.block, 0, s, true, f, n, o.scale);
+        if (e == cudaSuccess) e = run(fx::scale_max_kernel, o.grid, o.block, 0, s, true, f, n, o.scale, o.status);
         if (e == cudaSuccess) e = run(fx::scale_finish_kernel, one, dim3(32), 0, s, true, o.scale);
         break;
     }
@@ -663,7 +667,7 @@ cudaError_t enqueue_all(srfmg_plan *h, const Io &io, cudaStream_t s) {
     }
     if (io.fout)    // the segments' partials -> the functionals of each problem
         return run(functionals_finish_kernel, dim3(1, (unsigned)h->batch), dim3(kFinishThreads), 0, s, true,
-                   (const double *)io.fpart, (int)(h->n / h->W), h->M, io.fout);
+                   (const double *)io.fpart, (int)(h->n / h->W), h->M, io.fout, h->status);
     return cudaSuccess;
 }
 
@@ -785,6 +789,12 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         double *flag = nullptr;
         if (st == SRFMG_OK) st = alloc_dev(h, &flag, 1);
         h->coef_bad = (int *)flag;
+    }
+    if (st == SRFMG_OK) {
+        double *w = nullptr;
+        st = alloc_dev(h, &w, 1);
+        h->status = (int *)w;
+        if (st == SRFMG_OK && (e = cudaMemset(w, 0, sizeof(double))) != cudaSuccess) st = cuda_fail(h, e, "cudaMemset");
     }
     const int n0 = 1 << h->M0;
     if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
@@ -1002,6 +1012,20 @@ srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *st
     return fail(h, SRFMG_EINVAL,
                 "log_a: a value is not finite or beyond +-700, or adjacent faces of a level of 128 or more "
                 "cells differ by more than a factor 1.5 (ln 1.5 in log a); the coefficient was reset to a = 1");
+}
+
+srfmg_status srfmg_check(srfmg_handle h, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int word = 0;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "srfmg_check");
+    if (word & kStatusNonFinite)
+        return fail(h, SRFMG_ENONFINITE, "a non-finite value was found in f or in the functionals since the last check");
+    return SRFMG_OK;
 }
 
 srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {

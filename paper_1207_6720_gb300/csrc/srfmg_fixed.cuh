@@ -255,7 +255,7 @@ __global__ void scale_reset_kernel(Scale *sc) {
     if (threadIdx.x == 0) { sc->E = -2000; sc->S = 0; sc->Sg0 = 0; }
 }
 
-__global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
+__global__ void scale_max_kernel(const double *f, long long n, Scale *sc, int *status) {
     pdl_enter();
     f = batch_at(f, n);
     sc += blockIdx.y;
@@ -266,6 +266,7 @@ __global__ void scale_max_kernel(const double *f, long long n, Scale *sc) {
     }
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     if ((threadIdx.x & 31) == 0) atomicMax(&sc->E, emax - 1022);
+    if ((threadIdx.x & 31) == 0 && emax == 0x7ff && status) atomicOr(status, kStatusNonFinite);   // inf or NaN in f
 }
 
 __global__ void scale_finish_kernel(Scale *sc) {

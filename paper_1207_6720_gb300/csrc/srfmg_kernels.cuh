@@ -551,8 +551,17 @@ __device__ __forceinline__ double tau_nl(double cl, double u0, double u1) {
 // Level lin is read from `in` scaled by 2^in_exp (f with in_exp = -2M).
 // Each block reduces 2^depth consecutive cells of level lin in shared memory.
 // ---------------------------------------------------------------------------
+// Non-finite detection: kernels that read the caller's f (or form the
+// functionals) OR kStatusNonFinite into the plan's status word, which the host
+// reads with srfmg_check.  The exponent field 0x7ff marks inf and NaN.
+constexpr int kStatusNonFinite = 1;
+__device__ __forceinline__ bool nonfinite(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+}
+
 struct RhsArgs {
     const double *in;
+    int *status;               // non-finite f (when in is f)
     int in_exp;
     int lin, lstop, depth;
     int chunk_log;             // log2 of the cells each block reduces (>= depth)
@@ -569,9 +578,13 @@ __global__ void rhs_hierarchy_kernel(RhsArgs a) {
     stage_range(cur, in + base, chunk);
     stage_wait();
     __syncthreads();
+    bool bad = false;
     if (a.in_exp)
-        for (int i = threadIdx.x; i < chunk; i += blockDim.x) cur[i] = scale2(cur[i], a.in_exp);
-    __syncthreads();
+        for (int i = threadIdx.x; i < chunk; i += blockDim.x) {
+            bad = bad || nonfinite(cur[i]);
+            cur[i] = scale2(cur[i], a.in_exp);
+        }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusNonFinite);
     int len = chunk;
     for (int l = a.lin; l > a.lstop && len > 1; --l) {
         const int half = len >> 1;
@@ -931,7 +944,7 @@ __device__ __forceinline__ void func_block_reduce(FuncAcc &q) {
 // problem; one block of kFinishThreads threads per problem (a few segments per
 // thread, so the chain of dependent loads and adds stays short).
 __global__ void __launch_bounds__(kFinishThreads) functionals_finish_kernel(const double *fpart, int nseg, int M,
-                                                                        double *out) {
+                                                                        double *out, int *status) {
     pdl_enter();
     const double *src = batch_at(fpart, (long long)nseg * kNumFunc);
     FuncAcc q;
@@ -945,6 +958,10 @@ __global__ void __launch_bounds__(kFinishThreads) functionals_finish_kernel(cons
         o[2] = q.v[2];
         o[3] = q.v[3] * h;
         o[4] = q.v[4];
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < kNumFunc; ++k) bad = bad || nonfinite(o[k]);
+        if (bad && status) atomicOr(status, kStatusNonFinite);
     }
 }
 
@@ -1173,6 +1190,7 @@ struct TailArgs {
     const double *u_in;        // mode 1: level Mc iterate
     const double *g_in;        // level Mc rhs, scaled by 2^g_exp on load
     int g_exp;
+    int *status;               // non-finite f (when g_in is f)
     double *u_out;             // level Mc result
     const double *Ainv;        // inverse of the scaled coarsest operator, row-major
     double lam;                // Bratu: lam (0 otherwise)
@@ -1337,9 +1355,13 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(const __grid_constant_
     if (a.mode == 1) stage_range(m.u + m.off(a.Mc), u_in, nMc);
     stage_wait();
     __syncthreads();
+    bool bad = false;
     if (a.g_exp)
-        for (int i = threadIdx.x; i < nMc; i += blockDim.x) m.g[m.off(a.Mc) + i] = scale2(m.g[m.off(a.Mc) + i], a.g_exp);
-    __syncthreads();
+        for (int i = threadIdx.x; i < nMc; i += blockDim.x) {
+            bad = bad || nonfinite(m.g[m.off(a.Mc) + i]);
+            m.g[m.off(a.Mc) + i] = scale2(m.g[m.off(a.Mc) + i], a.g_exp);
+        }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && a.status) atomicOr(a.status, kStatusNonFinite);
     if (a.mode == 0) {
         for (int l = a.Mc; l > a.M0; --l) {
             const double *g = m.g + m.off(l);

@@ -21,7 +21,7 @@ NUM_FUNCTIONALS = 5          # functionals per problem of srfmg_solve_functional
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
-           "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct",
+           "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version")
 
 
@@ -91,12 +91,13 @@ def load(build_if_missing=True):
     lib.srfmg_coef_gradient.argtypes = [H, vp, vp, vp, vp]
     lib.srfmg_solve_functionals.argtypes = [H, vp, vp, vp, vp, vp]
     lib.srfmg_reconstruct.argtypes = [H, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
+    lib.srfmg_check.argtypes = [H, vp]
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
                  "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
-                 "srfmg_solve_functionals", "srfmg_reconstruct"):
+                 "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -219,6 +220,11 @@ class Solver:
                                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
                     "reconstruct")
         return out
+
+    def check(self, stream=None):
+        """Raise SrfmgError (SRFMG_ENONFINITE) if an inf or NaN was seen in f or
+        in the functionals since the last check; synchronises the stream."""
+        self._check(self.lib.srfmg_check(self.h, _stream_ptr(stream)), "check")
 
     def _check_vec(self, name, t):
         import torch
