@@ -6,6 +6,7 @@
 #include "srfmg_fixed.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>   // tracing ranges (no-ops unless a profiler is attached)
 
 #include <algorithm>
 #include <cmath>
@@ -660,8 +661,10 @@ cudaError_t launch_coef(srfmg_plan *h, const double *log_a, cudaStream_t s) {
 // with the preceding kernel (programmatic dependent launch).
 cudaError_t enqueue_all(srfmg_plan *h, const Io &io, cudaStream_t s) {
     bool first = true;
-    for (const Op &o : h->ops) {
-        cudaError_t e = launch(o, io, s, !first);
+    for (size_t i = 0; i < h->ops.size(); ++i) {
+        nvtxRangePushA(h->names[i].c_str());       // one range per launch (level and kernel)
+        cudaError_t e = launch(h->ops[i], io, s, !first);
+        nvtxRangePop();
         if (e != cudaSuccess) return e;
         first = false;
     }
@@ -834,7 +837,13 @@ namespace {
 
 // Enqueue one solve with the caller's pointers io (checked by the caller):
 // replay the captured graph of this pointer set, capturing it first.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 srfmg_status solve_io(srfmg_handle h, const Io &io, cudaStream_t s) {
+    NvtxRange range(io.fout ? "srfmg_solve_functionals" : "srfmg_solve");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     if (!h->use_graph) {
@@ -1056,7 +1065,9 @@ srfmg_status srfmg_profile(srfmg_handle h, const double *f, double *u, void *str
         for (int i = 0; i < nops && e == cudaSuccess; ++i) {
             size_t idx = ((size_t)k * nops + i) * 2;
             e = cudaEventRecord(ev[idx], s);
+            nvtxRangePushA(h->names[i].c_str());
             if (e == cudaSuccess) e = launch(h->ops[i], Io{f, u, nullptr, nullptr, nullptr}, s, false);
+            nvtxRangePop();
             if (e == cudaSuccess) e = cudaEventRecord(ev[idx + 1], s);
         }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
