@@ -71,7 +71,7 @@ def sine_series_batch(M, seeds, nmodes, device):
     return (cf @ S).reshape(-1).contiguous(), c
 
 
-def varcoef_series(M, nmodes, seed, amp=1.0, gmodes=8):
+def varcoef_series(M, nmodes, seed, amp=1.0, gmodes=16):
     """(f, u_exact, log_a) for -(a u')' = f: log_a at the 2^M + 1 faces
     x_j = j / 2^M, f and u_exact at the cell centres."""
     n = 1 << M
