@@ -21,9 +21,10 @@ restatement) on the host cores, one bounded sample of the workload per step.
 
 --workload batch: 8192 independent problems of N = 2^m cells, m ~ U{10..20}
 (seed 11; about 1.55e9 unknowns in all), each a 32-mode sine series with its
-own seed; one batched plan per size (segments of min(4096, N/4) cells, 8
-buffer cells), all sizes on their own streams at once; 64-bit fixed point.
-value = all problems' unknowns / time of one pass over all sizes.
+own seed; one srfmg group: a batched plan per size with its segment layout
+autotuned (--no-tune: min(4096, N/4)-cell segments, 8 buffer cells), all
+replayed as one CUDA graph with a branch per size; 64-bit fixed point.
+value = all problems' unknowns / time of one group solve.
 
 --workload varcoef: -(a u')' = f, a = exp(g/2) at the faces with g a seeded
 8-mode cosine series, N = 2^24 cells, 4096 segments of 4096 cells, V(1,1), FP64;
@@ -98,6 +99,8 @@ def parse_args():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
                     help="mixed: 64-bit fixed point for solution/residual/tau, FP64 coarse solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch: fixed segment layout min(4096, N/4), buffer 8, instead of autotuning each size")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
                          "the minimal run used for ncu captures")
@@ -124,7 +127,8 @@ def workload_config(a):
         return {
             "workload": f"{a.nprob} independent 1D -u''=f problems, N=2^m with m ~ U{{10..20}} (seed 11), "
                         f"FMG-FAS V(1,1) lexicographic GS, 1 SR level of min(4096, N/4)-cell segments, "
-                        f"buffer 8, 64-bit fixed point; one batched plan per size, sizes on concurrent streams",
+                        f"buffer 8, 64-bit fixed point; one srfmg group (a batched plan per size, all sizes "
+                        f"replayed as one CUDA graph with a branch per size)",
             "precision": "mixed", "nprob": a.nprob, "m_range": [10, 20], "size_seed": 11,
             "modes": 32, "buffer_width": 8, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
             "l2": "inputs larger than L2 (about 12 GB of f and 12 GB of u)",
@@ -648,7 +652,8 @@ def run_gpu_bratu(a):
 
 
 def run_gpu_batch(a):
-    """Many independent problems: one batched plan per size, sizes concurrent."""
+    """Many independent problems of uneven sizes: one srfmg group (a batched
+    plan per size, all replayed as one CUDA graph), one group solve per step."""
     import torch
     from paper_1207_6720_gb300 import srfmg, workloads
 
@@ -661,104 +666,103 @@ def run_gpu_batch(a):
     for k, m in enumerate(sizes):
         classes.setdefault(int(m), []).append(k + 1000)       # problem k's series seed
     total = int(sum(len(v) << m for m, v in classes.items()))
-    fs, us, streams = {}, {}, {}
-    for m, seeds in sorted(classes.items()):
-        fs[m], _ = workloads.sine_series_batch(m, seeds, 32, dev)
-        us[m] = torch.empty_like(fs[m])
-        streams[m] = torch.cuda.Stream(device=dev)
+    # the packed layout: by size, then by index (srfmg_group_offsets)
+    parts = [workloads.sine_series_batch(m, classes[m], 32, dev)[0] for m in sorted(classes)]
+    fd = torch.cat(parts)
+    del parts
+    ud = torch.empty_like(fd)
+    assert fd.numel() == total == int(srfmg.group_offsets(sizes)[-1])
     torch.cuda.synchronize()
 
-    def make(prec, nRS):
-        out = {}
-        for m, seeds in classes.items():
-            kw = dict(batch=len(seeds), precision=prec, n_sr_levels=nRS)
-            if nRS:
-                kw.update(segment_width=min(4096, (1 << m) // 4), buffer_width=8)
-            out[m] = srfmg.Solver(m, device=dev, **kw)
-        return out
+    def make(prec, nRS, tune):
+        kw = dict(precision=prec, n_sr_levels=nRS)
+        if nRS:
+            kw.update(segment_width=4096, buffer_width=8)
+        return srfmg.Group(sizes, device=dev, tune=tune, **kw)
 
-    def one_pass(solvers):
-        e0 = torch.cuda.Event()
-        e0.record(master)
-        done = []
-        for m, sv in solvers.items():
-            st = streams[m]
-            st.wait_event(e0)
-            sv.solve(fs[m], us[m], stream=st)
-            done.append(st.record_event())
-        for ev in done:
-            master.wait_event(ev)
-
-    def timed(solvers, steps, warmup):
+    def timed(group, steps, warmup):
         for _ in range(warmup):
-            one_pass(solvers)
+            group.solve(fd, ud, stream=master)
         torch.cuda.synchronize()
         dist.barrier()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(master)
         for _ in range(steps):
-            one_pass(solvers)
+            group.solve(fd, ud, stream=master)
         t1.record(master)
         t1.synchronize()
         torch.cuda.synchronize()
         dist.barrier()
         return t0.elapsed_time(t1) / steps
 
-    solvers = make(srfmg.MIXED, 1)
-    launches = sum(sv.info().kernels_per_solve for sv in solvers.values())
+    tune = 0 if a.no_tune else 3
+    t_create = time.perf_counter()
+    group = make(srfmg.MIXED, 1, tune)
+    t_create = time.perf_counter() - t_create
+    members = group.members()
+    launches = sum(mb.info().kernels_per_solve for mb in members)
+    layouts = {str(mb.n.bit_length() - 1): [mb.params.segment_width, mb.params.buffer_width] for mb in members}
     sampler = ClockSampler(dev)
     sampler.start()
-    ms = dist.max(timed(solvers, a.steps, a.warmup))
+    ms = dist.max(timed(group, a.steps, a.warmup))
     clocks = sampler.stop()
     value = dist.world * total / (ms * 1e-3)
+    cfg = workload_config(a)
+    cfg["segment_layout"] = ("autotuned per size (srfmg_autotune, 3 timed solves per candidate)" if tune
+                             else "min(4096, N/4) cells, buffer 8")
+    cfg["layouts"] = layouts
     line = {"metric": METRIC_BATCH, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": workload_config(a), "gpu_launches": launches * a.steps, "clocks": clocks,
-            "unknowns_per_step": total}
+            "config": cfg, "gpu_launches": launches * a.steps, "clocks": clocks,
+            "unknowns_per_step": total, "group_create_s": t_create}
     # accuracy on a sample: the first problem of every size against its exact solution
+    offs = srfmg.group_offsets(sizes)
     worst = 0.0
     samples = {}
-    for m, seeds in classes.items():
-        u0 = us[m][: 1 << m].cpu().numpy()
-        f0, ue, _ = workloads.sine_series(m, 32, seeds[0])
-        samples[m] = (fs[m][: 1 << m].cpu().numpy(), ue, u0)
+    u_all = None
+    for mb in members:
+        m = mb.n.bit_length() - 1
+        if m in samples:
+            continue
+        o = int(mb.offset)
+        u0 = ud[o:o + mb.n].cpu().numpy()
+        f0, ue, _ = workloads.sine_series(m, 32, classes[m][0])
+        samples[m] = (fd[o:o + mb.n].cpu().numpy(), ue, u0, mb.params.segment_width, mb.params.buffer_width)
         worst = max(worst, float(np.max(np.abs(u0 - ue))))
     if not a.only_solve:
-        # end to end: every size through srfmg_solve_host from pinned host buffers, in turn
-        hosts = {m: (fs[m].cpu().pin_memory(), torch.empty(fs[m].numel(), dtype=torch.float64).pin_memory())
-                 for m in classes}
-        for m, sv in solvers.items():
-            sv.solve_host(hosts[m][0].numpy(), hosts[m][1].numpy(), stream=master)
+        # end to end: the whole group through srfmg_group_solve_host from pinned host buffers
+        fh = fd.cpu().pin_memory()
+        uh = torch.empty(total, dtype=torch.float64).pin_memory()
+        group.solve_host(fh.numpy(), uh.numpy(), stream=master)
         t0 = time.perf_counter()
-        for m, sv in solvers.items():
-            sv.solve_host(hosts[m][0].numpy(), hosts[m][1].numpy(), stream=master)
+        group.solve_host(fh.numpy(), uh.numpy(), stream=master)
         dt_e2e = dist.max(time.perf_counter() - t0)
-        hb = int(sum(h[0].numel() for h in hosts.values()) * 8)
-        line["e2e"] = {"value": dist.world * total / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": hb,
-                       "d2h_bytes_per_step": hb}
-        # roofline: the longest launch of the largest size's batch
-        mbig = max(classes)
-        prof = solvers[mbig].profile(fs[mbig], torch.empty_like(fs[mbig]), nsolves=2, stream=master)
+        line["e2e"] = {"value": dist.world * total / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total * 8,
+                       "d2h_bytes_per_step": total * 8}
+        del fh, uh
+        # roofline: the longest launch of the largest size's plan
+        big = max(members, key=lambda mb: mb.n * mb.batch)
+        o = int(big.offset)
+        prof = big.profile(fd[o:o + big.n * big.batch], torch.empty(big.n * big.batch, dtype=torch.float64,
+                                                                    device=fd.device), nsolves=2, stream=master)
         torch.cuda.synchronize()
         top_name, top_ms = max(prof, key=lambda x: x[1])
         kind, lvl = top_name.split(" L")
         kind = kind.replace("fx.", "")
-        bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * len(classes[mbig]) * (1 << int(lvl))
+        bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * big.batch * (1 << int(lvl))
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        line["roofline"] = {"bound": "hbm", "kernel": f"{top_name} (batch of {len(classes[mbig])})",
+        line["roofline"] = {"bound": "hbm", "kernel": f"{top_name} (batch of {big.batch})",
                             "achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                             "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
                             "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
                             "launch_ms": top_ms}
-    for sv in solvers.values():
-        sv.close()
+    group.close()
     if not a.only_solve:
-        plain = make(srfmg.FP64, 0)
+        plain = make(srfmg.FP64, 0, 0)
         ms_plain = dist.max(timed(plain, max(3, a.steps // 2), 1))
-        for sv in plain.values():
-            sv.close()
+        plain.close()
         line["plain_fp64"] = {"value": dist.world * total / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                               "speedup_over_plain": ms_plain / ms}
     acc = {"err_max_vs_exact_sample": worst, "sample": "first problem of each size"}
@@ -768,8 +772,8 @@ def run_gpu_batch(a):
         t0 = time.perf_counter()
         reps = 0
         while True:
-            for m, (f0, ue, u0) in samples.items():
-                refs[m] = oracle.fmg_v(oracle.sr_params(m, min(4096, (1 << m) // 4), 8), f0)
+            for m, (f0, ue, u0, W, b) in samples.items():
+                refs[m] = oracle.fmg_v(oracle.sr_params(m, W, b), f0)
             reps += 1
             if time.perf_counter() - t0 > 10.0 or reps >= 20:
                 break
@@ -779,9 +783,9 @@ def run_gpu_batch(a):
                                 "sample": f"{reps} x one problem of each size ({n_sample} unknowns) "
                                           f"with the serial C oracle"}
         ok = all(np.max(np.abs(u0 - ue)) <= 1.5 * np.max(np.abs(refs[m] - ue))
-                 for m, (f0, ue, u0) in samples.items())
+                 for m, (f0, ue, u0, W, b) in samples.items())
         acc.update({"rel_maxnorm_vs_oracle_sample": max(
-            float(np.max(np.abs(u0 - refs[m])) / np.max(np.abs(refs[m]))) for m, (f0, ue, u0) in samples.items()),
+            float(np.max(np.abs(u0 - refs[m])) / np.max(np.abs(refs[m]))) for m, (f0, ue, u0, W, b) in samples.items()),
             "at_discretization_accuracy_sample": bool(ok)})
     line["accuracy"] = acc
     if dist.rank == 0:

@@ -104,7 +104,10 @@ typedef struct {
     int32_t kernels_per_solve; /* kernel launches enqueued by one srfmg_solve */
     int32_t coarse_tail_level; /* finest level handled by the one-block coarse tail */
     int32_t n_segments;        /* segments on the finest level (0 without SR) */
-    int32_t reserved[7];
+    int32_t segment_width;     /* W of the plan (0 without SR) */
+    int32_t buffer_width;      /* b of the plan (0 without SR) */
+    int32_t batch;             /* problems solved together (>= 1) */
+    int32_t reserved[4];
 } srfmg_info;
 
 /* Fill *p with the defaults for N = 2^log2_n: M0 = 2, one SR level,
@@ -308,6 +311,82 @@ srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, 
                             float *ms, int32_t capacity, int32_t *ncand);
 srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32_t *segment_width,
                                       int32_t *buffer_width);
+
+/* Independent problems of uneven sizes solved together (many problems with
+ * N = 2^m cells for varying m; the paper solves one problem, this is the
+ * data-parallel use of its solver on independent ones).  A group holds one
+ * batched plan per distinct size (srfmg_params.batch = the number of problems
+ * of that size, at most 65535 per plan; more are split over several plans)
+ * and replays all of them as ONE CUDA graph in which every plan runs on a
+ * branch of its own, so the launch chains of the sizes overlap on the GPU.
+ *
+ * Packed layout: the problems lie back to back, ordered by size (ascending)
+ * and, within a size, in their given order.  It depends only on the sizes:
+ * srfmg_group_offsets gives it without a device, so a caller can arrange its
+ * data before creating the group. */
+typedef struct srfmg_group *srfmg_group_handle;
+
+/* offsets: host array of nprob + 1 int64; offsets[k] receives the first cell
+ * of problem k in the packed arrays and offsets[nprob] the total number of
+ * cells.  log2_n: host array of nprob sizes, each in [1, 28].  Pure host
+ * function.  Errors: SRFMG_EINVAL for nprob < 1, NULL pointers or a size
+ * outside [1, 28]. */
+srfmg_status srfmg_group_offsets(int32_t nprob, const int32_t *log2_n, int64_t *offsets);
+
+/* Create a group on `device`.  base: the settings every problem shares (op,
+ * precision, log2_n_coarsest, n_sr_levels, nu1, nu2, smoother, lambda,
+ * tau_edge, n_vcycles, and the segment layout below); base->log2_n and
+ * base->batch are ignored.  log2_n: host array of nprob sizes.
+ * Segment layout of each size (plans with SR levels): with tune = 0,
+ * W = min(base->segment_width, max(16, N/4)) and b = min(base->buffer_width,
+ * W); with tune > 0, srfmg_autotune picks (W, b) for each size (`tune` timed
+ * solves per candidate, on a sample of min(count, max(1, 2^24 / N)) problems
+ * of that size; needs n_sr_levels = 1).  Every size must make a valid plan
+ * (srfmg_create's checks: N > 2^log2_n_coarsest, ...).  On success *out is a
+ * new handle.  Errors: as srfmg_create and srfmg_autotune; SRFMG_EINVAL for
+ * nprob < 1, NULL pointers or tune < 0. */
+srfmg_status srfmg_group_create(const srfmg_params *base, int32_t nprob, const int32_t *log2_n, int32_t tune,
+                                int device, srfmg_group_handle *out);
+
+/* Solve every problem of the group.  f, u: device pointers to the packed
+ * arrays (offsets[nprob] doubles each), 16-byte aligned, not overlapping.
+ * Asynchronous on `stream`: the first call for an (f, u) pair captures the
+ * launches of all plans into one CUDA graph (a fork from `stream` into one
+ * branch per plan and a join back), later calls replay it; a new pair is
+ * captured anew.  Each problem's result is the one a single srfmg_solve with
+ * its size's parameters gives, bit for bit.  Errors: SRFMG_EINVAL for a NULL
+ * handle or pointer, misalignment or overlap; SRFMG_ECUDA. */
+srfmg_status srfmg_group_solve(srfmg_group_handle g, const double *f, double *u, void *stream);
+
+/* The same from and to HOST memory (the packed layout), with device staging
+ * buffers owned by the group: every plan's branch copies its part of f in,
+ * solves it and copies its part of u out (launched directly, not from the
+ * graph), so the copies of one size overlap the work of the others; then
+ * `stream` is synchronised.  Pinned host buffers give the fastest copies and
+ * the overlap; pageable ones work. */
+srfmg_status srfmg_group_solve_host(srfmg_group_handle g, const double *f, double *u, void *stream);
+
+/* The group's plans, by ascending size: *nplans (optional) and *total_cells
+ * (optional) of the packed arrays. */
+srfmg_status srfmg_group_query(srfmg_group_handle g, int32_t *nplans, int64_t *total_cells);
+
+/* Plan i of the group (0 <= i < nplans): *plan (optional) is its handle, owned
+ * by the group (valid until srfmg_group_destroy; do not destroy it), usable
+ * with srfmg_query, srfmg_check, srfmg_profile, srfmg_set_coefficient and the
+ * other per-plan calls on its part of the packed arrays; *log2_n, *count and
+ * *offset (each optional) receive its size, its number of problems and the
+ * first cell of its part.  Errors: SRFMG_EINVAL for a NULL handle or i out of
+ * range. */
+srfmg_status srfmg_group_member(srfmg_group_handle g, int32_t i, srfmg_handle *plan, int32_t *log2_n,
+                                int32_t *count, int64_t *offset);
+
+/* Release the group, its plans and its graph (synchronises the device first).
+ * Accepts NULL. */
+srfmg_status srfmg_group_destroy(srfmg_group_handle g);
+
+/* Message of the last error on g (or of the last failed srfmg_group_create
+ * when g is NULL); never NULL. */
+const char *srfmg_group_last_error(srfmg_group_handle g);
 
 /* Release the device workspace and graphs.  Synchronises the device first.
  * Accepts NULL (returns SRFMG_OK). */

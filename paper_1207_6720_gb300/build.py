@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsrfmg.so")
 SOURCES = ["srfmg.cu"]
-DEPS = ["srfmg.cu", "srfmg_kernels.cuh"]
+DEPS = ["srfmg.cu", "srfmg_kernels.cuh", "srfmg_fixed.cuh"]
 
 
 def nvcc_path():

@@ -1044,6 +1044,9 @@ srfmg_status srfmg_query(srfmg_handle h, srfmg_info *info) {
     info->kernels_per_solve = (int32_t)h->ops.size();
     info->coarse_tail_level = h->Mc;
     info->n_segments = h->nRS ? (int32_t)(h->n / h->W) : 0;
+    info->segment_width = h->nRS ? h->W : 0;
+    info->buffer_width = h->nRS ? h->b : 0;
+    info->batch = h->batch;
     return SRFMG_OK;
 }
 
@@ -1174,6 +1177,286 @@ srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32
 }
 
 const char *srfmg_version(void) { return "srfmg 0.1 sm_103a"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Groups: independent problems of uneven sizes, one batched plan per size,
+// all plans replayed as one CUDA graph with a branch per plan.
+// ---------------------------------------------------------------------------
+struct srfmg_group {
+    int device = 0;
+    std::vector<srfmg_plan *> plans;       // ascending size
+    std::vector<int> m, count;             // size and problems of each plan
+    std::vector<size_t> off;               // first cell of each plan's part
+    size_t total = 0;
+    cudaStream_t cap = nullptr;            // capture origin
+    std::vector<cudaStream_t> side;        // one branch per plan
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;        // captured for (gf, gu)
+    const double *gf = nullptr;
+    double *gu = nullptr;
+    bool use_graph = true;
+    double *f_stage = nullptr, *u_stage = nullptr;
+    std::string err = "no error";
+};
+
+namespace {
+
+constexpr int kGroupPlanMax = 65535;       // problems per plan (grid rows)
+thread_local std::string g_group_create_error = "no error";
+
+srfmg_status gfail(srfmg_group *g, srfmg_status st, const std::string &msg) {
+    if (g) g->err = msg; else g_group_create_error = msg;
+    return st;
+}
+
+// Problem order of the packed layout: by size, then by index.
+std::vector<int> group_order(int32_t nprob, const int32_t *log2_n) {
+    std::vector<int> idx(nprob);
+    for (int k = 0; k < nprob; ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return log2_n[a] < log2_n[b]; });
+    return idx;
+}
+
+void group_release(srfmg_group *g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (cudaEvent_t e : g->join) if (e) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    for (cudaStream_t s : g->side) if (s) cudaStreamDestroy(s);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    if (g->f_stage) cudaFree(g->f_stage);
+    if (g->u_stage) cudaFree(g->u_stage);
+    for (srfmg_plan *h : g->plans) srfmg_destroy(h);
+    g->plans.clear();
+}
+
+// Fork from s into one branch per plan, enqueue each plan's launches on its
+// branch, join back into s.  Under capture this records the group's graph.
+cudaError_t group_enqueue(srfmg_group *g, const double *f, double *u, cudaStream_t s) {
+    cudaError_t e = cudaEventRecord(g->fork, s);
+    for (size_t c = 0; c < g->plans.size() && e == cudaSuccess; ++c) {
+        e = cudaStreamWaitEvent(g->side[c], g->fork, 0);
+        if (e == cudaSuccess)
+            e = enqueue_all(g->plans[c], Io{f + g->off[c], u + g->off[c], nullptr, nullptr, nullptr}, g->side[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(g->join[c], g->side[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g->join[c], 0);
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+srfmg_status srfmg_group_offsets(int32_t nprob, const int32_t *log2_n, int64_t *offsets) {
+    if (nprob < 1 || !log2_n || !offsets) return gfail(nullptr, SRFMG_EINVAL, "nprob must be >= 1 and the arrays non-NULL");
+    for (int k = 0; k < nprob; ++k)
+        if (log2_n[k] < 1 || log2_n[k] > 28) return gfail(nullptr, SRFMG_EINVAL, "every log2_n must be in [1, 28]");
+    int64_t at = 0;
+    for (int k : group_order(nprob, log2_n)) {
+        offsets[k] = at;
+        at += (int64_t)1 << log2_n[k];
+    }
+    offsets[nprob] = at;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_create(const srfmg_params *base, int32_t nprob, const int32_t *log2_n, int32_t tune,
+                                int device, srfmg_group_handle *out) {
+    if (!out) return gfail(nullptr, SRFMG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!base || tune < 0) return gfail(nullptr, SRFMG_EINVAL, "base is NULL or tune < 0");
+    std::vector<int64_t> offs((size_t)std::max(nprob, 0) + 1);
+    if (srfmg_group_offsets(nprob, log2_n, offs.data()) != SRFMG_OK) return SRFMG_EINVAL;
+    if (tune > 0 && base->n_sr_levels != 1)
+        return gfail(nullptr, SRFMG_EINVAL, "tune > 0 tunes the SR segment layout (n_sr_levels = 1)");
+    // the plans: runs of equal size in the packed order, at most kGroupPlanMax problems each
+    std::vector<int> order = group_order(nprob, log2_n);
+    std::vector<srfmg_params> ps;
+    std::vector<int> pm, pcount;
+    std::vector<size_t> poff;
+    for (size_t i = 0; i < order.size();) {
+        const int mk = log2_n[order[i]];
+        size_t j = i;
+        while (j < order.size() && log2_n[order[j]] == mk && j - i < (size_t)kGroupPlanMax) ++j;
+        srfmg_params p = *base;
+        p.log2_n = mk;
+        p.batch = (int32_t)(j - i);
+        if (p.n_sr_levels >= 1) {
+            const int N = 1 << mk;
+            p.segment_width = std::min(base->segment_width, std::max(16, N / 4));
+            p.buffer_width = std::min(base->buffer_width, p.segment_width);
+        }
+        std::string msg = check_params(&p);
+        if (!msg.empty()) return gfail(nullptr, SRFMG_EINVAL, "size 2^" + std::to_string(mk) + ": " + msg);
+        ps.push_back(p);
+        pm.push_back(mk);
+        pcount.push_back((int)(j - i));
+        poff.push_back((size_t)offs[order[i]]);
+        i = j;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return gfail(nullptr, SRFMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= ndev) return gfail(nullptr, SRFMG_EINVAL, "device index out of range");
+    srfmg_group *g = new srfmg_group();
+    g->device = device;
+    g->total = (size_t)offs[nprob];
+    const char *env = std::getenv("SRFMG_NO_GRAPH");
+    g->use_graph = !(env && env[0] == '1');
+    srfmg_status st = SRFMG_OK;
+    for (size_t c = 0; c < ps.size() && st == SRFMG_OK; ++c) {
+        srfmg_params p = ps[c];
+        if (tune > 0) {          // the layout of this size, timed on a sample of its problems
+            srfmg_params probe = p, best;
+            const int sample = std::max(1, (1 << 24) >> pm[c]);
+            probe.batch = std::min(pcount[c], sample);
+            st = srfmg_autotune(&probe, device, tune, &best, nullptr, 0, nullptr);
+            if (st != SRFMG_OK) { st = gfail(g, st, "autotune of size 2^" + std::to_string(pm[c]) + ": " + g_create_error); break; }
+            p.segment_width = best.segment_width;
+            p.buffer_width = best.buffer_width;
+        }
+        srfmg_handle h = nullptr;
+        st = srfmg_create(&p, device, &h);
+        if (st != SRFMG_OK) { st = gfail(g, st, "plan of size 2^" + std::to_string(pm[c]) + ": " + g_create_error); break; }
+        g->plans.push_back(h);
+        g->m.push_back(pm[c]);
+        g->count.push_back(pcount[c]);
+        g->off.push_back(poff[c]);
+    }
+    if (st == SRFMG_OK) {
+        e = cudaSetDevice(device);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+        for (size_t c = 0; c < g->plans.size() && e == cudaSuccess; ++c) {
+            cudaStream_t sc = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking);
+            if (e == cudaSuccess) g->side.push_back(sc);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) g->join.push_back(ev);
+        }
+        if (e != cudaSuccess) st = gfail(g, SRFMG_ECUDA, std::string("group streams: ") + cudaGetErrorString(e));
+    }
+    if (st != SRFMG_OK) {
+        g_group_create_error = g->err;
+        group_release(g);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_solve(srfmg_group_handle g, const double *f, double *u, void *stream) {
+    if (!g) return gfail(nullptr, SRFMG_EINVAL, "group handle is NULL");
+    if (!f || !u) return gfail(g, SRFMG_EINVAL, "f and u must be device pointers");
+    if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return gfail(g, SRFMG_EINVAL, "f and u must be 16-byte aligned");
+    if (overlap(f, g->total * sizeof(double), u, g->total * sizeof(double))) return gfail(g, SRFMG_EINVAL, "f and u overlap");
+    NvtxRange range("srfmg_group_solve");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) return gfail(g, SRFMG_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (!g->use_graph) {
+        e = group_enqueue(g, f, u, s);
+        if (e != cudaSuccess) return gfail(g, SRFMG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    } else {
+        if (!g->exec || g->gf != f || g->gu != u) {
+            if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return gfail(g, SRFMG_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+            cudaError_t le = group_enqueue(g, f, u, g->cap);
+            e = cudaStreamEndCapture(g->cap, &graph);
+            if (le != cudaSuccess || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return gfail(g, SRFMG_ECUDA, std::string("group capture: ") + cudaGetErrorString(le != cudaSuccess ? le : e));
+            }
+            e = cudaGraphInstantiate(&g->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { g->exec = nullptr; return gfail(g, SRFMG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)); }
+            g->gf = f;
+            g->gu = u;
+        }
+        e = cudaGraphLaunch(g->exec, s);
+        if (e != cudaSuccess) return gfail(g, SRFMG_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    }
+    for (srfmg_plan *h : g->plans) h->solved = true;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_solve_host(srfmg_group_handle g, const double *f, double *u, void *stream) {
+    if (!g) return gfail(nullptr, SRFMG_EINVAL, "group handle is NULL");
+    if (!f || !u) return gfail(g, SRFMG_EINVAL, "f and u must be host pointers");
+    NvtxRange range("srfmg_group_solve_host");
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e == cudaSuccess && !g->f_stage) {
+        e = cudaMalloc(&g->f_stage, g->total * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&g->u_stage, g->total * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (g->f_stage) cudaFree(g->f_stage);
+            g->f_stage = nullptr;
+            return gfail(g, SRFMG_ENOMEM, std::string("group staging buffers: ") + cudaGetErrorString(e));
+        }
+    }
+    // every branch copies its own part in, solves it and copies it out, so
+    // one size's copies overlap the others' kernels and copies
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess) e = cudaEventRecord(g->fork, s);
+    for (size_t c = 0; c < g->plans.size() && e == cudaSuccess; ++c) {
+        const size_t o = g->off[c], cells = (size_t)g->count[c] << g->m[c];
+        cudaStream_t b = g->side[c];
+        e = cudaStreamWaitEvent(b, g->fork, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->f_stage + o, f + o, cells * sizeof(double), cudaMemcpyHostToDevice, b);
+        if (e == cudaSuccess)
+            e = enqueue_all(g->plans[c], Io{g->f_stage + o, g->u_stage + o, nullptr, nullptr, nullptr}, b);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u + o, g->u_stage + o, cells * sizeof(double), cudaMemcpyDeviceToHost, b);
+        if (e == cudaSuccess) e = cudaEventRecord(g->join[c], b);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g->join[c], 0);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return gfail(g, SRFMG_ECUDA, std::string("group solve from host memory: ") + cudaGetErrorString(e));
+    for (srfmg_plan *h : g->plans) h->solved = true;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_query(srfmg_group_handle g, int32_t *nplans, int64_t *total_cells) {
+    if (!g) return gfail(nullptr, SRFMG_EINVAL, "group handle is NULL");
+    if (nplans) *nplans = (int32_t)g->plans.size();
+    if (total_cells) *total_cells = (int64_t)g->total;
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_member(srfmg_group_handle g, int32_t i, srfmg_handle *plan, int32_t *log2_n,
+                                int32_t *count, int64_t *offset) {
+    if (!g) return gfail(nullptr, SRFMG_EINVAL, "group handle is NULL");
+    if (i < 0 || i >= (int32_t)g->plans.size()) return gfail(g, SRFMG_EINVAL, "plan index out of range");
+    if (plan) *plan = g->plans[i];
+    if (log2_n) *log2_n = g->m[i];
+    if (count) *count = g->count[i];
+    if (offset) *offset = (int64_t)g->off[i];
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_group_destroy(srfmg_group_handle g) {
+    if (!g) return SRFMG_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    group_release(g);
+    delete g;
+    return SRFMG_OK;
+}
+
+const char *srfmg_group_last_error(srfmg_group_handle g) {
+    return g ? g->err.c_str() : g_group_create_error.c_str();
+}
 
 }  // extern "C"
 

@@ -22,7 +22,9 @@ EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_h
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
            "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
-           "srfmg_destroy", "srfmg_last_error", "srfmg_version")
+           "srfmg_destroy", "srfmg_last_error", "srfmg_version",
+           "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
+           "srfmg_group_query", "srfmg_group_member", "srfmg_group_destroy", "srfmg_group_last_error")
 
 
 class Params(ctypes.Structure):
@@ -38,7 +40,8 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("workspace_bytes", ctypes.c_int64), ("kernels_per_solve", ctypes.c_int32),
                 ("coarse_tail_level", ctypes.c_int32), ("n_segments", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("segment_width", ctypes.c_int32), ("buffer_width", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class SrfmgError(RuntimeError):
@@ -92,12 +95,25 @@ def load(build_if_missing=True):
     lib.srfmg_solve_functionals.argtypes = [H, vp, vp, vp, vp, vp]
     lib.srfmg_reconstruct.argtypes = [H, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.srfmg_check.argtypes = [H, vp]
+    i32p, i64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    lib.srfmg_group_offsets.argtypes = [ctypes.c_int32, i32p, i64p]
+    lib.srfmg_group_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, i32p, ctypes.c_int32,
+                                       ctypes.c_int, ctypes.POINTER(H)]
+    lib.srfmg_group_solve.argtypes = [H, vp, vp, vp]
+    lib.srfmg_group_solve_host.argtypes = [H, dp, dp, vp]
+    lib.srfmg_group_query.argtypes = [H, i32p, i64p]
+    lib.srfmg_group_member.argtypes = [H, ctypes.c_int32, ctypes.POINTER(H), i32p, i32p, i64p]
+    lib.srfmg_group_destroy.argtypes = [H]
+    lib.srfmg_group_last_error.argtypes = [H]
+    lib.srfmg_group_last_error.restype = ctypes.c_char_p
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
                  "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
-                 "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check"):
+                 "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check", "srfmg_group_offsets",
+                 "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host", "srfmg_group_query",
+                 "srfmg_group_member", "srfmg_group_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -273,6 +289,113 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.srfmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def group_offsets(log2_n):
+    """Packed layout of a group (host only): offsets[k] = first cell of problem
+    k, offsets[-1] = total cells; problems ordered by size, then by index."""
+    import numpy as np
+    sizes = np.ascontiguousarray(log2_n, dtype=np.int32)
+    offs = np.empty(sizes.size + 1, dtype=np.int64)
+    st = load().srfmg_group_offsets(sizes.size, sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if st != OK:
+        raise SrfmgError(st, load().srfmg_group_last_error(None).decode())
+    return offs
+
+
+class _Member(Solver):
+    """A plan owned by a group (srfmg_group_member): the per-plan calls of
+    Solver on its part of the packed arrays; closing it does nothing."""
+
+    def __init__(self, lib, h, log2_n, count, offset, params):
+        self.lib, self.h, self.device = lib, h, None
+        self.params = params
+        self.n, self.batch = 1 << log2_n, count
+        self.offset = offset
+
+    def close(self):
+        self.h = None
+
+
+class Group:
+    """Independent problems of uneven sizes: ``Group(log2_n_list, **params)``.
+
+    One batched plan per distinct size, all replayed as one CUDA graph.  The
+    packed arrays hold the problems ordered by size, then by index
+    (``offsets``).  ``tune=k`` autotunes each size's segment layout with k
+    timed solves per candidate."""
+
+    def __init__(self, log2_n, device=0, tune=0, **overrides):
+        import numpy as np
+        self.lib = load()
+        self.sizes = np.ascontiguousarray(log2_n, dtype=np.int32)
+        self.offsets = group_offsets(self.sizes)
+        self.total = int(self.offsets[-1])
+        self.params = default_params(int(self.sizes.max()), **overrides)
+        h = ctypes.c_void_p()
+        st = self.lib.srfmg_group_create(ctypes.byref(self.params), self.sizes.size,
+                                         self.sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         tune, device, ctypes.byref(h))
+        if st != OK:
+            raise SrfmgError(st, self.lib.srfmg_group_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def _check(self, st, what):
+        if st != OK:
+            raise SrfmgError(st, f"{what}: {self.lib.srfmg_group_last_error(self.h).decode()}")
+
+    def members(self):
+        """The plans, by ascending size (Solver views owned by the group)."""
+        n = ctypes.c_int32()
+        self._check(self.lib.srfmg_group_query(self.h, ctypes.byref(n), None), "query")
+        out = []
+        for i in range(n.value):
+            hp, m, c, o = ctypes.c_void_p(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+            self._check(self.lib.srfmg_group_member(self.h, i, ctypes.byref(hp), ctypes.byref(m), ctypes.byref(c),
+                                                    ctypes.byref(o)), "member")
+            inf = Info()
+            self._check(self.lib.srfmg_query(hp, ctypes.byref(inf)), "query")
+            p = default_params(m.value, precision=self.params.precision, n_sr_levels=self.params.n_sr_levels,
+                               batch=c.value)
+            p.segment_width, p.buffer_width = inf.segment_width or p.segment_width, inf.buffer_width or p.buffer_width
+            out.append(_Member(self.lib, hp, m.value, c.value, o.value, p))
+        return out
+
+    def solve(self, f, u=None, stream=None):
+        import torch
+        if not (f.is_cuda and f.dtype == torch.float64 and f.is_contiguous() and f.numel() == self.total):
+            raise ValueError("f must be a contiguous CUDA float64 tensor of the group's total cells")
+        if u is None:
+            u = torch.empty_like(f)
+        self._check(self.lib.srfmg_group_solve(self.h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                               _stream_ptr(stream)), "solve")
+        return u
+
+    def solve_host(self, f, u=None, stream=None):
+        """Solve from and to host numpy arrays of the packed layout (synchronises)."""
+        import numpy as np
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.size != self.total:
+            raise ValueError("f must hold the group's total cells")
+        if u is None:
+            u = np.empty_like(f)
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.srfmg_group_solve_host(self.h, f.ctypes.data_as(dp), u.ctypes.data_as(dp),
+                                                    _stream_ptr(stream)), "solve_host")
+        return u
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.srfmg_group_destroy(self.h)
             self.h = None
 
     def __del__(self):
