@@ -521,8 +521,8 @@ void build_schedule(srfmg_plan *h) {
     sc.scale = h->scale;
     sc.status = h->status;
     sc.level = h->M;
-    // max|f| of each problem: one block per 4096 cells (at most 4 x 152)
-    const size_t sblocks = std::min<size_t>(608, std::max<size_t>(1, h->n / 4096));
+    // max|f| of each problem: one block per 4096 cells (at most 8 x 152)
+    const size_t sblocks = std::min<size_t>(1216, std::max<size_t>(1, h->n / 4096));
     sc.grid = dim3((unsigned)sblocks, (unsigned)h->batch);
     sc.block = dim3(256);
     h->ops.insert(h->ops.begin(), sc);
@@ -568,10 +568,7 @@ cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     switch (o.kind) {
     case OP_SCALE: {
         const long long n = (long long)o.level < 63 ? (1LL << o.level) : 0;
-        const dim3 one(1, o.grid.y);
-        e = run(fx::scale_reset_kernel, one, dim3(32), 0, s, pdl, o.scale);
-        if (e == cudaSuccess) e = run(fx::scale_max_kernel, o.grid, o.block, 0, s, true, f, n, o.scale, o.status);
-        if (e == cudaSuccess) e = run(fx::scale_finish_kernel, one, dim3(32), 0, s, true, o.scale);
+        e = run(fx::scale_kernel, o.grid, o.block, 0, s, pdl, f, n, o.scale, o.status);
         break;
     }
     case OP_RHS: e = run(fx::rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.frhs); break;
@@ -784,8 +781,12 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     if (st == SRFMG_OK && h->nRS >= 1) st = alloc_dev(h, &h->fpart, B * (h->n / h->W) * kNumFunc);
     if (st == SRFMG_OK && h->fixed) {
         double *sc = nullptr;
-        st = alloc_dev(h, &sc, 2 * B);
+        static_assert(sizeof(fx::Scale) % sizeof(double) == 0, "Scale is a whole number of doubles");
+        st = alloc_dev(h, &sc, B * (sizeof(fx::Scale) / sizeof(double)));
         h->scale = (fx::Scale *)sc;
+        // the scale kernel's accumulators start at zero (it restores them after every solve)
+        if (st == SRFMG_OK && (e = cudaMemset(sc, 0, B * sizeof(fx::Scale))) != cudaSuccess)
+            st = cuda_fail(h, e, "cudaMemset(scales)");
     }
     if (p->op == SRFMG_OP_VARCOEF) {
         for (int l = h->M0; l <= h->M && st == SRFMG_OK; ++l) st = alloc_dev(h, &h->coef[l], B * (((size_t)1 << l) + 1));

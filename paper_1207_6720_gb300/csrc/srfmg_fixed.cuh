@@ -36,6 +36,11 @@ struct Scale {
     int Sg0;     // g_l = G 2^-(Sg0 + 2l)
     int E;       // max|f| < 2^E
     int pad;
+    // scale_kernel's accumulators: zero between solves (set at plan creation,
+    // restored by the kernel's last block)
+    int emax;           // largest biased exponent field of f seen so far
+    unsigned done;      // blocks of this problem that have finished
+    int pad2, pad3;
 };
 
 // x / 2^k rounded half up, 0 < k < 63.
@@ -249,31 +254,45 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
 // Scale: E with max|f| < 2^E from the largest exponent field of f.
 // --------------------------------------------------------------------------
 // (one Scale per problem of a batch: sc[blockIdx.y])
-__global__ void scale_reset_kernel(Scale *sc) {
+// One launch: every block reduces the exponent fields of its part of f (16-byte
+// loads; n is even and f 16-byte aligned) into sc->emax; the last block of the
+// problem to finish (a counter, after a fence) turns the maximum into E, S and
+// Sg0 and restores the accumulators to zero for the next solve.  An inf or
+// NaN in f (exponent field 0x7ff) is recorded in the status word.
+__global__ void scale_kernel(const double *f, long long n, Scale *sc, int *status) {
     pdl_enter();
-    sc += blockIdx.y;
-    if (threadIdx.x == 0) { sc->E = -2000; sc->S = 0; sc->Sg0 = 0; }
-}
-
-__global__ void scale_max_kernel(const double *f, long long n, Scale *sc, int *status) {
-    pdl_enter();
-    f = batch_at(f, n);
+    const double2 *f2 = reinterpret_cast<const double2 *>(batch_at(f, n));
     sc += blockIdx.y;
     int emax = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int e = (int)((__double_as_longlong(f[i]) >> 52) & 0x7ff);
-        emax = max(emax, e);
+    const long long n2 = n >> 1, stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; i + 7 * stride < n2; i += 8 * stride) {     // eight 16-byte loads in flight per thread
+        double2 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = f2[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            emax = max(emax, (int)((__double_as_longlong(v[k].x) >> 52) & 0x7ff));
+            emax = max(emax, (int)((__double_as_longlong(v[k].y) >> 52) & 0x7ff));
+        }
+    }
+    for (; i < n2; i += stride) {
+        const double2 v = f2[i];
+        emax = max(emax, (int)((__double_as_longlong(v.x) >> 52) & 0x7ff));
+        emax = max(emax, (int)((__double_as_longlong(v.y) >> 52) & 0x7ff));
     }
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&sc->E, emax - 1022);
-    if ((threadIdx.x & 31) == 0 && emax == 0x7ff && status) atomicOr(status, kStatusNonFinite);   // inf or NaN in f
-}
-
-__global__ void scale_finish_kernel(Scale *sc) {
-    pdl_enter();
-    sc += blockIdx.y;
-    if (threadIdx.x == 0) {
-        int E = sc->E;
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&sc->emax, emax);
+        if (emax == 0x7ff && status) atomicOr(status, kStatusNonFinite);   // inf or NaN in f
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&sc->done, 1u) == gridDim.x - 1) {
+        __threadfence();
+        const int raw = atomicExch(&sc->emax, 0);
+        sc->done = 0;
+        int E = raw - 1022;                      // 2^E bounds max|f| (raw 0: f = 0)
         E = E < -100 ? -100 : (E > 900 ? 900 : E);
         sc->E = E;
         sc->S = 62 - E;
@@ -553,8 +572,12 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
 // the right-hand side gs = G >> (2M-2) in solution units, G converted from f
 // on the finest level or read from g_in below it; with gr, also the restricted
 // right-hand side of the segment's coarse cells [J0, J1).  The staged range
-// may start at an odd cell, so pairs are clipped to it.
-__device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) {
+// may start at an odd cell, so pairs are clipped to it.  With kacz, the first
+// Kaczmarz pass of the post-leg (Fig. 5) is applied to the pairs inside the
+// extended patch as they are interpolated (the same arithmetic as the
+// separate pass, without its extra sweep over shared memory); the return value
+// says whether that happened (not when the iterate is staged instead of Pi).
+__device__ bool seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1, bool kacz = false) {
     const int nc = a.n >> 1, kg = (a.sc + blockIdx.y)->Sg0, gsh = 2 * a.M - 2;
     const bool from_f = (a.g_in == nullptr);
     if (a.u_in) stage_range(m.u, batch_at(a.u_in, a.n) + m.lo, m.hi - m.lo);
@@ -581,14 +604,20 @@ __device__ void seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1) 
         }
     }
     __syncthreads();
-    if (a.u_in || a.u_in_f64) return;
+    if (a.u_in || a.u_in_f64) return false;
     for (int J = (m.lo >> 1) + (int)threadIdx.x; 2 * J < m.hi; J += (int)blockDim.x) {
         i64 l, r;
         fmg_interp2(m.c, m.C0, J, l, r);
+        if (kacz && 2 * J >= m.e0 && 2 * J + 1 < m.e1) {
+            const i64 k = m.c[J - m.C0] - ((l + r) >> 1);
+            l += k;
+            r += k;
+        }
         if (2 * J >= m.lo) m.u[2 * J - m.lo] = l;
         if (2 * J + 1 < m.hi) m.u[2 * J + 1 - m.lo] = r;
     }
     __syncthreads();
+    return kacz;
 }
 
 __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
@@ -745,16 +774,18 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     const int s = (a.seg0 + (int)blockIdx.x) * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(smi, a, s);
-    seg_load(m, a, nullptr, 0, 0);
+    const bool first_done = seg_load(m, a, nullptr, 0, 0, true);
     i64 *p = m.u;
     for (int k = 0; k < a.nu; ++k) {
-        for (int J = (m.e0 >> 1) + (int)threadIdx.x; J < (m.e1 >> 1); J += (int)blockDim.x) {
-            int i0 = 2 * J - m.lo;
-            i64 r = m.c[J - m.C0] - ((p[i0] + p[i0 + 1]) >> 1);
-            p[i0] += r;
-            p[i0 + 1] += r;
+        if (k > 0 || !first_done) {
+            for (int J = (m.e0 >> 1) + (int)threadIdx.x; J < (m.e1 >> 1); J += (int)blockDim.x) {
+                int i0 = 2 * J - m.lo;
+                i64 r = m.c[J - m.C0] - ((p[i0] + p[i0 + 1]) >> 1);
+                p[i0] += r;
+                p[i0 + 1] += r;
+            }
+            __syncthreads();
         }
-        __syncthreads();
         lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
     const int S = (a.sc + blockIdx.y)->S;

@@ -90,10 +90,29 @@ __device__ __forceinline__ void stage8(void *smem, const void *gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
 }
 // copy count 8-byte words src[0..count) to dst[0..count)
+__device__ __forceinline__ void stage16(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    size_t g = __cvta_generic_to_global(gmem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+// copy count 8-byte words src[0..count) to dst[0..count): 16-byte copies when
+// both addresses share their offset within 16 bytes (an odd first or last
+// word by itself), 8-byte copies otherwise
 __device__ __forceinline__ void stage_range(void *dst, const void *src, int count) {
     char *d = (char *)dst;
     const char *g = (const char *)src;
-    for (int k = threadIdx.x; k < count; k += blockDim.x) stage8(d + 8 * (size_t)k, g + 8 * (size_t)k);
+    if (count <= 0) return;
+    if ((((uintptr_t)d ^ (uintptr_t)g) & 15) == 0) {
+        const int head = ((uintptr_t)d & 15) ? 1 : 0;
+        const int pairs = (count - head) >> 1;
+        if (head && threadIdx.x == 0) stage8(d, g);
+        for (int k = threadIdx.x; k < pairs; k += blockDim.x)
+            stage16(d + 8 * head + 16 * (size_t)k, g + 8 * head + 16 * (size_t)k);
+        if (((count - head) & 1) && threadIdx.x == blockDim.x - 1)
+            stage8(d + 8 * (size_t)(count - 1), g + 8 * (size_t)(count - 1));
+    } else {
+        for (int k = threadIdx.x; k < count; k += blockDim.x) stage8(d + 8 * (size_t)k, g + 8 * (size_t)k);
+    }
 }
 // wait for this thread's copies; follow with __syncthreads() before reading
 __device__ __forceinline__ void stage_wait() {
