@@ -187,6 +187,25 @@ srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begi
  * buffers give the fastest copies; pageable ones work.  f and u may alias. */
 srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream);
 
+/* Pipelined solves from and to HOST memory, for a stream of right-hand sides:
+ * like srfmg_solve_host, but the call only enqueues and returns.  Each call
+ * copies f into one of two device staging buffers of the plan (used in turn),
+ * solves on `stream` into the matching solution buffer, and copies the
+ * solution back into u; the copies run on two streams of the plan, so a
+ * call's copy-in overlaps the previous call's solve and its copy-out the next
+ * call's solve.  Ordering: the solves run in call order on `stream`, each
+ * after the work enqueued on `stream` before it; a call's copy-in does not wait
+ * for `stream` (f is read from host memory as it is when the call is made, and
+ * must not be written by work still pending on the GPU).
+ * srfmg_solve_host_join(h, stream) makes `stream` wait for every copy-out
+ * enqueued so far; only after that stream reaches the join may u be read, and f
+ * and u (host buffers) must stay valid and unchanged until then.  Pinned host
+ * buffers are needed for the overlap (pageable ones work, without it).  The
+ * first call allocates the staging buffers (4 x N doubles per problem).
+ * Errors as srfmg_solve_host (SRFMG_EINVAL for NULL pointers). */
+srfmg_status srfmg_solve_host_async(srfmg_handle h, const double *f, double *u, void *stream);
+srfmg_status srfmg_solve_host_join(srfmg_handle h, void *stream);
+
 /* Gradient of a loss L(u) through the solve (the paper has no adjoint; the
  * operator is the one of Sec. 4).  The discrete operator L of SRFMG_OP_LAPLACE
  * (cell-centred finite volumes with odd ghosts: tridiag(-1, 2, -1)/h^2 with 3 in

@@ -89,6 +89,12 @@ struct srfmg_plan {
     bool solved = false;           // a solve has been enqueued (its coarse solution is kept)
     bool fixed = false;
     double *f_stage = nullptr, *u_stage = nullptr;
+    // pipelined host solves (srfmg_solve_host_async): two staging pairs used in
+    // turn, copy-in and copy-out streams, and the events that order them
+    double *hf[2] = {}, *hu[2] = {};
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_join = nullptr, ev_in[2] = {}, ev_solved[2] = {}, ev_out[2] = {};
+    int hslot = 0;
     size_t ws_bytes = 0;
     std::vector<Op> ops;
     std::vector<std::string> names;
@@ -705,6 +711,11 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
 void release(srfmg_plan *h) {
     for (auto &g : h->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t ev : {h->ev_join, h->ev_in[0], h->ev_in[1], h->ev_solved[0], h->ev_solved[1],
+                           h->ev_out[0], h->ev_out[1]})
+        if (ev) cudaEventDestroy(ev);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void *ptr : h->allocs) cudaFree(ptr);
     h->allocs.clear();
@@ -969,6 +980,60 @@ srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
     return SRFMG_OK;
+}
+
+srfmg_status srfmg_solve_host_async(srfmg_handle h, const double *f, double *u, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (!f || !u) return fail(h, SRFMG_EINVAL, "f and u must be host pointers");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t total = h->n * (size_t)h->batch, bytes = total * sizeof(double);
+    if (!h->s_out) {            // first call: staging pairs, streams and events
+        srfmg_status st = SRFMG_OK;
+        for (int b = 0; b < 2 && st == SRFMG_OK; ++b) {
+            st = alloc_dev(h, &h->hf[b], total);
+            if (st == SRFMG_OK) st = alloc_dev(h, &h->hu[b], total);
+        }
+        if (st != SRFMG_OK) return st;
+        cudaEvent_t *evs[] = {&h->ev_join, &h->ev_in[0], &h->ev_in[1], &h->ev_solved[0],
+                              &h->ev_solved[1], &h->ev_out[0], &h->ev_out[1]};
+        for (cudaEvent_t *ev : evs)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline set-up");
+    }
+    const int b = h->hslot;
+    h->hslot ^= 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    // copy in as soon as the solve that last read this staging buffer (two
+    // calls back) is done; f is host memory, ready when the call is made, so
+    // the copy does not wait for `stream` (it overlaps the previous solve)
+    e = cudaStreamWaitEvent(h->s_in, h->ev_solved[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->hf[b], f, bytes, cudaMemcpyHostToDevice, h->s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[b], h->s_in);
+    // solve on `stream` once f is in and this solution buffer's last copy-out is done
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_in[b], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_out[b], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline (copy in)");
+    srfmg_status st = srfmg_solve(h, h->hf[b], h->hu[b], stream);
+    if (st != SRFMG_OK) return st;
+    // copy out after the solve, overlapping the next call's solve
+    e = cudaEventRecord(h->ev_solved[b], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_solved[b], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, h->hu[b], bytes, cudaMemcpyDeviceToHost, h->s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[b], h->s_out);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host pipeline (copy out)");
+    return SRFMG_OK;
+}
+
+srfmg_status srfmg_solve_host_join(srfmg_handle h, void *stream) {
+    if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
+    if (!h->s_out) return SRFMG_OK;        // nothing was enqueued
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, h->ev_join, 0);
+    return e == cudaSuccess ? SRFMG_OK : cuda_fail(h, e, "srfmg_solve_host_join");
 }
 
 // The operator of SRFMG_OP_LAPLACE (cell-centred, odd ghosts: tridiag(-1, 2, -1)/h^2

@@ -23,7 +23,7 @@ EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_h
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
            "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version",
-           "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
+           "srfmg_solve_host_async", "srfmg_solve_host_join", "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
            "srfmg_group_query", "srfmg_group_member", "srfmg_group_destroy", "srfmg_group_last_error")
 
 
@@ -74,6 +74,8 @@ def load(build_if_missing=True):
     lib.srfmg_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(H)]
     lib.srfmg_solve.argtypes = [H, vp, vp, vp]
     lib.srfmg_solve_host.argtypes = [H, dp, dp, vp]
+    lib.srfmg_solve_host_async.argtypes = [H, dp, dp, vp]
+    lib.srfmg_solve_host_join.argtypes = [H, vp]
     lib.srfmg_adjoint.argtypes = [H, vp, vp, vp]
     lib.srfmg_query.argtypes = [H, ctypes.POINTER(Info)]
     lib.srfmg_destroy.argtypes = [H]
@@ -111,7 +113,8 @@ def load(build_if_missing=True):
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
                  "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
-                 "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check", "srfmg_group_offsets",
+                 "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check", "srfmg_solve_host_async",
+                 "srfmg_solve_host_join", "srfmg_group_offsets",
                  "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host", "srfmg_group_query",
                  "srfmg_group_member", "srfmg_group_destroy"):
         getattr(lib, name).restype = ctypes.c_int
@@ -273,6 +276,22 @@ class Solver:
         self._check(self.lib.srfmg_solve_host(self.h, f.ctypes.data_as(dp), u.ctypes.data_as(dp),
                                                _stream_ptr(stream)), "solve_host")
         return u
+
+    def solve_host_async(self, f, u, stream=None):
+        """Enqueue a solve from and to host numpy arrays (pinned for overlap); the
+        copies overlap the neighbouring solves.  Call host_join (and synchronise
+        the stream) before reading u or changing f."""
+        if f.dtype.name != "float64" or u.dtype.name != "float64" or not (
+                f.flags.c_contiguous and u.flags.c_contiguous) or f.size != self.n * self.batch or u.size != f.size:
+            raise ValueError("f and u must be contiguous float64 arrays of batch * 2^log2_n values")
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._check(self.lib.srfmg_solve_host_async(self.h, f.ctypes.data_as(dp), u.ctypes.data_as(dp),
+                                                     _stream_ptr(stream)), "solve_host_async")
+        return u
+
+    def host_join(self, stream=None):
+        """Make the stream wait for every copy-out of solve_host_async so far."""
+        self._check(self.lib.srfmg_solve_host_join(self.h, _stream_ptr(stream)), "solve_host_join")
 
     def profile(self, f, u=None, nsolves=3, stream=None):
         """Per-launch average durations (ms) of one solve: list of (name, ms)."""

@@ -87,6 +87,8 @@ def test_null_handle_calls():
     lib = srfmg.load()
     assert lib.srfmg_solve(None, None, None, None) == srfmg.EINVAL
     assert lib.srfmg_solve_host(None, None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_solve_host_async(None, None, None, None) == srfmg.EINVAL
+    assert lib.srfmg_solve_host_join(None, None) == srfmg.EINVAL
     assert lib.srfmg_adjoint(None, None, None, None) == srfmg.EINVAL
     assert lib.srfmg_query(None, None) == srfmg.EINVAL
     assert lib.srfmg_destroy(None) == srfmg.OK
