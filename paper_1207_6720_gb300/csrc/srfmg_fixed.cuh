@@ -60,24 +60,25 @@ __device__ __forceinline__ i64 f64_to_fixed(double x, int k) {
     return (b >> 63) ? -v : v;
 }
 
-// U 2^-S as the nearest double (ties to even).
+// U 2^-S as the nearest double (ties to even), for |U| < 2^59.  m = |U| has
+// its leading one at bit p; above 53 significant bits it is rounded by adding
+// half a unit minus one plus the lowest kept bit and truncating (ties go to the
+// even quotient), and the 53-bit q (implicit one at bit 52, or 2^53 after a
+// rounding carry) is added to the exponent field (p - S + 1022) << 52, so that
+// a carry out of the mantissa raises the exponent by itself.
 __device__ __forceinline__ double fixed_to_f64(i64 U, int S) {
-    if (U == 0) return 0.0;
-    u64 sign = (U < 0) ? (1ULL << 63) : 0ULL;
-    u64 m = (U < 0) ? (u64)(-U) : (u64)U;
-    int p = 63 - __clzll((long long)m);          // position of the leading bit
-    u64 mant;
+    const u64 sign = (u64)U & (1ULL << 63);
+    const u64 m = sign ? (u64)0 - (u64)U : (u64)U;
+    const int p = 63 - __clzll((long long)(m | 1));
+    u64 q;
     if (p > 52) {
-        int sh = p - 52;
-        u64 q = m >> sh, rem = m & ((1ULL << sh) - 1), half = 1ULL << (sh - 1);
-        if (rem > half || (rem == half && (q & 1))) ++q;
-        if (q >> 53) { q >>= 1; ++p; }
-        mant = q;
+        const int sh = p - 52;
+        q = (m + ((1ULL << (sh - 1)) - 1) + ((m >> sh) & 1)) >> sh;
     } else {
-        mant = m << (52 - p);
+        q = m << (52 - p);
     }
-    u64 expo = (u64)(p - S + 1023);
-    return __longlong_as_double((long long)(sign | (expo << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+    const u64 b = sign | ((((u64)(p - S + 1022)) << 52) + q);
+    return __longlong_as_double((long long)(U == 0 ? 0ULL : b));
 }
 
 // Fourth order FMG interpolation Pi (Sec. 4) in fixed point: 128 Pi is the
@@ -791,9 +792,16 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     const int S = (a.sc + blockIdx.y)->S;
     const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
     double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;
-    if (u_out)
+    if (u_out && ((uintptr_t)u_out & 15) == 0) {      // pairs of cells, 16-byte stores (W is even)
+        double2 *o2 = reinterpret_cast<double2 *>(u_out + (s - s0));
+        for (int j = (int)threadIdx.x; j < (a.W >> 1); j += (int)blockDim.x) {
+            const int i = s + 2 * j - m.lo;
+            o2[j] = make_double2(fixed_to_f64(p[i], S), fixed_to_f64(p[i + 1], S));
+        }
+    } else if (u_out) {
         for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x)
             u_out[i - s0] = fixed_to_f64(p[i - m.lo], S);
+    }
     if (a.u_out_fx) {
         i64 *uo = batch_at(a.u_out_fx, a.n);
         for (int i = s + (int)threadIdx.x; i < s + a.W; i += (int)blockDim.x) uo[i] = p[i - m.lo];
