@@ -30,7 +30,10 @@
  *   - The caller owns f and u; the handle owns its device workspace (the
  *     stored coarse levels, the seam buffer, the coarsest-grid inverse and
  *     the captured CUDA graphs).
- *   - A handle may be used from one host thread at a time.
+ *   - A handle may be used from one host thread at a time.  Its calls share
+ *     the handle's device workspace, so calls that use it (solves, adjoints,
+ *     reconstructions) must be ordered on the GPU: enqueue them on one
+ *     stream, or order their streams with events.
  *   - There is no CPU fallback: without a usable CUDA device srfmg_create
  *     returns SRFMG_ECUDA.
  */

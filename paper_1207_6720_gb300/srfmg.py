@@ -383,9 +383,11 @@ class Group:
                                                     ctypes.byref(o)), "member")
             inf = Info()
             self._check(self.lib.srfmg_query(hp, ctypes.byref(inf)), "query")
-            p = default_params(m.value, precision=self.params.precision, n_sr_levels=self.params.n_sr_levels,
-                               batch=c.value)
-            p.segment_width, p.buffer_width = inf.segment_width or p.segment_width, inf.buffer_width or p.buffer_width
+            p = Params()
+            ctypes.memmove(ctypes.byref(p), ctypes.byref(self.params), ctypes.sizeof(Params))
+            p.log2_n, p.batch = m.value, c.value
+            if inf.segment_width:
+                p.segment_width, p.buffer_width = inf.segment_width, inf.buffer_width
             out.append(_Member(self.lib, hp, m.value, c.value, o.value, p))
         return out
 

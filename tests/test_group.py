@@ -78,11 +78,12 @@ def test_group_without_gpu_is_an_error():
     assert st == srfmg.ECUDA and h.value is None
 
 
-def _packed(sizes, seeds):
+def _packed(sizes, seeds, bratu=False):
     offs = srfmg.group_offsets(sizes)
     f = np.empty(offs[-1])
     for k, (m, s) in enumerate(zip(sizes, seeds)):
-        f[offs[k]:offs[k] + (1 << m)] = workloads.sine_series(m, 16, seed=s)[0]
+        gen = workloads.bratu_series(m, 16, seed=s, lam=1.0) if bratu else workloads.sine_series(m, 16, seed=s)
+        f[offs[k]:offs[k] + (1 << m)] = gen[0]
     return f, offs
 
 
@@ -92,6 +93,7 @@ GROUPS = [
     ([10, 8, 12, 10, 14, 8, 10, 12, 6, 13], dict(precision=srfmg.FP64)),
     ([11, 9, 15, 11, 7], dict(precision=srfmg.FP64, n_sr_levels=0)),
     ([12, 10, 12, 16], dict(precision=srfmg.MIXED, segment_width=1024, buffer_width=4, nu1=2)),
+    ([12, 9, 13, 12], dict(precision=srfmg.FP64, op=srfmg.BRATU, lambda_=1.0, nu1=2, segment_width=512)),
 ]
 
 
@@ -100,7 +102,8 @@ GROUPS = [
 def test_group_equals_single_solves_gpu(sizes, kw):
     torch = pytest.importorskip("torch")
     seeds = [100 + k for k in range(len(sizes))]
-    f, offs = _packed(sizes, seeds)
+    bratu = kw.get("op") == srfmg.BRATU
+    f, offs = _packed(sizes, seeds, bratu)
     g = srfmg.Group(sizes, **kw)
     try:
         members = g.members()
@@ -117,6 +120,7 @@ def test_group_equals_single_solves_gpu(sizes, kw):
         uh = g.solve_host(f)                    # host buffers, copies inside
         assert np.array_equal(uh, u1)
         info = {mb.n: (mb.params.segment_width, mb.params.buffer_width) for mb in members}
+        assert all(mb.params.op == kw.get("op", 0) for mb in members)
     finally:
         g.close()
     nRS = kw.get("n_sr_levels", 1)
@@ -136,7 +140,8 @@ def test_group_equals_single_solves_gpu(sizes, kw):
     k = int(np.argmax(sizes))
     m = sizes[k]
     W, b = info[1 << m]
-    p = oracle.sr_params(m, W, b, nu1=kw.get("nu1", 1)) if nRS else oracle.Params(m, nRS=0)
+    extra = dict(op="bratu", lam=1.0) if bratu else {}
+    p = oracle.sr_params(m, W, b, nu1=kw.get("nu1", 1), **extra) if nRS else oracle.Params(m, nRS=0)
     r = oracle.fmg_h(p, f[offs[k]:offs[k] + (1 << m)])
     assert np.max(np.abs(u1[offs[k]:offs[k] + (1 << m)] - r)) <= 1e-10 * np.max(np.abs(r))
 
