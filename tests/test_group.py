@@ -194,3 +194,39 @@ def test_group_member_calls_gpu():
                                      None) == srfmg.EINVAL     # overlap
     finally:
         g.close()
+
+
+@pytest.mark.gpu
+def test_group_variable_coefficient_through_members_gpu():
+    """-(a u')' = f in a group: each plan's coefficient is set through its
+    member handle (its problems' log a back to back), and every problem equals
+    its own single solve with the same coefficient."""
+    torch = pytest.importorskip("torch")
+    sizes = [11, 13, 11, 12]
+    offs = srfmg.group_offsets(sizes)
+    data = [workloads.varcoef_series(m, 16, seed=40 + k) for k, m in enumerate(sizes)]
+    f = np.empty(offs[-1])
+    for k, m in enumerate(sizes):
+        f[offs[k]:offs[k] + (1 << m)] = data[k][0]
+    kw = dict(op=srfmg.VARCOEF, precision=srfmg.FP64, segment_width=1024)
+    g = srfmg.Group(sizes, **kw)
+    try:
+        lay = {}
+        for mb in g.members():
+            m = mb.n.bit_length() - 1
+            ks = [k for k in sorted(range(len(sizes)), key=lambda k: (sizes[k], k)) if sizes[k] == m]
+            assert len(ks) == mb.batch
+            mb.set_coefficient(torch.from_numpy(np.concatenate([data[k][2] for k in ks])).cuda())
+            lay[m] = (mb.params.segment_width, mb.params.buffer_width)
+        u = g.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    finally:
+        g.close()
+    for k, m in enumerate(sizes):
+        W, b = lay[m]
+        s = srfmg.Solver(m, op=srfmg.VARCOEF, precision=srfmg.FP64, segment_width=W, buffer_width=b)
+        try:
+            s.set_coefficient(torch.from_numpy(data[k][2]).cuda())
+            ref = s.solve(torch.from_numpy(data[k][0]).cuda()).cpu().numpy()
+        finally:
+            s.close()
+        assert np.array_equal(u[offs[k]:offs[k] + (1 << m)], ref), (k, m)
