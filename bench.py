@@ -324,7 +324,9 @@ def run_reference(a):
     dt = time.perf_counter() - t0
     value = a.steps * (1 << Ms) / dt
     sample = f"one serial oracle solve of the same workload family at N=2^{Ms} per step"
-    line = {"metric": {"bratu": METRIC_BRATU, "varcoef": METRIC_VARCOEF}.get(a.workload, METRIC),
+    if a.workload == "batch":
+        sample = f"one serial oracle solve of a problem of the batch's family at N=2^{Ms} per step"
+    line = {"metric": {"bratu": METRIC_BRATU, "varcoef": METRIC_VARCOEF, "batch": METRIC_BATCH}.get(a.workload, METRIC),
             "value": value, "unit": UNIT,
             "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
