@@ -190,8 +190,9 @@ srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begi
  * buffers give the fastest copies; pageable ones work.  f and u may alias. */
 srfmg_status srfmg_solve_host(srfmg_handle h, const double *f, double *u, void *stream);
 
-/* Pipelined solves from and to HOST memory, for a stream of right-hand sides:
- * like srfmg_solve_host, but the call only enqueues and returns.  Each call
+/* Pipelined solves from and to HOST memory, for a stream of right-hand sides
+ * (no counterpart in the paper: a way to feed the solver of Figs. 2-3 from host
+ * memory): like srfmg_solve_host, but the call only enqueues and returns.  Each call
  * copies f into one of two device staging buffers of the plan (used in turn),
  * solves on `stream` into the matching solution buffer, and copies the
  * solution back into u; the copies run on two streams of the plan, so a
