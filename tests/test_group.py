@@ -230,3 +230,21 @@ def test_group_variable_coefficient_through_members_gpu():
         finally:
             s.close()
         assert np.array_equal(u[offs[k]:offs[k] + (1 << m)], ref), (k, m)
+
+
+def test_group_offsets_property_random_sizes():
+    """For random size lists the offsets tile [0, total) without gaps or
+    overlaps, in (size, index) order."""
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        n = int(rng.integers(1, 60))
+        sizes = [int(m) for m in rng.integers(1, 21, size=n)]
+        offs = srfmg.group_offsets(sizes)
+        order = sorted(range(n), key=lambda k: (sizes[k], k))
+        at = 0
+        for k in order:
+            assert offs[k] == at
+            at += 1 << sizes[k]
+        assert offs[n] == at
+        spans = sorted((int(offs[k]), int(offs[k]) + (1 << sizes[k])) for k in range(n))
+        assert all(a[1] == b[0] for a, b in zip(spans, spans[1:])) and spans[0][0] == 0
