@@ -248,3 +248,63 @@ def test_group_offsets_property_random_sizes():
         assert offs[n] == at
         spans = sorted((int(offs[k]), int(offs[k]) + (1 << sizes[k])) for k in range(n))
         assert all(a[1] == b[0] for a, b in zip(spans, spans[1:])) and spans[0][0] == 0
+
+
+@pytest.mark.gpu
+def test_group_splits_sizes_beyond_one_plan_gpu():
+    """More than 65535 problems of one size (the grid-row limit of a plan) are
+    split over several plans; every problem still equals its own solve."""
+    torch = pytest.importorskip("torch")
+    n_small = 65535 + 7
+    sizes = [4] * n_small + [8, 4]
+    offs = srfmg.group_offsets(sizes)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(int(offs[-1]))
+    g = srfmg.Group(sizes, precision=srfmg.MIXED, n_sr_levels=0)
+    try:
+        members = g.members()
+        assert [(mb.n, mb.batch) for mb in members] == [(16, 65535), (16, 8), (256, 1)]
+        assert [mb.offset for mb in members] == [0, 65535 * 16, (65535 + 8) * 16]
+        u = g.solve(torch.from_numpy(f).cuda()).cpu().numpy()
+    finally:
+        g.close()
+    s4 = srfmg.Solver(4, precision=srfmg.MIXED, n_sr_levels=0, batch=8)
+    s8 = srfmg.Solver(8, precision=srfmg.MIXED, n_sr_levels=0)
+    try:
+        for k in (0, 1, 65534, 65535, 65536, n_small - 1, n_small + 1):
+            a, b = int(offs[k]), int(offs[k]) + (1 << sizes[k])
+            # the same problem through a plan of its own (the second plan's 8 rows hold it)
+            fb = np.zeros(8 << 4) if sizes[k] == 4 else None
+            if sizes[k] == 4:
+                fb[:16] = f[a:b]
+                ref = s4.solve(torch.from_numpy(fb).cuda()).cpu().numpy()[:16]
+            else:
+                ref = s8.solve(torch.from_numpy(f[a:b].copy()).cuda()).cpu().numpy()
+            assert np.array_equal(u[a:b], ref), k
+    finally:
+        s4.close()
+        s8.close()
+
+
+@pytest.mark.gpu
+def test_group_without_graph_equals_graph_gpu(monkeypatch):
+    """SRFMG_NO_GRAPH=1 at creation: the group enqueues its branches directly
+    (no capture); results are the same bits as the graph's."""
+    torch = pytest.importorskip("torch")
+    sizes = [10, 12, 10, 13]
+    f, offs = _packed(sizes, [7, 8, 9, 10])
+    fd = torch.from_numpy(f).cuda()
+    g = srfmg.Group(sizes, precision=srfmg.MIXED)
+    try:
+        u_graph = g.solve(fd).cpu().numpy()
+    finally:
+        g.close()
+    monkeypatch.setenv("SRFMG_NO_GRAPH", "1")
+    g = srfmg.Group(sizes, precision=srfmg.MIXED)
+    monkeypatch.delenv("SRFMG_NO_GRAPH")
+    try:
+        u_direct = g.solve(fd).cpu().numpy()
+        u_direct2 = g.solve(fd).cpu().numpy()
+    finally:
+        g.close()
+    assert np.array_equal(u_direct, u_graph) and np.array_equal(u_direct2, u_graph)
