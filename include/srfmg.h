@@ -301,14 +301,18 @@ const char *srfmg_launch_name(srfmg_handle h, int32_t i);
  *   aligned, not overlapping; stream as in srfmg_solve.
  * Sizes beyond these limits return SRFMG_EINVAL and enqueue nothing; errors
  * are reported by the status code only (srfmg_last_error is not updated).
+ * This entry point has no status word and no srfmg_check: an inf or NaN in f
+ * is not detected and gives a non-finite u with SRFMG_OK.
  * The first call on a device (with that device current) does a synchronous
  * set-up: it looks up the static array's device address, raises the kernel's
  * shared-memory limit and uploads the inverse for log2_n_coarsest; a later
  * call with a different log2_n_coarsest uploads again.  Make the first call,
  * and any call that changes log2_n_coarsest, before any stream capture.  All
  * calls share the array and it keeps the last upload: calls with different
- * log2_n_coarsest that overlap on the GPU race.  Nothing in it has to start
- * at zero. */
+ * log2_n_coarsest whose kernels overlap on the GPU race.  Concurrent host
+ * calls are serialised by a lock held until the kernel is enqueued, so a call
+ * never launches with another call's table.  Nothing in the array has to
+ * start at zero. */
 #define SRFMG_NOALLOC_MAX_N 4096
 #define SRFMG_NOALLOC_MAX_COARSE 64
 srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n_coarsest, int32_t nu1,

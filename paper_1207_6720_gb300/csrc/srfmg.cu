@@ -1590,9 +1590,12 @@ extern "C" srfmg_status srfmg_solve_small_noalloc(int32_t log2_n, int32_t log2_n
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SRFMG_ECUDA; }
     if (dev < 0 || dev >= kNoallocMaxDevices) return SRFMG_EUNSUPPORTED;
 
+    // The lock is held through the launch: another host thread that changes
+    // the uploaded coarsest level then does so only after this call's kernel
+    // is enqueued (kernels of calls that overlap on the GPU still race).
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     double *ainv = nullptr;
     {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         NoallocDevice &d = g_noalloc_dev[dev];
         if (!d.ready) {
             void *ptr = nullptr;

@@ -484,7 +484,12 @@ def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None)
     """Plain FMG-FAS for N <= 4096 through srfmg_solve_small_noalloc, which
     allocates no device memory (for callers that cannot call cudaMalloc: open
     stream captures, pool-owned device memory, allocation-free loops).  f: CUDA
-    float64 tensor of 2^k values; returns u.  The first call on a device does a
+    float64 tensor of 2^k values; u: a CUDA float64 tensor of the same size on
+    the same device, which receives the solution and is returned.  With
+    u=None this wrapper allocates u (torch.empty_like), so a caller that must
+    not allocate passes u.  The call runs with f's device current (the entry
+    point finds its static array on the current device) and on that device's
+    current stream unless `stream` is given.  The first call on a device does a
     synchronous set-up and should come before any stream capture."""
     import torch
     n = f.numel()
@@ -493,9 +498,13 @@ def solve_small_noalloc(f, u=None, log2_n_coarsest=2, nu1=1, nu2=1, stream=None)
         raise ValueError("f must be a contiguous CUDA float64 tensor of 2^k values")
     if u is None:
         u = torch.empty_like(f)
-    st = load().srfmg_solve_small_noalloc(log2_n, log2_n_coarsest, nu1, nu2,
-                                           ctypes.c_void_p(f.data_ptr()),
-                                           ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream))
+    elif not (u.is_cuda and u.dtype == torch.float64 and u.is_contiguous() and u.numel() == n
+              and u.device == f.device):
+        raise ValueError("u must be a contiguous CUDA float64 tensor of f's size on f's device")
+    with torch.cuda.device(f.device):
+        st = load().srfmg_solve_small_noalloc(log2_n, log2_n_coarsest, nu1, nu2,
+                                               ctypes.c_void_p(f.data_ptr()),
+                                               ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream))
     if st != OK:
         raise SrfmgError(st, "srfmg_solve_small_noalloc (status code only)")
     return u
