@@ -18,23 +18,40 @@ plain FP64 stored-grid FMG-FAS on the same GPU, the roofline of
 the dominant kernel, the oracle on the host cores, clocks sampled during the
 timed region, and the accuracy of the result against the exact solution.
 
+The default line also carries the other workloads under their own keys
+(each with its plain FP64 stored-grid baseline and accuracy flags): "batch"
+(the batch of variable-coefficient problems below, mixed precision) and
+"bratu" (the Bratu problem at N = 2^26, mixed precision); "plain_fixed" (plain
+stored FMG-FAS in the same fixed point, which separates what segmental
+refinement adds from what the arithmetic adds); "alu_peak" (measured
+integer, FP64 and FP32 throughput, srfmg_alu_peaks) and
+"cpu_baseline_allcores" (the oracle on every host core, one independent solve
+per core).  --quick leaves those out.
+
 --impl reference times the CPU oracle (the method's plain serial C
-restatement) on the host cores, one bounded sample of the workload per step.
+restatement) on the host cores: one solve of the full workload per step
+(a bounded sample for Bratu and the batch, stated in its config).
 
 --workload batch: 8192 independent problems of N = 2^m cells, m ~ U{10..20}
-(seed 11; about 1.55e9 unknowns in all), each a 32-mode sine series with its
-own seed; one srfmg group: a batched plan per size with its segment layout
-autotuned (--no-tune: min(4096, N/4)-cell segments, 8 buffer cells), all
-replayed as one CUDA graph with a branch per size; 64-bit fixed point.
-value = all problems' unknowns / time of one group solve.
+(seed 11; about 1.55e9 unknowns in all), each -(a u')' = f with its own
+seeded a = exp(g/2) (16 cosine modes) and 32-mode sine solution (--batch-op
+laplace: -u'' = f, 64-bit fixed point); one srfmg group: a batched plan per
+size with its segment layout autotuned (--no-tune: min(4096, N/4)-cell
+segments, 8 buffer cells), all replayed as one CUDA graph with a branch per
+size; mixed precision.  value = all problems' unknowns / time of one group
+solve.
 
 --workload varcoef: -(a u')' = f, a = exp(g/2) at the faces with g a seeded
-8-mode cosine series, N = 2^24 cells, 4096 segments of 4096 cells, V(1,1), FP64;
+16-mode cosine series, N = 2^24 cells, 4096 segments of 4096 cells, V(1,1);
 u = sum_{k=1..16} c_k sin(k pi x) (seed 1).
 
 --workload bratu: the nonlinear -u'' + lam e^u = f (lam = 1) with the same
 discretisation and FAS cycles, N = 2^26 cells, 16384 segments of 4096 cells,
-V(2,1), FP64; u = 1/2 sum_{k=1..16} c_k sin(k pi x) (seed 1).
+V(2,1); u = 1/2 sum_{k=1..16} c_k sin(k pi x) (seed 1).
+
+--precision mixed (default): 64-bit fixed point for -u'' = f; for the
+variable coefficient and Bratu, FP64 residuals, tau, interpolations and
+coarsest solves with FP32 Gauss-Seidel correction recurrences.
 
 Multi-GPU: the solve does not shard across GPUs here; with --gpus N every rank
 solves its own copy (replicas, weak scaling) and the value is the sum over
@@ -82,6 +99,16 @@ FLOPS_PER_CELL_VARCOEF = {"sr_post": 6.5 + 1 * (2 + 8), "sr_pre": 6.5 + 8 + 0.5 
 FLOPS_PER_CELL_BRATU = {"sr_post": 6.5 + 1 * (2 + 9), "sr_pre": 6.5 + 2 * 9 + 0.5 + 6,
                         "level_down_fmg": 6.5 + 2 * 9 + 0.5 + 6, "level_down": 2 * 9 + 0.5 + 6,
                         "level_up": 2.0 + 1 * 9}
+# mixed precision of those two: the Gauss-Seidel recurrence, the Newton denominator and
+# its reciprocal run in FP32; the FP64 part of a sweep is the residual (flux, flux
+# difference, residual, plus the product by the coefficient or c e^u and its term)
+# and the update
+FLOPS_PER_CELL_VARCOEF_MX = {"sr_post": 6.5 + 1 * (2 + 5), "sr_pre": 6.5 + 5 + 0.5 + 6.5,
+                             "level_down_fmg": 6.5 + 5 + 0.5 + 6.5, "level_down": 5 + 0.5 + 6.5,
+                             "level_up": 2.0 + 5}
+FLOPS_PER_CELL_BRATU_MX = {"sr_post": 6.5 + 1 * (2 + 6), "sr_pre": 6.5 + 2 * 6 + 0.5 + 6,
+                           "level_down_fmg": 6.5 + 2 * 6 + 0.5 + 6, "level_down": 2 * 6 + 0.5 + 6,
+                           "level_up": 2.0 + 1 * 6}
 BYTES_PER_CELL = {"sr_post": 20.0, "sr_pre": 20.0, "level_down_fmg": 20.0,
                   "level_down": 24.0, "level_up": 28.0, "rhs_hierarchy": 16.0}
 
@@ -103,15 +130,25 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch: fixed segment layout min(4096, N/4), buffer 8, instead of autotuning each size")
+    ap.add_argument("--batch-op", choices=["varcoef", "laplace"], default="varcoef",
+                    help="batch: operator of the problems")
+    ap.add_argument("--quick", action="store_true",
+                    help="leave the batch, Bratu, all-core oracle and ALU probes out of the default line")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
                          "the minimal run used for ncu captures")
     a = ap.parse_args()
     if a.log2n is None:
         a.log2n = 26 if a.workload == "bratu" else 24
-    if a.workload in ("bratu", "varcoef"):
-        a.precision = "fp64"
     return a
+
+
+def precision_text(op, precision):
+    if precision == "fp64":
+        return "FP64"
+    if op == "laplace":
+        return "64-bit fixed point (solution, residual, tau, interpolation) + FP64 coarsest solve"
+    return "mixed: FP64 solution, residual, tau, interpolation and coarsest solve; FP32 Gauss-Seidel corrections"
 
 
 def workload_config(a):
@@ -119,19 +156,21 @@ def workload_config(a):
         return {
             "workload": f"1D -(a u')'=f, a=exp(g/2) (8-mode cosine series g, seed 1), N=2^{a.log2n}, FMG-FAS "
                         f"V(1,1) lexicographic GS, 1 SR level of {(1 << a.log2n) // a.segment_width} segments x "
-                        f"{a.segment_width} cells, buffer {a.buffer_width}, FP64",
-            "precision": "fp64", "N": 1 << a.log2n, "segment_width": a.segment_width,
+                        f"{a.segment_width} cells, buffer {a.buffer_width}, {precision_text('varcoef', a.precision)}",
+            "precision": a.precision, "N": 1 << a.log2n, "segment_width": a.segment_width,
             "buffer_width": a.buffer_width, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
             "modes": 16, "seed": 1,
             "l2": "inputs larger than L2 (f and u 128 MiB each, log a 128 MiB, the stored levels)",
         }
     if getattr(a, "workload", "poisson") == "batch":
+        op = getattr(a, "batch_op", "varcoef")
+        eq = "-(a u')'=f, a=exp(g/2) (16-mode cosine series g per problem)" if op == "varcoef" else "-u''=f"
         return {
-            "workload": f"{a.nprob} independent 1D -u''=f problems, N=2^m with m ~ U{{10..20}} (seed 11), "
-                        f"FMG-FAS V(1,1) lexicographic GS, 1 SR level of min(4096, N/4)-cell segments, "
-                        f"buffer 8, 64-bit fixed point; one srfmg group (a batched plan per size, all sizes "
+            "workload": f"{a.nprob} independent 1D {eq} problems, N=2^m with m ~ U{{10..20}} (seed 11), "
+                        f"FMG-FAS V(1,1) lexicographic GS, 1 SR level, buffer 8, "
+                        f"{precision_text(op, 'mixed')}; one srfmg group (a batched plan per size, all sizes "
                         f"replayed as one CUDA graph with a branch per size)",
-            "precision": "mixed", "nprob": a.nprob, "m_range": [10, 20], "size_seed": 11,
+            "operator": op, "precision": "mixed", "nprob": a.nprob, "m_range": [10, 20], "size_seed": 11,
             "modes": 32, "buffer_width": 8, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
             "l2": "inputs larger than L2 (about 12 GB of f and 12 GB of u)",
         }
@@ -139,8 +178,8 @@ def workload_config(a):
         return {
             "workload": f"1D -u''+lam e^u=f, lam={a.lam}, N=2^{a.log2n}, FMG-FAS V(2,1) pointwise Newton "
                         f"lexicographic GS, 1 SR level of {(1 << a.log2n) // a.segment_width} segments x "
-                        f"{a.segment_width} cells, buffer {a.buffer_width}, FP64",
-            "precision": "fp64", "N": 1 << a.log2n, "segment_width": a.segment_width,
+                        f"{a.segment_width} cells, buffer {a.buffer_width}, {precision_text('bratu', a.precision)}",
+            "precision": a.precision, "N": 1 << a.log2n, "segment_width": a.segment_width,
             "buffer_width": a.buffer_width, "n_sr_levels": 1, "nu": [2, 1], "coarsest_level": 2,
             "lam": a.lam, "modes": 16, "seed": 1,
             "l2": "inputs larger than L2 (f and u 512 MiB each plus the stored coarse levels)",
@@ -255,18 +294,42 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_kind, precision):
-    """DRAM bytes per launch of `kernel_kind` from the committed ncu summary,
+def recorded_field(kernel_kind, precision, field):
+    """A per-launch figure (`field`: dram_bytes_per_full_launch or
+    warp_inst_per_full_launch) of `kernel_kind` from the committed ncu summary,
     or None if there is none or the kernels changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel_kind}_{precision}_ncu.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_src = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    m_b = re.search(field + r":\s*([0-9.eE+]+)", text)
     if not (m_src and m_b) or m_src.group(1) != kernel_source_hash():
         return None
     return float(m_b.group(1))
+
+
+def recorded_traffic(kernel_kind, precision):
+    return recorded_field(kernel_kind, precision, "dram_bytes_per_full_launch")
+
+
+_ALU = None
+
+
+def alu_peak(dev):
+    """Measured integer, FP64 and FP32 throughput of the device (srfmg_alu_peaks),
+    once per process."""
+    global _ALU
+    if _ALU is None:
+        from paper_1207_6720_gb300 import srfmg
+        _ALU = srfmg.alu_peaks(dev)
+    return _ALU
+
+
+def fp64_peak_tflops():
+    if _ALU:
+        return _ALU["fp64_flops"] / 1e12, "measured FP64 FMA throughput (srfmg_alu_peaks)"
+    return NOMINAL_FP64_TFLOPS, "nominal FP64 from unit counts and the maximum SM clock"
 
 
 def measured_peaks():
@@ -293,6 +356,41 @@ def cpu_baseline(f, M, W, b, u_exact):
     return ref, {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                  "sample": f"{reps} serial solves of the full N=2^{M} workload "
                            f"(C oracle, serial SR with the finest level never stored)"}
+
+
+_AC_F = None
+
+
+def _allcore_init(M):
+    global _AC_F
+    import oracle
+    from paper_1207_6720_gb300 import workloads
+    oracle.lib()
+    _AC_F = workloads.sine_series(M, 32, seed=1)[0]
+
+
+def _allcore_solve(args):
+    import oracle
+    M, W, b = args
+    oracle.fmg_v(oracle.sr_params(M, W, b, nRS=1), _AC_F)
+    return 1
+
+
+def cpu_baseline_allcores(M, W, b):
+    """The oracle as it stands on every host core at once: one independent
+    serial solve of the full workload per core (processes started with spawn),
+    after one untimed round; value = cores x N / wall time of the round."""
+    import multiprocessing as mp
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n, initializer=_allcore_init, initargs=(M,)) as pool:
+        pool.map(_allcore_solve, [(M, W, b)] * n, chunksize=1)
+        t0 = time.perf_counter()
+        pool.map(_allcore_solve, [(M, W, b)] * n, chunksize=1)
+        dt = time.perf_counter() - t0
+    return {"value": n * (1 << M) / dt, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} concurrent serial solves of the full N=2^{M} workload, one per host core "
+                      f"(C oracle, serial SR), wall time of one round"}
 
 
 # ---------------------------------------------------------------------------
@@ -410,6 +508,17 @@ def run_gpu(a):
     u_plain = ud.cpu().numpy()
     plain_info = plain.info()
     plain.close()
+    # plain stored-grid FMG-FAS in the same arithmetic as the headline: what SR itself
+    # adds or costs on this GPU, apart from the arithmetic
+    plain_fixed = None
+    if prec != srfmg.FP64:
+        pfx = srfmg.Solver(M, device=dev, n_sr_levels=0, precision=prec)
+        ms_pfx = dist.max(time_solves(pfx, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
+        u_pfx = ud.cpu().numpy()
+        plain_fixed = {"value": dist.world * N / (ms_pfx * 1e-3), "ms_per_step": ms_pfx,
+                       "kernels_per_solve": pfx.info().kernels_per_solve, "sr_speedup_over_it": ms_pfx / ms,
+                       "err_max_vs_exact": float(np.max(np.abs(u_pfx - u_exact)))}
+        pfx.close()
     # the same SR solve in FP64 arithmetic (when the headline is the fixed-point one)
     sr64 = None
     if prec != srfmg.FP64:
@@ -515,14 +624,29 @@ def run_gpu(a):
     bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * cells
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     traffic = recorded_traffic(kind, a.precision)
+    alu = alu_peak(dev)
+    fp64_peak, fp64_src = fp64_peak_tflops()
     hbm_achieved = bytes_alg / (top_ms * 1e-3) / 1e9
     hbm_view = {"bound": "hbm", "kernel": top_name, "achieved": hbm_achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": hbm_achieved / hbm_peak, "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, recorded in "
+                                   f"profiles/{kind}_{a.precision}_ncu.md at the current kernel sources"
+                                   if traffic is not None else "no ncu capture at the current kernel sources"),
                 "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic_bytes": bytes_alg, "launch_ms": top_ms}
-    fp64_view = {"bound": "alu", "kernel": top_name, "achieved": achieved_tf, "peak": NOMINAL_FP64_TFLOPS,
-                 "unit": "TFLOP/s", "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": traffic,
-                 "peak_source": "nominal FP64 from unit counts and the maximum SM clock",
+    # issue view: the kernel's executed warp instructions (ncu, recorded) per launch time
+    # against the measured issue rate (one FP32 FMA warp instruction per scheduler and
+    # clock: FP32 flops / 2 / 32)
+    winst = recorded_field(kind, a.precision, "warp_inst_per_full_launch")
+    issue_peak = alu["fp32_flops"] / 2.0 / 32.0 / 1e12
+    if winst is not None:
+        hbm_view["issue_view"] = {"achieved": winst / (top_ms * 1e-3) / 1e12, "peak": issue_peak,
+                                  "unit": "T warp instructions/s", "frac": winst / (top_ms * 1e-3) / 1e12 / issue_peak,
+                                  "warp_inst_per_launch": winst,
+                                  "peak_source": "measured FP32 FMA rate / 64 (srfmg_alu_peaks)"}
+    fp64_view = {"bound": "alu", "kernel": top_name, "achieved": achieved_tf, "peak": fp64_peak,
+                 "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak, "traffic": traffic,
+                 "peak_source": fp64_src,
                  "algorithmic_flops": flops, "launch_ms": top_ms}
     if prec == srfmg.FP64:
         # FP64 arithmetic: the FP64 pipe binds (about 79% busy in the segment kernels)
@@ -547,6 +671,7 @@ def run_gpu(a):
         "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                        "kernels_per_solve": plain_info.kernels_per_solve,
                        "speedup_over_plain": ms_plain / ms},
+        "plain_fixed": plain_fixed,
         "sr_fp64": sr64,
         "sr_levels_2": sr2,
         "adjoint": adjoint,
@@ -555,6 +680,10 @@ def run_gpu(a):
         "roofline": roofline,
         "kernel_share": {k: round(v / tot, 4) for k, v in sorted(by_kind.items(), key=lambda x: -x[1])},
         "clocks": clocks,
+        "alu_peak": {"i64_add_per_s": alu["i64_add_per_s"], "i64_avg_ops_per_s": alu["i64_avg_ops_per_s"],
+                     "fp64_tflops": alu["fp64_flops"] / 1e12, "fp32_tflops": alu["fp32_flops"] / 1e12,
+                     "how": "srfmg_alu_peaks: 8 blocks x 256 threads per SM, 8 interleaved dependent chains per "
+                            "thread, CUDA events, best of 5"},
     }
     err_gpu = float(np.max(np.abs(u - u_exact)))
     acc = {"err_max_vs_exact": err_gpu,
@@ -569,63 +698,81 @@ def run_gpu(a):
         line["cpu_baseline"] = cpu
     line["accuracy"] = acc
     solver.close()
+    del fd, ud
+    torch.cuda.empty_cache()
+    if not a.quick:
+        # the other workloads, each with its plain FP64 baseline and accuracy flags
+        a_b = argparse.Namespace(**vars(a))
+        a_b.workload, a_b.batch_op = "batch", "varcoef"
+        r = measure_batch(a_b, dev, dist, stream, max(3, a.steps // 4), min(a.warmup, 2), op="varcoef")
+        r["config"] = dict(workload_config(a_b), segment_layout=r.pop("segment_layout"), layouts=r.pop("layouts"))
+        r["metric"] = METRIC_BATCH
+        line["batch"] = r
+        a_r = argparse.Namespace(**vars(a))
+        a_r.workload, a_r.log2n, a_r.precision = "bratu", 26, "mixed"
+        r = measure_single(a_r, dev, dist, stream, "bratu", "mixed", max(5, a.steps // 2), min(a.warmup, 3))
+        r["config"] = workload_config(a_r)
+        r["metric"] = METRIC_BRATU
+        line["bratu"] = r
+        if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline:
+            line["cpu_baseline_allcores"] = cpu_baseline_allcores(M, W, b)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()
 
 
-def run_gpu_bratu(a):
-    """The Bratu or variable-coefficient workload: SR solve vs the plain stored
-    solve, FP64."""
+def measure_single(a, dev, dist, stream, kind, precision, steps, warmup, full=True, oracle_check=True):
+    """One problem of the variable-coefficient ("varcoef") or Bratu ("bratu")
+    workload at N = 2^a.log2n: the SR solve in `precision` ("mixed" or
+    "fp64"); with `full`, the plain FP64 stored-grid solve of the same problem,
+    the solve from host memory, the longest launch's FP64 roofline and, with
+    `oracle_check`, the oracle's solve for the accuracy flags.  Returns a dict."""
     import torch
     from paper_1207_6720_gb300 import srfmg, workloads
 
-    dist = Dist(a.gpus, use_cuda=True)
-    dev = dist.local_rank
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
     M, W, b = a.log2n, a.segment_width, a.buffer_width
     N = 1 << M
-    vcoef = a.workload == "varcoef"
+    vcoef = kind == "varcoef"
+    mixed = precision == "mixed"
+    prec = srfmg.MIXED if mixed else srfmg.FP64
     if vcoef:
         f, u_exact, log_a = workloads.varcoef_series(M, 16, seed=1)
         kw = dict(op=srfmg.VARCOEF, nu1=1, nu2=1)
-        metric, flops_table = METRIC_VARCOEF, FLOPS_PER_CELL_VARCOEF
+        flops_table = FLOPS_PER_CELL_VARCOEF_MX if mixed else FLOPS_PER_CELL_VARCOEF
     else:
         f, u_exact, _ = workloads.bratu_series(M, 16, seed=1, lam=a.lam)
         kw = dict(op=srfmg.BRATU, lambda_=a.lam, nu1=2, nu2=1)
-        metric, flops_table = METRIC_BRATU, FLOPS_PER_CELL_BRATU
+        flops_table = FLOPS_PER_CELL_BRATU_MX if mixed else FLOPS_PER_CELL_BRATU
     fd = torch.from_numpy(f).to(dev)
     ud = torch.empty_like(fd)
-    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, **kw)
+    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, precision=prec, **kw)
+    log_a_d = None
     if vcoef:
         log_a_d = torch.from_numpy(log_a).to(dev)
         solver.set_coefficient(log_a_d, stream=stream)
     info = solver.info()
     sampler = ClockSampler(dev)
     sampler.start()
-    ms = time_solves(solver, fd, ud, a.steps, a.warmup, dist, stream)
+    ms = dist.max(time_solves(solver, fd, ud, steps, warmup, dist, stream))
     clocks = sampler.stop()
-    ms = dist.max(ms)
-    value = dist.world * N / (ms * 1e-3)
     u = ud.cpu().numpy()
-    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": dist.world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(a), "gpu_launches": info.kernels_per_solve * a.steps,
-            "clocks": clocks}
-    if not a.only_solve:
+    out = {"value": dist.world * N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "warmup": warmup, "precision": precision, "N": N, "gpu_launches": info.kernels_per_solve * steps,
+           "clocks": clocks}
+    if full:
+        alu_peak(dev)
         plain = srfmg.Solver(M, device=dev, n_sr_levels=0, **kw)
         if vcoef:
             plain.set_coefficient(log_a_d, stream=stream)
-        ms_plain = dist.max(time_solves(plain, fd, ud, max(5, a.steps // 4), a.warmup, dist, stream))
+        ms_plain = dist.max(time_solves(plain, fd, ud, max(5, steps // 4), min(warmup, 3), dist, stream))
+        u_plain = ud.cpu().numpy()
         plain.close()
         fh = torch.from_numpy(f).pin_memory()
         uh = torch.empty(N, dtype=torch.float64).pin_memory()
         fh_np, uh_np = fh.numpy(), uh.numpy()
         solver.solve_host(fh_np, uh_np, stream=stream)
         dist.barrier()
-        e2e_steps = max(3, a.steps // 10)
+        e2e_steps = max(3, steps // 10)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             solver.solve_host(fh_np, uh_np, stream=stream)
@@ -633,31 +780,31 @@ def run_gpu_bratu(a):
         prof = solver.profile(fd, torch.empty_like(fd), nsolves=3, stream=stream)
         torch.cuda.synchronize()
         top_name, top_ms = max(prof, key=lambda x: x[1])
-        kind, lvl = top_name.split(" L")
+        kname, lvl = top_name.split(" L")
         cells = 1 << int(lvl)
-        flops = flops_table.get(kind, 0.0) * cells
+        flops = flops_table.get(kname, 0.0) * cells
         achieved_tf = flops / (top_ms * 1e-3) / 1e12
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * cells
-        line.update({
+        bytes_alg = BYTES_PER_CELL.get(kname, 0.0) * cells
+        fp64_peak, fp64_src = fp64_peak_tflops()
+        out.update({
             "e2e": {"value": dist.world * N / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": int(f.nbytes),
                     "d2h_bytes_per_step": int(uh_np.nbytes)},
             "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                           "speedup_over_plain": ms_plain / ms},
+                           "speedup_over_plain": ms_plain / ms,
+                           "err_max_vs_exact": float(np.max(np.abs(u_plain - u_exact)))},
             "roofline": {"bound": "alu", "kernel": top_name, "achieved": achieved_tf,
-                         "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / NOMINAL_FP64_TFLOPS, "traffic": None,
-                         "peak_source": "nominal FP64 from unit counts and the maximum SM clock "
-                                        "(exponential and reciprocal counted as one operation)",
+                         "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak, "traffic": None,
+                         "peak_source": fp64_src + " (FP64 operations of the method per cell; exponential and "
+                                                   "reciprocal counted as one operation)",
                          "algorithmic_flops": flops, "launch_ms": top_ms,
                          "hbm_view": {"achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak,
-                                      "unit": "GB/s",
-                                      "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak}},
+                                      "unit": "GB/s", "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak}},
         })
     err = float(np.max(np.abs(u - u_exact)))
     acc = {"err_max_vs_exact": err, "rel_err_max_vs_exact": err / float(np.max(np.abs(u_exact)))}
-    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and not a.only_solve:
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and full and oracle_check:
         import oracle
         if vcoef:
             p = oracle.sr_params(M, W, b, nRS=1, op="varcoef", coef=np.exp(log_a))
@@ -666,100 +813,145 @@ def run_gpu_bratu(a):
         t0 = time.perf_counter()
         ref = oracle.fmg_v(p, f)
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one serial solve of the full N=2^{M} workload (C oracle, "
-                                          f"serial SR with the finest level never stored)"}
+        out["cpu_baseline"] = {"value": N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"one serial solve of the full N=2^{M} workload (C oracle, "
+                                         f"serial SR with the finest level never stored)"}
         err_ref = float(np.max(np.abs(ref - u_exact)))
-        acc.update({"oracle_err_max_vs_exact": err_ref,
-                    "rel_maxnorm_vs_oracle": float(np.max(np.abs(u - ref)) / np.max(np.abs(ref))),
-                    "at_discretization_accuracy": bool(err <= 1.5 * err_ref)})
-    line["accuracy"] = acc
+        rel_or = float(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
+        acc.update({"oracle_err_max_vs_exact": err_ref, "rel_maxnorm_vs_oracle": rel_or,
+                    "at_discretization_accuracy": bool(err <= 1.5 * err_ref),
+                    "parity_vs_oracle_1e-10": bool(rel_or <= 1e-10)})
+        if err_ref < 1e-11 * float(np.max(np.abs(u_exact))) * 100:
+            acc["note"] = ("rounding-limited size: the O(h^2) truncation error is below the FP64 rounding of "
+                           "either solve, so the error against the exact solution compares roundings; the "
+                           "parity flag is the accuracy criterion here")
+    out["accuracy"] = acc
     solver.close()
+    del fd, ud
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_gpu_bratu(a):
+    """The Bratu or variable-coefficient workload as its own JSON line."""
+    import torch
+    dist = Dist(a.gpus, use_cuda=True)
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    r = measure_single(a, dev, dist, stream, a.workload, a.precision, a.steps, a.warmup, full=not a.only_solve)
+    metric = METRIC_VARCOEF if a.workload == "varcoef" else METRIC_BRATU
+    line = {"metric": metric, "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": dist.world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if a.precision == "mixed" else "f64",
+            "data": "synthetic", "config": workload_config(a)}
+    for k in ("steps", "warmup", "precision", "N"):
+        r.pop(k)
+    line.update(r)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()
 
 
-def run_gpu_batch(a):
-    """Many independent problems of uneven sizes: one srfmg group (a batched
-    plan per size, all replayed as one CUDA graph), one group solve per step."""
+def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, full=True):
+    """Many independent problems of uneven sizes (8192 by default, N = 2^m with
+    m ~ U{10..20}): one srfmg group (a batched plan per size, all replayed as
+    one CUDA graph), one group solve per step, in the mixed precision; with
+    `full`, also the group of plain FP64 stored-grid plans on the same problems,
+    the group solve from host memory, the longest launch's roofline and the
+    accuracy of a sample against the exact solution and the oracle.  Returns
+    the measurement as a dict (the workload's JSON line without its header)."""
     import torch
     from paper_1207_6720_gb300 import srfmg, workloads
 
-    dist = Dist(a.gpus, use_cuda=True)
-    dev = dist.local_rank
-    torch.cuda.set_device(dev)
-    master = torch.cuda.current_stream()
     sizes = workloads.batch_sizes(a.nprob, 10, 20, seed=11)
     classes = {}
     for k, m in enumerate(sizes):
         classes.setdefault(int(m), []).append(k + 1000)       # problem k's series seed
     total = int(sum(len(v) << m for m, v in classes.items()))
-    # the packed layout: by size, then by index (srfmg_group_offsets)
-    parts = [workloads.sine_series_batch(m, classes[m], 32, dev)[0] for m in sorted(classes)]
-    fd = torch.cat(parts)
-    del parts
+    vc = op == "varcoef"
+    # the packed layout: by size, then by index (srfmg_group_offsets); log a per plan
+    fparts, laparts = [], []
+    for m in sorted(classes):
+        if vc:
+            fm, lam = workloads.varcoef_series_batch(m, classes[m], 32, dev)
+            fparts.append(fm)
+            laparts.append(lam)
+        else:
+            fparts.append(workloads.sine_series_batch(m, classes[m], 32, dev)[0])
+    fd = torch.cat(fparts)
+    del fparts
+    la_d = torch.cat(laparts) if vc else None
+    del laparts
     ud = torch.empty_like(fd)
     assert fd.numel() == total == int(srfmg.group_offsets(sizes)[-1])
     torch.cuda.synchronize()
+    kw_op = dict(op=srfmg.VARCOEF) if vc else {}
 
-    def make(prec, nRS, tune):
-        kw = dict(precision=prec, n_sr_levels=nRS)
+    def make(prec, nRS, tune_reps):
+        kw = dict(precision=prec, n_sr_levels=nRS, **kw_op)
         if nRS:
             kw.update(segment_width=4096, buffer_width=8)
-        return srfmg.Group(sizes, device=dev, tune=tune, **kw)
+        g = srfmg.Group(sizes, device=dev, tune=tune_reps, **kw)
+        if vc:       # every plan's coefficient from its part of the packed log a
+            o = 0
+            for mb in g.members():
+                cnt = mb.batch * (mb.n + 1)
+                mb.set_coefficient(la_d[o:o + cnt], stream=master)
+                o += cnt
+            assert o == la_d.numel()
+        return g
 
-    def timed(group, steps, warmup):
-        for _ in range(warmup):
+    def timed(group, nsteps, nwarm):
+        for _ in range(nwarm):
             group.solve(fd, ud, stream=master)
         torch.cuda.synchronize()
         dist.barrier()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(master)
-        for _ in range(steps):
+        for _ in range(nsteps):
             group.solve(fd, ud, stream=master)
         t1.record(master)
         t1.synchronize()
         torch.cuda.synchronize()
         dist.barrier()
-        return t0.elapsed_time(t1) / steps
+        return t0.elapsed_time(t1) / nsteps
 
-    tune = 0 if a.no_tune else 3
+    tune_reps = 3 if tune else 0
     t_create = time.perf_counter()
-    group = make(srfmg.MIXED, 1, tune)
+    group = make(srfmg.MIXED, 1, tune_reps)
     t_create = time.perf_counter() - t_create
     members = group.members()
     launches = sum(mb.info().kernels_per_solve for mb in members)
     layouts = {str(mb.n.bit_length() - 1): [mb.params.segment_width, mb.params.buffer_width] for mb in members}
     sampler = ClockSampler(dev)
     sampler.start()
-    ms = dist.max(timed(group, a.steps, a.warmup))
+    ms = dist.max(timed(group, steps, warmup))
     clocks = sampler.stop()
     value = dist.world * total / (ms * 1e-3)
-    cfg = workload_config(a)
-    cfg["segment_layout"] = ("autotuned per size (srfmg_autotune, 3 timed solves per candidate)" if tune
-                             else "min(4096, N/4) cells, buffer 8")
-    cfg["layouts"] = layouts
-    line = {"metric": METRIC_BATCH, "value": value, "unit": UNIT, "n_gpus": dist.world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": cfg, "gpu_launches": launches * a.steps, "clocks": clocks,
-            "unknowns_per_step": total, "group_create_s": t_create}
-    # accuracy on a sample: the first problem of every size against its exact solution
-    offs = srfmg.group_offsets(sizes)
-    worst = 0.0
+    out = {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "unknowns_per_step": total, "group_create_s": t_create, "gpu_launches": launches * steps,
+           "clocks": clocks,
+           "segment_layout": ("autotuned per size (srfmg_autotune, 3 timed solves per candidate)" if tune
+                              else "min(4096, N/4) cells, buffer 8"),
+           "layouts": layouts}
+    # accuracy sample: the first problem of every size against its exact solution
     samples = {}
-    u_all = None
+    worst = 0.0
     for mb in members:
         m = mb.n.bit_length() - 1
         if m in samples:
             continue
         o = int(mb.offset)
         u0 = ud[o:o + mb.n].cpu().numpy()
-        f0, ue, _ = workloads.sine_series(m, 32, classes[m][0])
-        samples[m] = (fd[o:o + mb.n].cpu().numpy(), ue, u0, mb.params.segment_width, mb.params.buffer_width)
+        if vc:
+            f0, ue, la0 = workloads.varcoef_series(m, 32, classes[m][0])
+        else:
+            f0, ue, _ = workloads.sine_series(m, 32, classes[m][0])
+            la0 = None
+        samples[m] = (f0, ue, la0, u0, mb.params.segment_width, mb.params.buffer_width)
         worst = max(worst, float(np.max(np.abs(u0 - ue))))
-    if not a.only_solve:
+    if full:
         # end to end: the whole group through srfmg_group_solve_host from pinned host buffers
         fh = fd.cpu().pin_memory()
         uh = torch.empty(total, dtype=torch.float64).pin_memory()
@@ -767,10 +959,10 @@ def run_gpu_batch(a):
         t0 = time.perf_counter()
         group.solve_host(fh.numpy(), uh.numpy(), stream=master)
         dt_e2e = dist.max(time.perf_counter() - t0)
-        line["e2e"] = {"value": dist.world * total / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total * 8,
-                       "d2h_bytes_per_step": total * 8}
+        out["e2e"] = {"value": dist.world * total / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": total * 8,
+                      "d2h_bytes_per_step": total * 8}
         del fh, uh
-        # roofline: the longest launch of the largest size's plan
+        # roofline view: the longest launch of the largest size's plan
         big = max(members, key=lambda mb: mb.n * mb.batch)
         o = int(big.offset)
         prof = big.profile(fd[o:o + big.n * big.batch], torch.empty(big.n * big.batch, dtype=torch.float64,
@@ -782,41 +974,72 @@ def run_gpu_batch(a):
         bytes_alg = BYTES_PER_CELL.get(kind, 0.0) * big.batch * (1 << int(lvl))
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        line["roofline"] = {"bound": "hbm", "kernel": f"{top_name} (batch of {big.batch})",
-                            "achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
-                            "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
-                            "launch_ms": top_ms}
+        out["roofline"] = {"bound": "hbm", "kernel": f"{top_name} (batch of {big.batch})",
+                           "achieved": bytes_alg / (top_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": bytes_alg / (top_ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                           "peak_source": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback",
+                           "launch_ms": top_ms}
     group.close()
-    if not a.only_solve:
+    if full:
         plain = make(srfmg.FP64, 0, 0)
-        ms_plain = dist.max(timed(plain, max(3, a.steps // 2), 1))
+        ms_plain = dist.max(timed(plain, max(2, steps // 2), 1))
         plain.close()
-        line["plain_fp64"] = {"value": dist.world * total / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                              "speedup_over_plain": ms_plain / ms}
+        first = {}
+        for mb in members:
+            first.setdefault(mb.n.bit_length() - 1, int(mb.offset))
+        err_plain = max(float(np.max(np.abs(ud[o:o + (1 << m)].cpu().numpy() - samples[m][1])))
+                        for m, o in first.items())
+        out["plain_fp64"] = {"value": dist.world * total / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                             "speedup_over_plain": ms_plain / ms, "err_max_vs_exact_sample": err_plain}
     acc = {"err_max_vs_exact_sample": worst, "sample": "first problem of each size"}
-    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and not a.only_solve:
+    if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline and full:
         import oracle
         refs = {}
         t0 = time.perf_counter()
         reps = 0
         while True:
-            for m, (f0, ue, u0, W, b) in samples.items():
-                refs[m] = oracle.fmg_v(oracle.sr_params(m, W, b), f0)
+            for m, (f0, ue, la0, u0, W, b) in samples.items():
+                okw = dict(op="varcoef", coef=np.exp(la0)) if vc else {}
+                refs[m] = oracle.fmg_v(oracle.sr_params(m, W, b, **okw), f0)
             reps += 1
-            if time.perf_counter() - t0 > 10.0 or reps >= 20:
+            if time.perf_counter() - t0 > 5.0 or reps >= 10:
                 break
         dt = time.perf_counter() - t0
         n_sample = sum(1 << m for m in samples)
-        line["cpu_baseline"] = {"value": reps * n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{reps} x one problem of each size ({n_sample} unknowns) "
-                                          f"with the serial C oracle"}
+        out["cpu_baseline"] = {"value": reps * n_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{reps} x one problem of each size ({n_sample} unknowns) "
+                                         f"with the serial C oracle"}
         ok = all(np.max(np.abs(u0 - ue)) <= 1.5 * np.max(np.abs(refs[m] - ue))
-                 for m, (f0, ue, u0, W, b) in samples.items())
+                 for m, (f0, ue, la0, u0, W, b) in samples.items())
         acc.update({"rel_maxnorm_vs_oracle_sample": max(
-            float(np.max(np.abs(u0 - refs[m])) / np.max(np.abs(refs[m]))) for m, (f0, ue, u0, W, b) in samples.items()),
+            float(np.max(np.abs(u0 - refs[m])) / np.max(np.abs(refs[m])))
+            for m, (f0, ue, la0, u0, W, b) in samples.items()),
             "at_discretization_accuracy_sample": bool(ok)})
-    line["accuracy"] = acc
+    out["accuracy"] = acc
+    del fd, ud, la_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_gpu_batch(a):
+    """The batch workload as its own JSON line."""
+    import torch
+    dist = Dist(a.gpus, use_cuda=True)
+    dev = dist.local_rank
+    torch.cuda.set_device(dev)
+    master = torch.cuda.current_stream()
+    r = measure_batch(a, dev, dist, master, a.steps, a.warmup, op=a.batch_op, tune=not a.no_tune,
+                      full=not a.only_solve)
+    cfg = workload_config(a)
+    cfg["segment_layout"] = r.pop("segment_layout")
+    cfg["layouts"] = r.pop("layouts")
+    line = {"metric": METRIC_BATCH, "value": r.pop("value"), "unit": r.pop("unit"), "n_gpus": dist.world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if a.batch_op == "varcoef" else "int64",
+            "data": "synthetic", "config": cfg}
+    r.pop("steps")
+    r.pop("warmup")
+    line.update(r)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()

@@ -424,6 +424,22 @@ srfmg_status srfmg_destroy(srfmg_handle h);
  * the same handle. */
 const char *srfmg_last_error(srfmg_handle h);
 
+/* Arithmetic throughput of the device, measured (no counterpart in the paper:
+ * the denominators of the arithmetic rooflines of this library's kernels).
+ * Runs four short probe kernels on `device` (a grid of 8 blocks of 256
+ * threads per SM, eight interleaved dependent chains per thread, CUDA events
+ * on a stream of its own, best of five timed runs after one warm-up) and
+ * writes to ops_per_s[0..3]:
+ *   [0] 64-bit integer adds per second,
+ *   [1] 64-bit integer operations per second in the rounding halving
+ *       (x + y + 1) >> 1 of the fixed-point sweep (two adds and a shift),
+ *   [2] FP64 flops per second (fused multiply-adds, two flops each),
+ *   [3] FP32 flops per second (fused multiply-adds, two flops each).
+ * Synchronous; allocates and frees a small device buffer.  Errors:
+ * SRFMG_EINVAL for NULL ops_per_s or a bad device index, SRFMG_ECUDA,
+ * SRFMG_ENOMEM. */
+srfmg_status srfmg_alu_peaks(int device, double *ops_per_s);
+
 /* Library version string, e.g. "srfmg 0.1 sm_103a". */
 const char *srfmg_version(void);
 

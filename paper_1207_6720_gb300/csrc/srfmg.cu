@@ -47,7 +47,8 @@ struct Op {
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
     PtrTag seg_uin;   // a V-cycle's pre-leg from the caller's current fine solution
-    // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu)
+    // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu; kOpVarcoefMx,
+    // kOpBratuMx: the mixed precision of those two, FP32 correction recurrences)
     int opk;
     // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
     bool fixed;
@@ -512,9 +513,12 @@ void build_schedule_ops(srfmg_plan *h) {
 void build_schedule(srfmg_plan *h) {
     build_schedule_ops(h);
     for (Op &o : h->ops) {
-        o.opk = (h->p.op == SRFMG_OP_BRATU) ? kOpBratu : (h->p.op == SRFMG_OP_VARCOEF) ? kOpVarcoef : kOpLaplace;
+        const bool mx = (h->p.precision == SRFMG_MIXED);
+        o.opk = (h->p.op == SRFMG_OP_BRATU)     ? (mx ? kOpBratuMx : kOpBratu)
+                : (h->p.op == SRFMG_OP_VARCOEF) ? (mx ? kOpVarcoefMx : kOpVarcoef)
+                                                : kOpLaplace;
         // the variable-coefficient kernels stage their face coefficients
-        if (o.opk == kOpVarcoef && (o.kind == OP_DOWN || o.kind == OP_DOWN_PI || o.kind == OP_UP ||
+        if (op_vc(o.opk) && (o.kind == OP_DOWN || o.kind == OP_DOWN_PI || o.kind == OP_UP ||
                                     o.kind == OP_SR_PRE || o.kind == OP_SR_POST))
             o.smem += (size_t)((o.kind == OP_SR_PRE || o.kind == OP_SR_POST) ? o.seg.maxlen : o.lev.maxlen) *
                       sizeof(double) + 2 * sizeof(double);
@@ -626,7 +630,9 @@ cudaError_t launch(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     }
     if (o.seg_uin == TAG_U) o.seg.u_in = u;
     if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
+    if (o.opk == kOpBratuMx) return launch_fp64<kOpBratuMx>(o, s, pdl);
     if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
+    if (o.opk == kOpVarcoefMx) return launch_fp64<kOpVarcoefMx>(o, s, pdl);
     return launch_fp64<kOpLaplace>(o, s, pdl);
 }
 
@@ -692,6 +698,7 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
         (const void *)level_up_kernel<OPK>, (const void *)sr_pre_kernel<OPK>, (const void *)sr_post_kernel<OPK>, \
         (const void *)tail_kernel<OPK>
     const void *fns[] = {SRFMG_FP64_KERNELS(kOpLaplace), SRFMG_FP64_KERNELS(kOpVarcoef), SRFMG_FP64_KERNELS(kOpBratu),
+                         SRFMG_FP64_KERNELS(kOpVarcoefMx), SRFMG_FP64_KERNELS(kOpBratuMx),
                          (const void *)rhs_hierarchy_kernel,
                          (const void *)fx::level_down_kernel<true>, (const void *)fx::level_down_kernel<false>,
                          (const void *)fx::level_up_kernel, (const void *)fx::sr_pre_kernel,
@@ -748,8 +755,6 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     *out = nullptr;
     std::string msg = check_params(p);
     if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
-    if (p->op != SRFMG_OP_LAPLACE && p->precision != SRFMG_FP64)
-        return fail(nullptr, SRFMG_EUNSUPPORTED, "SRFMG_OP_BRATU and SRFMG_OP_VARCOEF run in FP64 only");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -773,7 +778,9 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     int top_stored = h->M - h->nRS;
     h->Mc = top_stored < kMaxTailLevel ? top_stored : kMaxTailLevel;
     if (h->Mc < h->M0) h->Mc = h->M0;
-    h->fixed = (p->precision == SRFMG_MIXED);
+    // the 64-bit fixed-point kernels serve the constant-coefficient operator; the
+    // mixed precision of the other two is their FP64 kernels with FP32 corrections
+    h->fixed = (p->precision == SRFMG_MIXED && p->op == SRFMG_OP_LAPLACE);
     const char *env = std::getenv("SRFMG_NO_GRAPH");
     h->use_graph = !(env && env[0] == '1');
 
@@ -1243,6 +1250,139 @@ srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32
 }
 
 const char *srfmg_version(void) { return "srfmg 0.1 sm_103a"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Throughput probes for the roofline denominators of the arithmetic-bound
+// kernels.  Each thread runs eight interleaved dependent chains (enough
+// independent work per warp to hide the pipe latency); the chains feed one
+// another, so no chain can be folded into a closed form, and every thread
+// writes its result.  Per chain step: one 64-bit add (i64_add), two 64-bit adds
+// and a 64-bit arithmetic shift (i64_avg: (x + y + 1) >> 1, the rounding halving
+// of the fixed-point sweep), one FP64 or one FP32 fused multiply-add.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kProbeChains = 8;
+
+__global__ void probe_i64_add(long long *out, int iters) {
+    long long a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = threadIdx.x * 7 + k + blockIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] += a[(k + 1) % kProbeChains];
+    }
+    long long r = 0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) r ^= a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void probe_i64_avg(long long *out, int iters) {
+    long long a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = ((long long)(threadIdx.x * 7 + k + blockIdx.x)) << 40;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] = (a[k] + a[(k + 1) % kProbeChains] + 1) >> 1;
+    }
+    long long r = 0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) r ^= a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void probe_dfma(double *out, int iters) {
+    double a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    const double x = 0.999999, y = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], x, y);
+    }
+    double r = 0.0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) r += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void probe_ffma(double *out, int iters) {
+    float a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = 1.0f + 1e-3f * (threadIdx.x + k);
+    const float x = 0.9999f, y = 1e-5f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] = fmaf(a[k], x, y);
+    }
+    float r = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) r += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+}  // namespace
+
+extern "C" {
+
+srfmg_status srfmg_alu_peaks(int device, double *ops_per_s) {
+    if (!ops_per_s) return fail(nullptr, SRFMG_EINVAL, "ops_per_s is NULL");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, SRFMG_ECUDA, "no CUDA device");
+    }
+    if (device < 0 || device >= ndev) return fail(nullptr, SRFMG_EINVAL, "device index out of range");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int threads = 256, blocks = 8 * (sms > 0 ? sms : 1);
+    const size_t nthr = (size_t)threads * blocks;
+    void *buf = nullptr;
+    if ((e = cudaMalloc(&buf, nthr * sizeof(double))) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, SRFMG_ENOMEM, "cudaMalloc(probe)");
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // (iterations, operations per chain step) of each probe
+    const int iters[4] = {4096, 2048, 256, 8192};
+    const double ops_per_step[4] = {1.0, 3.0, 2.0, 2.0};   // adds; adds + shift; flops of an FMA
+    srfmg_status rc = SRFMG_OK;
+    for (int p = 0; p < 4 && rc == SRFMG_OK; ++p) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 6; ++rep) {
+            cudaEventRecord(e0, st);
+            switch (p) {
+            case 0: probe_i64_add<<<blocks, threads, 0, st>>>((long long *)buf, iters[p]); break;
+            case 1: probe_i64_avg<<<blocks, threads, 0, st>>>((long long *)buf, iters[p]); break;
+            case 2: probe_dfma<<<blocks, threads, 0, st>>>((double *)buf, iters[p]); break;
+            default: probe_ffma<<<blocks, threads, 0, st>>>((double *)buf, iters[p]); break;
+            }
+            cudaEventRecord(e1, st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
+                rc = cuda_fail(nullptr, e, "throughput probe");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;      // the first run warms up
+        }
+        ops_per_s[p] = (double)nthr * iters[p] * kProbeChains * ops_per_step[p] / (best * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(buf);
+    return rc;
+}
 
 }  // extern "C"
 

@@ -29,6 +29,13 @@ constexpr int kChunk = 9;
 // Operators of the FP64 kernels (template parameter OP): -u'' = f, the
 // variable-coefficient -(a u')' = f, and the Bratu problem -u'' + lam e^u = f.
 constexpr int kOpLaplace = 0, kOpVarcoef = 1, kOpBratu = 2;
+// The same operators in the mixed precision (SRFMG_MIXED) of the variable-
+// coefficient and Bratu problems: the solution, the residual, the tau
+// correction, the interpolations and the coarsest solve in FP64, the
+// Gauss-Seidel correction recurrence in FP32 (lex_sweep_vc_mx, lex_sweep_nl_mx).
+constexpr int kOpVarcoefMx = 3, kOpBratuMx = 4;
+__host__ __device__ constexpr bool op_vc(int op) { return op == kOpVarcoef || op == kOpVarcoefMx; }
+__host__ __device__ constexpr bool op_nl(int op) { return op == kOpBratu || op == kOpBratuMx; }
 
 // Largest block of the level and segment kernels: one thread per chunk of at
 // most 4224 + 2 cells (a segment) or 2944 cells (a tile).  Segment kernels
@@ -496,6 +503,200 @@ __device__ __forceinline__ void lex_sweep_vc(double *__restrict__ u, const doubl
     else lex_sweep_vc_dir<C, false>(u, g, a, abase, base, lo, hi, n, X, Y);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision sweeps (SRFMG_MIXED for the variable-coefficient and Bratu
+// problems).  The split follows the precision roles of iterative refinement:
+// the residual r of the old values is formed in FP64 (it decides what the
+// smoother converges to), the correction recurrence that the Gauss-Seidel
+// step solves for r runs in FP32 (it only decides how fast), and the
+// correction is added to the FP64 solution.  GB300 issues FP64 at about 1/64
+// of its FP32 rate, so the recurrence, the Newton denominator and the carry
+// sums leave the FP64 pipe; the FP32 rounding of a correction (2^-24 of it)
+// is far below the FP64 work it feeds, since the last corrections of a
+// solve are of the size of its discretization error.  Layout, chunking and
+// wall handling are those of lex_sweep_vc / lex_sweep_nl; X and Y hold one
+// float per thread each (the caller's double arrays reinterpreted).  The carry
+// covers fewer chunks than in FP64: terms weighted below 2^-33 are dropped
+// (multipliers <= 0.6 over 45 cells, or <= 1/2 over 36 cells).
+// ---------------------------------------------------------------------------
+constexpr int kTruncVcMx = 45;
+constexpr int kTruncNlMx = 36;
+
+template <int C, bool ASC>
+__device__ __noinline__ void lex_sweep_vc_mx_dir(double *__restrict__ u, const double *__restrict__ g,
+                                                 const double *__restrict__ a, int abase, int base, int lo, int hi,
+                                                 int n, float *X, float *Y) {
+    constexpr int s = ASC ? 1 : -1;
+    const int t = threadIdx.x;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);
+    const bool wall1 = (q0 + k1 == n);
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int a0 = ASC ? -base : n - 1 - base;
+    const int fb0 = ASC ? 0 : n, fmin = lo, fmax = hi;
+    float rr[C], aa[C];
+    float p = 0.0f, A = 1.0f, r_end = 0.0f, b_end = 0.0f, al_end = 0.0f;
+    if (active) {
+        double w[C + 2], an[C + 1];
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+#pragma unroll
+        for (int j = 0; j <= C; ++j) an[j] = a[min(max(fb0 + s * (q0 + j), fmin), fmax) - abase];
+        // FP64 fluxes through the chunk's faces (sweep direction), FP32 coefficients
+        double F[C + 1];
+        float af[C + 1];
+#pragma unroll
+        for (int j = 0; j <= C; ++j) {
+            F[j] = an[j] * (w[j + 1] - w[j]);
+            af[j] = (float)an[j];
+        }
+        if (wall0) {
+            const double r = g[a0] - (an[0] * scale2(w[1], 1) - F[1]);
+            p = (float)r * __frcp_rn(2.0f * af[0] + af[1]);
+            A = 0.0f;
+        }
+        if (wall1) {
+            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+            const double anr = a[fb0 + s * (n - 1) - abase], aw = a[fb0 + s * n - abase];
+            const double r = g[a0 + s * (n - 1)] - (anr * (ue - um) - aw * (-scale2(ue, 1)));
+            const float anf = (float)anr;
+            b_end = __frcp_rn(anf + 2.0f * (float)aw);
+            al_end = anf * b_end;
+            r_end = (float)r;
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            const float r = (float)(gv - (F[k] - F[k + 1]));
+            const float b = __frcp_rn(af[k] + af[k + 1]);
+            const float m = af[k] * b;
+            const bool in = k >= ka && k < kb;
+            p = in ? fmaf(m, p, r * b) : p;
+            A = in ? m * A : A;
+            rr[k] = p;
+            aa[k] = A;
+        }
+        X[t] = p;
+        Y[t] = A;
+    }
+    __syncthreads();
+    if (active) {
+        constexpr int J = (kTruncVcMx + C - 1) / C - 1;
+        float cin = 0.0f;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const float x = X[max(idx, 0)], y = Y[max(idx, 0)];
+            cin = idx >= 0 ? fmaf(y, cin, x) : 0.0f;
+        }
+        float dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                dl = fmaf(aa[k], cin, rr[k]);
+                u[a0 + s * (q0 + k)] += (double)dl;
+            }
+        if (wall1) u[a0 + s * (n - 1)] += (double)fmaf(al_end, dl, b_end * r_end);
+    }
+    __syncthreads();
+}
+
+template <int C>
+__device__ __forceinline__ void lex_sweep_vc_mx(double *__restrict__ u, const double *__restrict__ g,
+                                                const double *__restrict__ a, int abase, int base, int lo, int hi,
+                                                int n, bool asc, double *X, double *Y) {
+    float *Xf = reinterpret_cast<float *>(X), *Yf = reinterpret_cast<float *>(Y);
+    if (asc) lex_sweep_vc_mx_dir<C, true>(u, g, a, abase, base, lo, hi, n, Xf, Yf);
+    else lex_sweep_vc_mx_dir<C, false>(u, g, a, abase, base, lo, hi, n, Xf, Yf);
+}
+
+// Pointwise Newton Gauss-Seidel for -u'' + lam e^u = f, mixed: e_i = cl e^{u_i}
+// and the residual r_i = g_i - e_i - (F_{i-1/2} - F_{i+1/2}) in FP64; the
+// Newton denominator 2 + e_i (3 + e_i at a wall), its reciprocal and the
+// recurrence delta_i = a_i (r_i + delta_{i-1}) in FP32.
+template <int C, bool ASC>
+__device__ __noinline__ void lex_sweep_nl_mx_dir(double *__restrict__ u, const double *__restrict__ g, double cl,
+                                                 int base, int lo, int hi, int n, float *X, float *Y) {
+    constexpr int s = ASC ? 1 : -1;
+    const int t = threadIdx.x;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const bool wall0 = (q0 == 0) && (qlo == 0);
+    const bool wall1 = (q0 + k1 == n);
+    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int a0 = ASC ? -base : n - 1 - base;
+    float rr[C], aa[C];
+    float p = 0.0f, A = 1.0f, r_end = 0.0f, a_end = 0.0f;
+    if (active) {
+        double w[C + 2];
+#pragma unroll
+        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
+        if (wall0) {
+            const double e = cl * exp(w[1]);
+            const float a = __frcp_rn(3.0f + (float)e);
+            p = a * (float)((g[a0] - e) - (scale2(w[1], 1) - (w[2] - w[1])));
+            A = a;
+        }
+        if (wall1) {
+            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
+            const double e = cl * exp(ue);
+            r_end = (float)((g[a0 + s * (n - 1)] - e) - ((ue - um) - (-scale2(ue, 1))));
+            a_end = __frcp_rn(3.0f + (float)e);
+        }
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
+            const double e = cl * exp(w[k + 1]);
+            const float r = (float)((gv - e) - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1])));
+            const float a = __frcp_rn(2.0f + (float)e);
+            const bool in = k >= ka && k < kb;
+            p = in ? a * (r + p) : p;
+            A = in ? a * A : A;
+            rr[k] = p;
+            aa[k] = A;
+        }
+        X[t] = p;
+        Y[t] = A;
+    }
+    __syncthreads();
+    if (active) {
+        constexpr int J = (kTruncNlMx + C - 1) / C - 1;
+        float cin = 0.0f;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const float x = X[max(idx, 0)], y = Y[max(idx, 0)];
+            cin = idx >= 0 ? fmaf(y, cin, x) : 0.0f;
+        }
+        float dl = cin;
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < kb) {
+                dl = fmaf(aa[k], cin, rr[k]);
+                u[a0 + s * (q0 + k)] += (double)dl;
+            }
+        if (wall1) u[a0 + s * (n - 1)] += (double)(a_end * (r_end + dl));
+    }
+    __syncthreads();
+}
+
+template <int C>
+__device__ __forceinline__ void lex_sweep_nl_mx(double *__restrict__ u, const double *__restrict__ g, double cl,
+                                                int base, int lo, int hi, int n, bool asc, double *X, double *Y) {
+    float *Xf = reinterpret_cast<float *>(X), *Yf = reinterpret_cast<float *>(Y);
+    if (asc) lex_sweep_nl_mx_dir<C, true>(u, g, cl, base, lo, hi, n, Xf, Yf);
+    else lex_sweep_nl_mx_dir<C, false>(u, g, cl, base, lo, hi, n, Xf, Yf);
+}
+
 // One smoothing sweep of the operator OP (cl = lam h^2 of the level for the
 // Bratu problem; a, abase: the face coefficients for the variable-coefficient
 // problem; Y: a second per-thread array).
@@ -504,7 +705,9 @@ __device__ __forceinline__ void sweep_op(double *__restrict__ u, const double *_
                                          const double *a, int abase, int base, int lo, int hi, int n, bool asc,
                                          double *X, double *Y) {
     if (OP == kOpBratu) lex_sweep_nl<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
+    else if (OP == kOpBratuMx) lex_sweep_nl_mx<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
     else if (OP == kOpVarcoef) lex_sweep_vc<kChunk>(u, g, a, abase, base, lo, hi, n, asc, X, Y);
+    else if (OP == kOpVarcoefMx) lex_sweep_vc_mx<kChunk>(u, g, a, abase, base, lo, hi, n, asc, X, Y);
     else lex_sweep<kChunk, PRELOAD>(u, g, base, lo, hi, n, asc, X);
 }
 
@@ -768,7 +971,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
     const double *u_src = batch_at(a.u_src, FROM_PI ? nc : n), *g = batch_at(a.g, n);
     double *u_out = batch_at(a.u_out, n), *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    if (OP == kOpVarcoef) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
+    if (op_vc(OP)) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
     stage_range(m.g, g + m.L0, m.L1 - m.L0);
     if (FROM_PI) stage_coarse_async(m.c, u_src, m.C0, m.C1, nc);
     else stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
@@ -793,11 +996,11 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         uc_out[J] = scale2(u[i0] + u[i0 + 1], -1);
-        double gc = (OP == kOpVarcoef)
+        double gc = (op_vc(OP))
                         ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
                                      m.a[i0 + 2])
                         : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-        if (OP == kOpBratu) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+        if (op_nl(OP)) gc += tau_nl(cl, u[i0], u[i0 + 1]);
         gc_out[J] = gc;
     }
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
@@ -813,7 +1016,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
     const double *u_src = batch_at(a.u_src, n), *g = batch_at(a.g, n), *uc_src = batch_at(a.uc_src, nc);
     double *u_out = batch_at(a.u_out, n);
     LevelSmem m = level_smem(sm, s, a.tile, a.halo, n, a.maxlen, a.maxc, a.maxch);
-    if (OP == kOpVarcoef) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
+    if (op_vc(OP)) stage_range(m.a, batch_at(a.coef, n + 1) + m.L0, m.L1 - m.L0 + 1);
     stage_range(m.g, g + m.L0, m.L1 - m.L0);
     stage_range(m.u, u_src + m.L0, m.L1 - m.L0);
     stage_coarse_async(m.c, uc_src, m.C0, m.C1, nc);
@@ -1086,11 +1289,11 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
         if (!edge) {
             double um2 = (J > 0) ? u[i0 - 2] : 0.0, um1 = (J > 0) ? u[i0 - 1] : 0.0;
             double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
-            double gc = (OP == kOpVarcoef)
+            double gc = (op_vc(OP))
                             ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
                                          m.a[i0 + 2])
                             : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-            if (OP == kOpBratu) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+            if (op_nl(OP)) gc += tau_nl(cl, u[i0], u[i0 + 1]);
             gc_out[J] = gc;
         }
     }
@@ -1123,7 +1326,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     const double hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
     // variable coefficient: faces s-2, s, s+2 (coarse faces J, J+1, J+2 coincide with them)
     double am = 1.0, a0 = 1.0, ap = 1.0;
-    if (OP == kOpVarcoef) {
+    if (op_vc(OP)) {
         const double *co = batch_at(a.coef, a.n + 1);
         am = co[s - 2];
         a0 = co[s];
@@ -1132,18 +1335,18 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     {
         double Gl = h0 - hm1, Gr = h1 - h0;
         double Fl = f2 - f3, Fr = p0 - f1;
-        if (OP == kOpVarcoef) { Gl *= am; Fl *= am; Gr *= a0; Fr *= a0; }
+        if (op_vc(OP)) { Gl *= am; Fl *= am; Gr *= a0; Fr *= a0; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
+        if (op_nl(OP)) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
         gc_out[J] = scale2(rf[2 * J] + rf[2 * J + 1], rexp) + tau;
     }
     {
         int J2 = J + 1;
         double Gl = h1 - h0, Gr = h2 - h1;
         double Fl = p0 - f1, Fr = p2 - p1;
-        if (OP == kOpVarcoef) { Gl *= a0; Fl *= a0; Gr *= ap; Fr *= ap; }
+        if (op_vc(OP)) { Gl *= a0; Fl *= a0; Gr *= ap; Fr *= ap; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (OP == kOpBratu) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
+        if (op_nl(OP)) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
         gc_out[J2] = scale2(rf[2 * J2] + rf[2 * J2 + 1], rexp) + tau;
     }
 }
@@ -1230,7 +1433,7 @@ template <int OP>
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     double *u = m.u + m.off(l), *g = m.g + m.off(l);
-    const double *a = (OP == kOpVarcoef) ? m.a(l) : nullptr;
+    const double *a = (op_vc(OP)) ? m.a(l) : nullptr;
     for (int k = 0; k < nu; ++k)
         sweep_op<OP, true>(u, g, scale2(m.lam, -2 * l), a, 0, 0, 0, n, n, (k & 1) == 0, m.X, m.Y);
 }
@@ -1248,13 +1451,13 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         double u2 = (J < nc - 1) ? u[i0 + 2] : 0.0, u3 = (J < nc - 1) ? u[i0 + 3] : 0.0;
         uc[J] = scale2(u[i0] + u[i0 + 1], -1);
         double gcv;
-        if (OP == kOpVarcoef) {
+        if (op_vc(OP)) {
             const double *a = m.a(l);
             gcv = tau_rhs_vc(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, a[i0], a[i0 + 2]);
         } else {
             gcv = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
         }
-        if (OP == kOpBratu) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
+        if (op_nl(OP)) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
         gc[J] = gcv;
     }
     __syncthreads();
@@ -1296,14 +1499,14 @@ __device__ void coarsest_newton(double *u, const double *g, int n, double c, dou
 
 template <int OP>
 __device__ void tail_coarsest(TailSmem &m, const double *Ainv) {
-    if (OP == kOpBratu) {
+    if (op_nl(OP)) {
         const int n0 = 1 << m.M0;
         if (threadIdx.x == 0)
             coarsest_newton(m.u + m.off(m.M0), m.g + m.off(m.M0), n0, scale2(m.lam, -2 * m.M0), m.S, m.X);
         __syncthreads();
         return;
     }
-    if (OP == kOpVarcoef) {
+    if (op_vc(OP)) {
         const int n0 = 1 << m.M0;
         if (threadIdx.x == 0)
             coarsest_thomas_vc(m.u + m.off(m.M0), m.g + m.off(m.M0), n0, m.a(m.M0), m.S, m.X);

@@ -22,7 +22,7 @@ EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_h
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
            "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
-           "srfmg_destroy", "srfmg_last_error", "srfmg_version",
+           "srfmg_destroy", "srfmg_last_error", "srfmg_version", "srfmg_alu_peaks",
            "srfmg_solve_host_async", "srfmg_solve_host_join", "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
            "srfmg_group_query", "srfmg_group_member", "srfmg_group_destroy", "srfmg_group_last_error")
 
@@ -110,6 +110,7 @@ def load(build_if_missing=True):
     lib.srfmg_group_last_error.restype = ctypes.c_char_p
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
+    lib.srfmg_alu_peaks.argtypes = [ctypes.c_int, dp]
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
                  "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
@@ -532,3 +533,15 @@ def autotune(log2_n, device=0, reps=5, **overrides):
 
 def version():
     return load().srfmg_version().decode()
+
+
+def alu_peaks(device=0):
+    """Measured arithmetic throughput of the device (srfmg_alu_peaks): a dict of
+    64-bit integer adds/s, 64-bit operations/s in the (x + y + 1) >> 1 step,
+    FP64 flops/s and FP32 flops/s."""
+    lib = load()
+    out = (ctypes.c_double * 4)()
+    st = lib.srfmg_alu_peaks(device, out)
+    if st != OK:
+        raise SrfmgError(st, lib.srfmg_last_error(None).decode())
+    return {"i64_add_per_s": out[0], "i64_avg_ops_per_s": out[1], "fp64_flops": out[2], "fp32_flops": out[3]}

@@ -18,7 +18,8 @@ x_i = (i + 1/2)/N.
   sampled sines.
 * ``varcoef_series``: -(a u')' = f with a = exp(g/2) at the faces,
   g = amp * sum_{k=1..K} d_k cos(k pi x) (d_k ~ N(0,1)/k), the manufactured
-  u = sine series, f = -(a u')' = -(a' u' + a u'') at the centres.
+  u = sine series, f = -(a u')' = -(a' u' + a u'') at the centres;
+  ``varcoef_series_batch`` the same for many problems on the device.
 * ``bratu_series``: the nonlinear problem -u'' + lam e^u = f with the
   manufactured solution u = scale * sum c_k sin(k pi x) (default scale 1/2),
   f = -u'' + lam e^u sampled at the centres.
@@ -75,9 +76,7 @@ def varcoef_series(M, nmodes, seed, amp=1.0, gmodes=16):
     """(f, u_exact, log_a) for -(a u')' = f: log_a at the 2^M + 1 faces
     x_j = j / 2^M, f and u_exact at the cell centres."""
     n = 1 << M
-    rng = np.random.default_rng(seed + 7919)
-    d = amp * rng.standard_normal(gmodes) / np.arange(1, gmodes + 1)
-    c = sine_coefficients(nmodes, seed)
+    d, c = _varcoef_coefficients(nmodes, seed, amp, gmodes)
     faces = np.arange(n + 1, dtype=np.float64) / n
     x = centres(M)
     log_a = np.zeros(n + 1)
@@ -98,6 +97,43 @@ def varcoef_series(M, nmodes, seed, amp=1.0, gmodes=16):
         upp -= c[k - 1] * (k * np.pi) ** 2 * np.sin(k * np.pi * x)
     f = -(ap * up + a * upp)
     return f, u, log_a
+
+
+def _varcoef_coefficients(nmodes, seed, amp, gmodes):
+    rng = np.random.default_rng(seed + 7919)
+    d = amp * rng.standard_normal(gmodes) / np.arange(1, gmodes + 1)
+    return d, sine_coefficients(nmodes, seed)
+
+
+def varcoef_series_batch(M, seeds, nmodes, device, amp=1.0, gmodes=16, chunk=64):
+    """(f, log_a): float64 tensors on `device` of len(seeds) problems of 2^M cells,
+    problem k holding varcoef_series(M, nmodes, seeds[k]) (f at the centres,
+    log_a at the 2^M + 1 faces), formed as matrix products of the coefficients
+    with the sampled cosines and sines, `chunk` problems at a time."""
+    import torch
+    n = 1 << M
+    kg = torch.arange(1, gmodes + 1, dtype=torch.float64, device=device)
+    ku = torch.arange(1, nmodes + 1, dtype=torch.float64, device=device)
+    x = torch.from_numpy(centres(M)).to(device)
+    faces = torch.arange(n + 1, dtype=torch.float64, device=device) / n
+    cos_f = torch.cos(torch.pi * kg[:, None] * faces[None, :])
+    cos_g = torch.cos(torch.pi * kg[:, None] * x[None, :])
+    sin_g = torch.sin(torch.pi * kg[:, None] * x[None, :])
+    cos_u = torch.cos(torch.pi * ku[:, None] * x[None, :])
+    sin_u = torch.sin(torch.pi * ku[:, None] * x[None, :])
+    fs, las = [], []
+    for c0 in range(0, len(seeds), chunk):
+        co = [_varcoef_coefficients(nmodes, int(sd), amp, gmodes) for sd in seeds[c0:c0 + chunk]]
+        d = torch.from_numpy(np.stack([e[0] for e in co])).to(device)
+        c = torch.from_numpy(np.stack([e[1] for e in co])).to(device)
+        las.append((0.5 * d) @ cos_f)
+        g = (0.5 * d) @ cos_g
+        gp = -(0.5 * d * kg * torch.pi) @ sin_g
+        up = (c * ku * torch.pi) @ cos_u
+        upp = -(c * (ku * torch.pi) ** 2) @ sin_u
+        a = torch.exp(g)
+        fs.append(-(gp * a * up + a * upp))
+    return torch.cat(fs).reshape(-1).contiguous(), torch.cat(las).reshape(-1).contiguous()
 
 
 def bratu_series(M, nmodes, seed, lam, scale=0.5):

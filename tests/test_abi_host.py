@@ -110,3 +110,8 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(srfmg.SrfmgError) as ei:
         srfmg.Solver(12)
     assert ei.value.status == srfmg.ECUDA
+
+
+def test_alu_peaks_rejects_null_on_the_host():
+    lib = srfmg.load()
+    assert lib.srfmg_alu_peaks(0, None) == srfmg.EINVAL

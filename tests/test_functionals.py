@@ -146,8 +146,6 @@ def test_functionals_of_a_batch_equal_single_solves_gpu(precision):
 @pytest.mark.parametrize("op", [srfmg.LAPLACE, srfmg.BRATU])
 def test_reconstruct_equals_the_solve_gpu(precision, op):
     torch = pytest.importorskip("torch")
-    if op == srfmg.BRATU and precision == srfmg.MIXED:
-        pytest.skip("Bratu runs in FP64 only")
     M, W, b, B = 14, 512, 8, 2
     kw = dict(op=srfmg.BRATU, lambda_=1.0) if op == srfmg.BRATU else {}
     if op == srfmg.BRATU:

@@ -133,8 +133,6 @@ SEGMENT_TAU_CASES = [
 @pytest.mark.parametrize("M,nRS,W,b,op", SEGMENT_TAU_CASES)
 def test_segment_local_tau_parity_gpu(M, nRS, W, b, op, precision):
     torch = pytest.importorskip("torch")
-    if op != "laplace" and precision == srfmg.MIXED:
-        pytest.skip("Bratu and the variable coefficient run in FP64 only")
     kw, okw, log_a = {}, {}, None
     if op == "bratu":
         f, _, _ = workloads.bratu_series(M, 16, seed=M, lam=1.0)

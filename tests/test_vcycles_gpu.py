@@ -54,8 +54,6 @@ CASES = [
 @pytest.mark.parametrize("M,nRS,W,b,k,op", CASES)
 def test_vcycles_after_fmg_parity_gpu(M, nRS, W, b, k, op, precision):
     pytest.importorskip("torch")
-    if op == "bratu" and precision == srfmg.MIXED:
-        pytest.skip("Bratu runs in FP64 only")
     if op == "bratu":
         f, _, _ = workloads.bratu_series(M, 16, seed=M, lam=1.0)
         kw, okw = dict(op=srfmg.BRATU, lambda_=1.0), dict(op="bratu", lam=1.0)
