@@ -65,7 +65,15 @@ typedef enum {
  * -(a u')' = f with a > 0 at the cell faces (fluxes a_{i+1/2} (u_{i+1} - u_i),
  * a wall face counted twice by the odd ghost; coarse faces take the
  * coefficient of the coinciding fine face), set by srfmg_set_coefficient.
- * Both run in FP64 only. */
+ * Precisions: SRFMG_FP64 runs every step in FP64.  SRFMG_MIXED keeps the
+ * accuracy-bearing quantities exact or rounded below FP64's unit and takes the
+ * rest off GB300's narrow FP64 pipe: for SRFMG_OP_LAPLACE and SRFMG_OP_VARCOEF
+ * the solution, residual, tau correction, restriction and interpolations are
+ * 64-bit fixed-point integers (the variable coefficient's fluxes exact 128-bit
+ * products, its Gauss-Seidel multipliers 31-bit), the coarsest solve FP64; for
+ * SRFMG_OP_BRATU the solution, residual (with lambda e^u), tau correction,
+ * interpolations and coarsest Newton solve are FP64 and the Newton Gauss-Seidel
+ * correction recurrence FP32. */
 typedef enum { SRFMG_OP_LAPLACE = 0, SRFMG_OP_VARCOEF = 1, SRFMG_OP_BRATU = 2 } srfmg_op;
 typedef enum { SRFMG_FP64 = 0, SRFMG_MIXED = 1 } srfmg_precision;
 typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
@@ -121,8 +129,7 @@ srfmg_status srfmg_default_params(int32_t log2_n, srfmg_params *p);
 /* Create a plan on CUDA device `device`: validates *p (Sec. 3/4 parameter
  * meanings above), allocates the device workspace and records the level
  * schedule (the FMG loop of Fig. 2 with the SR steps of Fig. 3).
- * On success *out is a new handle; on failure *out is NULL.  SRFMG_OP_BRATU
- * with SRFMG_MIXED returns SRFMG_EUNSUPPORTED. */
+ * On success *out is a new handle; on failure *out is NULL. */
 srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out);
 
 /* One FMG-FAS(-SR) solve (Figs. 2-4).
@@ -237,8 +244,12 @@ srfmg_status srfmg_adjoint(srfmg_handle h, const double *dL_du, double *dL_df, v
  * with |log_a| <= 700, and on every level of 128 or more cells adjacent faces
  * within a factor 1.5 of each other (|log a_{j+1} - log a_j| <= ln 1.5; the
  * Gauss-Seidel carry over 99 cells is exact to 2^-72 for multipliers
- * a_near / (a_near + a_far) <= 0.6).  The call synchronises `stream` to read
- * the check; log_a may be freed when it returns.  Until the first call a = 1.
+ * a_near / (a_near + a_far) <= 0.6); with SRFMG_MIXED also a contrast
+ * max a / min a below 2^8 over the problem (the fixed-point face coefficients
+ * then keep at least 52 bits).  With SRFMG_MIXED the call also forms the fixed-
+ * point face coefficients and multipliers of every level.  The call
+ * synchronises `stream` to read the check; log_a may be freed when it
+ * returns.  Until the first call a = 1.
  * Errors: SRFMG_EINVAL for a NULL handle or pointer, a plan of another
  * operator, or a coefficient that fails the check (the plan's coefficient is
  * then reset to a = 1). */

@@ -47,11 +47,12 @@ struct Op {
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
     PtrTag seg_uin;   // a V-cycle's pre-leg from the caller's current fine solution
-    // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu; kOpVarcoefMx,
-    // kOpBratuMx: the mixed precision of those two, FP32 correction recurrences)
+    // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu; kOpBratuMx: the
+    // mixed precision of the Bratu problem, FP32 correction recurrences)
     int opk;
-    // fixed-point variant (precision SRFMG_MIXED): the same op with integer kernels
-    bool fixed;
+    // fixed-point variant (precision SRFMG_MIXED of -u'' = f and -(a u')' = f): the
+    // same op with integer kernels; vc: their variable-coefficient instantiation
+    bool fixed, vc;
     fx::RhsArgs frhs;
     fx::LevelArgs flev;
     fx::SegArgs fseg;
@@ -83,6 +84,8 @@ struct srfmg_plan {
     double *seam = nullptr;
     double *Ainv = nullptr;
     double *coef[32] = {};         // variable coefficient: face coefficients of levels M0..M
+    fx::u64 *fA[32] = {};          // fixed-point variable coefficient: A per face, levels M0..M
+    fx::u64 *fBM[32] = {};         // fixed-point variable coefficient: two multiplier words per cell
     int *coef_bad = nullptr;       // variable coefficient: set by the coefficient kernel's check
     fx::Scale *scale = nullptr;    // fixed-point scales (precision SRFMG_MIXED)
     double *fpart = nullptr;       // SR plans: functional partials, kNumFunc per segment and problem
@@ -345,6 +348,7 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
 // doubles or 64-bit integers of the same size).
 void to_fixed(srfmg_plan *h, Op &o) {
     o.fixed = true;
+    o.vc = (h->p.op == SRFMG_OP_VARCOEF);
     o.scale = h->scale;
     typedef fx::i64 i64;
     switch (o.kind) {
@@ -368,6 +372,8 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.flev.u_out = (i64 *)o.lev.u_out;
         o.flev.uc_out = (i64 *)o.lev.uc_out;
         o.flev.gc_out = (i64 *)o.lev.gc_out;
+        o.flev.cA = h->fA[o.lev.l];
+        o.flev.cBM = h->fBM[o.lev.l];
         break;
     case OP_SR_PRE: case OP_SEAM: case OP_SR_POST:
         o.fseg.M = o.seg.M; o.fseg.n = o.seg.n; o.fseg.W = o.seg.W; o.fseg.b = o.seg.b; o.fseg.nu = o.seg.nu;
@@ -381,6 +387,8 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.fseg.u_in = (const i64 *)o.seg.u_in;
         o.fseg.u_out_fx = (i64 *)o.seg.u_out;   // a level below the finest (the finest: patched per solve)
         o.fseg.local_tau = o.seg.local_tau;
+        o.fseg.cA = h->fA[o.seg.M];
+        o.fseg.cBM = h->fBM[o.seg.M];
         break;
     case OP_TAIL:
         o.ftail.M0 = o.tail.M0; o.ftail.Mc = o.tail.Mc; o.ftail.nu1 = o.tail.nu1; o.ftail.nu2 = o.tail.nu2;
@@ -390,6 +398,11 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.ftail.g_in = (o.tail_g == TAG_F) ? nullptr : (const i64 *)o.tail.g_in;
         o.ftail.u_out = (i64 *)o.tail.u_out;
         o.ftail.Ainv = o.tail.Ainv;
+        for (int l = 0; l < 32; ++l) {
+            o.ftail.cA[l] = h->fA[l];
+            o.ftail.cBM[l] = h->fBM[l];
+        }
+        o.ftail.coef0 = h->coef[h->M0];
         break;
     case OP_SCALE:
         break;
@@ -515,19 +528,23 @@ void build_schedule(srfmg_plan *h) {
     for (Op &o : h->ops) {
         const bool mx = (h->p.precision == SRFMG_MIXED);
         o.opk = (h->p.op == SRFMG_OP_BRATU)     ? (mx ? kOpBratuMx : kOpBratu)
-                : (h->p.op == SRFMG_OP_VARCOEF) ? (mx ? kOpVarcoefMx : kOpVarcoef)
+                : (h->p.op == SRFMG_OP_VARCOEF) ? kOpVarcoef
                                                 : kOpLaplace;
-        // the variable-coefficient kernels stage their face coefficients
-        if (op_vc(o.opk) && (o.kind == OP_DOWN || o.kind == OP_DOWN_PI || o.kind == OP_UP ||
-                                    o.kind == OP_SR_PRE || o.kind == OP_SR_POST))
-            o.smem += (size_t)((o.kind == OP_SR_PRE || o.kind == OP_SR_POST) ? o.seg.maxlen : o.lev.maxlen) *
-                      sizeof(double) + 2 * sizeof(double);
+        // the variable-coefficient kernels stage their face coefficients (FP64), or
+        // A, the multipliers and a second carry array (fixed point)
+        const bool seg = (o.kind == OP_SR_PRE || o.kind == OP_SR_POST);
+        if (op_vc(o.opk) && (o.kind == OP_DOWN || o.kind == OP_DOWN_PI || o.kind == OP_UP || seg)) {
+            const size_t ml = (size_t)(seg ? o.seg.maxlen : o.lev.maxlen), mch = (size_t)(seg ? o.seg.maxch : o.lev.maxch);
+            if (h->fixed) o.smem += (3 * ml + 1 + mch) * sizeof(double);
+            else o.smem += ml * sizeof(double) + 2 * sizeof(double);
+        }
         o.grid.y = (unsigned)h->batch;           // one grid row per problem of the batch
     }
     if (!h->fixed) return;
     for (Op &o : h->ops) to_fixed(h, o);
     Op sc = make_op(OP_SCALE);
     sc.fixed = true;
+    sc.vc = (h->p.op == SRFMG_OP_VARCOEF);
     sc.scale = h->scale;
     sc.status = h->status;
     sc.level = h->M;
@@ -558,6 +575,23 @@ cudaError_t run(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// The fixed-point kernels of one op (VC: the variable-coefficient instantiation).
+template <bool VC>
+cudaError_t launch_fixed_ops(const Op &o, cudaStream_t s, bool pdl) {
+    cudaError_t e = cudaSuccess;
+    switch (o.kind) {
+    case OP_TAIL: e = run(fx::tail_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.ftail); break;
+    case OP_DOWN_PI: e = run(fx::level_down_kernel<true, VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_DOWN: e = run(fx::level_down_kernel<false, VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_UP: e = run(fx::level_up_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_SR_PRE: e = run(fx::sr_pre_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
+    case OP_SEAM: e = run(fx::seam_tau_kernel<VC>, o.grid, o.block, 0, s, pdl, o.fseg, o.nseg); break;
+    case OP_SR_POST: e = run(fx::sr_post_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
+    default: break;
+    }
+    return e;
+}
+
 cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     Op o = o0;
     const double *f = io.f;
@@ -578,17 +612,11 @@ cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     switch (o.kind) {
     case OP_SCALE: {
         const long long n = (long long)o.level < 63 ? (1LL << o.level) : 0;
-        e = run(fx::scale_kernel, o.grid, o.block, 0, s, pdl, f, n, o.scale, o.status);
+        e = run(fx::scale_kernel, o.grid, o.block, 0, s, pdl, f, n, o.scale, o.status, o.vc ? 1 : 0);
         break;
     }
     case OP_RHS: e = run(fx::rhs_hierarchy_kernel, o.grid, o.block, o.smem, s, pdl, o.frhs); break;
-    case OP_TAIL: e = run(fx::tail_kernel, o.grid, o.block, o.smem, s, pdl, o.ftail); break;
-    case OP_DOWN_PI: e = run(fx::level_down_kernel<true>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
-    case OP_DOWN: e = run(fx::level_down_kernel<false>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
-    case OP_UP: e = run(fx::level_up_kernel, o.grid, o.block, o.smem, s, pdl, o.flev); break;
-    case OP_SR_PRE: e = run(fx::sr_pre_kernel, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
-    case OP_SEAM: e = run(fx::seam_tau_kernel, o.grid, o.block, 0, s, pdl, o.fseg, o.nseg); break;
-    case OP_SR_POST: e = run(fx::sr_post_kernel, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
+    default: e = o.vc ? launch_fixed_ops<true>(o, s, pdl) : launch_fixed_ops<false>(o, s, pdl); break;
     }
     return e;
 }
@@ -632,7 +660,6 @@ cudaError_t launch(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
     if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
     if (o.opk == kOpBratuMx) return launch_fp64<kOpBratuMx>(o, s, pdl);
     if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
-    if (o.opk == kOpVarcoefMx) return launch_fp64<kOpVarcoefMx>(o, s, pdl);
     return launch_fp64<kOpLaplace>(o, s, pdl);
 }
 
@@ -663,6 +690,22 @@ cudaError_t launch_coef(srfmg_plan *h, const double *log_a, cudaStream_t s) {
     const size_t nf = ((size_t)1 << h->M) + 1;
     const unsigned blocks = (unsigned)std::min<size_t>(4 * 152, (nf + 255) / 256);
     coef_hierarchy_kernel<<<dim3(blocks, (unsigned)h->batch), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !h->fixed) return e;
+    // fixed point: the coefficient's scales per problem, then A and the multipliers of every level
+    fx::CoefFxArgs fa;
+    std::memset(&fa, 0, sizeof(fa));
+    for (int l = 0; l < 32; ++l) {
+        fa.coef[l] = h->coef[l];
+        fa.A[l] = h->fA[l];
+        fa.BM[l] = h->fBM[l];
+    }
+    fa.sc = h->scale;
+    fa.bad = h->coef_bad;
+    fa.M = h->M;
+    fa.M0 = h->M0;
+    fx::coef_scale_kernel<<<dim3((unsigned)h->batch), 1024, 0, s>>>(fa);
+    fx::coef_fixed_kernel<<<dim3(blocks, (unsigned)h->batch), 256, 0, s>>>(fa);
     return cudaGetLastError();
 }
 
@@ -698,11 +741,14 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
         (const void *)level_up_kernel<OPK>, (const void *)sr_pre_kernel<OPK>, (const void *)sr_post_kernel<OPK>, \
         (const void *)tail_kernel<OPK>
     const void *fns[] = {SRFMG_FP64_KERNELS(kOpLaplace), SRFMG_FP64_KERNELS(kOpVarcoef), SRFMG_FP64_KERNELS(kOpBratu),
-                         SRFMG_FP64_KERNELS(kOpVarcoefMx), SRFMG_FP64_KERNELS(kOpBratuMx),
+                         SRFMG_FP64_KERNELS(kOpBratuMx),
                          (const void *)rhs_hierarchy_kernel,
-                         (const void *)fx::level_down_kernel<true>, (const void *)fx::level_down_kernel<false>,
-                         (const void *)fx::level_up_kernel, (const void *)fx::sr_pre_kernel,
-                         (const void *)fx::sr_post_kernel, (const void *)fx::tail_kernel,
+                         (const void *)fx::level_down_kernel<true, false>, (const void *)fx::level_down_kernel<false, false>,
+                         (const void *)fx::level_up_kernel<false>, (const void *)fx::sr_pre_kernel<false>,
+                         (const void *)fx::sr_post_kernel<false>, (const void *)fx::tail_kernel<false>,
+                         (const void *)fx::level_down_kernel<true, true>, (const void *)fx::level_down_kernel<false, true>,
+                         (const void *)fx::level_up_kernel<true>, (const void *)fx::sr_pre_kernel<true>,
+                         (const void *)fx::sr_post_kernel<true>, (const void *)fx::tail_kernel<true>,
                          (const void *)fx::rhs_hierarchy_kernel};
     for (const void *fn : fns) {
         // the opt-in limit covers static and dynamic shared memory together
@@ -780,7 +826,7 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     if (h->Mc < h->M0) h->Mc = h->M0;
     // the 64-bit fixed-point kernels serve the constant-coefficient operator; the
     // mixed precision of the other two is their FP64 kernels with FP32 corrections
-    h->fixed = (p->precision == SRFMG_MIXED && p->op == SRFMG_OP_LAPLACE);
+    h->fixed = (p->precision == SRFMG_MIXED && p->op != SRFMG_OP_BRATU);
     const char *env = std::getenv("SRFMG_NO_GRAPH");
     h->use_graph = !(env && env[0] == '1');
 
@@ -808,6 +854,13 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     }
     if (p->op == SRFMG_OP_VARCOEF) {
         for (int l = h->M0; l <= h->M && st == SRFMG_OK; ++l) st = alloc_dev(h, &h->coef[l], B * (((size_t)1 << l) + 1));
+        for (int l = h->M0; l <= h->M && st == SRFMG_OK && h->fixed; ++l) {
+            double *w = nullptr;
+            st = alloc_dev(h, &w, B * (((size_t)1 << l) + 1));
+            h->fA[l] = (fx::u64 *)w;
+            if (st == SRFMG_OK) st = alloc_dev(h, &w, B * ((size_t)2 << l));
+            h->fBM[l] = (fx::u64 *)w;
+        }
         double *flag = nullptr;
         if (st == SRFMG_OK) st = alloc_dev(h, &flag, 1);
         h->coef_bad = (int *)flag;
@@ -836,7 +889,10 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         if (e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamCreate");
     }
     if (st == SRFMG_OK && p->op == SRFMG_OP_VARCOEF) {          // a = 1 until srfmg_set_coefficient
-        e = launch_coef(h, nullptr, h->cap_stream);
+        // (after the workspace memsets on the legacy stream, which the capture
+        // stream does not wait for: the fixed-point scales are written here)
+        e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = launch_coef(h, nullptr, h->cap_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->cap_stream);
         if (e != cudaSuccess) st = cuda_fail(h, e, "coefficient initialisation");
     }
@@ -1093,7 +1149,8 @@ srfmg_status srfmg_set_coefficient(srfmg_handle h, const double *log_a, void *st
     if (e != cudaSuccess) return cuda_fail(h, e, "coefficient reset");
     return fail(h, SRFMG_EINVAL,
                 "log_a: a value is not finite or beyond +-700, or adjacent faces of a level of 128 or more "
-                "cells differ by more than a factor 1.5 (ln 1.5 in log a); the coefficient was reset to a = 1");
+                "cells differ by more than a factor 1.5 (ln 1.5 in log a), or (SRFMG_MIXED) max a / min a is "
+                "2^8 or more; the coefficient was reset to a = 1");
 }
 
 srfmg_status srfmg_check(srfmg_handle h, void *stream) {

@@ -30,17 +30,20 @@ namespace fx {
 typedef long long i64;
 typedef unsigned long long u64;
 
-// Fixed-point scales of one solve, written on the device by scale_kernel.
+// Fixed-point scales of one solve, written on the device by scale_kernel
+// (S, Sg0, E) and, for the variable coefficient, by coef_scale_kernel (Ka, Ea,
+// Kb).
 struct Scale {
     int S;       // u = U 2^-S
     int Sg0;     // g_l = G 2^-(Sg0 + 2l)
     int E;       // max|f| < 2^E
-    int pad;
+    int Ka;      // variable coefficient: 2^Ka >= 1 / min a', a' = a 2^-Ea (0 otherwise)
     // scale_kernel's accumulators: zero between solves (set at plan creation,
     // restored by the kernel's last block)
     int emax;           // largest biased exponent field of f seen so far
     unsigned done;      // blocks of this problem that have finished
-    int pad2, pad3;
+    int Ea;      // variable coefficient: max a < 2^Ea
+    int Kb;      // variable coefficient: 62 - Ka, the scale of the reciprocal diagonals
 };
 
 // x / 2^k rounded half up, 0 < k < 63.
@@ -252,6 +255,249 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
 }
 
 // --------------------------------------------------------------------------
+// Variable coefficient -(a u')' = f in fixed point.
+//
+// The operator is normalised by an exact power of two, a' = a 2^-Ea with
+// max a < 2^Ea, and the right-hand side with it (G carries 2^-Ea, folded into
+// Sg0), which leaves u unchanged; 1/2 <= max a' < 1 and min a' >= 2^-Ka.
+// Per level, the face coefficients are A = round(a' 2^61) (at least 52 bits
+// for a contrast max a / min a below 2^8), and each cell keeps its Gauss-Seidel
+// multipliers in two words: the reciprocal diagonal b = 1/(a'_near + a'_far) as
+// round(b 2^(62 - Ka)) and the ascending multiplier m = a'_left / (a'_left +
+// a'_right) as round(m 2^63) (a wall face counts twice; the descending
+// multiplier is 2^63 - m).  The fluxes a' (U_{i+1} - U_i) are exact 128-bit
+// products rounded to units (half a unit each, as the rounding of the
+// right-hand side into solution units), and tau keeps the coarse right-hand
+// side's finer grid; every product that enters a correction is an exact
+// 128-bit product rounded to the nearest unit (a biased rounding of a few units
+// per cell would act as a smooth right-hand side on the fine levels, whose
+// right-hand side in solution units is small, and reach the coarse levels
+// through tau at the walls).  The scale S = 61 - E + Ea - Ka bounds |U| below
+// 2^59: with the Green's function of -(a'u')' = f', |u| <= max|f'| / (4 min a').
+// --------------------------------------------------------------------------
+constexpr int kSaVc = 61;           // A = round(a' 2^61)
+constexpr int kKaMax = 9;           // contrast max a / min a below 2^8
+
+
+// round(A d / 2^sh) (half away from zero) for A < 2^62, 1 <= sh <= 63, an exact
+// 128-bit product; |result| < 2^63
+__device__ __forceinline__ i64 mul_shr_round(u64 A, i64 d, int sh) {
+    const u64 ad = d < 0 ? (u64)0 - (u64)d : (u64)d;
+    const u64 lo = A * ad;
+    u64 hi = __umul64hi(A, ad);
+    const u64 lo2 = lo + (1ULL << (sh - 1));
+    hi += (lo2 < lo) ? 1ULL : 0ULL;
+    const u64 r = (hi << (64 - sh)) | (lo2 >> sh);
+    return d < 0 ? -(i64)r : (i64)r;
+}
+
+// Signed 128-bit product A d (two's complement hi:lo)
+struct S128 {
+    u64 lo;
+    u64 hi;
+};
+__device__ __forceinline__ S128 mul_s128(u64 A, i64 d) {
+    const u64 ad = d < 0 ? (u64)0 - (u64)d : (u64)d;
+    S128 r;
+    r.lo = A * ad;
+    r.hi = __umul64hi(A, ad);
+    if (d < 0) {
+        r.lo = ~r.lo + 1ULL;
+        r.hi = ~r.hi + (r.lo == 0 ? 1ULL : 0ULL);
+    }
+    return r;
+}
+// round((a - b) / 2^k) for 1 <= k <= 63 when the result fits 64 bits
+__device__ __forceinline__ i64 s128_diff_shr_round(S128 a, S128 b, int k) {
+    const u64 lo = a.lo - b.lo;
+    u64 hi = a.hi - b.hi - (a.lo < b.lo ? 1ULL : 0ULL);
+    const u64 lo2 = lo + (1ULL << (k - 1));
+    hi += (lo2 < lo) ? 1ULL : 0ULL;
+    return (i64)((hi << (64 - k)) | (lo2 >> k));
+}
+
+// Lexicographic Gauss-Seidel sweep of -(a u')' = f in place, fixed point, with
+// the layout and chunking of lex_sweep_dir: the residual of the old values
+//   r_q = gs_q - (F_near - F_far),  F = round(A (U_{q} - U_{q-1}) / 2^61)
+// (sweep coordinates; the odd ghost -U at both walls), the correction
+// recurrence delta_q = b_q r_q + m_q delta_{q-1}, an affine recurrence whose
+// chunk carries are the nested sum over the 11 preceding chunks
+// (X_{c-1} + Y_{c-1}(X_{c-2} + ...), Y the product of a chunk's multipliers, as
+// in the FP64 variable-coefficient sweep: multipliers <= 0.6 over 99 cells
+// leave less than one unit of a 64-bit value), update U += delta.
+// A[f - abase]: faces of the staged range; BM[i - base]: the cells'
+// multipliers (two words per cell).  X, Y: one word per thread each.  SHIFT as
+// in lex_sweep_dir.
+constexpr int kTruncVcFx = 96;
+
+template <int C, bool ASC, bool SHIFT = false>
+__device__ __noinline__ void lex_sweep_vc_dir(i64 *__restrict__ u, const i64 *__restrict__ gs,
+                                              const u64 *__restrict__ A, const u64 *__restrict__ BM, int base,
+                                              int abase, int lo, int hi, int n, i64 *X, i64 *Y, int Kb,
+                                              int gsh = 0) {
+    auto G = [gsh](i64 x) { return SHIFT ? shr_round(x, gsh) : x; };
+    constexpr int s = ASC ? 1 : -1;
+    const int t = threadIdx.x;
+    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
+    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
+    const bool active = t < nch;
+    const int q0 = (c_first + t) * C;
+    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
+    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
+    const int a0 = ASC ? -base : n - 1 - base;      // cell of position q: a0 + s q
+    const int f0 = ASC ? -abase : n - abase;        // face before position q: f0 + s q
+    i64 rr[C];
+    u64 aa[C];
+    i64 p = 0;
+    u64 yp = 1ULL << 62;                           // the chunk's product of multipliers, scaled by 2^62
+    if (active) {
+        i64 wp = u[a0 + s * min(max(q0 - 1, qmin), qmax)];
+        if (q0 == 0 && qlo == 0) wp = -u[a0];                            // odd ghost at the first wall
+        i64 wc = u[a0 + s * min(max(q0, qmin), qmax)];
+        i64 Fn = mul_shr_round(A[f0 + s * min(max(q0, qlo), qhi)], wc - wp, kSaVc);
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const int q = q0 + k;
+            i64 wn = u[a0 + s * min(max(q + 1, qmin), qmax)];
+            if (q + 1 >= n) wn = -wc;                                    // odd ghost at the last wall
+            const i64 Ff = mul_shr_round(A[f0 + s * min(max(q + 1, qlo), qhi)], wn - wc, kSaVc);
+            const i64 r = G(gs[a0 + s * min(max(q, qmin), qmax)]) - (Fn - Ff);
+            const int ci = 2 * (a0 + s * min(max(q, qmin), qmax));
+            const u64 B = BM[ci], ma = BM[ci + 1];
+            const u64 m = ASC ? ma : (1ULL << 63) - ma;
+            const bool in = k >= k0 && k < k1;
+            p = in ? mul_shr_round(B, r, Kb) + mul_shr_round(m, p, 63) : p;
+            yp = in ? __umul64hi(yp, m) << 1 : yp;   // relative error 2^-62: the carries' weights
+            rr[k] = p;
+            aa[k] = yp;
+            Fn = Ff;
+            wc = wn;
+        }
+        X[t] = p;
+        Y[t] = (i64)yp;
+    }
+    __syncthreads();
+    if (active) {
+        constexpr int J = (kTruncVcFx + C - 1) / C - 1;
+        i64 cin = 0;
+#pragma unroll
+        for (int j = J; j >= 0; --j) {
+            const int idx = t - 1 - j;
+            const i64 x = X[max(idx, 0)];
+            const u64 y = (u64)Y[max(idx, 0)];
+            cin = idx >= 0 ? x + mul_shr_round(y, cin, 62) : 0;
+        }
+        i64 uo[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) uo[k] = u[a0 + s * min(max(q0 + k, qmin), qmax)];
+#pragma unroll
+        for (int k = 0; k < C; ++k)
+            if (k >= k0 && k < k1) u[a0 + s * (q0 + k)] = uo[k] + rr[k] + mul_shr_round(aa[k], cin, 62);
+    }
+    __syncthreads();
+}
+
+template <int C, bool SHIFT = false>
+__device__ __forceinline__ void lex_sweep_vc(i64 *__restrict__ u, const i64 *__restrict__ gs, const u64 *A,
+                                             const u64 *BM, int base, int abase, int lo, int hi, int n, bool asc,
+                                             i64 *X, i64 *Y, int Kb, int gsh = 0) {
+    if (asc) lex_sweep_vc_dir<C, true, SHIFT>(u, gs, A, BM, base, abase, lo, hi, n, X, Y, Kb, gsh);
+    else lex_sweep_vc_dir<C, false, SHIFT>(u, gs, A, BM, base, abase, lo, hi, n, X, Y, Kb, gsh);
+}
+
+// tau-corrected coarse right-hand side of -(a u')' = f (Eqs. 6-7 with the
+// level's own coefficients): the terms of tau_rhs weighted by the fine faces
+// 2J (left) and 2J + 2 (right), which the coarse faces J and J + 1 coincide
+// with, as one exact 128-bit combination moved into the coarse right-hand
+// side's units (2^tsh solution units) and rounded there.
+__device__ __forceinline__ i64 tau_rhs_vc(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1, i64 u2, i64 u3, int J, int nc,
+                                          int tsh, u64 AL, u64 AR) {
+    const i64 hJ = (u0 + u1) >> 1;
+    const i64 Gl = (J == 0) ? 2 * hJ : hJ - ((um2 + um1) >> 1);
+    const i64 Gr = (J == nc - 1) ? -2 * hJ : ((u2 + u3) >> 1) - hJ;
+    const i64 Fl = (J == 0) ? 2 * u0 : u0 - um1;
+    const i64 Fr = (J == nc - 1) ? -2 * u1 : u2 - u1;
+    return gr + s128_diff_shr_round(mul_s128(AL, Gl - 2 * Fl), mul_s128(AR, Gr - 2 * Fr), kSaVc - tsh);
+}
+
+// The fixed-point coefficient of every level from the FP64 face coefficients
+// (coef_hierarchy_kernel's output): coef_scale_kernel (one block per problem)
+// reduces max a and min a over the finest level's faces into Ea, Ka, Kb and
+// flags a contrast beyond 2^8; coef_fixed_kernel (grid-stride over the faces
+// of every level, problem blockIdx.y) writes A and the packed multipliers.
+struct CoefFxArgs {
+    const double *coef[32];    // FP64 a per level (2^l + 1 faces per problem)
+    u64 *A[32];                // round(a 2^(61 - Ea)) per face
+    u64 *BM[32];               // multipliers per cell, two words each
+    Scale *sc;
+    int *bad;
+    int M, M0;
+};
+
+__global__ void coef_scale_kernel(CoefFxArgs a) {
+    const long long nf = (1LL << a.M) + 1;
+    const double *c = a.coef[a.M] + (long long)blockIdx.x * nf;
+    // a > 0: the bit patterns of positive doubles order like the values
+    long long mx = 0, mn = 0x7fefffffffffffffLL;
+    for (long long j = threadIdx.x; j < nf; j += blockDim.x) {
+        const long long b = __double_as_longlong(c[j]);
+        mx = b > mx ? b : mx;
+        mn = b < mn ? b : mn;
+    }
+    __shared__ long long smx[32], smn[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long x = __shfl_xor_sync(0xffffffffu, mx, o), y = __shfl_xor_sync(0xffffffffu, mn, o);
+        mx = x > mx ? x : mx;
+        mn = y < mn ? y : mn;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smx[threadIdx.x >> 5] = mx;
+        smn[threadIdx.x >> 5] = mn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mx = smx[w] > mx ? smx[w] : mx;
+            mn = smn[w] < mn ? smn[w] : mn;
+        }
+        // 2^(e-1) <= x < 2^e with e = biased exponent - 1022
+        const int Ea = (int)((mx >> 52) & 0x7ff) - 1022;
+        const int emin = (int)((mn >> 52) & 0x7ff) - 1022;
+        int Ka = Ea - emin + 1;                    // 1 / min a' <= 2^(Ea - emin + 1)
+        // contrast below 2^8 keeps Ka <= 9 (A with at least 52 bits)
+        if (!(__longlong_as_double(mx) < 256.0 * __longlong_as_double(mn)) || Ka > kKaMax) {
+            atomicOr(a.bad, 1);
+            Ka = kKaMax;
+        }
+        Scale *sc = a.sc + blockIdx.x;
+        sc->Ea = Ea;
+        sc->Ka = Ka;
+        sc->Kb = 62 - Ka;
+    }
+}
+
+__global__ void coef_fixed_kernel(CoefFxArgs a) {
+    const Scale *sc = a.sc + blockIdx.y;
+    const int Ea = sc->Ea, Ka = sc->Ka;
+    for (int l = a.M; l >= a.M0; --l) {
+        const long long n = 1LL << l;
+        const double *c = batch_at(a.coef[l], n + 1);
+        u64 *A = batch_at(a.A[l], n + 1), *BM = batch_at(a.BM[l], 2 * n);
+        for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j <= n;
+             j += (long long)gridDim.x * blockDim.x) {
+            A[j] = (u64)f64_to_fixed(c[j], kSaVc - Ea);
+            if (j < n) {
+                const double al = (j == 0) ? 2.0 * c[0] : c[j];
+                const double ar = (j == n - 1) ? 2.0 * c[n] : c[j + 1];
+                const double D = al + ar;
+                BM[2 * j] = (u64)rint(scale2(1.0 / D, Ea + 62 - Ka));   // b' 2^(62 - Ka) < 2^61
+                BM[2 * j + 1] = (u64)rint(scale2(al / D, 63));          // m 2^63, m <= 256/257
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
 // Scale: E with max|f| < 2^E from the largest exponent field of f.
 // --------------------------------------------------------------------------
 // (one Scale per problem of a batch: sc[blockIdx.y])
@@ -260,7 +506,7 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
 // problem to finish (a counter, after a fence) turns the maximum into E, S and
 // Sg0 and restores the accumulators to zero for the next solve.  An inf or
 // NaN in f (exponent field 0x7ff) is recorded in the status word.
-__global__ void scale_kernel(const double *f, long long n, Scale *sc, int *status) {
+__global__ void scale_kernel(const double *f, long long n, Scale *sc, int *status, int vc) {
     pdl_enter();
     const double2 *f2 = reinterpret_cast<const double2 *>(batch_at(f, n));
     sc += blockIdx.y;
@@ -296,8 +542,13 @@ __global__ void scale_kernel(const double *f, long long n, Scale *sc, int *statu
         int E = raw - 1022;                      // 2^E bounds max|f| (raw 0: f = 0)
         E = E < -100 ? -100 : (E > 900 ? 900 : E);
         sc->E = E;
-        sc->S = 62 - E;
-        sc->Sg0 = 60 - E;
+        if (vc) {                                // -(a u')' = f: |u| <= max|f'| / (4 min a'), f' = f 2^-Ea
+            sc->S = 61 - E + sc->Ea - sc->Ka;
+            sc->Sg0 = sc->S - 2 - sc->Ea;
+        } else {
+            sc->S = 62 - E;
+            sc->Sg0 = 60 - E;
+        }
     }
 }
 
@@ -360,13 +611,17 @@ struct LevelArgs {
     i64 *u_out;                // level l after the pass (tile), when u_out_f64 is NULL
     double *u_out_f64;         // finest level without SR: the FP64 solution
     i64 *uc_out, *gc_out;      // down pass: restricted solution and tau rhs on level l-1
+    const u64 *cA, *cBM;       // variable coefficient: this level's A (faces) and multipliers (cells)
 };
 
 // Shared memory: u, gs (staged G or f, then the right-hand side in solution
 // units), the coarse cells, the chunk carries, gr (restricted G of the tile's
-// coarse cells, down pass): 2 maxlen + 2 maxc + maxch words.
+// coarse cells, down pass): 2 maxlen + 2 maxc + maxch words; the variable
+// coefficient adds A (maxlen + 1 faces), BM (two words per cell) and the
+// carries' Y (maxch): 3 maxlen + 1 + maxch words more.
 struct LevelSmem {
-    i64 *u, *gs, *c, *X, *gr;
+    i64 *u, *gs, *c, *X, *gr, *Y;
+    u64 *A, *BM;
     int L0, L1, C0, C1;
     // this problem's arrays (see batch_at)
     const Scale *sc;
@@ -389,6 +644,9 @@ __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs 
     m.c = m.gs + a.maxlen;
     m.X = m.c + a.maxc;
     m.gr = m.X + a.maxch;
+    m.A = (u64 *)(m.gr + a.maxc);
+    m.BM = m.A + a.maxlen + 1;
+    m.Y = (i64 *)(m.BM + 2 * a.maxlen);
     const long long n = a.n;
     m.sc = a.sc + blockIdx.y;
     m.usrc = batch_at(a.u_src, u_src_coarse ? n / 2 : n);
@@ -402,11 +660,16 @@ __device__ __forceinline__ LevelSmem level_smem(i64 *sm, int s, const LevelArgs 
     return m;
 }
 
-// Issue the staging copies of G_l (or of f, converted by prepare_rhs).
+// Issue the staging copies of G_l (or of f, converted by prepare_rhs) and,
+// for the variable coefficient, of the level's A and multipliers.
+template <bool VC>
 __device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
-    (void)a;
     if (m.gin) stage_range(m.gs, m.gin + m.L0, m.L1 - m.L0);
     else stage_range(m.gs, m.fin + m.L0, m.L1 - m.L0);
+    if (VC) {
+        stage_range(m.A, batch_at(a.cA, (long long)a.n + 1) + m.L0, m.L1 - m.L0 + 1);
+        stage_range(m.BM, batch_at(a.cBM, 2LL * a.n) + 2 * m.L0, 2 * (m.L1 - m.L0));
+    }
 }
 
 // In place over the staged cells (pairs 2J, 2J+1; L0 and L1 are even):
@@ -430,11 +693,14 @@ __device__ void prepare_rhs(LevelSmem &m, const LevelArgs &a, int gsh, i64 *gr, 
     }
 }
 
+template <bool VC>
 __device__ void smooth_range(LevelSmem &m, int n, int nu) {
     int lo = (m.L0 == 0) ? 0 : m.L0 + 1;
     int hi = (m.L1 == n) ? n : m.L1 - 1;
+    const int Kb = VC ? m.sc->Kb : 0;
     for (int k = 0; k < nu; ++k) {
-        lex_sweep<kChunk>(m.u, m.gs, m.L0, lo, hi, n, (k & 1) == 0, m.X);
+        if (VC) lex_sweep_vc<kChunk>(m.u, m.gs, m.A, m.BM, m.L0, m.L0, lo, hi, n, (k & 1) == 0, m.X, m.Y, Kb);
+        else lex_sweep<kChunk>(m.u, m.gs, m.L0, lo, hi, n, (k & 1) == 0, m.X);
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
@@ -446,15 +712,15 @@ __device__ __forceinline__ i64 coarse_reflect(const i64 *src, int j, int nc) {
     return src[j];
 }
 
-template <bool FROM_PI>
-__global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs a) {
+template <bool FROM_PI, bool VC>
+__global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_down_kernel(LevelArgs a) {
     pdl_enter();
 
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a, FROM_PI);
-    stage_g_async(m, a);
+    stage_g_async<VC>(m, a);
     if (FROM_PI) stage_coarse_async(m.c, m.usrc, m.C0, m.C1, nc);
     else stage_range(m.u, m.usrc + m.L0, m.L1 - m.L0);
     stage_wait();
@@ -468,7 +734,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
             fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
     __syncthreads();
-    smooth_range(m, n, a.nu);
+    smooth_range<VC>(m, n, a.nu);
     const i64 *u = m.u;
     const int tsh = 2 * a.l - 4;
     for (int J = J0 + (int)threadIdx.x; J < ((s + a.tile) >> 1); J += (int)blockDim.x) {
@@ -476,20 +742,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
         m.ucout[J] = (u[i0] + u[i0 + 1]) >> 1;
-        m.gcout[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+        m.gcout[J] = VC ? tau_rhs_vc(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh, m.A[i0],
+                                     m.A[i0 + 2])
+                        : tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
     }
     for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) m.uout[i] = u[i - m.L0];
 }
 
 // Up pass (Eq. 4): U_l += P (U_{l-1} - R U_l) (rounded to units), then nu sweeps.
-__global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a) {
+template <bool VC>
+__global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_up_kernel(LevelArgs a) {
     pdl_enter();
 
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.tile;
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a, false);
-    stage_g_async(m, a);
+    stage_g_async<VC>(m, a);
     stage_range(m.u, m.usrc + m.L0, m.L1 - m.L0);
     stage_coarse_async(m.c, m.ucsrc, m.C0, m.C1, nc);
     stage_wait();
@@ -511,7 +780,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_kernel(LevelArgs a
         m.u[i - m.L0] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
     }
     __syncthreads();
-    smooth_range(m, n, a.nu);
+    smooth_range<VC>(m, n, a.nu);
     const i64 *u = m.u;
     if (m.uout64) {
         const int S = m.sc->S;
@@ -541,11 +810,14 @@ struct SegArgs {
     double *u_out;             // post-leg: FP64 solution of segments seg0.. (NULL: not written)
     const double *u_ref;       // post-leg: reference for the functionals (NULL: none)
     double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
+    const u64 *cA, *cBM;       // variable coefficient: the level's A (faces) and multipliers (cells)
 };
 
-// Shared memory as LevelSmem: u, gs, c, X, gr (2 maxlen + 2 maxc + maxch words).
+// Shared memory as LevelSmem: u, gs, c, X, gr (2 maxlen + 2 maxc + maxch words),
+// and for the variable coefficient A, BM and Y (3 maxlen + 1 + maxch more).
 struct SegSmem {
-    i64 *u, *gs, *c, *X, *gr;
+    i64 *u, *gs, *c, *X, *gr, *Y;
+    u64 *A, *BM;
     int e0, e1, lo, hi, C0, C1;
 };
 
@@ -565,6 +837,9 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
     m.c = m.gs + a.maxlen;
     m.X = m.c + a.maxc;
     m.gr = m.X + a.maxch;
+    m.A = (u64 *)(m.gr + a.maxc);
+    m.BM = m.A + a.maxlen + 1;
+    m.Y = (i64 *)(m.BM + 2 * a.maxlen);
     return m;
 }
 
@@ -578,9 +853,14 @@ __device__ __forceinline__ SegSmem seg_smem(i64 *sm, const SegArgs &a, int s) {
 // extended patch as they are interpolated (the same arithmetic as the
 // separate pass, without its extra sweep over shared memory); the return value
 // says whether that happened (not when the iterate is staged instead of Pi).
+template <bool VC>
 __device__ bool seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1, bool kacz = false) {
     const int nc = a.n >> 1, kg = (a.sc + blockIdx.y)->Sg0, gsh = 2 * a.M - 2;
     const bool from_f = (a.g_in == nullptr);
+    if (VC) {
+        stage_range(m.A, batch_at(a.cA, (long long)a.n + 1) + m.lo, m.hi - m.lo + 1);
+        stage_range(m.BM, batch_at(a.cBM, 2LL * a.n) + 2 * m.lo, 2 * (m.hi - m.lo));
+    }
     if (a.u_in) stage_range(m.u, batch_at(a.u_in, a.n) + m.lo, m.hi - m.lo);
     else if (a.u_in_f64) stage_range(m.u, batch_at(a.u_in_f64, a.n) + m.lo, m.hi - m.lo);
     else stage_coarse_async(m.c, batch_at(a.uc_src, nc), m.C0, m.C1, nc);
@@ -621,16 +901,21 @@ __device__ bool seg_load(SegSmem &m, const SegArgs &a, i64 *gr, int J0, int J1, 
     return kacz;
 }
 
-__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
+template <bool VC>
+__global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) sr_pre_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
     const int s = blockIdx.x * a.W;
     const int n = a.n, nc = n >> 1;
     SegSmem m = seg_smem(smi, a, s);
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
-    seg_load(m, a, m.gr, J0, J1);
+    seg_load<VC>(m, a, m.gr, J0, J1);
     const int tsh = 2 * a.M - 4;
-    for (int k = 0; k < a.nu; ++k) lex_sweep<kChunk>(m.u, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    const int Kb = VC ? (a.sc + blockIdx.y)->Kb : 0;
+    for (int k = 0; k < a.nu; ++k) {
+        if (VC) lex_sweep_vc<kChunk>(m.u, m.gs, m.A, m.BM, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y, Kb);
+        else lex_sweep<kChunk>(m.u, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    }
     const i64 *u = m.u;
     i64 *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) {
@@ -640,7 +925,9 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
         if (!edge) {
             i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
             i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
-            gc_out[J] = tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+            gc_out[J] = VC ? tau_rhs_vc(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh, m.A[i0],
+                                        m.A[i0 + 2])
+                           : tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
         }
     }
     if (threadIdx.x < 6) {
@@ -652,6 +939,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
 
 // tau rhs at the two coarse cells of each interior segment boundary from the
 // assembled fine values (seams) and the restricted solution.
+template <bool VC>
 __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     pdl_enter();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -666,16 +954,30 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
     const i64 f3 = L[3], f2 = L[4], f1 = L[5], p0 = R[0], p1 = R[1], p2 = R[2];
     const int J = (s >> 1) - 1;
     const i64 hm1 = uc_out[J - 1], h0 = uc_out[J], h1 = uc_out[J + 1], h2 = uc_out[J + 2];
+    // variable coefficient: the fine faces s - 2, s, s + 2 (coarse faces J, J + 1, J + 2)
+    const u64 *cA = VC ? batch_at(a.cA, (long long)a.n + 1) : nullptr;
     {
-        i64 tau = ((h0 - hm1) - (h1 - h0)) - 2 * ((f2 - f3) - (p0 - f1));
         i64 g0 = gl ? gl[2 * J] : f64_to_fixed(f[2 * J], kg), g1 = gl ? gl[2 * J + 1] : f64_to_fixed(f[2 * J + 1], kg);
-        gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        if (VC) {
+            const i64 dl = (h0 - hm1) - 2 * (f2 - f3), dr = (h1 - h0) - 2 * (p0 - f1);
+            gc_out[J] = ((g0 + g1 + 1) >> 1) +
+                        s128_diff_shr_round(mul_s128(cA[s - 2], dl), mul_s128(cA[s], dr), kSaVc - tsh);
+        } else {
+            i64 tau = ((h0 - hm1) - (h1 - h0)) - 2 * ((f2 - f3) - (p0 - f1));
+            gc_out[J] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        }
     }
     {
         const int J2 = J + 1;
-        i64 tau = ((h1 - h0) - (h2 - h1)) - 2 * ((p0 - f1) - (p2 - p1));
         i64 g0 = gl ? gl[2 * J2] : f64_to_fixed(f[2 * J2], kg), g1 = gl ? gl[2 * J2 + 1] : f64_to_fixed(f[2 * J2 + 1], kg);
-        gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        if (VC) {
+            const i64 dl = (h1 - h0) - 2 * (p0 - f1), dr = (h2 - h1) - 2 * (p2 - p1);
+            gc_out[J2] = ((g0 + g1 + 1) >> 1) +
+                         s128_diff_shr_round(mul_s128(cA[s], dl), mul_s128(cA[s + 2], dr), kSaVc - tsh);
+        } else {
+            i64 tau = ((h1 - h0) - (h2 - h1)) - 2 * ((p0 - f1) - (p2 - p1));
+            gc_out[J2] = ((g0 + g1 + 1) >> 1) + tau * (1LL << tsh);
+        }
     }
 }
 
@@ -769,13 +1071,15 @@ __device__ __forceinline__ void fx_block_functionals(FxFunc &t, int S, double *d
 }
 
 // K6 in fixed point; output and functionals as in the FP64 kernel.
-__global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
+template <bool VC>
+__global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) sr_post_kernel(SegArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
     const int s = (a.seg0 + (int)blockIdx.x) * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(smi, a, s);
-    const bool first_done = seg_load(m, a, nullptr, 0, 0, true);
+    const bool first_done = seg_load<VC>(m, a, nullptr, 0, 0, true);
+    const int Kb = VC ? (a.sc + blockIdx.y)->Kb : 0;
     i64 *p = m.u;
     for (int k = 0; k < a.nu; ++k) {
         if (k > 0 || !first_done) {
@@ -787,7 +1091,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
             }
             __syncthreads();
         }
-        lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+        if (VC) lex_sweep_vc<kChunk>(p, m.gs, m.A, m.BM, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y, Kb);
+        else lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
     }
     const int S = (a.sc + blockIdx.y)->S;
     const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
@@ -858,24 +1163,40 @@ struct TailArgs {
     i64 *u_out;
     double *u_out_f64;         // whole problem in the tail: the FP64 solution
     const double *Ainv;
+    // variable coefficient: per level, A (faces) and the multipliers (cells), and the
+    // FP64 face coefficients of the coarsest level (its Thomas solve)
+    const u64 *cA[32];
+    const u64 *cBM[32];
+    const double *coef0;
 };
 
 struct TailSmem {
-    i64 *u, *g, *S, *X;
-    int M0;
+    i64 *u, *g, *S, *X, *Y;
+    int M0, Kb;
+    const u64 *const *cA;
+    const u64 *const *cBM;
     __device__ int off(int l) const { return (1 << l) - (1 << M0); }
+    // this problem's coefficient words of level l
+    __device__ const u64 *A(int l) const { return batch_at(cA[l], (1LL << l) + 1); }
+    __device__ const u64 *BM(int l) const { return batch_at(cBM[l], 2LL << l); }
 };
 
 // nu sweeps of level l on G_l directly (the sweep shifts it into solution units)
+template <bool VC>
 __device__ void tail_smooth(TailSmem &m, int l, int nu) {
     const int n = 1 << l;
     i64 *u = m.u + m.off(l);
     const i64 *g = m.g + m.off(l);
-    for (int k = 0; k < nu; ++k) lex_sweep<kChunk, true, true>(u, g, 0, 0, n, n, (k & 1) == 0, m.X, 2 * l - 2);
+    for (int k = 0; k < nu; ++k) {
+        if (VC) lex_sweep_vc<kChunk, true>(u, g, m.A(l), m.BM(l), 0, 0, 0, n, n, (k & 1) == 0, m.X, m.Y, m.Kb,
+                                           2 * l - 2);
+        else lex_sweep<kChunk, true, true>(u, g, 0, 0, n, n, (k & 1) == 0, m.X, 2 * l - 2);
+    }
 }
 
+template <bool VC>
 __device__ void tail_down(TailSmem &m, int l, int nu) {
-    tail_smooth(m, l, nu);
+    tail_smooth<VC>(m, l, nu);
     const int nc = 1 << (l - 1);
     const i64 *u = m.u + m.off(l), *g = m.g + m.off(l);
     i64 *uc = m.u + m.off(l - 1), *gc = m.g + m.off(l - 1);
@@ -884,7 +1205,45 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
         uc[J] = (u[i0] + u[i0 + 1]) >> 1;
-        gc[J] = tau_rhs(restrict_rhs(g[i0], g[i0 + 1]), um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4);
+        if (VC) {
+            const u64 *A = m.A(l);
+            gc[J] = tau_rhs_vc(restrict_rhs(g[i0], g[i0 + 1]), um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4,
+                               A[i0], A[i0 + 2]);
+        } else {
+            gc[J] = tau_rhs(restrict_rhs(g[i0], g[i0 + 1]), um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, 2 * l - 4);
+        }
+    }
+    __syncthreads();
+}
+
+// The coarsest level of -(a u')' = f in FP64: Thomas on the level's operator
+// with the FP64 face coefficients a (G 2^-(Sg0 + 2 M0) is h^2 rhs of -(a u')'
+// = f: the normalisation 2^-Ea of the fixed-point levels is folded into Sg0),
+// row i: -a_i u_{i-1} + (a_i + a_{i+1}) u_i - a_{i+1} u_{i+1} (a wall face
+// counted twice), the result onto the fixed-point grid.  One thread.
+__device__ void tail_coarsest_vc(TailSmem &m, const double *a, const Scale *sc) {
+    const int n0 = 1 << m.M0;
+    i64 *u = m.u + m.off(m.M0);
+    const i64 *g = m.g + m.off(m.M0);
+    if (threadIdx.x == 0) {
+        const int gexp = sc->Sg0 + 2 * m.M0, S = sc->S;
+        double *cp = reinterpret_cast<double *>(m.S), *dp = cp + n0;
+        for (int i = 0; i < n0; ++i) {
+            const double ai = a[i], ai1 = a[i + 1];
+            const double al = (i == 0) ? scale2(ai, 1) : ai;
+            const double ar = (i == n0 - 1) ? scale2(ai1, 1) : ai1;
+            const double lower = (i > 0) ? -ai : 0.0, upper = (i < n0 - 1) ? -ai1 : 0.0;
+            const double gi = fixed_to_f64(g[i], gexp);
+            const double denom = (i > 0) ? (al + ar) - lower * cp[i - 1] : al + ar;
+            cp[i] = upper / denom;
+            dp[i] = ((i > 0) ? gi - lower * dp[i - 1] : gi) / denom;
+        }
+        double x = dp[n0 - 1];
+        u[n0 - 1] = f64_to_fixed(x, S);
+        for (int i = n0 - 2; i >= 0; --i) {
+            x = dp[i] - cp[i] * x;
+            u[i] = f64_to_fixed(x, S);
+        }
     }
     __syncthreads();
 }
@@ -905,6 +1264,7 @@ __device__ void tail_coarsest(TailSmem &m, const double *Ainv, const Scale *sc) 
     __syncthreads();
 }
 
+template <bool VC>
 __device__ void tail_up(TailSmem &m, int l, int nu) {
     const int n = 1 << l, nc = n >> 1;
     i64 *u = m.u + m.off(l);
@@ -917,7 +1277,7 @@ __device__ void tail_up(TailSmem &m, int l, int nu) {
         u[i] += (3 * m.S[J] + cn + 2) >> 2;
     }
     __syncthreads();
-    tail_smooth(m, l, nu);
+    tail_smooth<VC>(m, l, nu);
 }
 
 __device__ void tail_interp(TailSmem &m, int l) {
@@ -931,7 +1291,8 @@ __device__ void tail_interp(TailSmem &m, int l) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
+template <bool VC>
+__global__ void __launch_bounds__(kTailBlock) tail_kernel(const __grid_constant__ TailArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
     TailSmem m;
@@ -941,8 +1302,17 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
     m.g = m.u + tot;
     m.S = m.g + tot;
     m.X = m.S + (1 << a.Mc) + 8;
+    m.Y = m.X + blockDim.x;
+    m.cA = a.cA;
+    m.cBM = a.cBM;
     const int nMc = 1 << a.Mc;
     const Scale *sc = a.sc + blockIdx.y;
+    m.Kb = VC ? sc->Kb : 0;
+    const double *coef0 = VC ? batch_at(a.coef0, (1LL << a.M0) + 1) : nullptr;
+    auto coarsest = [&]() {
+        if (VC) tail_coarsest_vc(m, coef0, sc);
+        else tail_coarsest(m, a.Ainv, sc);
+    };
     const i64 *u_in = batch_at(a.u_in, nMc), *g_in = batch_at(a.g_in, nMc);
     const double *f = batch_at(a.f, nMc);
     i64 *u_out = batch_at(a.u_out, nMc);
@@ -964,17 +1334,17 @@ __global__ void __launch_bounds__(kTailBlock) tail_kernel(TailArgs a) {
             for (int J = threadIdx.x; J < (1 << (l - 1)); J += blockDim.x) gc[J] = (g[2 * J] + g[2 * J + 1] + 1) >> 1;
             __syncthreads();
         }
-        tail_coarsest(m, a.Ainv, sc);
+        coarsest();
         for (int k = a.M0; k < a.Mc; ++k) {
             tail_interp(m, k + 1);
-            for (int l = k + 1; l > a.M0; --l) tail_down(m, l, a.nu1);
-            tail_coarsest(m, a.Ainv, sc);
-            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up(m, l, a.nu2);
+            for (int l = k + 1; l > a.M0; --l) tail_down<VC>(m, l, a.nu1);
+            coarsest();
+            for (int l = a.M0 + 1; l <= k + 1; ++l) tail_up<VC>(m, l, a.nu2);
         }
     } else {
-        for (int l = a.Mc; l > a.M0; --l) tail_down(m, l, a.nu1);
-        tail_coarsest(m, a.Ainv, sc);
-        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up(m, l, a.nu2);
+        for (int l = a.Mc; l > a.M0; --l) tail_down<VC>(m, l, a.nu1);
+        coarsest();
+        for (int l = a.M0 + 1; l <= a.Mc; ++l) tail_up<VC>(m, l, a.nu2);
     }
     if (u_out_f64) {
         const int S = sc->S;

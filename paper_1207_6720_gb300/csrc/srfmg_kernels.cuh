@@ -29,12 +29,13 @@ constexpr int kChunk = 9;
 // Operators of the FP64 kernels (template parameter OP): -u'' = f, the
 // variable-coefficient -(a u')' = f, and the Bratu problem -u'' + lam e^u = f.
 constexpr int kOpLaplace = 0, kOpVarcoef = 1, kOpBratu = 2;
-// The same operators in the mixed precision (SRFMG_MIXED) of the variable-
-// coefficient and Bratu problems: the solution, the residual, the tau
-// correction, the interpolations and the coarsest solve in FP64, the
-// Gauss-Seidel correction recurrence in FP32 (lex_sweep_vc_mx, lex_sweep_nl_mx).
-constexpr int kOpVarcoefMx = 3, kOpBratuMx = 4;
-__host__ __device__ constexpr bool op_vc(int op) { return op == kOpVarcoef || op == kOpVarcoefMx; }
+// The Bratu operator in the mixed precision (SRFMG_MIXED): the solution, the
+// residual, the tau correction, the interpolations and the coarsest solve in
+// FP64, the Newton Gauss-Seidel correction recurrence in FP32 (lex_sweep_nl_mx).
+// (The mixed precision of the other two operators is the 64-bit fixed point of
+// srfmg_fixed.cuh.)
+constexpr int kOpBratuMx = 4;
+__host__ __device__ constexpr bool op_vc(int op) { return op == kOpVarcoef; }
 __host__ __device__ constexpr bool op_nl(int op) { return op == kOpBratu || op == kOpBratuMx; }
 
 // Largest block of the level and segment kernels: one thread per chunk of at
@@ -504,8 +505,8 @@ __device__ __forceinline__ void lex_sweep_vc(double *__restrict__ u, const doubl
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision sweeps (SRFMG_MIXED for the variable-coefficient and Bratu
-// problems).  The split follows the precision roles of iterative refinement:
+// Mixed-precision sweep (SRFMG_MIXED for the Bratu problem).  The split
+// follows the precision roles of iterative refinement:
 // the residual r of the old values is formed in FP64 (it decides what the
 // smoother converges to), the correction recurrence that the Gauss-Seidel
 // step solves for r runs in FP32 (it only decides how fast), and the
@@ -514,106 +515,12 @@ __device__ __forceinline__ void lex_sweep_vc(double *__restrict__ u, const doubl
 // sums leave the FP64 pipe; the FP32 rounding of a correction (2^-24 of it)
 // is far below the FP64 work it feeds, since the last corrections of a
 // solve are of the size of its discretization error.  Layout, chunking and
-// wall handling are those of lex_sweep_vc / lex_sweep_nl; X and Y hold one
-// float per thread each (the caller's double arrays reinterpreted).  The carry
-// covers fewer chunks than in FP64: terms weighted below 2^-33 are dropped
-// (multipliers <= 0.6 over 45 cells, or <= 1/2 over 36 cells).
+// wall handling are those of lex_sweep_nl; X and Y hold one float per thread
+// each (the caller's double arrays reinterpreted).  The carry covers fewer
+// chunks than in FP64: terms weighted below 2^-33 are dropped (multipliers
+// <= 1/2 over 36 cells).
 // ---------------------------------------------------------------------------
-constexpr int kTruncVcMx = 45;
 constexpr int kTruncNlMx = 36;
-
-template <int C, bool ASC>
-__device__ __noinline__ void lex_sweep_vc_mx_dir(double *__restrict__ u, const double *__restrict__ g,
-                                                 const double *__restrict__ a, int abase, int base, int lo, int hi,
-                                                 int n, float *X, float *Y) {
-    constexpr int s = ASC ? 1 : -1;
-    const int t = threadIdx.x;
-    const int qlo = ASC ? lo : n - hi, qhi = ASC ? hi : n - lo;
-    const int c_first = qlo / C, nch = (qhi - 1) / C - c_first + 1;
-    const bool active = t < nch;
-    const int q0 = (c_first + t) * C;
-    const int k0 = max(qlo - q0, 0), k1 = min(qhi - q0, C);
-    const bool wall0 = (q0 == 0) && (qlo == 0);
-    const bool wall1 = (q0 + k1 == n);
-    const int ka = wall0 ? 1 : k0, kb = wall1 ? k1 - 1 : k1;
-    const int qmin = max(qlo - 1, 0), qmax = min(qhi, n - 1);
-    const int a0 = ASC ? -base : n - 1 - base;
-    const int fb0 = ASC ? 0 : n, fmin = lo, fmax = hi;
-    float rr[C], aa[C];
-    float p = 0.0f, A = 1.0f, r_end = 0.0f, b_end = 0.0f, al_end = 0.0f;
-    if (active) {
-        double w[C + 2], an[C + 1];
-#pragma unroll
-        for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
-#pragma unroll
-        for (int j = 0; j <= C; ++j) an[j] = a[min(max(fb0 + s * (q0 + j), fmin), fmax) - abase];
-        // FP64 fluxes through the chunk's faces (sweep direction), FP32 coefficients
-        double F[C + 1];
-        float af[C + 1];
-#pragma unroll
-        for (int j = 0; j <= C; ++j) {
-            F[j] = an[j] * (w[j + 1] - w[j]);
-            af[j] = (float)an[j];
-        }
-        if (wall0) {
-            const double r = g[a0] - (an[0] * scale2(w[1], 1) - F[1]);
-            p = (float)r * __frcp_rn(2.0f * af[0] + af[1]);
-            A = 0.0f;
-        }
-        if (wall1) {
-            const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
-            const double anr = a[fb0 + s * (n - 1) - abase], aw = a[fb0 + s * n - abase];
-            const double r = g[a0 + s * (n - 1)] - (anr * (ue - um) - aw * (-scale2(ue, 1)));
-            const float anf = (float)anr;
-            b_end = __frcp_rn(anf + 2.0f * (float)aw);
-            al_end = anf * b_end;
-            r_end = (float)r;
-        }
-#pragma unroll
-        for (int k = 0; k < C; ++k) {
-            const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
-            const float r = (float)(gv - (F[k] - F[k + 1]));
-            const float b = __frcp_rn(af[k] + af[k + 1]);
-            const float m = af[k] * b;
-            const bool in = k >= ka && k < kb;
-            p = in ? fmaf(m, p, r * b) : p;
-            A = in ? m * A : A;
-            rr[k] = p;
-            aa[k] = A;
-        }
-        X[t] = p;
-        Y[t] = A;
-    }
-    __syncthreads();
-    if (active) {
-        constexpr int J = (kTruncVcMx + C - 1) / C - 1;
-        float cin = 0.0f;
-#pragma unroll
-        for (int j = J; j >= 0; --j) {
-            const int idx = t - 1 - j;
-            const float x = X[max(idx, 0)], y = Y[max(idx, 0)];
-            cin = idx >= 0 ? fmaf(y, cin, x) : 0.0f;
-        }
-        float dl = cin;
-#pragma unroll
-        for (int k = 0; k < C; ++k)
-            if (k >= k0 && k < kb) {
-                dl = fmaf(aa[k], cin, rr[k]);
-                u[a0 + s * (q0 + k)] += (double)dl;
-            }
-        if (wall1) u[a0 + s * (n - 1)] += (double)fmaf(al_end, dl, b_end * r_end);
-    }
-    __syncthreads();
-}
-
-template <int C>
-__device__ __forceinline__ void lex_sweep_vc_mx(double *__restrict__ u, const double *__restrict__ g,
-                                                const double *__restrict__ a, int abase, int base, int lo, int hi,
-                                                int n, bool asc, double *X, double *Y) {
-    float *Xf = reinterpret_cast<float *>(X), *Yf = reinterpret_cast<float *>(Y);
-    if (asc) lex_sweep_vc_mx_dir<C, true>(u, g, a, abase, base, lo, hi, n, Xf, Yf);
-    else lex_sweep_vc_mx_dir<C, false>(u, g, a, abase, base, lo, hi, n, Xf, Yf);
-}
 
 // Pointwise Newton Gauss-Seidel for -u'' + lam e^u = f, mixed: e_i = cl e^{u_i}
 // and the residual r_i = g_i - e_i - (F_{i-1/2} - F_{i+1/2}) in FP64; the
@@ -707,7 +614,6 @@ __device__ __forceinline__ void sweep_op(double *__restrict__ u, const double *_
     if (OP == kOpBratu) lex_sweep_nl<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
     else if (OP == kOpBratuMx) lex_sweep_nl_mx<kChunk>(u, g, cl, base, lo, hi, n, asc, X, Y);
     else if (OP == kOpVarcoef) lex_sweep_vc<kChunk>(u, g, a, abase, base, lo, hi, n, asc, X, Y);
-    else if (OP == kOpVarcoefMx) lex_sweep_vc_mx<kChunk>(u, g, a, abase, base, lo, hi, n, asc, X, Y);
     else lex_sweep<kChunk, PRELOAD>(u, g, base, lo, hi, n, asc, X);
 }
 

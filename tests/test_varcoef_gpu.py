@@ -180,3 +180,32 @@ def test_rough_coefficient_is_rejected_and_reset_gpu():
             assert rel_maxnorm(u, ref1) <= TOL
     finally:
         s.close()
+
+
+@pytest.mark.gpu
+def test_mixed_refuses_a_contrast_beyond_2_to_the_8_gpu():
+    # a smooth ramp of log a from 0 to 6 (contrast e^6 > 2^8): every pair of
+    # neighbouring faces is within the sweep's factor 1.5, so FP64 takes it; the
+    # fixed-point coefficient refuses it and falls back to a = 1
+    torch = pytest.importorskip("torch")
+    M, W, b = 12, 512, 8
+    n = 1 << M
+    ramp = np.linspace(0.0, 6.0, n + 1)
+    f, _, _ = workloads.sine_series(M, 16, seed=3)
+    fd = torch.from_numpy(f).cuda()
+    s64 = srfmg.Solver(M, **_kw(1, W, b, 1, 1, 2))
+    smx = srfmg.Solver(M, **_kw(1, W, b, 1, 1, 2, srfmg.MIXED))
+    try:
+        s64.set_coefficient(torch.from_numpy(ramp).cuda())
+        with pytest.raises(srfmg.SrfmgError):
+            smx.set_coefficient(torch.from_numpy(ramp).cuda())
+        u = smx.solve(fd).cpu().numpy()
+        ref1 = oracle.fmg_h(oracle.sr_params(M, W, b), f)
+        assert rel_maxnorm(u, ref1) <= TOL
+        ok = ramp * (np.log(200.0) / 6.0)               # contrast 200: accepted
+        smx.set_coefficient(torch.from_numpy(ok).cuda())
+        ue_ref = oracle.fmg_h(oracle.sr_params(M, W, b, op="varcoef", coef=np.exp(ok)), f)
+        assert rel_maxnorm(smx.solve(fd).cpu().numpy(), ue_ref) <= 1e-9
+    finally:
+        s64.close()
+        smx.close()
