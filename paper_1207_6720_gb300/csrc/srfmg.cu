@@ -243,7 +243,11 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     o.level = l;
     const int n = 1 << l;
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
-    const int T = n < kTileMax ? n : kTileMax;
+    // levels up to 2^18 are latency-bound (a few microseconds per pass whatever
+    // their size): smaller tiles spread them over more SMs (measured: 1.8% off the
+    // N = 2^24 solve; 128-cell tiles, or 256 up to level 20, were slower)
+    const int Tmax = (l <= 18) ? 256 : kTileMax;
+    const int T = n < Tmax ? n : Tmax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
     // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9); 12 * 9 = 108
     // for the variable coefficient's 11 carry chunks), every sweep shrinks its
