@@ -31,6 +31,7 @@ class _Params(ctypes.Structure):
         ("seg_b", ctypes.c_int32 * (MAXLEV + 1)),
         ("op", ctypes.c_int32), ("lam", ctypes.c_double),
         ("coef", ctypes.POINTER(ctypes.c_double)), ("coef_level", ctypes.c_int32),
+        ("post", ctypes.c_int32),
     ]
 
 
@@ -90,8 +91,11 @@ class Params:
     """Solve parameters; ``seg[l] = (w, b)`` segments level l (w = 0: whole level)."""
 
     def __init__(self, M, M0=2, nRS=1, nu1=1, nu2=1, smoother="lex", tau_src="assembled", seg=None,
-                 op="laplace", lam=0.0, coef=None):
+                 op="laplace", lam=0.0, coef=None, post="full_update"):
         self.M, self.M0, self.nRS, self.nu1, self.nu2 = M, M0, nRS, nu1, nu2
+        # post-smoothing leg of the SR levels: "full_update" (Eq. 5 + Fig. 5) or
+        # "fas_recompute" (Eq. 4 on the recomputed pre-smoothed level)
+        self.post = post
         self.smoother, self.tau_src = smoother, tau_src
         self.seg = dict(seg or {})
         self.op, self.lam = op, lam
@@ -107,6 +111,7 @@ class Params:
             p.seg_w[l] = w
             p.seg_b[l] = b
         p.op = {"laplace": 0, "bratu": 1, "varcoef": 2}[self.op]
+        p.post = {"full_update": 0, "fas_recompute": 1}[self.post]
         p.lam = self.lam
         if self.coef is not None:
             p.coef = _ptr(self.coef)          # self.coef keeps the array alive
@@ -120,7 +125,7 @@ class Params:
 
 
 def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assembled", op="laplace",
-              lam=0.0, coef=None):
+              lam=0.0, coef=None, post="full_update"):
     """SR levels (the finest nRS) split into segments of W >> (M-l) cells with
     b buffer cells per side; every other level is smoothed as a whole."""
     seg = {}
@@ -130,7 +135,7 @@ def sr_params(M, W, b, nRS=1, nu1=1, nu2=1, M0=2, smoother="lex", tau_src="assem
             raise ValueError("segment narrower than 2 cells on an SR level")
         seg[l] = (w, b)
     return Params(M, M0=M0, nRS=nRS, nu1=nu1, nu2=nu2, smoother=smoother, tau_src=tau_src, seg=seg,
-                  op=op, lam=lam, coef=coef)
+                  op=op, lam=lam, coef=coef, post=post)
 
 
 def paper_params(M, nRS, halo_type, ns, M0=2):

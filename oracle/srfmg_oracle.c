@@ -63,6 +63,12 @@ typedef struct {
     double lam;             /* op 1: lam >= 0 (op 0: ignored) */
     const double *coef;     /* op 2: a at the 2^coef_level + 1 faces x = j 2^-coef_level */
     int32_t coef_level;     /* op 2: the level coef is given on (the finest) */
+    int32_t post;           /* post-smoothing leg of an SR level: 0: the full update
+                                  u_l = Pi u_{l-1} (Eq. 5) with compatible relaxation
+                                  (Fig. 5), the paper's (default); 1: the FAS
+                                  correction (Eq. 4) of the pre-smoothed level, which
+                                  the serial SR variant recomputes segment by segment,
+                                  then S without Kaczmarz */
 } or_params;
 
 /* lam of the operator (0 for the linear problem). */
@@ -397,7 +403,7 @@ static void postsmooth_update(or_state *st, int l) {
     const or_params *p = st->p;
     int n = 1 << l, nc = n / 2;
     double *ul = st->u[l], *uc = st->u[l - 1], *t = st->tmp;
-    if (is_sr_level(p, l)) {
+    if (is_sr_level(p, l) && p->post == 0) {
         for (int i = 0; i < n; i++) t[i] = prolong_fmg_at(uc, i, nc);
         smooth_level(st, l, t, ul, p->nu2, uc);
     } else {
@@ -437,6 +443,7 @@ static int check_params(const or_params *p) {
     }
     if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 > 16 || p->nu2 > 16) return OR_EINVAL;
     if (p->smoother < 0 || p->smoother > 1 || p->tau_src < 0 || p->tau_src > 1) return OR_EINVAL;
+    if (p->post < 0 || p->post > 1) return OR_EINVAL;
     for (int l = p->M0 + 1; l <= p->M; l++) {
         int w = p->seg_w[l], b = p->seg_b[l], n = 1 << l;
         if (w == 0) continue;
@@ -629,12 +636,21 @@ int or_vcycles_h(const or_params *p, const double *f, double *u_inout, int ncycl
  * relaxation and only its interior is emitted (Fig. 3 post-smoothing leg).
  * Memory for level M: one extended patch and a window of at most w + 8 cells.
  * Requires level M to be an SR level, segmented, with tau from the assembled
- * level (tau_src = 0). */
+ * level (tau_src = 0).
+ * With post = 1 the post-smoothing leg instead recomputes each segment's
+ * pre-smoothed patch from the level M-1 iterate the pre-leg interpolated
+ * (kept), puts the neighbouring segments' pre-smoothed interior cells (b + 1 per
+ * side, kept from the pre-leg) into its buffer and frozen cells, so that the
+ * patch holds the assembled pre-smoothed level, applies the FAS correction of
+ * Eq. 4 with the restricted pre-smoothed solution (kept) and smooths without
+ * Kaczmarz; then b + 1 <= w is required. */
 int or_fmg_v(const or_params *p, const double *f, double *u_out) {
     if (check_params(p)) return OR_EINVAL;
     int M = p->M, n = 1 << M, nc = n / 2;
     if (p->nRS < 1 || !segmented(p, M) || p->tau_src != 0 || M - 1 < p->M0) return OR_EINVAL;
     int w = p->seg_w[M], b = p->seg_b[M];
+    if (p->post == 1 && b + 1 > w) return OR_EINVAL;
+    const int nseg = n / w, ne = b + 1;   /* post = 1: pre-smoothed cells kept per segment side */
     or_params pc = *p;            /* the stored part: levels M0 .. M-1 */
     pc.M = M - 1;
     pc.nRS = p->nRS - 1;
@@ -647,7 +663,15 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
     double *win = (double *)malloc(sizeof(double) * (size_t)wcap);
     double *uc_new = (double *)malloc(sizeof(double) * (size_t)nc);
     double *aM = level_coef(p, M);
-    if (!patch || !frhs || !win || !uc_new || (p->op == 2 && !aM)) { rc = OR_ENOMEM; goto done; }
+    double *u_old = NULL, *uhat = NULL, *edge = NULL, *corr = NULL;
+    if (p->post == 1) {
+        u_old = (double *)malloc(sizeof(double) * (size_t)nc);
+        uhat = (double *)malloc(sizeof(double) * (size_t)nc);
+        edge = (double *)malloc(sizeof(double) * (size_t)nseg * 2 * ne);
+        corr = (double *)malloc(sizeof(double) * (size_t)nc);
+    }
+    if (!patch || !frhs || !win || !uc_new || (p->op == 2 && !aM) ||
+        (p->post == 1 && (!u_old || !uhat || !edge || !corr))) { rc = OR_ENOMEM; goto done; }
 
     /* right-hand sides of levels M-1 .. M0 (restriction of f), FMG to M-1 */
     for (int J = 0; J < nc; J++) uc_new[J] = restrict_at(f, 0, J);
@@ -667,6 +691,10 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
                 frhs[i - lo] = f[i];
             }
             patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL, op_lam(p), aM);
+            if (p->post == 1) {        /* the interior cells the neighbours' patches read */
+                memcpy(edge + (size_t)(s / w) * 2 * ne, patch + (s - lo), sizeof(double) * (size_t)ne);
+                memcpy(edge + (size_t)(s / w) * 2 * ne + ne, patch + (s + w - ne - lo), sizeof(double) * (size_t)ne);
+            }
             memcpy(win + (win_hi - win_lo), patch + (s - lo), sizeof(double) * (size_t)w);
             win_hi += w;
             /* coarse cells whose fine stencil 2J-2 .. 2J+3 is now assembled */
@@ -681,11 +709,39 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
             win_lo = keep_from;
         }
     }
+    if (p->post == 1) {
+        memcpy(u_old, st.u[M - 1], sizeof(double) * (size_t)nc);
+        memcpy(uhat, uc_new, sizeof(double) * (size_t)nc);
+    }
     memcpy(st.u[M - 1], uc_new, sizeof(double) * (size_t)nc);
 
     /* coarse part of the last V-cycle on the stored levels M-1 .. M0 */
     rc = vcycle(&st, M - 1);
     if (rc) goto done;
+
+    if (p->post == 1) {
+        /* post-smoothing leg with the FAS correction (Eq. 4) of the recomputed
+         * pre-smoothed segment, S without Kaczmarz, interior emitted */
+        for (int J = 0; J < nc; J++) corr[J] = st.u[M - 1][J] - uhat[J];
+        for (int s = 0; s < n; s += w) {
+            int e0, e1, lo, hi;
+            extended_patch(s, w, b, n, &e0, &e1, &lo, &hi);
+            for (int i = lo; i < hi; i++) {
+                patch[i - lo] = prolong_fmg_at(u_old, i, nc);
+                frhs[i - lo] = f[i];
+            }
+            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu1, NULL, op_lam(p), aM);
+            const int k = s / w;
+            if (s > 0)              /* cells [lo, s): the last ne of the left segment */
+                for (int i = lo; i < s; i++) patch[i - lo] = edge[(size_t)(k - 1) * 2 * ne + ne + (i - (s - ne))];
+            if (s + w < n)          /* cells [s + w, hi): the first ne of the right segment */
+                for (int i = s + w; i < hi; i++) patch[i - lo] = edge[(size_t)(k + 1) * 2 * ne + (i - (s + w))];
+            for (int i = lo; i < hi; i++) patch[i - lo] += prolong_lin_at(corr, i, nc);
+            patch_sweeps(p->smoother, patch, lo, frhs, lo, n, e0, e1, p->nu2, NULL, op_lam(p), aM);
+            memcpy(u_out + s, patch + (s - lo), sizeof(double) * (size_t)w);
+        }
+        goto done;
+    }
 
     /* post-smoothing leg of level M, segment by segment: full update from the
      * corrected level M-1, compatible relaxation, interior emitted */
@@ -701,6 +757,7 @@ int or_fmg_v(const or_params *p, const double *f, double *u_out) {
     }
 done:
     free(patch); free(frhs); free(win); free(uc_new); free(aM);
+    free(u_old); free(uhat); free(edge); free(corr);
     free_state(&st);
     return rc;
 }

@@ -424,3 +424,74 @@ def test_reading_segment_local_tau_seam_error():
     loc = np.max(np.abs(oracle.fmg_h(oracle.sr_params(M, 4096, 4, tau_src="segment"), f) - us))
     assert asm < 1.5 * stored
     assert loc > 10 * asm
+
+
+# ---------------------------------------------------------------- post-smoothing leg option
+# The SR post-leg reading "FAS recompute" (the correction of Eq. 4 applied to the
+# pre-smoothed level, which the serial SR variant recomputes segment by segment,
+# then S without Kaczmarz) against the stored-grid FAS V-cycle with the same
+# segmented smoother: the reading's defining property is that SR then changes
+# nothing but the storage.
+
+RECOMPUTE_CASES = [
+    # (M, W, b, nu1, nu2, M0, op)
+    (8, 32, 4, 1, 1, 2, "laplace"),
+    (10, 256, 8, 1, 1, 2, "laplace"),
+    (11, 64, 62, 2, 1, 3, "laplace"),      # b = W - 2, the widest even buffer below W
+    (12, 512, 16, 2, 2, 2, "laplace"),
+    (10, 128, 8, 2, 1, 2, "bratu"),
+    (10, 128, 8, 1, 1, 2, "varcoef"),
+]
+
+
+def _recompute_kw(M, op, seed=3):
+    if op == "bratu":
+        f, ue, _ = wl.bratu_series(M, 16, seed=seed, lam=1.0)
+        return f, ue, dict(op="bratu", lam=1.0)
+    if op == "varcoef":
+        f, ue, la = wl.varcoef_series(M, 16, seed=seed)
+        return f, ue, dict(op="varcoef", coef=np.exp(la))
+    f, ue, _ = wl.sine_series(M, 16, seed=seed)
+    return f, ue, {}
+
+
+@pytest.mark.parametrize("M,W,b,nu1,nu2,M0,op", RECOMPUTE_CASES)
+def test_fas_recompute_equals_stored_fas_with_the_segmented_smoother(M, W, b, nu1, nu2, M0, op):
+    f, _, kw = _recompute_kw(M, op)
+    sr = oracle.sr_params(M, W, b, nu1=nu1, nu2=nu2, M0=M0, post="fas_recompute", **kw)
+    stored = oracle.Params(M, M0=M0, nRS=0, nu1=nu1, nu2=nu2, seg={M: (W, b)}, **kw)
+    assert np.array_equal(oracle.fmg_h(sr, f), oracle.fmg_h(stored, f))
+
+
+@pytest.mark.parametrize("M,W,b,nu1,nu2,M0,op", RECOMPUTE_CASES)
+def test_fas_recompute_serial_sr_equals_stored_solve(M, W, b, nu1, nu2, M0, op):
+    # the serial SR variant never stores level M: it recomputes each segment's
+    # pre-smoothed patch and takes its buffer cells from the neighbours' kept
+    # edge cells; the result is the stored solve's bit for bit
+    f, _, kw = _recompute_kw(M, op)
+    p = oracle.sr_params(M, W, b, nu1=nu1, nu2=nu2, M0=M0, post="fas_recompute", **kw)
+    assert np.array_equal(oracle.fmg_v(p, f), oracle.fmg_h(p, f))
+
+
+def test_fas_recompute_is_another_reading_and_reaches_discretization_accuracy():
+    # it differs from the paper's full update + compatible relaxation, and one FMG
+    # cycle with it still reaches discretization accuracy with second order
+    errs = []
+    for M in (10, 11, 12):
+        f, ue, _ = wl.sine_series(M, 8, seed=2)
+        W = min(1024, (1 << M) // 4)
+        u_rc = oracle.fmg_v(oracle.sr_params(M, W, 8, post="fas_recompute"), f)
+        u_fu = oracle.fmg_v(oracle.sr_params(M, W, 8), f)
+        assert np.max(np.abs(u_rc - u_fu)) > 0.0
+        u_disc = wl.discrete_solution(M, wl.sine_coefficients(8, 2))
+        e_disc = np.max(np.abs(u_disc - ue))
+        e = np.max(np.abs(u_rc - ue))
+        assert e <= 1.5 * e_disc
+        errs.append(e)
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_fas_recompute_serial_sr_needs_b_below_w():
+    f, _, _ = wl.sine_series(8, 8, seed=1)
+    with pytest.raises(oracle.OracleError):
+        oracle.fmg_v(oracle.sr_params(8, 16, 16, post="fas_recompute"), f)
