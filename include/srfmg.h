@@ -86,6 +86,19 @@ typedef enum { SRFMG_SMOOTH_LEX = 0 } srfmg_smoother;
  * exchange; at large N its rounding-level mismatch with the assembled
  * restriction grows like N^2). */
 typedef enum { SRFMG_TAU_ASSEMBLED = 0, SRFMG_TAU_SEGMENT = 1 } srfmg_tau_edge;
+/* The post-smoothing leg of the SR level (Fig. 3): SRFMG_POST_FULL_UPDATE
+ * (default) rebuilds the level from the corrected coarse grid by the full
+ * update of Eq. 5 and smooths with the Kaczmarz compatible relaxation of
+ * Fig. 5, the paper's method; SRFMG_POST_FAS_RECOMPUTE applies the FAS
+ * correction of Eq. 4 to the pre-smoothed level instead, which each segment
+ * recomputes from the coarse iterate the pre-leg interpolated (kept), with the
+ * neighbouring segments' pre-smoothed edge cells (b + 1 per side, kept) in its
+ * buffer, and smooths without Kaczmarz: the result is that of stored-grid FAS
+ * with the same segmented smoother, at the cost of a second pre-smoothing and
+ * two coarse-level arrays.  SRFMG_POST_FAS_RECOMPUTE needs n_sr_levels = 1,
+ * tau_edge = SRFMG_TAU_ASSEMBLED, n_vcycles = 0 and buffer_width <
+ * segment_width. */
+typedef enum { SRFMG_POST_FULL_UPDATE = 0, SRFMG_POST_FAS_RECOMPUTE = 1 } srfmg_post;
 
 /* Solve parameters (the paper's problem statement and cycle type). */
 typedef struct {
@@ -106,7 +119,7 @@ typedef struct {
     int32_t n_vcycles;         /* FAS V-cycles (Fig. 1, with the SR steps of Fig. 3 on the SR levels)
                                   after the FMG cycle, each from the current fine solution:
                                   0..16 (default 0); plans with an SR level only */
-    int32_t reserved[1];       /* must be zero */
+    int32_t post_leg;          /* srfmg_post (SR levels only; 0 without SR) */
 } srfmg_params;
 
 /* Information about a created plan. */
@@ -177,7 +190,8 @@ srfmg_status srfmg_solve_functionals(srfmg_handle h, const double *f, double *u,
  * from the coarse solution u_{M-1} that the plan keeps after its last solve
  * (srfmg_solve, srfmg_solve_functionals or srfmg_adjoint), by that solve's
  * post-leg: the full update Pi u_{M-1} and the nu2 compatible-relaxation
- * iterations on each segment's extended patch.  The result equals, bit for
+ * iterations on each segment's extended patch (plans with
+ * SRFMG_POST_FAS_RECOMPUTE return SRFMG_EUNSUPPORTED).  The result equals, bit for
  * bit, the same cells of that solve's u.  f: device pointer, the right-hand
  * side of that solve (N doubles per problem).  u_seg: device pointer,
  * seg_count * W doubles per problem (problem k at offset k * seg_count * W),

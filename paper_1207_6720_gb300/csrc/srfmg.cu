@@ -82,6 +82,7 @@ struct srfmg_plan {
     double *ulev[32][2] = {};
     double *glev[32] = {};
     double *seam = nullptr;
+    double *uold = nullptr, *uhat = nullptr, *edge = nullptr;   // post-leg option FAS recompute
     double *Ainv = nullptr;
     double *coef[32] = {};         // variable coefficient: face coefficients of levels M0..M
     fx::u64 *fA[32] = {};          // fixed-point variable coefficient: A per face, levels M0..M
@@ -136,7 +137,13 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
-    if (p->reserved[0]) return "reserved fields must be zero";
+    if (p->post_leg != SRFMG_POST_FULL_UPDATE && p->post_leg != SRFMG_POST_FAS_RECOMPUTE)
+        return "post_leg must be SRFMG_POST_FULL_UPDATE or SRFMG_POST_FAS_RECOMPUTE";
+    if (p->post_leg == SRFMG_POST_FAS_RECOMPUTE &&
+        (p->n_sr_levels != 1 || p->tau_edge != SRFMG_TAU_ASSEMBLED || p->n_vcycles != 0 ||
+         p->buffer_width >= p->segment_width))
+        return "SRFMG_POST_FAS_RECOMPUTE needs n_sr_levels = 1, tau_edge = SRFMG_TAU_ASSEMBLED, n_vcycles = 0 "
+               "and buffer_width < segment_width";
     if (p->n_vcycles < 0 || p->n_vcycles > 16) return "n_vcycles must be in [0, 16]";
     if (p->n_vcycles > 0 && p->n_sr_levels == 0) return "n_vcycles applies to plans with an SR level";
     if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->tau_edge != SRFMG_TAU_SEGMENT)
@@ -393,6 +400,12 @@ void to_fixed(srfmg_plan *h, Op &o) {
         o.fseg.local_tau = o.seg.local_tau;
         o.fseg.cA = h->fA[o.seg.M];
         o.fseg.cBM = h->fBM[o.seg.M];
+        o.fseg.u_old_out = (i64 *)o.seg.u_old_out;
+        o.fseg.edge_out = (i64 *)o.seg.edge_out;
+        o.fseg.uc_corr = (const i64 *)o.seg.uc_corr;
+        o.fseg.uhat = (const i64 *)o.seg.uhat;
+        o.fseg.edge_in = (const i64 *)o.seg.edge_in;
+        o.fseg.nu_pre = o.seg.nu_pre;
         break;
     case OP_TAIL:
         o.ftail.M0 = o.tail.M0; o.ftail.Mc = o.tail.Mc; o.ftail.nu1 = o.tail.nu1; o.ftail.nu2 = o.tail.nu2;
@@ -453,13 +466,16 @@ void build_schedule_ops(srfmg_plan *h) {
     cur[Mc] ^= 1;
 
     // one V-cycle below a level that was just restricted to Mc
-    auto vcycle_below = [&](int top_stored) {
+    // (src: the top level's iterate when it is not in the level's own buffers)
+    auto vcycle_below = [&](int top_stored, const double *src) {
         for (int l = top_stored; l > Mc; --l) {
-            h->ops.push_back(level_op(h, OP_DOWN, l, U(l), nullptr, Unext(l), Unext(l - 1), h->glev[l - 1]));
+            const double *u_src = (l == top_stored && src) ? src : U(l);
+            h->ops.push_back(level_op(h, OP_DOWN, l, u_src, nullptr, Unext(l), Unext(l - 1), h->glev[l - 1]));
             cur[l] ^= 1;
             cur[l - 1] ^= 1;
         }
-        h->ops.push_back(tail_op(h, 1, U(Mc), h->glev[Mc], 0, Unext(Mc), false, false));
+        h->ops.push_back(tail_op(h, 1, (top_stored == Mc && src) ? src : U(Mc), h->glev[Mc], 0, Unext(Mc), false,
+                                 false));
         cur[Mc] ^= 1;
         for (int l = Mc + 1; l <= top_stored; ++l) {
             h->ops.push_back(level_op(h, OP_UP, l, U(l), U(l - 1), Unext(l), nullptr, nullptr));
@@ -474,7 +490,7 @@ void build_schedule_ops(srfmg_plan *h) {
         h->ops.push_back(level_op(h, OP_DOWN_PI, top, U(k), nullptr, Unext(top), Unext(k), h->glev[k]));
         cur[top] ^= 1;
         cur[k] ^= 1;
-        vcycle_below(k);
+        vcycle_below(k, nullptr);
         h->ops.push_back(level_op(h, OP_UP, top, U(top), U(k), Unext(top), nullptr, nullptr));
         cur[top] ^= 1;
     }
@@ -484,15 +500,25 @@ void build_schedule_ops(srfmg_plan *h) {
         // stored V-cycle; the post-legs (full update + compatible relaxation)
         // of the SR levels from the bottom up, the finest writing the caller's u
         // from_u: a further V-cycle on level M from the caller's current u
+        // (FAS recompute: the pre-leg writes the restricted solution to uhat, keeps
+        // the interpolated iterate in uold and its edge cells; the V-cycle starts
+        // from uhat and the post-leg recomputes the pre-smoothed segments)
         auto sr_step = [&](int T, bool from_u) {
+            const bool rcm = (h->p.post_leg == SRFMG_POST_FAS_RECOMPUTE);
             const double *gT = (T == M) ? nullptr : h->glev[T];
-            Op pre = seg_op(h, OP_SR_PRE, T, from_u ? nullptr : U(T - 1), Unext(T - 1), h->glev[T - 1], gT, nullptr,
+            double *uhat_out = rcm ? h->uhat : Unext(T - 1);
+            Op pre = seg_op(h, OP_SR_PRE, T, from_u ? nullptr : U(T - 1), uhat_out, h->glev[T - 1], gT, nullptr,
                             nullptr);
             if (from_u) pre.seg_uin = TAG_U;
+            if (rcm) {
+                pre.seg.u_old_out = h->uold;
+                pre.seg.edge_out = h->edge;
+            }
             h->ops.push_back(pre);
-            cur[T - 1] ^= 1;
+            if (!rcm) cur[T - 1] ^= 1;
             if (h->p.tau_edge == SRFMG_TAU_ASSEMBLED)
-                h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, U(T - 1), h->glev[T - 1], gT, nullptr, nullptr));
+                h->ops.push_back(seg_op(h, OP_SEAM, T, nullptr, rcm ? h->uhat : U(T - 1), h->glev[T - 1], gT, nullptr,
+                                        nullptr));
             for (int L = T - 1; L > R; --L) {
                 h->ops.push_back(seg_op(h, OP_SR_PRE, L, nullptr, Unext(L - 1), h->glev[L - 1], h->glev[L], U(L),
                                         nullptr));
@@ -501,12 +527,19 @@ void build_schedule_ops(srfmg_plan *h) {
                     h->ops.push_back(seg_op(h, OP_SEAM, L, nullptr, U(L - 1), h->glev[L - 1], h->glev[L], nullptr,
                                             nullptr));
             }
-            vcycle_below(R);
+            vcycle_below(R, rcm ? h->uhat : nullptr);
             for (int L = R + 1; L < T; ++L) {
                 h->ops.push_back(seg_op(h, OP_SR_POST, L, U(L - 1), nullptr, nullptr, h->glev[L], nullptr, Unext(L)));
                 cur[L] ^= 1;
             }
-            if (T == M) {
+            if (T == M && rcm) {
+                Op post = seg_op(h, OP_SR_POST, M, h->uold, nullptr, nullptr, nullptr, nullptr, nullptr);
+                post.seg.uc_corr = U(M - 1);
+                post.seg.uhat = h->uhat;
+                post.seg.edge_in = h->edge;
+                post.seg.nu_pre = h->p.nu1;
+                h->ops.push_back(post);
+            } else if (T == M) {
                 h->ops.push_back(seg_op(h, OP_SR_POST, M, U(M - 1), nullptr, nullptr, nullptr, nullptr, nullptr));
             } else {
                 h->ops.push_back(seg_op(h, OP_SR_POST, T, U(T - 1), nullptr, nullptr, h->glev[T], nullptr, Unext(T)));
@@ -520,7 +553,7 @@ void build_schedule_ops(srfmg_plan *h) {
         h->ops.push_back(level_op(h, OP_DOWN_PI, M, U(M - 1), nullptr, h->ulev[M][0], Unext(M - 1),
                                   h->glev[M - 1]));
         cur[M - 1] ^= 1;
-        vcycle_below(M - 1);
+        vcycle_below(M - 1, nullptr);
         Op o = level_op(h, OP_UP, M, h->ulev[M][0], U(M - 1), nullptr, nullptr, nullptr);
         o.lev_out = TAG_U;
         h->ops.push_back(o);
@@ -543,6 +576,10 @@ void build_schedule(srfmg_plan *h) {
             else o.smem += ml * sizeof(double) + 2 * sizeof(double);
         }
         o.grid.y = (unsigned)h->batch;           // one grid row per problem of the batch
+        if (o.kind == OP_SR_POST && o.seg.uc_corr && !h->fixed) {   // FP64 recompute: a second coarse array
+            o.seg.c2_off = (int)(o.smem / sizeof(double));
+            o.smem += (size_t)o.seg.maxc * sizeof(double);
+        }
     }
     if (!h->fixed) return;
     for (Op &o : h->ops) to_fixed(h, o);
@@ -846,6 +883,11 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         if (st == SRFMG_OK) st = alloc_dev(h, &h->glev[l], B << l);
     }
     if (st == SRFMG_OK && h->nRS >= 1) st = alloc_dev(h, &h->seam, B * (h->n / h->W) * 6);
+    if (st == SRFMG_OK && p->post_leg == SRFMG_POST_FAS_RECOMPUTE) {
+        st = alloc_dev(h, &h->uold, B * (h->n / 2));
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->uhat, B * (h->n / 2));
+        if (st == SRFMG_OK) st = alloc_dev(h, &h->edge, B * (h->n / h->W) * 2 * (size_t)(h->b + 1));
+    }
     if (st == SRFMG_OK && h->nRS >= 1) st = alloc_dev(h, &h->fpart, B * (h->n / h->W) * kNumFunc);
     if (st == SRFMG_OK && h->fixed) {
         double *sc = nullptr;
@@ -1003,6 +1045,8 @@ srfmg_status srfmg_reconstruct(srfmg_handle h, const double *f, int32_t seg_begi
                                double *u_seg, void *stream) {
     if (!h) return fail(nullptr, SRFMG_EINVAL, "handle is NULL");
     if (h->nRS < 1) return fail(h, SRFMG_EUNSUPPORTED, "reconstruction expands SR segments: the plan needs an SR level");
+    if (h->p.post_leg == SRFMG_POST_FAS_RECOMPUTE)
+        return fail(h, SRFMG_EUNSUPPORTED, "reconstruction rebuilds segments by the full update (SRFMG_POST_FULL_UPDATE)");
     if (!h->solved) return fail(h, SRFMG_EINVAL, "no solve has been enqueued on this plan");
     const int nseg = (int)(h->n / h->W);
     if (seg_begin < 0 || seg_count < 1 || seg_begin > nseg - seg_count)

@@ -811,6 +811,11 @@ struct SegArgs {
     const double *u_ref;       // post-leg: reference for the functionals (NULL: none)
     double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
     const u64 *cA, *cBM;       // variable coefficient: the level's A (faces) and multipliers (cells)
+    // post-leg option FAS recompute, as in the FP64 SegArgs (the second coarse
+    // array of the post-leg is gr, which the post-leg does not otherwise use)
+    i64 *u_old_out, *edge_out;
+    const i64 *uc_corr, *uhat, *edge_in;
+    int nu_pre;
 };
 
 // Shared memory as LevelSmem: u, gs, c, X, gr (2 maxlen + 2 maxc + maxch words),
@@ -910,11 +915,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) sr_pre_kernel(SegA
     SegSmem m = seg_smem(smi, a, s);
     const int J0 = s >> 1, J1 = (s + a.W) >> 1;
     seg_load<VC>(m, a, m.gr, J0, J1);
+    if (a.u_old_out) {        // the interpolated iterate on the segment's coarse cells (post-leg recompute)
+        i64 *uo = batch_at(a.u_old_out, nc);
+        for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) uo[J] = m.c[J - m.C0];
+    }
     const int tsh = 2 * a.M - 4;
     const int Kb = VC ? (a.sc + blockIdx.y)->Kb : 0;
     for (int k = 0; k < a.nu; ++k) {
         if (VC) lex_sweep_vc<kChunk>(m.u, m.gs, m.A, m.BM, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y, Kb);
         else lex_sweep<kChunk>(m.u, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+    }
+    if (a.edge_out) {         // the pre-smoothed interior cells the neighbours' patches read
+        const int ne = a.b + 1;
+        i64 *eo = batch_at(a.edge_out, (long long)(n / a.W) * 2 * ne) + (size_t)blockIdx.x * 2 * ne;
+        for (int k = threadIdx.x; k < ne; k += blockDim.x) {
+            eo[k] = m.u[s + k - m.lo];
+            eo[ne + k] = m.u[s + a.W - ne + k - m.lo];
+        }
     }
     const i64 *u = m.u;
     i64 *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
@@ -1078,11 +1095,42 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) sr_post_kernel(Seg
     const int s = (a.seg0 + (int)blockIdx.x) * a.W;
     const int n = a.n;
     SegSmem m = seg_smem(smi, a, s);
-    const bool first_done = seg_load<VC>(m, a, nullptr, 0, 0, true);
+    const bool rcm = a.uc_corr != nullptr;          // post-leg option FAS recompute
+    const bool first_done = seg_load<VC>(m, a, nullptr, 0, 0, !rcm);
     const int Kb = VC ? (a.sc + blockIdx.y)->Kb : 0;
     i64 *p = m.u;
+    if (rcm) {
+        // the pre-smoothed patch as the pre-leg formed it ...
+        for (int k = 0; k < a.nu_pre; ++k) {
+            if (VC) lex_sweep_vc<kChunk>(p, m.gs, m.A, m.BM, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y, Kb);
+            else lex_sweep<kChunk>(p, m.gs, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X);
+        }
+        // ... with the assembled values in its buffer and frozen cells ...
+        const int ne = a.b + 1, seg = a.seg0 + (int)blockIdx.x, nseg = n / a.W;
+        const i64 *ei = batch_at(a.edge_in, (long long)nseg * 2 * ne);
+        for (int i = m.lo + (int)threadIdx.x; i < s; i += (int)blockDim.x)
+            p[i - m.lo] = ei[(size_t)(seg - 1) * 2 * ne + ne + (i - (s - ne))];
+        for (int i = s + a.W + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
+            p[i - m.lo] = ei[(size_t)(seg + 1) * 2 * ne + (i - (s + a.W))];
+        // ... corrected by Eq. 4: U += P (U_{M-1} - R Ubar), rounded to units ...
+        const int nc = n >> 1;
+        stage_coarse_async(m.c, batch_at(a.uc_corr, nc), m.C0, m.C1, nc);
+        stage_coarse_async(m.gr, batch_at(a.uhat, nc), m.C0, m.C1, nc);
+        stage_wait();
+        __syncthreads();
+        fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
+        fill_coarse_ghosts(m.gr, m.C0, m.C1, nc);
+        __syncthreads();
+        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) m.c[j - m.C0] -= m.gr[j - m.C0];
+        __syncthreads();
+        for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
+            const int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+            p[i - m.lo] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
+        }
+        __syncthreads();
+    }
     for (int k = 0; k < a.nu; ++k) {
-        if (k > 0 || !first_done) {
+        if (!rcm && (k > 0 || !first_done)) {   // Kaczmarz (Fig. 5), not in the FAS recompute
             for (int J = (m.e0 >> 1) + (int)threadIdx.x; J < (m.e1 >> 1); J += (int)blockDim.x) {
                 int i0 = 2 * J - m.lo;
                 i64 r = m.c[J - m.C0] - ((p[i0] + p[i0 + 1]) >> 1);

@@ -1110,6 +1110,17 @@ struct SegArgs {
     double *fpart;             // post-leg: kNumFunc partials per segment (NULL: no functionals)
     double lam;                // Bratu: lam (0 otherwise)
     const double *coef;        // variable coefficient: face coefficients of level M (2^M + 1)
+    // post-leg option FAS recompute (the correction of Eq. 4 on the recomputed
+    // pre-smoothed segment): the pre-leg keeps the level M-1 iterate it
+    // interpolates (its segment's coarse cells) and the first and last b + 1
+    // pre-smoothed interior cells of its segment; the post-leg (uc_corr set)
+    // interpolates uc_src = that iterate, smooths nu_pre times as the pre-leg did,
+    // takes its buffer and frozen cells from the neighbours' kept cells, adds
+    // P (uc_corr - uhat) and smooths nu times without Kaczmarz
+    double *u_old_out, *edge_out;
+    const double *uc_corr, *uhat, *edge_in;
+    int nu_pre;
+    int c2_off;                // FP64 post-leg recompute: offset (doubles) of a second coarse array
 };
 
 // (the host reserves 2 maxlen + 2 maxc + maxch doubles; this path uses the
@@ -1182,11 +1193,23 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
     const int n = a.n, nc = n >> 1;
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
+    const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    if (a.u_old_out) {        // the interpolated iterate on the segment's coarse cells (post-leg recompute)
+        double *uo = batch_at(a.u_old_out, nc);
+        for (int J = J0 + (int)threadIdx.x; J < J1; J += (int)blockDim.x) uo[J] = m.c[J - m.C0];
+    }
     const double cl = scale2(a.lam, -2 * a.M);
     for (int k = 0; k < a.nu; ++k)
         sweep_op<OP>(m.u, m.g, cl, m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
     const double *u = m.u;
-    const int J0 = s >> 1, J1 = (s + a.W) >> 1;
+    if (a.edge_out) {         // the pre-smoothed interior cells the neighbours' patches read
+        const int ne = a.b + 1;
+        double *eo = batch_at(a.edge_out, (long long)(n / a.W) * 2 * ne) + (size_t)blockIdx.x * 2 * ne;
+        for (int k = threadIdx.x; k < ne; k += blockDim.x) {
+            eo[k] = u[s + k - m.lo];
+            eo[ne + k] = u[s + a.W - ne + k - m.lo];
+        }
+    }
     double *uc_out = batch_at(a.uc_out, nc), *gc_out = batch_at(a.gc_out, nc);
     for (int J = J0 + threadIdx.x; J < J1; J += blockDim.x) {
         int i0 = 2 * J - m.lo;
@@ -1271,16 +1294,50 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_post_kernel(SegArgs a) {
     SegSmem m = seg_smem(sm, a, s);
     seg_load(m, a);
     double *p = m.u;
-    for (int k = 0; k < a.nu; ++k) {
-        // Kaczmarz (Fig. 5): r = u^H_J - (R u)_J added to both children
-        for (int J = (m.e0 >> 1) + threadIdx.x; J < (m.e1 >> 1); J += blockDim.x) {
-            int i0 = 2 * J - m.lo;
-            double r = m.c[J - m.C0] - scale2(p[i0] + p[i0 + 1], -1);
-            p[i0] += r;
-            p[i0 + 1] += r;
+    const double cl = scale2(a.lam, -2 * a.M);
+    if (a.uc_corr) {
+        // FAS recompute: the pre-smoothed patch as the pre-leg formed it ...
+        for (int k = 0; k < a.nu_pre; ++k)
+            sweep_op<OP>(p, m.g, cl, m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+        // ... with the assembled values in its buffer and frozen cells ...
+        const int ne = a.b + 1, seg = a.seg0 + (int)blockIdx.x, nseg = n / a.W;
+        const double *ei = batch_at(a.edge_in, (long long)nseg * 2 * ne);
+        for (int i = m.lo + (int)threadIdx.x; i < s; i += (int)blockDim.x)
+            p[i - m.lo] = ei[(size_t)(seg - 1) * 2 * ne + ne + (i - (s - ne))];
+        for (int i = s + a.W + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x)
+            p[i - m.lo] = ei[(size_t)(seg + 1) * 2 * ne + (i - (s + a.W))];
+        // ... corrected by Eq. 4 with P (u_{M-1} - R ubar) ...
+        const int nc = n >> 1;
+        double *c2 = sm + a.c2_off;
+        stage_coarse_async(m.c, batch_at(a.uc_corr, nc), m.C0, m.C1, nc);
+        stage_coarse_async(c2, batch_at(a.uhat, nc), m.C0, m.C1, nc);
+        stage_wait();
+        __syncthreads();
+        fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
+        fill_coarse_ghosts(c2, m.C0, m.C1, nc);
+        __syncthreads();
+        for (int j = m.C0 + (int)threadIdx.x; j < m.C1; j += (int)blockDim.x) m.c[j - m.C0] -= c2[j - m.C0];
+        __syncthreads();
+        for (int i = m.lo + (int)threadIdx.x; i < m.hi; i += (int)blockDim.x) {
+            const int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
+            p[i - m.lo] += scale2(fma(3.0, m.c[J - m.C0], m.c[nb - m.C0]), -2);
         }
         __syncthreads();
-        sweep_op<OP>(p, m.g, scale2(a.lam, -2 * a.M), m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+        // ... and smoothed without Kaczmarz
+        for (int k = 0; k < a.nu; ++k)
+            sweep_op<OP>(p, m.g, cl, m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+    } else {
+        for (int k = 0; k < a.nu; ++k) {
+            // Kaczmarz (Fig. 5): r = u^H_J - (R u)_J added to both children
+            for (int J = (m.e0 >> 1) + threadIdx.x; J < (m.e1 >> 1); J += blockDim.x) {
+                int i0 = 2 * J - m.lo;
+                double r = m.c[J - m.C0] - scale2(p[i0] + p[i0 + 1], -1);
+                p[i0] += r;
+                p[i0 + 1] += r;
+            }
+            __syncthreads();
+            sweep_op<OP>(p, m.g, cl, m.a, m.lo, m.lo, m.e0, m.e1, n, (k & 1) == 0, m.X, m.Y);
+        }
     }
     const long long s0 = (long long)a.seg0 * a.W;     // first cell of the output
     double *u_out = a.u_out ? batch_at(a.u_out, (long long)gridDim.x * a.W) : nullptr;

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "SRFMG_OK", 1: "SRFMG_EINVAL", 2: "SRFMG_ENOMEM", 3: "SRFMG_E
 FP64, MIXED = 0, 1
 LAPLACE, VARCOEF, BRATU = 0, 1, 2
 TAU_ASSEMBLED, TAU_SEGMENT = 0, 1
+POST_FULL_UPDATE, POST_FAS_RECOMPUTE = 0, 1
 NUM_FUNCTIONALS = 5          # functionals per problem of srfmg_solve_functionals
 
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
@@ -34,7 +35,7 @@ class Params(ctypes.Structure):
                                                       ("batch", ctypes.c_int32),
                                                       ("tau_edge", ctypes.c_int32),
                                                       ("n_vcycles", ctypes.c_int32),
-                                                      ("reserved", ctypes.c_int32 * 1)]
+                                                      ("post_leg", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

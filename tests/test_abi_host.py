@@ -72,12 +72,17 @@ def test_two_sr_levels_are_checked_before_cuda(overrides):
     assert h.value is None
 
 
-def test_create_rejects_reserved_and_null():
+def test_create_rejects_bad_post_leg_and_null():
     lib = srfmg.load()
-    p = srfmg.default_params(12)
-    p.reserved[0] = 1
     h = ctypes.c_void_p()
-    assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL
+    # an unknown post-leg option, and FAS recompute outside its preconditions
+    for kw in (dict(post_leg=7), dict(post_leg=1, n_sr_levels=2), dict(post_leg=1, n_sr_levels=0),
+               dict(post_leg=1, tau_edge=1), dict(post_leg=1, n_vcycles=1),
+               dict(post_leg=1, segment_width=16, buffer_width=16)):
+        p = srfmg.default_params(12)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL, kw
     assert lib.srfmg_create(None, 0, ctypes.byref(h)) == srfmg.EINVAL
     p = srfmg.default_params(12)
     assert lib.srfmg_create(ctypes.byref(p), 0, None) == srfmg.EINVAL
