@@ -667,9 +667,20 @@ __device__ void coarsest_thomas_vc(double *u, const double *g, int n, const doub
 
 // The nonlinear part of the scaled tau rhs (Eqs. 1-2 with N = L + lam e^u):
 // h_{l-1}^2 lam e^{uhat_J} - h_{l-1}^2 R(lam e^u)_J = cl (4 e^{uhat} - 2 (e^{u_2J} + e^{u_2J+1}))
-// with cl = lam h_l^2 of the fine level and uhat = (u_2J + u_2J+1) / 2.
+// with cl = lam h_l^2 of the fine level and uhat = (u_2J + u_2J+1) / 2.  With
+// u_2J = uhat + d, u_2J+1 = uhat - d this is -8 cl e^{uhat} sinh^2(d/2): one
+// exponential instead of three, and no cancellation between terms of size
+// 4 cl e^{uhat}.  For |d/2| < 2^-6 sinh(x)/x is its Taylor series to x^6 (the
+// first dropped term is below 2^-66 of the value); otherwise the three
+// exponentials.
 __device__ __forceinline__ double tau_nl(double cl, double u0, double u1) {
     const double uh = scale2(u0 + u1, -1);
+    const double x = scale2(u0 - u1, -2);
+    if (fabs(x) < 0.015625) {
+        const double x2 = x * x;
+        const double s = fma(x2, fma(x2, fma(x2, 1.0 / 5040.0, 1.0 / 120.0), 1.0 / 6.0), 1.0);
+        return -8.0 * cl * exp(uh) * (x2 * (s * s));
+    }
     return cl * (4.0 * exp(uh) - 2.0 * (exp(u0) + exp(u1)));
 }
 
