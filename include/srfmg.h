@@ -120,6 +120,14 @@ typedef struct {
                                   after the FMG cycle, each from the current fine solution:
                                   0..16 (default 0); plans with an SR level only */
     int32_t post_leg;          /* srfmg_post (SR levels only; 0 without SR) */
+    /* CTA shape (no effect on the result, which is the same bits for every choice:
+       the stored-level tiles compute their halo cells exactly like the tile that
+       owns them, and the coarse tail runs the same sweeps on whole levels): */
+    int32_t tail_level;        /* finest level of the one-block coarse tail: 0 (default:
+                                  min(12, M - n_sr_levels)) or in [log2_n_coarsest, 12] */
+    int32_t tile_cells;        /* cells per block of the stored-level passes on levels up
+                                  to 2^18 (levels above take 2048): 0 (default 256) or a
+                                  power of two in [64, 2048] */
 } srfmg_params;
 
 /* Information about a created plan. */
@@ -364,6 +372,21 @@ srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, 
 srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32_t *segment_width,
                                       int32_t *buffer_width);
 
+/* Autotuner for the CTA shape of a plan (no counterpart in the paper; the
+ * launch shapes leave the result unchanged, bit for bit): for the solve
+ * described by *base (any SR layout; base's tail_level and tile_cells are
+ * ignored) it times every candidate (tail_level, tile_cells) with tail_level in
+ * {9, 10, 11, 12} (those in [log2_n_coarsest, min(12, M - n_sr_levels)], each
+ * distinct coarse tail once) and tile_cells in {128, 256, 512} (candidate k in
+ * that order, tail level major; srfmg_autotune_shape_candidate names it), the
+ * same way as srfmg_autotune, and writes *base with the fastest pair to *best.
+ * ms (optional, capacity entries) and *ncand (optional) as in srfmg_autotune.
+ * Synchronous.  Errors as srfmg_autotune. */
+srfmg_status srfmg_autotune_shape(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
+                                  float *ms, int32_t capacity, int32_t *ncand);
+srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, int32_t *tail_level,
+                                            int32_t *tile_cells);
+
 /* Independent problems of uneven sizes solved together (many problems with
  * N = 2^m cells for varying m; the paper solves one problem, this is the
  * data-parallel use of its solver on independent ones).  A group holds one
@@ -391,7 +414,8 @@ srfmg_status srfmg_group_offsets(int32_t nprob, const int32_t *log2_n, int64_t *
  * base->batch are ignored.  log2_n: host array of nprob sizes.
  * Segment layout of each size (plans with SR levels): with tune = 0,
  * W = min(base->segment_width, max(16, N/4)) and b = min(base->buffer_width,
- * W); with tune > 0, srfmg_autotune picks (W, b) for each size (`tune` timed
+ * W); with tune > 0, srfmg_autotune picks (W, b) for each size and then
+ * srfmg_autotune_shape its CTA shape (tail_level, tile_cells) (`tune` timed
  * solves per candidate, on a sample of min(count, max(1, 2^24 / N)) problems
  * of that size; needs n_sr_levels = 1).  Every size must make a valid plan
  * (srfmg_create's checks: N > 2^log2_n_coarsest, ...).  On success *out is a

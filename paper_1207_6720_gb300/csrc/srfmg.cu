@@ -137,6 +137,10 @@ bool pow2(long long x) { return x > 0 && (x & (x - 1)) == 0; }
 
 std::string check_params(const srfmg_params *p) {
     if (!p) return "params is NULL";
+    if (p->tail_level != 0 && (p->tail_level < p->log2_n_coarsest || p->tail_level > 12))
+        return "tail_level must be 0 or in [log2_n_coarsest, 12]";
+    if (p->tile_cells != 0 && (!pow2(p->tile_cells) || p->tile_cells < 64 || p->tile_cells > 2048))
+        return "tile_cells must be 0 or a power of two in [64, 2048]";
     if (p->post_leg != SRFMG_POST_FULL_UPDATE && p->post_leg != SRFMG_POST_FAS_RECOMPUTE)
         return "post_leg must be SRFMG_POST_FULL_UPDATE or SRFMG_POST_FAS_RECOMPUTE";
     if (p->post_leg == SRFMG_POST_FAS_RECOMPUTE &&
@@ -253,7 +257,7 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     // levels up to 2^18 are latency-bound (a few microseconds per pass whatever
     // their size): smaller tiles spread them over more SMs (measured: 1.8% off the
     // N = 2^24 solve; 128-cell tiles, or 256 up to level 20, were slower)
-    const int Tmax = (l <= 18) ? 256 : kTileMax;
+    const int Tmax = (l <= 18) ? (h->p.tile_cells ? h->p.tile_cells : 256) : kTileMax;
     const int T = n < Tmax ? n : Tmax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
     // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9); 12 * 9 = 108
@@ -863,7 +867,8 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     h->n = (size_t)1 << h->M;
     h->batch = p->batch > 0 ? p->batch : 1;
     int top_stored = h->M - h->nRS;
-    h->Mc = top_stored < kMaxTailLevel ? top_stored : kMaxTailLevel;
+    const int tail_max = p->tail_level ? p->tail_level : kMaxTailLevel;
+    h->Mc = top_stored < tail_max ? top_stored : tail_max;
     if (h->Mc < h->M0) h->Mc = h->M0;
     // the 64-bit fixed-point kernels serve the constant-coefficient operator; the
     // mixed precision of the other two is their FP64 kernels with FP32 corrections
@@ -1284,19 +1289,17 @@ const char *srfmg_last_error(srfmg_handle h) {
     return h ? h->err.c_str() : g_create_error.c_str();
 }
 
-srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
-                            float *ms, int32_t capacity, int32_t *ncand) {
-    if (!base || !best || reps < 1 || (ms && capacity < 0)) return fail(nullptr, SRFMG_EINVAL, "bad arguments to srfmg_autotune");
-    std::string msg = check_params(base);
-    if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
-    if (base->n_sr_levels != 1) return fail(nullptr, SRFMG_EINVAL, "srfmg_autotune tunes the SR segment layout (n_sr_levels = 1)");
+}  // extern "C"
+
+namespace {
+
+// Time a plan per candidate parameter set (two warm-up solves of a zero right-
+// hand side, then reps timed ones, CUDA events on a stream of its own) and
+// return the fastest in *best; ms[k] receives candidate k's milliseconds per solve.
+srfmg_status time_candidates(const std::vector<srfmg_params> &cand, int device, int32_t reps, srfmg_params *best,
+                             float *ms, int32_t capacity) {
+    const srfmg_params *base = &cand[0];
     const long long N = 1LL << base->log2_n;
-    std::vector<std::pair<int, int>> cand;
-    for (int W = 256; W <= 4096; W *= 2)
-        for (int b : {4, 8})
-            if (W <= N / 2 && b <= W) cand.push_back({W, b});
-    if (cand.empty()) cand.push_back({(int)std::max<long long>(16, N), 4});
-    if (ncand) *ncand = (int32_t)cand.size();
     const size_t B = (size_t)(base->batch > 0 ? base->batch : 1);
     double *f = nullptr, *u = nullptr;
     cudaError_t e = cudaSetDevice(device);
@@ -1311,9 +1314,7 @@ srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, 
     srfmg_status st = (e == cudaSuccess) ? SRFMG_OK : fail(nullptr, SRFMG_ECUDA, std::string("autotune set-up: ") + cudaGetErrorString(e));
     float best_ms = 0.f;
     for (size_t k = 0; k < cand.size() && st == SRFMG_OK; ++k) {
-        srfmg_params p = *base;
-        p.segment_width = cand[k].first;
-        p.buffer_width = cand[k].second;
+        const srfmg_params p = cand[k];
         srfmg_handle h = nullptr;
         st = srfmg_create(&p, device, &h);
         for (int w = 0; w < 2 && st == SRFMG_OK; ++w) st = srfmg_solve(h, f, u, s);
@@ -1337,6 +1338,79 @@ srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, 
     cudaFree(f);
     cudaFree(u);
     return st;
+}
+
+// The shape candidates of srfmg_autotune_shape: distinct coarse tails, then tiles.
+std::vector<std::pair<int, int>> shape_candidates(const srfmg_params *base) {
+    std::vector<std::pair<int, int>> cand;
+    const int top = base->log2_n - base->n_sr_levels;
+    int prev_mc = -1;
+    for (int t = 9; t <= 12; ++t) {
+        if (t < base->log2_n_coarsest) continue;
+        const int mc = std::max(base->log2_n_coarsest, std::min(t, top));
+        if (mc == prev_mc) continue;
+        prev_mc = mc;
+        for (int tc : {128, 256, 512}) cand.push_back({t, tc});
+    }
+    if (cand.empty()) cand.push_back({12, 256});
+    return cand;
+}
+
+}  // namespace
+
+extern "C" {
+
+srfmg_status srfmg_autotune(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
+                            float *ms, int32_t capacity, int32_t *ncand) {
+    if (!base || !best || reps < 1 || (ms && capacity < 0)) return fail(nullptr, SRFMG_EINVAL, "bad arguments to srfmg_autotune");
+    std::string msg = check_params(base);
+    if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
+    if (base->n_sr_levels != 1) return fail(nullptr, SRFMG_EINVAL, "srfmg_autotune tunes the SR segment layout (n_sr_levels = 1)");
+    const long long N = 1LL << base->log2_n;
+    std::vector<srfmg_params> cand;
+    for (int W = 256; W <= 4096; W *= 2)
+        for (int b : {4, 8})
+            if (W <= N / 2 && b <= W) {
+                srfmg_params p = *base;
+                p.segment_width = W;
+                p.buffer_width = b;
+                cand.push_back(p);
+            }
+    if (cand.empty()) {
+        srfmg_params p = *base;
+        p.segment_width = (int)std::max<long long>(16, N);
+        p.buffer_width = 4;
+        cand.push_back(p);
+    }
+    if (ncand) *ncand = (int32_t)cand.size();
+    return time_candidates(cand, device, reps, best, ms, capacity);
+}
+
+srfmg_status srfmg_autotune_shape(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
+                                  float *ms, int32_t capacity, int32_t *ncand) {
+    if (!base || !best || reps < 1 || (ms && capacity < 0))
+        return fail(nullptr, SRFMG_EINVAL, "bad arguments to srfmg_autotune_shape");
+    std::string msg = check_params(base);
+    if (!msg.empty()) return fail(nullptr, SRFMG_EINVAL, msg);
+    std::vector<srfmg_params> cand;
+    for (const auto &c : shape_candidates(base)) {
+        srfmg_params p = *base;
+        p.tail_level = c.first;
+        p.tile_cells = c.second;
+        cand.push_back(p);
+    }
+    if (ncand) *ncand = (int32_t)cand.size();
+    return time_candidates(cand, device, reps, best, ms, capacity);
+}
+
+srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, int32_t *tail_level,
+                                            int32_t *tile_cells) {
+    if (!base || !tail_level || !tile_cells || k < 0) return fail(nullptr, SRFMG_EINVAL, "bad arguments");
+    const auto cand = shape_candidates(base);
+    if (k >= (int32_t)cand.size()) return fail(nullptr, SRFMG_EINVAL, "candidate index out of range");
+    *tail_level = cand[k].first;
+    *tile_cells = cand[k].second;
+    return SRFMG_OK;
 }
 
 srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32_t *segment_width,
@@ -1631,6 +1705,13 @@ srfmg_status srfmg_group_create(const srfmg_params *base, int32_t nprob, const i
             if (st != SRFMG_OK) { st = gfail(g, st, "autotune of size 2^" + std::to_string(pm[c]) + ": " + g_create_error); break; }
             p.segment_width = best.segment_width;
             p.buffer_width = best.buffer_width;
+            // then its CTA shape (coarse tail extent, tile cells) with that layout
+            probe.segment_width = p.segment_width;
+            probe.buffer_width = p.buffer_width;
+            st = srfmg_autotune_shape(&probe, device, tune, &best, nullptr, 0, nullptr);
+            if (st != SRFMG_OK) { st = gfail(g, st, "shape autotune of size 2^" + std::to_string(pm[c]) + ": " + g_create_error); break; }
+            p.tail_level = best.tail_level;
+            p.tile_cells = best.tile_cells;
         }
         srfmg_handle h = nullptr;
         st = srfmg_create(&p, device, &h);

@@ -22,6 +22,7 @@ NUM_FUNCTIONALS = 5          # functionals per problem of srfmg_solve_functional
 EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
            "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_launch_name",
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
+           "srfmg_autotune_shape", "srfmg_autotune_shape_candidate",
            "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
            "srfmg_destroy", "srfmg_last_error", "srfmg_version", "srfmg_alu_peaks",
            "srfmg_solve_host_async", "srfmg_solve_host_join", "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
@@ -35,7 +36,9 @@ class Params(ctypes.Structure):
                                                       ("batch", ctypes.c_int32),
                                                       ("tau_edge", ctypes.c_int32),
                                                       ("n_vcycles", ctypes.c_int32),
-                                                      ("post_leg", ctypes.c_int32)]
+                                                      ("post_leg", ctypes.c_int32),
+                                                      ("tail_level", ctypes.c_int32),
+                                                      ("tile_cells", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -93,6 +96,8 @@ def load(build_if_missing=True):
                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_autotune_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    lib.srfmg_autotune_shape.argtypes = lib.srfmg_autotune.argtypes
+    lib.srfmg_autotune_shape_candidate.argtypes = lib.srfmg_autotune_candidate.argtypes
     lib.srfmg_set_coefficient.argtypes = [H, vp, vp]
     lib.srfmg_coef_gradient.argtypes = [H, vp, vp, vp, vp]
     lib.srfmg_solve_functionals.argtypes = [H, vp, vp, vp, vp, vp]
@@ -114,7 +119,8 @@ def load(build_if_missing=True):
     lib.srfmg_alu_peaks.argtypes = [ctypes.c_int, dp]
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
-                 "srfmg_autotune_candidate", "srfmg_set_coefficient", "srfmg_coef_gradient",
+                 "srfmg_autotune_candidate", "srfmg_autotune_shape", "srfmg_autotune_shape_candidate",
+                 "srfmg_set_coefficient", "srfmg_coef_gradient",
                  "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check", "srfmg_solve_host_async",
                  "srfmg_solve_host_join", "srfmg_group_offsets",
                  "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host", "srfmg_group_query",
@@ -529,6 +535,29 @@ def autotune(log2_n, device=0, reps=5, **overrides):
         W, b = ctypes.c_int32(), ctypes.c_int32()
         lib.srfmg_autotune_candidate(ctypes.byref(base), k, ctypes.byref(W), ctypes.byref(b))
         table.append((W.value, b.value, float(ms[k])))
+    return best, table
+
+
+def autotune_shape(params, device=0, reps=5):
+    """Time the CTA shapes (coarse tail extent, cells per tile of the stored levels
+    up to 2^18) of the plan `params` and return (best Params,
+    [(tail_level, tile_cells, ms per solve), ...]); the shape does not change the
+    result."""
+    lib = load()
+    base = Params()
+    ctypes.memmove(ctypes.byref(base), ctypes.byref(params), ctypes.sizeof(Params))
+    best = Params()
+    cap = 16
+    ms = (ctypes.c_float * cap)()
+    n = ctypes.c_int32()
+    st = lib.srfmg_autotune_shape(ctypes.byref(base), device, reps, ctypes.byref(best), ms, cap, ctypes.byref(n))
+    if st != OK:
+        raise SrfmgError(st, lib.srfmg_last_error(None).decode())
+    table = []
+    for k in range(min(n.value, cap)):
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        lib.srfmg_autotune_shape_candidate(ctypes.byref(base), k, ctypes.byref(t), ctypes.byref(c))
+        table.append((t.value, c.value, float(ms[k])))
     return best, table
 
 

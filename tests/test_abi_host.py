@@ -44,6 +44,7 @@ def test_default_params():
     ("n_sr_levels", 3), ("n_sr_levels", -1), ("segment_width", 24), ("segment_width", 8),
     ("segment_width", 8192), ("buffer_width", 3), ("buffer_width", 0), ("buffer_width", 66),
     ("nu1", 0), ("nu2", 5), ("op", 3), ("smoother", 1), ("precision", 7),
+    ("tail_level", 1), ("tail_level", 13), ("tile_cells", 100), ("tile_cells", 32), ("tile_cells", 4096),
 ])
 def test_create_rejects_bad_params_before_cuda(field, value):
     lib = srfmg.load()
@@ -120,3 +121,22 @@ def test_no_cpu_fallback_without_gpu():
 def test_alu_peaks_rejects_null_on_the_host():
     lib = srfmg.load()
     assert lib.srfmg_alu_peaks(0, None) == srfmg.EINVAL
+
+
+def test_shape_candidates_on_the_host():
+    # distinct coarse tails (9..12 clipped to the levels below the SR level) x tiles
+    lib = srfmg.load()
+
+    def cands(M, **kw):
+        p = srfmg.default_params(M, **kw)
+        out = []
+        for k in range(64):
+            t, c = ctypes.c_int32(), ctypes.c_int32()
+            if lib.srfmg_autotune_shape_candidate(ctypes.byref(p), k, ctypes.byref(t), ctypes.byref(c)) != srfmg.OK:
+                break
+            out.append((t.value, c.value))
+        return out
+
+    assert cands(24) == [(t, c) for t in (9, 10, 11, 12) for c in (128, 256, 512)]
+    assert cands(11) == [(9, 128), (9, 256), (9, 512), (10, 128), (10, 256), (10, 512)]
+    assert cands(8) == [(9, 128), (9, 256), (9, 512)]      # one tail: the whole problem
