@@ -453,6 +453,20 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def tuned_solver(srfmg, M, dev, reps=3, coef=None, **kw):
+    """A plan with its CTA shape (coarse tail extent, cells per tile of the stored
+    levels of at most 2^18 cells) picked by srfmg_autotune_shape before any timing; the
+    shape changes no bit of the result.  coef: log a for the variable
+    coefficient (the tuning solves use a = 1)."""
+    best, table = srfmg.autotune_shape(srfmg.default_params(M, **kw), device=dev, reps=reps)
+    s = srfmg.Solver(M, device=dev, params=best)
+    if coef is not None:
+        s.set_coefficient(coef)
+    shape = {"tail_level": best.tail_level, "tile_cells": best.tile_cells,
+             "candidates_ms": {f"T{t}_C{c}": round(ms, 4) for t, c, ms in table}}
+    return s, shape
+
+
 def time_solves(solver, fd, ud, steps, warmup, dist, stream):
     import torch
     for _ in range(warmup):
@@ -487,7 +501,7 @@ def run_gpu(a):
     ud = torch.empty_like(fd)
 
     prec = srfmg.MIXED if a.precision == "mixed" else srfmg.FP64
-    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, precision=prec)
+    solver, shape = tuned_solver(srfmg, M, dev, segment_width=W, buffer_width=b, precision=prec)
     info = solver.info()
 
     sampler = ClockSampler(dev)
@@ -507,7 +521,7 @@ def run_gpu(a):
         return
 
     # plain FP64 stored-grid FMG-FAS (every level stored, no SR) on the same GPU
-    plain = srfmg.Solver(M, device=dev, n_sr_levels=0)
+    plain, _ = tuned_solver(srfmg, M, dev, n_sr_levels=0)
     ms_plain = dist.max(time_solves(plain, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
     u_plain = ud.cpu().numpy()
     plain_info = plain.info()
@@ -516,7 +530,7 @@ def run_gpu(a):
     # adds or costs on this GPU, apart from the arithmetic
     plain_fixed = None
     if prec != srfmg.FP64:
-        pfx = srfmg.Solver(M, device=dev, n_sr_levels=0, precision=prec)
+        pfx, _ = tuned_solver(srfmg, M, dev, n_sr_levels=0, precision=prec)
         ms_pfx = dist.max(time_solves(pfx, fd, ud, max(10, a.steps // 4), a.warmup, dist, stream))
         u_pfx = ud.cpu().numpy()
         plain_fixed = {"value": dist.world * N / (ms_pfx * 1e-3), "ms_per_step": ms_pfx,
@@ -669,7 +683,7 @@ def run_gpu(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64" if prec != srfmg.FP64 else "f64", "data": "synthetic",
-        "config": workload_config(a),
+        "config": dict(workload_config(a), cta_shape=shape),
         "e2e": e2e,
         "gpu_launches": info.kernels_per_solve * a.steps,
         "plain_fp64": {"value": dist.world * N / (ms_plain * 1e-3), "ms_per_step": ms_plain,
@@ -715,7 +729,7 @@ def run_gpu(a):
         a_r = argparse.Namespace(**vars(a))
         a_r.workload, a_r.log2n, a_r.precision = "bratu", 26, "mixed"
         r = measure_single(a_r, dev, dist, stream, "bratu", "mixed", max(5, a.steps // 2), min(a.warmup, 3))
-        r["config"] = workload_config(a_r)
+        r["config"] = dict(workload_config(a_r), cta_shape=r.pop("cta_shape"))
         r["metric"] = METRIC_BRATU
         line["bratu"] = r
         if dist.rank == 0 and dist.world == 1 and not a.no_cpu_baseline:
@@ -749,11 +763,9 @@ def measure_single(a, dev, dist, stream, kind, precision, steps, warmup, full=Tr
         flops_table = FLOPS_PER_CELL_BRATU_MX if mixed else FLOPS_PER_CELL_BRATU
     fd = torch.from_numpy(f).to(dev)
     ud = torch.empty_like(fd)
-    solver = srfmg.Solver(M, device=dev, segment_width=W, buffer_width=b, precision=prec, **kw)
-    log_a_d = None
-    if vcoef:
-        log_a_d = torch.from_numpy(log_a).to(dev)
-        solver.set_coefficient(log_a_d, stream=stream)
+    log_a_d = torch.from_numpy(log_a).to(dev) if vcoef else None
+    solver, shape = tuned_solver(srfmg, M, dev, reps=2, coef=log_a_d, segment_width=W, buffer_width=b,
+                                 precision=prec, **kw)
     info = solver.info()
     sampler = ClockSampler(dev)
     sampler.start()
@@ -762,12 +774,10 @@ def measure_single(a, dev, dist, stream, kind, precision, steps, warmup, full=Tr
     u = ud.cpu().numpy()
     out = {"value": dist.world * N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
            "warmup": warmup, "precision": precision, "N": N, "gpu_launches": info.kernels_per_solve * steps,
-           "clocks": clocks}
+           "clocks": clocks, "cta_shape": shape}
     if full:
         alu_peak(dev)
-        plain = srfmg.Solver(M, device=dev, n_sr_levels=0, **kw)
-        if vcoef:
-            plain.set_coefficient(log_a_d, stream=stream)
+        plain, _ = tuned_solver(srfmg, M, dev, reps=2, coef=log_a_d, n_sr_levels=0, **kw)
         ms_plain = dist.max(time_solves(plain, fd, ud, max(5, steps // 4), min(warmup, 3), dist, stream))
         u_plain = ud.cpu().numpy()
         plain.close()
@@ -862,7 +872,7 @@ def run_gpu_bratu(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": r.pop("ms_per_step"), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": ("int64" if a.workload == "varcoef" else "f64+f32") if a.precision == "mixed" else "f64",
-            "data": "synthetic", "config": workload_config(a)}
+            "data": "synthetic", "config": dict(workload_config(a), cta_shape=r.pop("cta_shape"))}
     for k in ("steps", "warmup", "precision", "N"):
         r.pop(k)
     line.update(r)
@@ -941,7 +951,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
     t_create = time.perf_counter() - t_create
     members = group.members()
     launches = sum(mb.info().kernels_per_solve for mb in members)
-    layouts = {str(mb.n.bit_length() - 1): [mb.params.segment_width, mb.params.buffer_width] for mb in members}
+    layouts = {str(mb.n.bit_length() - 1): [mb.params.segment_width, mb.params.buffer_width,
+                                            mb.info().coarse_tail_level] for mb in members}
     sampler = ClockSampler(dev)
     sampler.start()
     ms = dist.max(timed(group, steps, warmup))
@@ -950,8 +961,9 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
     out = {"value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
            "unknowns_per_step": total, "group_create_s": t_create, "gpu_launches": launches * steps,
            "clocks": clocks,
-           "segment_layout": ("autotuned per size (srfmg_autotune, 3 timed solves per candidate)" if tune
-                              else "min(4096, N/4) cells, buffer 8"),
+           "segment_layout": ("autotuned per size: (W, b) by srfmg_autotune, then the CTA shape by "
+                              "srfmg_autotune_shape, 3 timed solves per candidate; layouts: [W, b, coarse tail level]"
+                              if tune else "min(4096, N/4) cells, buffer 8"),
            "layouts": layouts}
     # accuracy sample: the first problem of every size against its exact solution
     samples = {}

@@ -125,9 +125,10 @@ typedef struct {
        owns them, and the coarse tail runs the same sweeps on whole levels): */
     int32_t tail_level;        /* finest level of the one-block coarse tail: 0 (default:
                                   min(12, M - n_sr_levels)) or in [log2_n_coarsest, 12] */
-    int32_t tile_cells;        /* cells per block of the stored-level passes on levels up
-                                  to 2^18 (levels above take 2048): 0 (default 256) or a
-                                  power of two in [64, 2048] */
+    int32_t tile_cells;        /* cells per block of the stored-level passes on levels of
+                                  at most 2^18 cells over the whole batch (latency-bound;
+                                  larger ones take 2048): 0 (default 256) or a power of
+                                  two in [64, 2048] */
 } srfmg_params;
 
 /* Information about a created plan. */

@@ -254,10 +254,13 @@ Op level_op(srfmg_plan *h, OpKind kind, int l, const double *u_src, const double
     o.level = l;
     const int n = 1 << l;
     const int nu = (kind == OP_UP) ? h->p.nu2 : h->p.nu1;
-    // levels up to 2^18 are latency-bound (a few microseconds per pass whatever
-    // their size): smaller tiles spread them over more SMs (measured: 1.8% off the
-    // N = 2^24 solve; 128-cell tiles, or 256 up to level 20, were slower)
-    const int Tmax = (l <= 18) ? (h->p.tile_cells ? h->p.tile_cells : 256) : kTileMax;
+    // a level of at most 2^18 cells over the whole batch is latency-bound (a few
+    // microseconds per pass whatever its size): smaller tiles spread it over more
+    // SMs (measured: 1.8% off the N = 2^24 solve; 128-cell tiles, or 256 up to
+    // level 20, were slower); a larger one is throughput-bound, and there the
+    // halos of small tiles cost (the batch of 8192 problems: 304 -> 394 ms)
+    const bool latency_bound = ((long long)n * h->batch) <= (1LL << 18);
+    const int Tmax = latency_bound ? (h->p.tile_cells ? h->p.tile_cells : 256) : kTileMax;
     const int T = n < Tmax ? n : Tmax;
     // halo: each sweep's values become tile-independent (J+2)*kChunk cells
     // after its range start (9 * 9 = 81 cells, J+1 = ceil(72/9); 12 * 9 = 108

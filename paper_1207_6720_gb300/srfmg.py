@@ -539,8 +539,8 @@ def autotune(log2_n, device=0, reps=5, **overrides):
 
 
 def autotune_shape(params, device=0, reps=5):
-    """Time the CTA shapes (coarse tail extent, cells per tile of the stored levels
-    up to 2^18) of the plan `params` and return (best Params,
+    """Time the CTA shapes (coarse tail extent, cells per tile of the latency-bound
+    stored levels) of the plan `params` and return (best Params,
     [(tail_level, tile_cells, ms per solve), ...]); the shape does not change the
     result."""
     lib = load()

@@ -1,5 +1,5 @@
 """The CTA shape of a plan (the coarse tail's extent and the cells per block of
-the stored-level passes up to 2^18) changes the launch shapes, not the
+the latency-bound stored-level passes) changes the launch shapes, not the
 result: every shape gives the same bits, in both precisions and for every
 operator; srfmg_autotune_shape picks one of them."""
 import numpy as np
