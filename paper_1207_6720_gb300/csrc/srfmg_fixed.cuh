@@ -254,6 +254,15 @@ __device__ __forceinline__ i64 tau_rhs(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1,
     return gr + tau * (1LL << tsh);
 }
 
+// tau_rhs of a coarse cell away from both walls, without the wall cases, the
+// same integers: (Gl - Gr) = 2 hJ - h_{J-1} - h_{J+1} and (Fl - Fr) = (u0 + u1)
+// - (um1 + u2).
+__device__ __forceinline__ i64 tau_rhs_interior(i64 gr, i64 um2, i64 um1, i64 u0, i64 u1, i64 u2, i64 u3, int tsh) {
+    const i64 hm = (um2 + um1) >> 1, h = (u0 + u1) >> 1, hp = (u2 + u3) >> 1;
+    const i64 tau = (2 * h - hm - hp) - 2 * ((u0 + u1) - (um1 + u2));
+    return gr + tau * (1LL << tsh);
+}
+
 // --------------------------------------------------------------------------
 // Variable coefficient -(a u')' = f in fixed point.
 //
@@ -622,6 +631,7 @@ struct LevelArgs {
 struct LevelSmem {
     i64 *u, *gs, *c, *X, *gr, *Y;
     u64 *A, *BM;
+    int gsh;                   // > 0: gs holds G_l, shifted into solution units by the sweeps
     int L0, L1, C0, C1;
     // this problem's arrays (see batch_at)
     const Scale *sc;
@@ -672,13 +682,17 @@ __device__ void stage_g_async(LevelSmem &m, const LevelArgs &a) {
     }
 }
 
-// In place over the staged cells (pairs 2J, 2J+1; L0 and L1 are even):
-// gs = G >> gsh rounded (the right-hand side in solution units), with f
-// converted to G first on the finest level; with gr, also the restricted
-// right-hand side of the coarse cells [J0, J1).
+// On the finest level (f staged), in place over the staged cells (pairs 2J,
+// 2J+1; L0 and L1 are even): f converted to G, then gs = G >> gsh rounded
+// (the right-hand side in solution units) and, with gr, the restricted
+// right-hand side of the coarse cells [J0, J1).  Below it gs keeps the staged
+// G_l (m.gsh = gsh): the sweeps shift each value as they load it and the down
+// pass restricts G where it forms tau, the same values without this pass.
 __device__ void prepare_rhs(LevelSmem &m, const LevelArgs &a, int gsh, i64 *gr, int J0, int J1) {
     (void)a;
     const bool from_f = (m.gin == nullptr);
+    m.gsh = from_f ? 0 : gsh;
+    if (!from_f) return;
     const int kg = m.sc->Sg0;
     for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x) {
         const int i = 2 * J - m.L0;
@@ -699,8 +713,14 @@ __device__ void smooth_range(LevelSmem &m, int n, int nu) {
     int hi = (m.L1 == n) ? n : m.L1 - 1;
     const int Kb = VC ? m.sc->Kb : 0;
     for (int k = 0; k < nu; ++k) {
-        if (VC) lex_sweep_vc<kChunk>(m.u, m.gs, m.A, m.BM, m.L0, m.L0, lo, hi, n, (k & 1) == 0, m.X, m.Y, Kb);
-        else lex_sweep<kChunk>(m.u, m.gs, m.L0, lo, hi, n, (k & 1) == 0, m.X);
+        const bool asc = (k & 1) == 0;
+        if (VC) {
+            if (m.gsh) lex_sweep_vc<kChunk, true>(m.u, m.gs, m.A, m.BM, m.L0, m.L0, lo, hi, n, asc, m.X, m.Y, Kb, m.gsh);
+            else lex_sweep_vc<kChunk>(m.u, m.gs, m.A, m.BM, m.L0, m.L0, lo, hi, n, asc, m.X, m.Y, Kb);
+        } else {
+            if (m.gsh) lex_sweep<kChunk, false, true>(m.u, m.gs, m.L0, lo, hi, n, asc, m.X, m.gsh);
+            else lex_sweep<kChunk>(m.u, m.gs, m.L0, lo, hi, n, asc, m.X);
+        }
         if (lo > 0) ++lo;
         if (hi < n) --hi;
     }
@@ -742,9 +762,10 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_down_kernel(
         i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
         i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
         m.ucout[J] = (u[i0] + u[i0 + 1]) >> 1;
-        m.gcout[J] = VC ? tau_rhs_vc(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh, m.A[i0],
-                                     m.A[i0 + 2])
-                        : tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+        const i64 gr = m.gsh ? restrict_rhs(m.gs[i0], m.gs[i0 + 1]) : m.gr[J - J0];
+        m.gcout[J] = VC ? tau_rhs_vc(gr, um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh, m.A[i0], m.A[i0 + 2])
+                     : (J > 0 && J < nc - 1) ? tau_rhs_interior(gr, um2, um1, u[i0], u[i0 + 1], u2, u3, tsh)
+                                             : tau_rhs(gr, um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
     }
     for (int i = s + (int)threadIdx.x; i < s + a.tile; i += (int)blockDim.x) m.uout[i] = u[i - m.L0];
 }
@@ -944,7 +965,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) sr_pre_kernel(SegA
             i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
             gc_out[J] = VC ? tau_rhs_vc(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh, m.A[i0],
                                         m.A[i0 + 2])
-                           : tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+                        : (J > 0 && J < nc - 1) ? tau_rhs_interior(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, tsh)
+                                                : tau_rhs(m.gr[J - J0], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
         }
     }
     if (threadIdx.x < 6) {
