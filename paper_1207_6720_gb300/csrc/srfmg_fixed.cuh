@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_down_kernel(
         for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x)
             fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
-    __syncthreads();
+    if (FROM_PI || !m.gin) __syncthreads();    // (below the finest level without Pi nothing was written)
     smooth_range<VC>(m, n, a.nu);
     const i64 *u = m.u;
     const int tsh = 2 * a.l - 4;
@@ -794,11 +794,11 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_up_kernel(Le
         m.c[j - m.C0] = inside ? m.c[j - m.C0] - ((m.u[i0 - m.L0] + m.u[i0 + 1 - m.L0]) >> 1) : 0;
     }
     __syncthreads();
-    fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
-    __syncthreads();
+    // the ghost coarse cells beyond the walls by odd reflection, read in place
     for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x) {
         int J = i >> 1, nb = (i & 1) ? J + 1 : J - 1;
-        m.u[i - m.L0] += (3 * m.c[J - m.C0] + m.c[nb - m.C0] + 2) >> 2;
+        const i64 cn = (nb < 0) ? -m.c[-m.C0] : ((nb >= nc) ? -m.c[nc - 1 - m.C0] : m.c[nb - m.C0]);
+        m.u[i - m.L0] += (3 * m.c[J - m.C0] + cn + 2) >> 2;
     }
     __syncthreads();
     smooth_range<VC>(m, n, a.nu);
