@@ -463,7 +463,9 @@ def tuned_solver(srfmg, M, dev, reps=3, coef=None, **kw):
     if coef is not None:
         s.set_coefficient(coef)
     shape = {"tail_level": best.tail_level, "tile_cells": best.tile_cells,
-             "candidates_ms": {f"T{t}_C{c}": round(ms, 4) for t, c, ms in table}}
+             "chain_down": best.chain_down, "chain_up": best.chain_up,
+             "candidates_ms": {f"T{t}_C{c}" + (f"_D{cd}_U{cu}" if cd or cu else ""): round(ms, 4)
+                               for t, c, cd, cu, ms in table}}
     return s, shape
 
 

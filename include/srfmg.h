@@ -129,6 +129,13 @@ typedef struct {
                                   at most 2^18 cells over the whole batch (latency-bound;
                                   larger ones take 2048): 0 (default 256) or a power of
                                   two in [64, 2048] */
+    int32_t chain_down;        /* 0 or 1 (off), or 2 .. 4: on the stored levels of at most
+                                  2^18 cells over the whole batch, the down passes of up to
+                                  chain_down consecutive levels run as one launch that
+                                  keeps them in shared memory (a wider halo instead of the
+                                  launches in between); the same bits as without it.
+                                  SRFMG_MIXED with SRFMG_OP_LAPLACE only. */
+    int32_t chain_up;          /* the same for the up passes (0 or 1: off, or 2 .. 4) */
 } srfmg_params;
 
 /* Information about a created plan. */
@@ -375,18 +382,20 @@ srfmg_status srfmg_autotune_candidate(const srfmg_params *base, int32_t k, int32
 
 /* Autotuner for the CTA shape of a plan (no counterpart in the paper; the
  * launch shapes leave the result unchanged, bit for bit): for the solve
- * described by *base (any SR layout; base's tail_level and tile_cells are
- * ignored) it times every candidate (tail_level, tile_cells) with tail_level in
+ * described by *base (any SR layout; base's tail_level, tile_cells, chain_down
+ * and chain_up are ignored) it times every candidate shape: tail_level in
  * {9, 10, 11, 12} (those in [log2_n_coarsest, min(12, M - n_sr_levels)], each
- * distinct coarse tail once) and tile_cells in {128, 256, 512} (candidate k in
- * that order, tail level major; srfmg_autotune_shape_candidate names it), the
- * same way as srfmg_autotune, and writes *base with the fastest pair to *best.
- * ms (optional, capacity entries) and *ncand (optional) as in srfmg_autotune.
- * Synchronous.  Errors as srfmg_autotune. */
+ * distinct coarse tail once) with tile_cells in {128, 256, 512} and no chained
+ * passes (tail level major), then, for SRFMG_MIXED with SRFMG_OP_LAPLACE, the
+ * two finest of those tails with tile_cells in {256, 512} and chain_down = 2,
+ * chain_up in {3, 4}.  Candidate k (srfmg_autotune_shape_candidate writes
+ * *base with its shape to *cand) is timed the same way as in srfmg_autotune,
+ * and *best is *base with the fastest shape.  ms (optional, capacity entries)
+ * and *ncand (optional) as in srfmg_autotune.  Synchronous.  Errors as
+ * srfmg_autotune. */
 srfmg_status srfmg_autotune_shape(const srfmg_params *base, int device, int32_t reps, srfmg_params *best,
                                   float *ms, int32_t capacity, int32_t *ncand);
-srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, int32_t *tail_level,
-                                            int32_t *tile_cells);
+srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, srfmg_params *cand);
 
 /* Independent problems of uneven sizes solved together (many problems with
  * N = 2^m cells for varying m; the paper solves one problem, this is the
@@ -416,7 +425,7 @@ srfmg_status srfmg_group_offsets(int32_t nprob, const int32_t *log2_n, int64_t *
  * Segment layout of each size (plans with SR levels): with tune = 0,
  * W = min(base->segment_width, max(16, N/4)) and b = min(base->buffer_width,
  * W); with tune > 0, srfmg_autotune picks (W, b) for each size and then
- * srfmg_autotune_shape its CTA shape (tail_level, tile_cells) (`tune` timed
+ * srfmg_autotune_shape its CTA shape (tail_level, tile_cells, chain_down, chain_up) (`tune` timed
  * solves per candidate, on a sample of min(count, max(1, 2^24 / N)) problems
  * of that size; needs n_sr_levels = 1).  Every size must make a valid plan
  * (srfmg_create's checks: N > 2^log2_n_coarsest, ...).  On success *out is a

@@ -29,7 +29,8 @@ constexpr int kTileMax = 2048;
 
 thread_local std::string g_create_error = "no error";
 
-enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST, OP_SCALE };
+enum OpKind { OP_RHS, OP_TAIL, OP_DOWN_PI, OP_DOWN, OP_UP, OP_SR_PRE, OP_SEAM, OP_SR_POST, OP_SCALE, OP_DOWN_CHAIN,
+              OP_UP_CHAIN };
 
 // Pointers that are only known at solve time are patched through these tags.
 enum PtrTag { TAG_NONE = 0, TAG_F = 1, TAG_U = 2 };   // f, u: the caller's pointers of a solve
@@ -57,6 +58,7 @@ struct Op {
     fx::LevelArgs flev;
     fx::SegArgs fseg;
     fx::TailArgs ftail;
+    fx::ChainArgs fchain;      // OP_DOWN_CHAIN, OP_UP_CHAIN (fixed point only)
     fx::Scale *scale;
     int *status;      // OP_SCALE: the plan's status word
 };
@@ -141,6 +143,10 @@ std::string check_params(const srfmg_params *p) {
         return "tail_level must be 0 or in [log2_n_coarsest, 12]";
     if (p->tile_cells != 0 && (!pow2(p->tile_cells) || p->tile_cells < 64 || p->tile_cells > 2048))
         return "tile_cells must be 0 or a power of two in [64, 2048]";
+    if (p->chain_down < 0 || p->chain_down > fx::kChainMax || p->chain_up < 0 || p->chain_up > fx::kChainMax)
+        return "chain_down and chain_up must be in [0, 4]";
+    if ((p->chain_down >= 2 || p->chain_up >= 2) && (p->precision != SRFMG_MIXED || p->op != SRFMG_OP_LAPLACE))
+        return "chain_down and chain_up apply to SRFMG_MIXED with SRFMG_OP_LAPLACE";
     if (p->post_leg != SRFMG_POST_FULL_UPDATE && p->post_leg != SRFMG_POST_FAS_RECOMPUTE)
         return "post_leg must be SRFMG_POST_FULL_UPDATE or SRFMG_POST_FAS_RECOMPUTE";
     if (p->post_leg == SRFMG_POST_FAS_RECOMPUTE &&
@@ -362,6 +368,63 @@ Op tail_op(srfmg_plan *h, int mode, const double *u_in, const double *g_in, int 
     return o;
 }
 
+// A stored level whose passes may be chained: fixed point, -u'' = f, at most
+// 2^18 cells over the whole batch (the latency-bound ones).
+bool chainable(const srfmg_plan *h, int l) {
+    return h->fixed && h->p.op == SRFMG_OP_LAPLACE && ((long long)1 << l) * h->batch <= (1LL << 18);
+}
+
+// A chain of k stored-level passes (fixed point): down from level l (levels l
+// .. l-k+1) or up from level l (levels l .. l+k-1); the pointers are set by
+// the caller.  Shared memory: U and G of each chain level's held range, the
+// coarse cells of an up step, the chunk carries (see the kernels).
+Op chain_op(srfmg_plan *h, OpKind kind, int l, int k) {
+    Op o = make_op(kind);
+    fx::ChainArgs &c = o.fchain;
+    const bool down = (kind == OP_DOWN_CHAIN);
+    const int fine = down ? l : l + k - 1;     // the chain's finest level
+    const int n = 1 << fine;
+    const int Tmax = h->p.tile_cells ? h->p.tile_cells : 256;
+    const int T = n < Tmax ? n : Tmax;
+    const int nu = down ? h->p.nu1 : h->p.nu2;
+    o.level = l;
+    c.k = k;
+    c.l = l;
+    c.tile = T;
+    c.H = 112 * nu;                            // the halo of level_op
+    c.nu = nu;
+    c.sc = h->scale;
+    int len[fx::kChainMax];
+    if (down) {
+        int hh = c.H;
+        for (int i = k - 1; i >= 0; --i) {
+            len[i] = (T >> i) + 2 * hh;
+            hh = 2 * hh + c.H;
+        }
+    } else {
+        len[k - 1] = T + 2 * c.H;
+        for (int i = k - 2; i >= 0; --i) len[i] = (len[i + 1] >> 1) + 6 + 2 * c.H;
+    }
+    size_t off = 0;
+    int maxlen = 0;
+    for (int i = 0; i < k; ++i) {
+        c.off[i] = (int)off;
+        c.len[i] = len[i];
+        off += 2 * (size_t)len[i];
+        maxlen = std::max(maxlen, len[i]);
+    }
+    c.off_c = (int)off;
+    if (!down) off += (size_t)maxlen / 2 + 8;
+    c.off_x = (int)off;
+    const int maxch = (maxlen + kChunk - 1) / kChunk + 2;
+    off += (size_t)maxch;
+    o.smem = off * sizeof(fx::i64);
+    o.grid = dim3(n / T);
+    o.block = dim3(((maxch + 31) / 32) * 32);
+    o.fixed = true;
+    return o;
+}
+
 // Fixed-point form of an op (same schedule, same buffers: a level array holds
 // doubles or 64-bit integers of the same size).
 void to_fixed(srfmg_plan *h, Op &o) {
@@ -428,7 +491,7 @@ void to_fixed(srfmg_plan *h, Op &o) {
         }
         o.ftail.coef0 = h->coef[h->M0];
         break;
-    case OP_SCALE:
+    case OP_SCALE: case OP_DOWN_CHAIN: case OP_UP_CHAIN:
         break;
     }
 }
@@ -475,18 +538,57 @@ void build_schedule_ops(srfmg_plan *h) {
     // one V-cycle below a level that was just restricted to Mc
     // (src: the top level's iterate when it is not in the level's own buffers)
     auto vcycle_below = [&](int top_stored, const double *src) {
-        for (int l = top_stored; l > Mc; --l) {
+        for (int l = top_stored; l > Mc;) {
             const double *u_src = (l == top_stored && src) ? src : U(l);
+            int k = chainable(h, l) ? std::min(h->p.chain_down, l - Mc) : 1;
+            while (k >= 2 && chain_op(h, OP_DOWN_CHAIN, l, k).block.x > (unsigned)kSweepBlockMax) --k;
+            if (k >= 2) {
+                // down passes of levels l .. l-k+1 in one launch; the buffers as the
+                // separate passes would leave them
+                Op o = chain_op(h, OP_DOWN_CHAIN, l, k);
+                o.fchain.u_src = (const fx::i64 *)u_src;
+                o.fchain.g[0] = (const fx::i64 *)h->glev[l];
+                for (int i = 0; i < k; ++i) {
+                    if (i > 0) cur[l - i] ^= 1;        // (the restriction the separate pass would store)
+                    o.fchain.u_out[i] = (fx::i64 *)Unext(l - i);
+                    cur[l - i] ^= 1;
+                    o.fchain.g_out[i] = (fx::i64 *)h->glev[l - i - 1];
+                }
+                o.fchain.uc_out = (fx::i64 *)Unext(l - k);
+                cur[l - k] ^= 1;
+                h->ops.push_back(o);
+                l -= k;
+                continue;
+            }
             h->ops.push_back(level_op(h, OP_DOWN, l, u_src, nullptr, Unext(l), Unext(l - 1), h->glev[l - 1]));
             cur[l] ^= 1;
             cur[l - 1] ^= 1;
+            --l;
         }
         h->ops.push_back(tail_op(h, 1, (top_stored == Mc && src) ? src : U(Mc), h->glev[Mc], 0, Unext(Mc), false,
                                  false));
         cur[Mc] ^= 1;
-        for (int l = Mc + 1; l <= top_stored; ++l) {
+        for (int l = Mc + 1; l <= top_stored;) {
+            int k = 0;
+            while (k < h->p.chain_up && l + k <= top_stored && chainable(h, l + k)) ++k;
+            while (k >= 2 && chain_op(h, OP_UP_CHAIN, l, k).block.x > (unsigned)kSweepBlockMax) --k;
+            if (k >= 2) {
+                // up passes of levels l .. l+k-1 in one launch
+                Op o = chain_op(h, OP_UP_CHAIN, l, k);
+                o.fchain.uc_src = (const fx::i64 *)U(l - 1);
+                for (int i = 0; i < k; ++i) {
+                    o.fchain.u_in[i] = (const fx::i64 *)U(l + i);
+                    o.fchain.g[i] = (const fx::i64 *)h->glev[l + i];
+                    o.fchain.u_out[i] = (fx::i64 *)Unext(l + i);
+                    cur[l + i] ^= 1;
+                }
+                h->ops.push_back(o);
+                l += k;
+                continue;
+            }
             h->ops.push_back(level_op(h, OP_UP, l, U(l), U(l - 1), Unext(l), nullptr, nullptr));
             cur[l] ^= 1;
+            ++l;
         }
     };
 
@@ -632,6 +734,8 @@ cudaError_t launch_fixed_ops(const Op &o, cudaStream_t s, bool pdl) {
     case OP_DOWN_PI: e = run(fx::level_down_kernel<true, VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
     case OP_DOWN: e = run(fx::level_down_kernel<false, VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
     case OP_UP: e = run(fx::level_up_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.flev); break;
+    case OP_DOWN_CHAIN: e = run(fx::level_down_chain_kernel, o.grid, o.block, o.smem, s, pdl, o.fchain); break;
+    case OP_UP_CHAIN: e = run(fx::level_up_chain_kernel, o.grid, o.block, o.smem, s, pdl, o.fchain); break;
     case OP_SR_PRE: e = run(fx::sr_pre_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
     case OP_SEAM: e = run(fx::seam_tau_kernel<VC>, o.grid, o.block, 0, s, pdl, o.fseg, o.nseg); break;
     case OP_SR_POST: e = run(fx::sr_post_kernel<VC>, o.grid, o.block, o.smem, s, pdl, o.fseg); break;
@@ -682,7 +786,7 @@ cudaError_t launch_fp64(const Op &o, cudaStream_t s, bool pdl) {
     case OP_SR_PRE: e = run(sr_pre_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.seg); break;
     case OP_SEAM: e = run(seam_tau_kernel<NL>, o.grid, o.block, 0, s, pdl, o.seg, o.nseg); break;
     case OP_SR_POST: e = run(sr_post_kernel<NL>, o.grid, o.block, o.smem, s, pdl, o.seg); break;
-    case OP_SCALE: break;
+    case OP_SCALE: case OP_DOWN_CHAIN: case OP_UP_CHAIN: break;
     }
     return e;
 }
@@ -722,6 +826,8 @@ const char *kind_name(OpKind k) {
     case OP_SEAM: return "seam_tau";
     case OP_SR_POST: return "sr_post";
     case OP_SCALE: return "fixed_scale";
+    case OP_DOWN_CHAIN: return "level_down_chain";
+    case OP_UP_CHAIN: return "level_up_chain";
     }
     return "?";
 }
@@ -797,7 +903,8 @@ srfmg_status set_smem_limits(srfmg_plan *h) {
                          (const void *)fx::level_down_kernel<true, true>, (const void *)fx::level_down_kernel<false, true>,
                          (const void *)fx::level_up_kernel<true>, (const void *)fx::sr_pre_kernel<true>,
                          (const void *)fx::sr_post_kernel<true>, (const void *)fx::tail_kernel<true>,
-                         (const void *)fx::rhs_hierarchy_kernel};
+                         (const void *)fx::rhs_hierarchy_kernel, (const void *)fx::level_down_chain_kernel,
+                         (const void *)fx::level_up_chain_kernel};
     for (const void *fn : fns) {
         // the opt-in limit covers static and dynamic shared memory together
         cudaFuncAttributes fa;
@@ -1344,8 +1451,17 @@ srfmg_status time_candidates(const std::vector<srfmg_params> &cand, int device, 
 }
 
 // The shape candidates of srfmg_autotune_shape: distinct coarse tails, then tiles.
-std::vector<std::pair<int, int>> shape_candidates(const srfmg_params *base) {
-    std::vector<std::pair<int, int>> cand;
+struct Shape {
+    int tail, tile, cdown, cup;
+};
+
+// The CTA shapes the shape autotuner times: every distinct coarse tail in
+// 9..12 with 128, 256 or 512 cells per tile; for the fixed-point -u'' = f
+// also the two finest of those tails with 256 or 512 cells per tile and
+// chained passes (down chains of 2, up chains of 3 or 4 levels).
+std::vector<Shape> shape_candidates(const srfmg_params *base) {
+    std::vector<Shape> cand;
+    std::vector<int> tails;
     const int top = base->log2_n - base->n_sr_levels;
     int prev_mc = -1;
     for (int t = 9; t <= 12; ++t) {
@@ -1353,9 +1469,15 @@ std::vector<std::pair<int, int>> shape_candidates(const srfmg_params *base) {
         const int mc = std::max(base->log2_n_coarsest, std::min(t, top));
         if (mc == prev_mc) continue;
         prev_mc = mc;
-        for (int tc : {128, 256, 512}) cand.push_back({t, tc});
+        tails.push_back(t);
+        for (int tc : {128, 256, 512}) cand.push_back({t, tc, 0, 0});
     }
-    if (cand.empty()) cand.push_back({12, 256});
+    if (cand.empty()) cand.push_back({12, 256, 0, 0});
+    if (base->precision == SRFMG_MIXED && base->op == SRFMG_OP_LAPLACE) {
+        for (size_t i = tails.size() >= 2 ? tails.size() - 2 : 0; i < tails.size(); ++i)
+            for (int tc : {256, 512})
+                for (int cu : {3, 4}) cand.push_back({tails[i], tc, 2, cu});
+    }
     return cand;
 }
 
@@ -1398,21 +1520,25 @@ srfmg_status srfmg_autotune_shape(const srfmg_params *base, int device, int32_t 
     std::vector<srfmg_params> cand;
     for (const auto &c : shape_candidates(base)) {
         srfmg_params p = *base;
-        p.tail_level = c.first;
-        p.tile_cells = c.second;
+        p.tail_level = c.tail;
+        p.tile_cells = c.tile;
+        p.chain_down = c.cdown;
+        p.chain_up = c.cup;
         cand.push_back(p);
     }
     if (ncand) *ncand = (int32_t)cand.size();
     return time_candidates(cand, device, reps, best, ms, capacity);
 }
 
-srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, int32_t *tail_level,
-                                            int32_t *tile_cells) {
-    if (!base || !tail_level || !tile_cells || k < 0) return fail(nullptr, SRFMG_EINVAL, "bad arguments");
-    const auto cand = shape_candidates(base);
-    if (k >= (int32_t)cand.size()) return fail(nullptr, SRFMG_EINVAL, "candidate index out of range");
-    *tail_level = cand[k].first;
-    *tile_cells = cand[k].second;
+srfmg_status srfmg_autotune_shape_candidate(const srfmg_params *base, int32_t k, srfmg_params *cand) {
+    if (!base || !cand || k < 0) return fail(nullptr, SRFMG_EINVAL, "bad arguments");
+    const auto list = shape_candidates(base);
+    if (k >= (int32_t)list.size()) return fail(nullptr, SRFMG_EINVAL, "candidate index out of range");
+    *cand = *base;
+    cand->tail_level = list[k].tail;
+    cand->tile_cells = list[k].tile;
+    cand->chain_down = list[k].cdown;
+    cand->chain_up = list[k].cup;
     return SRFMG_OK;
 }
 
@@ -1715,6 +1841,8 @@ srfmg_status srfmg_group_create(const srfmg_params *base, int32_t nprob, const i
             if (st != SRFMG_OK) { st = gfail(g, st, "shape autotune of size 2^" + std::to_string(pm[c]) + ": " + g_create_error); break; }
             p.tail_level = best.tail_level;
             p.tile_cells = best.tile_cells;
+            p.chain_down = best.chain_down;
+            p.chain_up = best.chain_up;
         }
         srfmg_handle h = nullptr;
         st = srfmg_create(&p, device, &h);

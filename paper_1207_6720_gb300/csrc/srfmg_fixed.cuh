@@ -813,6 +813,176 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_up_kernel(Le
 }
 
 // --------------------------------------------------------------------------
+// Chains of stored-level passes (-u'' = f): the down passes of k consecutive
+// levels, or their up passes, in one launch.  On the latency-bound small
+// levels a pass costs a launch, a grid-wide dependency and a staging round
+// more than its few sweeps; a chain keeps the k levels of a tile in shared
+// memory instead.  Each level of a chain is a tile of the ordinary pass with
+// a wider halo where the next level of the chain needs more exact cells: the
+// same sweeps over ranges that cover the ordinary tile's, so every cell
+// written is the same bits as the separate passes give.
+// --------------------------------------------------------------------------
+constexpr int kChainMax = 4;
+
+struct ChainArgs {
+    int k;                     // levels in the chain (2 .. kChainMax)
+    int l;                     // down: the first (finest) level; up: the first (coarsest) level
+    int tile;                  // owned cells of a block on the chain's finest level
+    int H;                     // halo of one level's sweeps (112 nu)
+    int nu;
+    int off[kChainMax], len[kChainMax];   // shared memory of chain level i: U at off[i], G at off[i] + len[i]
+    int off_c, off_x;          // coarse cells of an up step; chunk carries
+    const Scale *sc;
+    const i64 *u_src;          // down: the first level's iterate
+    const i64 *uc_src;         // up: the corrected level below the chain
+    const i64 *u_in[kChainMax];   // up: each level's iterate after its down pass
+    const i64 *g[kChainMax];   // G of each level (down: only g[0] is read)
+    i64 *u_out[kChainMax];     // each level after its sweeps (owned cells)
+    i64 *g_out[kChainMax];     // down: G (tau right-hand side) of the level below chain level i (owned cells)
+    i64 *uc_out;               // down: U of the level below the chain (restriction, owned cells)
+};
+
+__device__ __forceinline__ LevelSmem chain_level_smem(i64 *smi, const ChainArgs &a, int i, int l, int L0, int L1) {
+    LevelSmem m;
+    m.u = smi + a.off[i];
+    m.gs = m.u + a.len[i];
+    m.c = smi + a.off_c;
+    m.X = smi + a.off_x;
+    m.gr = nullptr;
+    m.Y = nullptr;
+    m.A = nullptr;
+    m.BM = nullptr;
+    m.gsh = 2 * l - 2;         // G below the finest level, shifted by the sweeps
+    m.L0 = L0;
+    m.L1 = L1;
+    m.C0 = (L0 >> 1) - 2;
+    m.C1 = ((L1 - 1) >> 1) + 3;
+    m.sc = a.sc + blockIdx.y;
+    return m;
+}
+
+// Down chain: chain level i is level l - i with owned cells [s >> i, (s + T) >> i)
+// and halo h_i, h_{k-1} = H, h_i = 2 h_{i+1} + H: after its sweeps the cells
+// the next level's halo is restricted from are exact (a tile of halo H gives
+// exact values H cells in, the tau stencil included).  Level i's restriction
+// and tau fill level i+1's whole held range in shared memory; the owned
+// coarse cells also go to global memory (G of every level below, for the up
+// passes; U of the level below the chain).
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_chain_kernel(const __grid_constant__ ChainArgs a) {
+    pdl_enter();
+    extern __shared__ i64 smi[];
+    int h[kChainMax];
+    h[a.k - 1] = a.H;
+    for (int i = a.k - 2; i >= 0; --i) h[i] = 2 * h[i + 1] + a.H;
+    const int s0 = blockIdx.x * a.tile;
+    {
+        const int n = 1 << a.l;
+        const int L0 = max(0, s0 - h[0]), L1 = min(n, s0 + a.tile + h[0]);
+        stage_range(smi + a.off[0], batch_at(a.u_src, n) + L0, L1 - L0);
+        stage_range(smi + a.off[0] + a.len[0], batch_at(a.g[0], n) + L0, L1 - L0);
+        stage_wait();
+        __syncthreads();
+    }
+    for (int i = 0; i < a.k; ++i) {
+        const int l = a.l - i, n = 1 << l, nc = n >> 1;
+        const int s = s0 >> i, T = a.tile >> i;
+        LevelSmem m = chain_level_smem(smi, a, i, l, max(0, s - h[i]), min(n, s + T + h[i]));
+        smooth_range<false>(m, n, a.nu);
+        const i64 *u = m.u;
+        i64 *uo = batch_at(a.u_out[i], n);
+        for (int q = s + (int)threadIdx.x; q < s + T; q += (int)blockDim.x) uo[q] = u[q - m.L0];
+        // the coarse cells of the next chain level's held range (or, after the
+        // last level, the owned ones)
+        const bool last = (i == a.k - 1);
+        const int Jo0 = s >> 1, Jo1 = (s + T) >> 1;
+        const int Jlo = last ? Jo0 : max(0, Jo0 - h[i + 1]), Jhi = last ? Jo1 : min(nc, Jo1 + h[i + 1]);
+        i64 *un = last ? nullptr : smi + a.off[i + 1];
+        i64 *gn = last ? nullptr : un + a.len[i + 1];
+        i64 *gco = batch_at(a.g_out[i], nc);
+        i64 *uco = last ? batch_at(a.uc_out, nc) : nullptr;
+        const int tsh = 2 * l - 4;
+        for (int J = Jlo + (int)threadIdx.x; J < Jhi; J += (int)blockDim.x) {
+            const int i0 = 2 * J - m.L0;
+            const i64 um2 = (J > 0) ? u[i0 - 2] : 0, um1 = (J > 0) ? u[i0 - 1] : 0;
+            const i64 u2 = (J < nc - 1) ? u[i0 + 2] : 0, u3 = (J < nc - 1) ? u[i0 + 3] : 0;
+            const i64 ucv = (u[i0] + u[i0 + 1]) >> 1;
+            const i64 gr = restrict_rhs(m.gs[i0], m.gs[i0 + 1]);
+            const i64 gcv = (J > 0 && J < nc - 1) ? tau_rhs_interior(gr, um2, um1, u[i0], u[i0 + 1], u2, u3, tsh)
+                                                  : tau_rhs(gr, um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, tsh);
+            if (!last) {
+                un[J - Jlo] = ucv;
+                gn[J - Jlo] = gcv;
+            }
+            if (J >= Jo0 && J < Jo1) {
+                gco[J] = gcv;
+                if (last) uco[J] = ucv;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Up chain: chain level i is level l + i, bottom up; the last (finest) level
+// is the ordinary up tile [s - H, s + T + H) of the block's T cells, and each
+// level below holds the coarse range that the level above interpolates from
+// plus a halo H, so that range comes out exact.  Every level's held range is
+// staged at once; the coarse cells of level i's correction are level i-1's
+// result in shared memory (the corrected level below the chain from global
+// memory for i = 0).  Each level writes its owned cells s >> (k-1-i) ...
+__global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_chain_kernel(const __grid_constant__ ChainArgs a) {
+    pdl_enter();
+    extern __shared__ i64 smi[];
+    int L0[kChainMax], L1[kChainMax];
+    const int top = a.k - 1;
+    const int s0 = blockIdx.x * a.tile;
+    L0[top] = max(0, s0 - a.H);
+    L1[top] = min(1 << (a.l + top), s0 + a.tile + a.H);
+    for (int i = top - 1; i >= 0; --i) {
+        const int n = 1 << (a.l + i);
+        const int C0 = max(0, (L0[i + 1] >> 1) - 2), C1 = min(n, ((L1[i + 1] - 1) >> 1) + 3);
+        L0[i] = max(0, C0 - a.H);
+        L1[i] = min(n, C1 + a.H);
+    }
+    for (int i = 0; i < a.k; ++i) {
+        const int n = 1 << (a.l + i);
+        stage_range(smi + a.off[i], batch_at(a.u_in[i], n) + L0[i], L1[i] - L0[i]);
+        stage_range(smi + a.off[i] + a.len[i], batch_at(a.g[i], n) + L0[i], L1[i] - L0[i]);
+    }
+    {
+        const int nc = 1 << (a.l - 1);
+        const int C0 = (L0[0] >> 1) - 2, C1 = ((L1[0] - 1) >> 1) + 3;
+        stage_coarse_async(smi + a.off_c, batch_at(a.uc_src, nc), C0, C1, nc);
+    }
+    stage_wait();
+    __syncthreads();
+    for (int i = 0; i < a.k; ++i) {
+        const int l = a.l + i, n = 1 << l, nc = n >> 1;
+        LevelSmem m = chain_level_smem(smi, a, i, l, L0[i], L1[i]);
+        const i64 *prev = (i > 0) ? smi + a.off[i - 1] : nullptr;   // level l-1, held from L0[i-1]
+        // c_J = U_{l-1,J} - (R U_l)_J, 0 for the coarse cells whose children lie
+        // outside the held range (they reach only its frozen end cells)
+        for (int j = max(m.C0, 0) + (int)threadIdx.x; j < min(m.C1, nc); j += (int)blockDim.x) {
+            const int i0 = 2 * j;
+            const bool inside = i0 >= m.L0 && i0 + 1 < m.L1;
+            const i64 uc = prev ? prev[j - L0[i - 1]] : m.c[j - m.C0];
+            m.c[j - m.C0] = inside ? uc - ((m.u[i0 - m.L0] + m.u[i0 + 1 - m.L0]) >> 1) : 0;
+        }
+        __syncthreads();
+        for (int q = m.L0 + (int)threadIdx.x; q < m.L1; q += (int)blockDim.x) {
+            const int J = q >> 1, nb = (q & 1) ? J + 1 : J - 1;
+            const i64 cn = (nb < 0) ? -m.c[-m.C0] : ((nb >= nc) ? -m.c[nc - 1 - m.C0] : m.c[nb - m.C0]);
+            m.u[q - m.L0] += (3 * m.c[J - m.C0] + cn + 2) >> 2;
+        }
+        __syncthreads();
+        smooth_range<false>(m, n, a.nu);
+        const int sh = top - i;
+        const int s = s0 >> sh, T = a.tile >> sh;
+        i64 *uo = batch_at(a.u_out[i], n);
+        for (int q = s + (int)threadIdx.x; q < s + T; q += (int)blockDim.x) uo[q] = m.u[q - m.L0];
+    }
+}
+
+// --------------------------------------------------------------------------
 // SR level (Fig. 3): one block per segment.
 // --------------------------------------------------------------------------
 struct SegArgs {

@@ -38,7 +38,9 @@ class Params(ctypes.Structure):
                                                       ("n_vcycles", ctypes.c_int32),
                                                       ("post_leg", ctypes.c_int32),
                                                       ("tail_level", ctypes.c_int32),
-                                                      ("tile_cells", ctypes.c_int32)]
+                                                      ("tile_cells", ctypes.c_int32),
+                                                      ("chain_down", ctypes.c_int32),
+                                                      ("chain_up", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -97,7 +99,7 @@ def load(build_if_missing=True):
     lib.srfmg_autotune_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     lib.srfmg_autotune_shape.argtypes = lib.srfmg_autotune.argtypes
-    lib.srfmg_autotune_shape_candidate.argtypes = lib.srfmg_autotune_candidate.argtypes
+    lib.srfmg_autotune_shape_candidate.argtypes = [ctypes.POINTER(Params), ctypes.c_int32, ctypes.POINTER(Params)]
     lib.srfmg_set_coefficient.argtypes = [H, vp, vp]
     lib.srfmg_coef_gradient.argtypes = [H, vp, vp, vp, vp]
     lib.srfmg_solve_functionals.argtypes = [H, vp, vp, vp, vp, vp]
@@ -540,14 +542,14 @@ def autotune(log2_n, device=0, reps=5, **overrides):
 
 def autotune_shape(params, device=0, reps=5):
     """Time the CTA shapes (coarse tail extent, cells per tile of the latency-bound
-    stored levels) of the plan `params` and return (best Params,
-    [(tail_level, tile_cells, ms per solve), ...]); the shape does not change the
-    result."""
+    stored levels, chained down and up passes) of the plan `params` and return
+    (best Params, [(tail_level, tile_cells, chain_down, chain_up, ms per solve),
+    ...]); the shape does not change the result."""
     lib = load()
     base = Params()
     ctypes.memmove(ctypes.byref(base), ctypes.byref(params), ctypes.sizeof(Params))
     best = Params()
-    cap = 16
+    cap = 64
     ms = (ctypes.c_float * cap)()
     n = ctypes.c_int32()
     st = lib.srfmg_autotune_shape(ctypes.byref(base), device, reps, ctypes.byref(best), ms, cap, ctypes.byref(n))
@@ -555,9 +557,9 @@ def autotune_shape(params, device=0, reps=5):
         raise SrfmgError(st, lib.srfmg_last_error(None).decode())
     table = []
     for k in range(min(n.value, cap)):
-        t, c = ctypes.c_int32(), ctypes.c_int32()
-        lib.srfmg_autotune_shape_candidate(ctypes.byref(base), k, ctypes.byref(t), ctypes.byref(c))
-        table.append((t.value, c.value, float(ms[k])))
+        c = Params()
+        lib.srfmg_autotune_shape_candidate(ctypes.byref(base), k, ctypes.byref(c))
+        table.append((c.tail_level, c.tile_cells, c.chain_down, c.chain_up, float(ms[k])))
     return best, table
 
 

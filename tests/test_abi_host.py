@@ -124,19 +124,39 @@ def test_alu_peaks_rejects_null_on_the_host():
 
 
 def test_shape_candidates_on_the_host():
-    # distinct coarse tails (9..12 clipped to the levels below the SR level) x tiles
+    # distinct coarse tails (9..12 clipped to the levels below the SR level) x tiles;
+    # for the fixed-point -u'' = f also chained passes on the two finest tails
     lib = srfmg.load()
 
     def cands(M, **kw):
         p = srfmg.default_params(M, **kw)
         out = []
         for k in range(64):
-            t, c = ctypes.c_int32(), ctypes.c_int32()
-            if lib.srfmg_autotune_shape_candidate(ctypes.byref(p), k, ctypes.byref(t), ctypes.byref(c)) != srfmg.OK:
+            c = srfmg.Params()
+            if lib.srfmg_autotune_shape_candidate(ctypes.byref(p), k, ctypes.byref(c)) != srfmg.OK:
                 break
-            out.append((t.value, c.value))
+            assert (c.log2_n, c.precision, c.segment_width) == (p.log2_n, p.precision, p.segment_width)
+            out.append((c.tail_level, c.tile_cells, c.chain_down, c.chain_up))
         return out
 
-    assert cands(24) == [(t, c) for t in (9, 10, 11, 12) for c in (128, 256, 512)]
-    assert cands(11) == [(9, 128), (9, 256), (9, 512), (10, 128), (10, 256), (10, 512)]
-    assert cands(8) == [(9, 128), (9, 256), (9, 512)]      # one tail: the whole problem
+    plain = [(t, c, 0, 0) for t in (9, 10, 11, 12) for c in (128, 256, 512)]
+    assert cands(24) == plain
+    assert cands(24, precision=srfmg.MIXED) == plain + [(t, c, 2, u) for t in (11, 12) for c in (256, 512)
+                                                         for u in (3, 4)]
+    assert cands(24, precision=srfmg.MIXED, op=srfmg.VARCOEF) == plain
+    assert cands(11) == [(9, 128, 0, 0), (9, 256, 0, 0), (9, 512, 0, 0), (10, 128, 0, 0), (10, 256, 0, 0),
+                         (10, 512, 0, 0)]
+    assert cands(11, precision=srfmg.MIXED)[6:] == [(t, c, 2, u) for t in (9, 10) for c in (256, 512)
+                                                    for u in (3, 4)]
+    assert cands(8) == [(9, 128, 0, 0), (9, 256, 0, 0), (9, 512, 0, 0)]      # one tail: the whole problem
+
+
+def test_chain_params_are_checked_on_the_host():
+    lib = srfmg.load()
+    for kw in (dict(chain_down=5), dict(chain_up=-1), dict(chain_up=2),
+               dict(chain_down=2, precision=srfmg.MIXED, op=srfmg.VARCOEF),
+               dict(chain_up=3, precision=srfmg.MIXED, op=srfmg.BRATU, lambda_=1.0)):
+        p = srfmg.default_params(16, **kw)
+        h = ctypes.c_void_p()
+        assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL, kw
+        assert "chain" in lib.srfmg_last_error(None).decode()
