@@ -135,6 +135,9 @@ def parse_args():
                     help="batch: operator of the problems")
     ap.add_argument("--quick", action="store_true",
                     help="leave the batch, Bratu, all-core oracle and ALU probes out of the default line")
+    ap.add_argument("--shape", default=None,
+                    help="TAIL,TILE,CHAIN_DOWN,CHAIN_UP: the headline plan's CTA shape instead of the shape "
+                         "autotuner's choice (every shape gives the same bits; for profiling runs)")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the SR solve only (no plain baseline, e2e, profile or CPU leg); "
                          "the minimal run used for ncu captures")
@@ -453,11 +456,19 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def tuned_solver(srfmg, M, dev, reps=3, coef=None, **kw):
+def tuned_solver(srfmg, M, dev, reps=3, coef=None, shape=None, **kw):
     """A plan with its CTA shape (coarse tail extent, cells per tile of the stored
-    levels of at most 2^18 cells) picked by srfmg_autotune_shape before any timing; the
+    levels of at most 2^18 cells, chained passes) picked by srfmg_autotune_shape
+    before any timing, or `shape` (TAIL,TILE,CHAIN_DOWN,CHAIN_UP) when given; the
     shape changes no bit of the result.  coef: log a for the variable
     coefficient (the tuning solves use a = 1)."""
+    if shape:
+        t, c, cd, cu = (int(x) for x in shape.split(","))
+        best = srfmg.default_params(M, tail_level=t, tile_cells=c, chain_down=cd, chain_up=cu, **kw)
+        s = srfmg.Solver(M, device=dev, params=best)
+        if coef is not None:
+            s.set_coefficient(coef)
+        return s, {"tail_level": t, "tile_cells": c, "chain_down": cd, "chain_up": cu, "given": True}
     best, table = srfmg.autotune_shape(srfmg.default_params(M, **kw), device=dev, reps=reps)
     s = srfmg.Solver(M, device=dev, params=best)
     if coef is not None:
@@ -503,7 +514,7 @@ def run_gpu(a):
     ud = torch.empty_like(fd)
 
     prec = srfmg.MIXED if a.precision == "mixed" else srfmg.FP64
-    solver, shape = tuned_solver(srfmg, M, dev, segment_width=W, buffer_width=b, precision=prec)
+    solver, shape = tuned_solver(srfmg, M, dev, shape=a.shape, segment_width=W, buffer_width=b, precision=prec)
     info = solver.info()
 
     sampler = ClockSampler(dev)
