@@ -118,7 +118,10 @@ typedef struct {
     int32_t tau_edge;          /* srfmg_tau_edge (SR levels only; 0 without SR) */
     int32_t n_vcycles;         /* FAS V-cycles (Fig. 1, with the SR steps of Fig. 3 on the SR levels)
                                   after the FMG cycle, each from the current fine solution:
-                                  0..16 (default 0); plans with an SR level only */
+                                  0..16 (default 0).  Without SR they converge to the exact
+                                  discrete solution (about a digit per cycle), which makes
+                                  srfmg_adjoint and srfmg_coef_gradient the exact gradients
+                                  of the solve; with SR they stop at the SR floor. */
     int32_t post_leg;          /* srfmg_post (SR levels only; 0 without SR) */
     /* CTA shape (no effect on the result, which is the same bits for every choice:
        the stored-level tiles compute their halo cells exactly like the tile that

@@ -48,6 +48,7 @@ struct Op {
     // tags for pointer fields patched per solve
     PtrTag rhs_in, lev_g, lev_out, tail_g, tail_out, seg_f, seg_u;
     PtrTag seg_uin;   // a V-cycle's pre-leg from the caller's current fine solution
+    PtrTag lev_uin;   // a V-cycle's down pass on the finest level of a plan without SR, from u
     // operator of the FP64 kernels (kOpLaplace, kOpVarcoef, kOpBratu; kOpBratuMx: the
     // mixed precision of the Bratu problem, FP32 correction recurrences)
     int opk;
@@ -155,7 +156,6 @@ std::string check_params(const srfmg_params *p) {
         return "SRFMG_POST_FAS_RECOMPUTE needs n_sr_levels = 1, tau_edge = SRFMG_TAU_ASSEMBLED, n_vcycles = 0 "
                "and buffer_width < segment_width";
     if (p->n_vcycles < 0 || p->n_vcycles > 16) return "n_vcycles must be in [0, 16]";
-    if (p->n_vcycles > 0 && p->n_sr_levels == 0) return "n_vcycles applies to plans with an SR level";
     if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->tau_edge != SRFMG_TAU_SEGMENT)
         return "tau_edge must be SRFMG_TAU_ASSEMBLED or SRFMG_TAU_SEGMENT";
     if (p->tau_edge != SRFMG_TAU_ASSEMBLED && p->n_sr_levels == 0) return "tau_edge applies to SR levels only";
@@ -666,6 +666,17 @@ void build_schedule_ops(srfmg_plan *h) {
         Op o = level_op(h, OP_UP, M, h->ulev[M][0], U(M - 1), nullptr, nullptr, nullptr);
         o.lev_out = TAG_U;
         h->ops.push_back(o);
+        // further V-cycles (Fig. 1) from the caller's current u
+        for (int c = 0; c < h->p.n_vcycles; ++c) {
+            Op d = level_op(h, OP_DOWN, M, nullptr, nullptr, h->ulev[M][0], Unext(M - 1), h->glev[M - 1]);
+            d.lev_uin = TAG_U;
+            h->ops.push_back(d);
+            cur[M - 1] ^= 1;
+            vcycle_below(M - 1, nullptr);
+            Op up = level_op(h, OP_UP, M, h->ulev[M][0], U(M - 1), nullptr, nullptr, nullptr);
+            up.lev_out = TAG_U;
+            h->ops.push_back(up);
+        }
     }
 }
 
@@ -760,6 +771,7 @@ cudaError_t launch_fixed(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
         o.fseg.fpart = io.fout ? io.fpart : nullptr;
     }
     if (o.seg_uin == TAG_U) o.fseg.u_in_f64 = u;
+    if (o.lev_uin == TAG_U) { o.flev.u_src_f64 = u; o.flev.u_src = nullptr; }
     cudaError_t e = cudaSuccess;
     switch (o.kind) {
     case OP_SCALE: {
@@ -809,6 +821,7 @@ cudaError_t launch(const Op &o0, const Io &io, cudaStream_t s, bool pdl) {
         o.seg.fpart = io.fout ? io.fpart : nullptr;
     }
     if (o.seg_uin == TAG_U) o.seg.u_in = u;
+    if (o.lev_uin == TAG_U) o.lev.u_src = u;
     if (o.opk == kOpBratu) return launch_fp64<kOpBratu>(o, s, pdl);
     if (o.opk == kOpBratuMx) return launch_fp64<kOpBratuMx>(o, s, pdl);
     if (o.opk == kOpVarcoef) return launch_fp64<kOpVarcoef>(o, s, pdl);
@@ -979,6 +992,9 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
     int top_stored = h->M - h->nRS;
     const int tail_max = p->tail_level ? p->tail_level : kMaxTailLevel;
     h->Mc = top_stored < tail_max ? top_stored : tail_max;
+    // further V-cycles without SR start from the caller's u with a down pass of
+    // the finest level, which must then be a stored level
+    if (h->nRS == 0 && p->n_vcycles > 0 && h->Mc >= h->M) h->Mc = h->M - 1;
     if (h->Mc < h->M0) h->Mc = h->M0;
     // the 64-bit fixed-point kernels serve the constant-coefficient operator; the
     // mixed precision of the other two is their FP64 kernels with FP32 corrections

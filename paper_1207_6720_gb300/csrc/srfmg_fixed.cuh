@@ -621,6 +621,8 @@ struct LevelArgs {
     double *u_out_f64;         // finest level without SR: the FP64 solution
     i64 *uc_out, *gc_out;      // down pass: restricted solution and tau rhs on level l-1
     const u64 *cA, *cBM;       // variable coefficient: this level's A (faces) and multipliers (cells)
+    const double *u_src_f64;   // down pass of a further V-cycle on the finest level of a plan
+                               // without SR: the caller's FP64 solution (instead of u_src)
 };
 
 // Shared memory: u, gs (staged G or f, then the right-hand side in solution
@@ -741,19 +743,26 @@ __global__ void __launch_bounds__(kSweepBlockMax, VC ? 1 : 2) level_down_kernel(
     const int n = a.n, nc = n >> 1;
     LevelSmem m = level_smem(smi, s, a, FROM_PI);
     stage_g_async<VC>(m, a);
+    const double *uf = batch_at(a.u_src_f64, n);
     if (FROM_PI) stage_coarse_async(m.c, m.usrc, m.C0, m.C1, nc);
+    else if (uf) stage_range(m.u, uf + m.L0, m.L1 - m.L0);
     else stage_range(m.u, m.usrc + m.L0, m.L1 - m.L0);
     stage_wait();
     __syncthreads();
     const int J0 = s >> 1;
     prepare_rhs(m, a, 2 * a.l - 2, m.gr, J0, (s + a.tile) >> 1);
+    if (uf) {           // the FP64 solution onto the fixed-point grid
+        const int S = m.sc->S;
+        for (int i = m.L0 + (int)threadIdx.x; i < m.L1; i += (int)blockDim.x)
+            m.u[i - m.L0] = f64_to_fixed(__longlong_as_double(m.u[i - m.L0]), S);
+    }
     if (FROM_PI) {
         fill_coarse_ghosts(m.c, m.C0, m.C1, nc);
         __syncthreads();
         for (int J = (m.L0 >> 1) + (int)threadIdx.x; J < (m.L1 >> 1); J += (int)blockDim.x)
             fmg_interp2(m.c, m.C0, J, m.u[2 * J - m.L0], m.u[2 * J + 1 - m.L0]);
     }
-    if (FROM_PI || !m.gin) __syncthreads();    // (below the finest level without Pi nothing was written)
+    if (FROM_PI || !m.gin || uf) __syncthreads();    // (below the finest level without Pi nothing was written)
     smooth_range<VC>(m, n, a.nu);
     const i64 *u = m.u;
     const int tsh = 2 * a.l - 4;

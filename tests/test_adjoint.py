@@ -169,3 +169,57 @@ def test_solve_and_adjoint_keep_their_graphs_gpu():
         assert all(torch.equal(o, u0) for o in outs)
     finally:
         s.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_converged_gradients_match_central_differences_gpu(precision):
+    # A plan without SR followed by V-cycles converges to the exact discrete
+    # solution, a symmetric linear map of f, so the adjoint solve and the
+    # coefficient gradient are the exact gradients of the solve itself:
+    # central differences of L = 1/2 |u - u_obs|^2 through the GPU solve, along
+    # 64 seeded directions of f and 16 of log a (-(a u')' = f, the adjoint
+    # workload's family), agree with them.  L is quadratic in f, so its central
+    # difference is exact up to rounding; L(+) - L(-) is formed as
+    # 1/2 sum (u+ - u-)(u+ + u- - 2 u_obs), free of the cancellation of two large L.
+    torch = pytest.importorskip("torch")
+    from paper_1207_6720_gb300 import srfmg
+    M = 14
+    f, ue, log_a = workloads.varcoef_series(M, 16, seed=1)
+    rng = np.random.default_rng(7)
+    uo = torch.from_numpy(ue + rng.normal(0.0, 1e-3, 1 << M)).cuda()
+    prec = srfmg.FP64 if precision == "fp64" else srfmg.MIXED
+    s = srfmg.Solver(M, n_sr_levels=0, op=srfmg.VARCOEF, precision=prec, n_vcycles=16)
+    try:
+        la = torch.from_numpy(log_a).cuda()
+        s.set_coefficient(la)
+        fd_ = torch.from_numpy(f).cuda()
+        u = torch.zeros_like(fd_)
+        s.solve(fd_, u)
+        lam = s.adjoint((u - uo).contiguous())
+        g_a = s.coef_gradient(u, lam)
+
+        def dL(up, um):
+            return float(0.5 * torch.sum((up - um) * (up + um - 2.0 * uo)))
+
+        def solve(ff):
+            out = torch.zeros_like(fd_)
+            s.solve(ff, out)
+            return out
+        rng = np.random.default_rng(11)
+        eps = float(np.max(np.abs(f)))
+        for _ in range(64):
+            d = torch.from_numpy(rng.normal(size=f.size)).cuda()
+            fdv = dL(solve(fd_ + eps * d), solve(fd_ - eps * d)) / (2.0 * eps)
+            assert abs(fdv - float(lam @ d)) <= 1e-6 * abs(fdv)
+        eps_a = 1e-5
+        for _ in range(16):
+            d = torch.from_numpy(rng.normal(size=log_a.size)).cuda()
+            s.set_coefficient((la + eps_a * d).contiguous())
+            up = solve(fd_)
+            s.set_coefficient((la - eps_a * d).contiguous())
+            um = solve(fd_)
+            fdv = dL(up, um) / (2.0 * eps_a)
+            assert abs(fdv - float(g_a @ d)) <= 1e-4 * abs(fdv)
+    finally:
+        s.close()

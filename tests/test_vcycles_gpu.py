@@ -31,7 +31,6 @@ def _create(**kw):
 def test_n_vcycles_is_checked_on_the_host():
     assert _create(n_vcycles=-1) == srfmg.EINVAL
     assert _create(n_vcycles=17) == srfmg.EINVAL
-    assert _create(n_vcycles=1, n_sr_levels=0) == srfmg.EINVAL
 
 
 def _dev(x):
@@ -46,6 +45,9 @@ CASES = [
     (13, 2, 512, 8, 1, "laplace"),
     (17, 1, 4096, 8, 3, "laplace"),
     (13, 1, 512, 8, 1, "bratu"),
+    (12, 0, 0, 0, 2, "laplace"),      # without SR: the whole problem below the tail, level M kept stored
+    (15, 0, 0, 0, 3, "laplace"),
+    (14, 0, 0, 0, 2, "bratu"),
 ]
 
 
@@ -65,7 +67,7 @@ def test_vcycles_after_fmg_parity_gpu(M, nRS, W, b, k, op, precision):
         u = s.solve(_dev(f)).cpu().numpy()
     finally:
         s.close()
-    p = oracle.sr_params(M, W, b, nRS=nRS, **okw)
+    p = oracle.sr_params(M, W, b, nRS=nRS, **okw) if nRS else oracle.Params(M, nRS=0, **okw)
     ref = oracle.vcycles_h(p, f, oracle.fmg_h(p, f), k)
     assert np.max(np.abs(u - ref)) <= TOL * np.max(np.abs(ref))
 
