@@ -121,7 +121,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["srfmg", "reference"], default="srfmg")
     ap.add_argument("--workload", choices=["poisson", "bratu", "varcoef", "batch"], default="poisson")
-    ap.add_argument("--nprob", type=int, default=8192, help="batch: number of problems")
+    ap.add_argument("--nprob", type=int, default=None, help="batch: number of problems (8192; 1024 for bratu)")
     ap.add_argument("--lam", type=float, default=1.0, help="Bratu: lam of -u'' + lam e^u = f")
     ap.add_argument("--log2n", type=int, default=None, help="default 24 (poisson), 26 (bratu)")
     ap.add_argument("--segment-width", type=int, default=4096)
@@ -131,8 +131,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch: fixed segment layout min(4096, N/4), buffer 8, instead of autotuning each size")
-    ap.add_argument("--batch-op", choices=["varcoef", "laplace"], default="varcoef",
-                    help="batch: operator of the problems")
+    ap.add_argument("--batch-op", choices=["varcoef", "laplace", "bratu"], default="varcoef",
+                    help="batch: operator of the problems (bratu: 1024 problems, m ~ U{12..18}, V(2,1))")
     ap.add_argument("--quick", action="store_true",
                     help="leave the batch, Bratu, all-core oracle and ALU probes out of the default line")
     ap.add_argument("--shape", default=None,
@@ -144,6 +144,8 @@ def parse_args():
     a = ap.parse_args()
     if a.log2n is None:
         a.log2n = 26 if a.workload == "bratu" else 24
+    if a.nprob is None:
+        a.nprob = 1024 if a.batch_op == "bratu" else 8192
     return a
 
 
@@ -168,6 +170,15 @@ def workload_config(a):
             "buffer_width": a.buffer_width, "n_sr_levels": 1, "nu": [1, 1], "coarsest_level": 2,
             "modes": 16, "seed": 1,
             "l2": "inputs larger than L2 (f and u 128 MiB each, log a 128 MiB, the stored levels)",
+        }
+    if getattr(a, "workload", "poisson") == "batch" and getattr(a, "batch_op", "varcoef") == "bratu":
+        return {
+            "workload": f"{a.nprob} independent 1D -u''+lam e^u=f problems (lam={a.lam}), N=2^m with m ~ "
+                        f"U{{12..18}} (seed 11), FMG-FAS V(2,1) pointwise Newton lexicographic GS, 1 SR level, "
+                        f"buffer 8, {precision_text('bratu', 'mixed')}; one srfmg group",
+            "operator": "bratu", "lam": a.lam, "precision": "mixed", "nprob": a.nprob, "m_range": [12, 18],
+            "size_seed": 11, "modes": 16, "buffer_width": 8, "n_sr_levels": 1, "nu": [2, 1],
+            "coarsest_level": 2, "l2": "inputs larger than L2 (about 0.6 GB of f and of u)",
         }
     if getattr(a, "workload", "poisson") == "batch":
         op = getattr(a, "batch_op", "varcoef")
@@ -739,6 +750,13 @@ def run_gpu(a):
         r["config"] = dict(workload_config(a_b), segment_layout=r.pop("segment_layout"), layouts=r.pop("layouts"))
         r["metric"] = METRIC_BATCH
         line["batch"] = r
+        # the Bratu workload's batch: 1024 problems of 2^12 .. 2^18 cells
+        a_nb = argparse.Namespace(**vars(a))
+        a_nb.workload, a_nb.batch_op, a_nb.nprob = "batch", "bratu", 1024
+        r = measure_batch(a_nb, dev, dist, stream, max(5, a.steps // 4), min(a.warmup, 2), op="bratu")
+        r["config"] = dict(workload_config(a_nb), segment_layout=r.pop("segment_layout"), layouts=r.pop("layouts"))
+        r["metric"] = METRIC_BATCH
+        line["bratu_batch"] = r
         a_r = argparse.Namespace(**vars(a))
         a_r.workload, a_r.log2n, a_r.precision = "bratu", 26, "mixed"
         r = measure_single(a_r, dev, dist, stream, "bratu", "mixed", max(5, a.steps // 2), min(a.warmup, 3))
@@ -905,7 +923,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
     import torch
     from paper_1207_6720_gb300 import srfmg, workloads
 
-    sizes = workloads.batch_sizes(a.nprob, 10, 20, seed=11)
+    nl = op == "bratu"
+    sizes = workloads.batch_sizes(a.nprob, 12, 18, seed=11) if nl else workloads.batch_sizes(a.nprob, 10, 20, seed=11)
     classes = {}
     for k, m in enumerate(sizes):
         classes.setdefault(int(m), []).append(k + 1000)       # problem k's series seed
@@ -918,6 +937,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
             fm, lam = workloads.varcoef_series_batch(m, classes[m], 32, dev)
             fparts.append(fm)
             laparts.append(lam)
+        elif nl:
+            fparts.append(workloads.bratu_series_batch(m, classes[m], 16, a.lam, dev))
         else:
             fparts.append(workloads.sine_series_batch(m, classes[m], 32, dev)[0])
     fd = torch.cat(fparts)
@@ -927,7 +948,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
     ud = torch.empty_like(fd)
     assert fd.numel() == total == int(srfmg.group_offsets(sizes)[-1])
     torch.cuda.synchronize()
-    kw_op = dict(op=srfmg.VARCOEF) if vc else {}
+    kw_op = (dict(op=srfmg.VARCOEF) if vc else
+             dict(op=srfmg.BRATU, lambda_=a.lam, nu1=2, nu2=1) if nl else {})
 
     def make(prec, nRS, tune_reps):
         kw = dict(precision=prec, n_sr_levels=nRS, **kw_op)
@@ -989,6 +1011,9 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
         u0 = ud[o:o + mb.n].cpu().numpy()
         if vc:
             f0, ue, la0 = workloads.varcoef_series(m, 32, classes[m][0])
+        elif nl:
+            f0, ue, _ = workloads.bratu_series(m, 16, classes[m][0], a.lam)
+            la0 = None
         else:
             f0, ue, _ = workloads.sine_series(m, 32, classes[m][0])
             la0 = None
@@ -1015,6 +1040,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
                                key=lambda x: x[1])
         kind, lvl = top_name.split(" L")
         kind = kind.replace("fx.", "")
+        # (the Bratu problem's kernels are the FP64 ones: 8-byte u; their bound is the FP64 pipe,
+        # reported for the single problem; here the data-movement view)
         bytes_alg = (BYTES_PER_CELL_VC_FX if vc else BYTES_PER_CELL).get(kind, 0.0) * big.batch * (1 << int(lvl))
         peaks = measured_peaks()
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -1043,7 +1070,8 @@ def measure_batch(a, dev, dist, master, steps, warmup, op="varcoef", tune=True, 
         reps = 0
         while True:
             for m, (f0, ue, la0, u0, W, b) in samples.items():
-                okw = dict(op="varcoef", coef=np.exp(la0)) if vc else {}
+                okw = (dict(op="varcoef", coef=np.exp(la0)) if vc else
+                       dict(op="bratu", lam=a.lam, nu1=2, nu2=1) if nl else {})
                 refs[m] = oracle.fmg_v(oracle.sr_params(m, W, b, **okw), f0)
             reps += 1
             if time.perf_counter() - t0 > 5.0 or reps >= 10:

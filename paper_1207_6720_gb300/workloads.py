@@ -150,6 +150,20 @@ def bratu_series(M, nmodes, seed, lam, scale=0.5):
     return f, u, c
 
 
+def bratu_series_batch(M, seeds, nmodes, lam, device, scale=0.5):
+    """float64 tensor of len(seeds) * 2^M right-hand-side values on `device`,
+    problem k holding bratu_series(M, nmodes, seeds[k], lam, scale)[0]."""
+    import torch
+    c = scale * np.stack([sine_coefficients(nmodes, int(s)) for s in seeds])
+    k = np.arange(1, nmodes + 1, dtype=np.float64)
+    x = torch.from_numpy(centres(M)).to(device)
+    kt = torch.from_numpy(k).to(device)
+    S = torch.sin(torch.pi * kt[:, None] * x[None, :])                 # (nmodes, 2^M)
+    u = torch.from_numpy(c).to(device) @ S                             # (B, 2^M)
+    f = torch.from_numpy(c * (k * np.pi) ** 2).to(device) @ S + lam * torch.exp(u)
+    return f.reshape(-1).contiguous()
+
+
 def paper_series(M):
     """(f, u_exact): odd modes j < N/16 with f-amplitude 1/j (appendix program)."""
     n = 1 << M
