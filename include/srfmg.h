@@ -502,6 +502,16 @@ const char *srfmg_last_error(srfmg_handle h);
  * SRFMG_ENOMEM. */
 srfmg_status srfmg_alu_peaks(int device, double *ops_per_s);
 
+/* Self-check of the exponential of the Bratu operator in SRFMG_MIXED (no
+ * counterpart in the paper; the mixed residual and tau take e^u from a
+ * table-driven method, Tang's, with about half of the FP64 work of exp):
+ * writes to *max_rel the largest relative difference to CUDA's exp at n
+ * evenly spaced points of [lo, hi].  Synchronous; allocates one word.  Errors:
+ * SRFMG_EINVAL for NULL max_rel, n outside [1, 2^26], lo > hi or |lo|, |hi|
+ * > 700 (checked before any device work), a bad device index; SRFMG_ECUDA,
+ * SRFMG_ENOMEM. */
+srfmg_status srfmg_exp_error(int device, double lo, double hi, int32_t n, double *max_rel);
+
 /* Library version string, e.g. "srfmg 0.1 sm_103a". */
 const char *srfmg_version(void);
 

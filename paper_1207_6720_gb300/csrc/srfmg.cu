@@ -186,6 +186,33 @@ std::string check_params(const srfmg_params *p) {
     return "";
 }
 
+// The table of the mixed precision's exponential (exp_mx): 2^(j/256) for
+// j < 256, each rounded once from long double, then ln2/256 as a leading double
+// and the rest; uploaded to the current device.
+cudaError_t upload_exp_table() {
+    double tab[258];
+    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
+    const long double L = logl(2.0L) / 256.0L;
+    tab[256] = (double)L;
+    tab[257] = (double)(L - (long double)tab[256]);
+    return cudaMemcpyToSymbol(g_exp2_tab, tab, sizeof(tab));
+}
+
+// exp_mx against exp at n evenly spaced points of [lo, hi]: the largest
+// relative difference, as the bits of a non-negative double (they order like
+// the values) combined by atomicMax.
+__global__ void exp_error_kernel(double lo, double hi, int n, unsigned long long *out) {
+    unsigned long long worst = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double x = (n > 1) ? lo + (hi - lo) * ((double)i / (double)(n - 1)) : lo;
+        const double ref = exp(x);
+        const double d = fabs(exp_mx(x) - ref) / ref;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        worst = b > worst ? b : worst;
+    }
+    atomicMax(out, worst);
+}
+
 // Inverse of the scaled coarsest operator h^2 L (tridiag(-1,2,-1), 3 in the
 // wall rows) by Gauss-Jordan elimination in long double.
 std::vector<double> coarsest_inverse(int n) {
@@ -1048,6 +1075,9 @@ srfmg_status srfmg_create(const srfmg_params *p, int device, srfmg_handle *out) 
         h->status = (int *)w;
         if (st == SRFMG_OK && (e = cudaMemset(w, 0, sizeof(double))) != cudaSuccess) st = cuda_fail(h, e, "cudaMemset");
     }
+    if (st == SRFMG_OK && p->op == SRFMG_OP_BRATU && p->precision == SRFMG_MIXED &&
+        (e = upload_exp_table()) != cudaSuccess)
+        st = cuda_fail(h, e, "exponential table");
     const int n0 = 1 << h->M0;
     if (st == SRFMG_OK) st = alloc_dev(h, &h->Ainv, (size_t)n0 * n0);
     if (st == SRFMG_OK) {
@@ -1651,6 +1681,36 @@ __global__ void probe_ffma(double *out, int iters) {
 }  // namespace
 
 extern "C" {
+
+srfmg_status srfmg_exp_error(int device, double lo, double hi, int32_t n, double *max_rel) {
+    if (!max_rel || n < 1 || n > (1 << 26) || !(lo <= hi) || !(fabs(lo) <= 700.0) || !(fabs(hi) <= 700.0))
+        return fail(nullptr, SRFMG_EINVAL, "bad arguments to srfmg_exp_error");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, SRFMG_ECUDA, "no CUDA device");
+    }
+    if (device < 0 || device >= ndev) return fail(nullptr, SRFMG_EINVAL, "device index out of range");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    if ((e = upload_exp_table()) != cudaSuccess) return cuda_fail(nullptr, e, "exponential table");
+    unsigned long long *d = nullptr;
+    if ((e = cudaMalloc(&d, sizeof(*d))) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, SRFMG_ENOMEM, "cudaMalloc");
+    }
+    unsigned long long bits = 0;
+    e = cudaMemset(d, 0, sizeof(*d));
+    if (e == cudaSuccess) {
+        exp_error_kernel<<<std::min(1216, (n + 255) / 256), 256>>>(lo, hi, n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "srfmg_exp_error");
+    std::memcpy(max_rel, &bits, sizeof(double));
+    return SRFMG_OK;
+}
 
 srfmg_status srfmg_alu_peaks(int device, double *ops_per_s) {
     if (!ops_per_s) return fail(nullptr, SRFMG_EINVAL, "ops_per_s is NULL");

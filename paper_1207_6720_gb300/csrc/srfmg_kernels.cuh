@@ -522,6 +522,33 @@ __device__ __forceinline__ void lex_sweep_vc(double *__restrict__ u, const doubl
 // ---------------------------------------------------------------------------
 constexpr int kTruncNlMx = 36;
 
+// e^x for the mixed precision's Bratu terms, by Tang's table-driven method
+// (P. T. P. Tang, ACM TOMS 15, 1989): x = (256 k + j) ln2/256 + r with
+// |r| <= ln2/512 (plus rounding), e^x = 2^k 2^(j/256) e^r, e^r - 1 = r + r^2/2
+// + r^3/6 (the dropped terms are below 1.5e-13 of the value).  The host fills
+// g_exp2_tab[j] = 2^(j/256), j < 256, in long double and rounds once, and
+// g_exp2_tab[256], [257] with ln2/256 split into a leading double and the
+// rest (srfmg.cu, at the creation of a mixed Bratu plan).  About half of the
+// FP64 operations of exp (slow on this part); relative error below 2e-13,
+// checked against exp by srfmg_exp_error.  The residual's exponential enters
+// the solution scaled by about lam / pi^2, far below the 1e-10 parity bound.
+__device__ double g_exp2_tab[258];
+
+__device__ __forceinline__ double exp_mx(double x) {
+    if (!(fabs(x) <= 700.0)) return exp(x);          // (and inf, NaN)
+    constexpr double kMagic = 6755399441055744.0;    // 1.5 * 2^52: adding it rounds to an integer
+    constexpr double kInvL = 369.32993046757462751;  // 256 / ln 2
+    const double sft = fma(x, kInvL, kMagic);
+    const double nd = sft - kMagic;
+    const int n = (int)(__double_as_longlong(sft) & 0xffffffffLL);
+    double r = fma(-nd, __ldg(&g_exp2_tab[256]), x);
+    r = fma(-nd, __ldg(&g_exp2_tab[257]), r);
+    const double p = r * fma(r, fma(r, 1.0 / 6.0, 0.5), 1.0);
+    const double T = __ldg(&g_exp2_tab[n & 255]);
+    const double y = fma(T, p, T);
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)(n >> 8) << 52));
+}
+
 // Pointwise Newton Gauss-Seidel for -u'' + lam e^u = f, mixed: e_i = cl e^{u_i}
 // and the residual r_i = g_i - e_i - (F_{i-1/2} - F_{i+1/2}) in FP64; the
 // Newton denominator 2 + e_i (3 + e_i at a wall), its reciprocal and the
@@ -548,21 +575,21 @@ __device__ __noinline__ void lex_sweep_nl_mx_dir(double *__restrict__ u, const d
 #pragma unroll
         for (int j = 0; j < C + 2; ++j) w[j] = u[a0 + s * min(max(q0 - 1 + j, qmin), qmax)];
         if (wall0) {
-            const double e = cl * exp(w[1]);
+            const double e = cl * exp_mx(w[1]);
             const float a = __frcp_rn(3.0f + (float)e);
             p = a * (float)((g[a0] - e) - (scale2(w[1], 1) - (w[2] - w[1])));
             A = a;
         }
         if (wall1) {
             const double ue = u[a0 + s * (n - 1)], um = u[a0 + s * (n - 2)];
-            const double e = cl * exp(ue);
+            const double e = cl * exp_mx(ue);
             r_end = (float)((g[a0 + s * (n - 1)] - e) - ((ue - um) - (-scale2(ue, 1))));
             a_end = __frcp_rn(3.0f + (float)e);
         }
 #pragma unroll
         for (int k = 0; k < C; ++k) {
             const double gv = g[a0 + s * min(max(q0 + k, qmin), qmax)];
-            const double e = cl * exp(w[k + 1]);
+            const double e = cl * exp_mx(w[k + 1]);
             const float r = (float)((gv - e) - ((w[k + 1] - w[k]) - (w[k + 2] - w[k + 1])));
             const float a = __frcp_rn(2.0f + (float)e);
             const bool in = k >= ka && k < kb;
@@ -672,16 +699,18 @@ __device__ void coarsest_thomas_vc(double *u, const double *g, int n, const doub
 // exponential instead of three, and no cancellation between terms of size
 // 4 cl e^{uhat}.  For |d/2| < 2^-6 sinh(x)/x is its Taylor series to x^6 (the
 // first dropped term is below 2^-66 of the value); otherwise the three
-// exponentials.
+// exponentials.  MX: the mixed precision's exponential (exp_mx).
+template <bool MX>
 __device__ __forceinline__ double tau_nl(double cl, double u0, double u1) {
+    auto E = [](double v) { return MX ? exp_mx(v) : exp(v); };
     const double uh = scale2(u0 + u1, -1);
     const double x = scale2(u0 - u1, -2);
     if (fabs(x) < 0.015625) {
         const double x2 = x * x;
         const double s = fma(x2, fma(x2, fma(x2, 1.0 / 5040.0, 1.0 / 120.0), 1.0 / 6.0), 1.0);
-        return -8.0 * cl * exp(uh) * (x2 * (s * s));
+        return -8.0 * cl * E(uh) * (x2 * (s * s));
     }
-    return cl * (4.0 * exp(uh) - 2.0 * (exp(u0) + exp(u1)));
+    return cl * (4.0 * E(uh) - 2.0 * (E(u0) + E(u1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -917,7 +946,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_kernel(LevelArgs
                         ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
                                      m.a[i0 + 2])
                         : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-        if (op_nl(OP)) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+        if (op_nl(OP)) gc += tau_nl<OP == kOpBratuMx>(cl, u[i0], u[i0 + 1]);
         gc_out[J] = gc;
     }
     for (int i = s + threadIdx.x; i < s + a.tile; i += blockDim.x) u_out[i] = u[i - m.L0];
@@ -1233,7 +1262,7 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) sr_pre_kernel(SegArgs a) {
                             ? tau_rhs_vc(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc, m.a[i0],
                                          m.a[i0 + 2])
                             : tau_rhs(m.g[i0], m.g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
-            if (op_nl(OP)) gc += tau_nl(cl, u[i0], u[i0 + 1]);
+            if (op_nl(OP)) gc += tau_nl<OP == kOpBratuMx>(cl, u[i0], u[i0 + 1]);
             gc_out[J] = gc;
         }
     }
@@ -1277,7 +1306,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         double Fl = f2 - f3, Fr = p0 - f1;
         if (op_vc(OP)) { Gl *= am; Fl *= am; Gr *= a0; Fr *= a0; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (op_nl(OP)) tau += tau_nl(scale2(a.lam, -2 * a.M), f2, f1);
+        if (op_nl(OP)) tau += tau_nl<OP == kOpBratuMx>(scale2(a.lam, -2 * a.M), f2, f1);
         gc_out[J] = scale2(rf[2 * J] + rf[2 * J + 1], rexp) + tau;
     }
     {
@@ -1286,7 +1315,7 @@ __global__ void seam_tau_kernel(SegArgs a, int nseg) {
         double Fl = p0 - f1, Fr = p2 - p1;
         if (op_vc(OP)) { Gl *= a0; Fl *= a0; Gr *= ap; Fr *= ap; }
         double tau = (Gl - Gr) - scale2(Fl - Fr, 1);
-        if (op_nl(OP)) tau += tau_nl(scale2(a.lam, -2 * a.M), p0, p1);
+        if (op_nl(OP)) tau += tau_nl<OP == kOpBratuMx>(scale2(a.lam, -2 * a.M), p0, p1);
         gc_out[J2] = scale2(rf[2 * J2] + rf[2 * J2 + 1], rexp) + tau;
     }
 }
@@ -1431,7 +1460,7 @@ __device__ void tail_down(TailSmem &m, int l, int nu) {
         } else {
             gcv = tau_rhs(g[i0], g[i0 + 1], um2, um1, u[i0], u[i0 + 1], u2, u3, J, nc);
         }
-        if (op_nl(OP)) gcv += tau_nl(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
+        if (op_nl(OP)) gcv += tau_nl<OP == kOpBratuMx>(scale2(m.lam, -2 * l), u[i0], u[i0 + 1]);
         gc[J] = gcv;
     }
     __syncthreads();

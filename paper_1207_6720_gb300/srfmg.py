@@ -24,7 +24,7 @@ EXPORTS = ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_h
            "srfmg_solve_small_noalloc", "srfmg_autotune", "srfmg_autotune_candidate",
            "srfmg_autotune_shape", "srfmg_autotune_shape_candidate",
            "srfmg_set_coefficient", "srfmg_coef_gradient", "srfmg_solve_functionals", "srfmg_reconstruct", "srfmg_check",
-           "srfmg_destroy", "srfmg_last_error", "srfmg_version", "srfmg_alu_peaks",
+           "srfmg_destroy", "srfmg_last_error", "srfmg_version", "srfmg_alu_peaks", "srfmg_exp_error",
            "srfmg_solve_host_async", "srfmg_solve_host_join", "srfmg_group_offsets", "srfmg_group_create", "srfmg_group_solve", "srfmg_group_solve_host",
            "srfmg_group_query", "srfmg_group_member", "srfmg_group_destroy", "srfmg_group_last_error")
 
@@ -119,6 +119,7 @@ def load(build_if_missing=True):
     lib.srfmg_version.argtypes = []
     lib.srfmg_version.restype = ctypes.c_char_p
     lib.srfmg_alu_peaks.argtypes = [ctypes.c_int, dp]
+    lib.srfmg_exp_error.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int32, dp]
     for name in ("srfmg_default_params", "srfmg_create", "srfmg_solve", "srfmg_solve_host",
                  "srfmg_adjoint", "srfmg_query", "srfmg_profile", "srfmg_destroy", "srfmg_autotune",
                  "srfmg_autotune_candidate", "srfmg_autotune_shape", "srfmg_autotune_shape_candidate",
@@ -565,6 +566,17 @@ def autotune_shape(params, device=0, reps=5):
 
 def version():
     return load().srfmg_version().decode()
+
+
+def exp_error(lo, hi, n, device=0):
+    """Largest relative difference between the mixed Bratu exponential and
+    CUDA's exp at n evenly spaced points of [lo, hi] (srfmg_exp_error)."""
+    lib = load()
+    out = ctypes.c_double()
+    st = lib.srfmg_exp_error(device, lo, hi, n, ctypes.byref(out))
+    if st != OK:
+        raise SrfmgError(st, lib.srfmg_last_error(None).decode())
+    return out.value
 
 
 def alu_peaks(device=0):

@@ -160,3 +160,11 @@ def test_chain_params_are_checked_on_the_host():
         h = ctypes.c_void_p()
         assert lib.srfmg_create(ctypes.byref(p), 0, ctypes.byref(h)) == srfmg.EINVAL, kw
         assert "chain" in lib.srfmg_last_error(None).decode()
+
+
+def test_exp_error_checks_its_arguments_on_the_host():
+    lib = srfmg.load()
+    out = ctypes.c_double()
+    for lo, hi, n in ((1.0, 0.0, 10), (0.0, 1.0, 0), (-800.0, 0.0, 10), (0.0, float("nan"), 10), (0.0, 1.0, 1 << 27)):
+        assert lib.srfmg_exp_error(0, lo, hi, n, ctypes.byref(out)) == srfmg.EINVAL
+    assert lib.srfmg_exp_error(0, 0.0, 1.0, 10, None) == srfmg.EINVAL

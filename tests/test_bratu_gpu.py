@@ -124,3 +124,12 @@ def test_bratu_has_no_adjoint_gpu():
             s.adjoint(x)
     finally:
         s.close()
+
+
+@pytest.mark.gpu
+def test_mixed_exponential_matches_exp_gpu():
+    # the mixed precision's exponential (Tang's table-driven method, cubic on
+    # |r| <= ln2/512) against CUDA's exp: the dropped terms bound it by 1.5e-13
+    from paper_1207_6720_gb300 import srfmg
+    for lo, hi, n in ((-40.0, 40.0, 1 << 22), (-1e-3, 1e-3, 1 << 16), (-700.0, 700.0, 1 << 22), (0.0, 0.0, 1)):
+        assert srfmg.exp_error(lo, hi, n) <= 1.6e-13, (lo, hi)
