@@ -157,7 +157,8 @@ def precision_text(op, precision):
     if op == "varcoef":
         return ("64-bit fixed point (solution, residual with exact 128-bit fluxes, tau, interpolation; 63-bit "
                 "Gauss-Seidel multipliers) + FP64 coarsest solve")
-    return "mixed: FP64 solution, residual, tau, interpolation and coarsest solve; FP32 Gauss-Seidel corrections"
+    return ("mixed: FP64 solution, residual, tau, interpolation and coarsest solve (e^u of the residual and tau "
+            "by a table-driven FP64 exponential, < 1.5e-13 relative); FP32 Gauss-Seidel corrections")
 
 
 def workload_config(a):
