@@ -937,7 +937,8 @@ __global__ void __launch_bounds__(kSweepBlockMax, 2) level_down_chain_kernel(con
 // plus a halo H, so that range comes out exact.  Every level's held range is
 // staged at once; the coarse cells of level i's correction are level i-1's
 // result in shared memory (the corrected level below the chain from global
-// memory for i = 0).  Each level writes its owned cells s >> (k-1-i) ...
+// memory for i = 0).  Each level writes its owned cells: the block's T cells
+// of the finest level, scaled by 2^-(k-1-i) on chain level i.
 __global__ void __launch_bounds__(kSweepBlockMax, 2) level_up_chain_kernel(const __grid_constant__ ChainArgs a) {
     pdl_enter();
     extern __shared__ i64 smi[];
