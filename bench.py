@@ -423,20 +423,33 @@ def run_reference(a):
     import oracle
     from paper_1207_6720_gb300 import workloads
     # one solve per step: the full workload for the Poisson and variable-coefficient
-    # problems (about 2 s per solve at N = 2^24 on one core); a bounded sample at
-    # N = 2^22 for the Bratu problem (its N = 2^26 solve takes about 12 s) and one
-    # problem of the batch's largest size for the batch
-    Ms = {"bratu": min(a.log2n, 22), "batch": 20}.get(a.workload, a.log2n)
-    Ws = min(a.segment_width, (1 << Ms) // 4)
-    if a.workload == "bratu":
-        f, _, _ = workloads.bratu_series(Ms, 16, seed=1, lam=a.lam)
-        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
-    elif a.workload == "varcoef":
-        f, _, log_a = workloads.varcoef_series(Ms, 16, seed=1)
-        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, op="varcoef", coef=np.exp(log_a))
-    else:
+    # problems (about 2 s per solve at N = 2^24 on one core) when warm-up and timed
+    # steps fit about 150 s of oracle time, else a bounded sample of the largest size
+    # that does (the rate of one untimed solve at N = 2^18 sets it); at most N = 2^22
+    # for the Bratu problem (its N = 2^26 solve takes about 12 s) and one problem of
+    # the batch's largest size for the batch
+    Mmax = {"bratu": min(a.log2n, 22), "batch": 20}.get(a.workload, a.log2n)
+
+    def problem(Ms):
+        Ws = min(a.segment_width, (1 << Ms) // 4)
+        if a.workload == "bratu":
+            f, _, _ = workloads.bratu_series(Ms, 16, seed=1, lam=a.lam)
+            return f, oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, nu1=2, nu2=1, op="bratu", lam=a.lam)
+        if a.workload == "varcoef":
+            f, _, log_a = workloads.varcoef_series(Ms, 16, seed=1)
+            return f, oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1, op="varcoef", coef=np.exp(log_a))
         f, _, _ = workloads.sine_series(Ms, 32, seed=1)
-        p = oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
+        return f, oracle.sr_params(Ms, Ws, a.buffer_width, nRS=1)
+
+    Mcal = min(Mmax, 18)
+    f, p = problem(Mcal)
+    t0 = time.perf_counter()
+    oracle.fmg_v(p, f)
+    rate = (1 << Mcal) / (time.perf_counter() - t0)
+    Ms = Mmax
+    while Ms > 16 and (a.warmup + a.steps) * (1 << Ms) / rate > 150.0:
+        Ms -= 1
+    f, p = problem(Ms)
     for _ in range(a.warmup):
         oracle.fmg_v(p, f)
     t0 = time.perf_counter()
